@@ -1,0 +1,464 @@
+"""FP64 CPU oracle of the registration scan operator (arXiv 2010.12478).
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the CUDA path (``paper_2010_12478_gb300``) and never imports it; the product
+never imports this.
+
+Layers:
+  * ``oracle.c`` (compiled to ``_build/liboracle.so`` with gcc, FP64, no fast
+    math): pyramid, bilinear sampling, NCC energy and gradient, the gradient
+    flow with Armijo backtracking (rigid and nonrigid), composition.
+  * this module: ctypes marshalling, the operators A and B (Sec. 2.1.1-2.1.2),
+    the scan DAG generators (Sec. 3, Table 1) and the scan driver that applies
+    B along a DAG, one call at a time.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIBDIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAX_LEVELS = 8
+STOP_NAMES = {0: "grad", 1: "rel", 2: "linesearch", 3: "maxiter"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (strict IEEE double: no fast math, no FMA contraction)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_rejects", ctypes.c_int),
+                ("tol_grad", ctypes.c_double), ("tol_rel_e", ctypes.c_double),
+                ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double),
+                ("step_cap", ctypes.c_double), ("lambda_", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int * MAX_LEVELS), ("evals", ctypes.c_int * MAX_LEVELS),
+                ("stop", ctypes.c_int * MAX_LEVELS), ("rejects", ctypes.c_int),
+                ("energy", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            ipp = ctypes.POINTER(ctypes.c_int)
+            dpp = ctypes.POINTER(dp)
+            L.or_downsample.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+            L.or_sample.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+            L.or_rigid_energy.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+            L.or_rigid_energy.restype = ctypes.c_int
+            L.or_rigid_compose.argtypes = [dp, dp, dp]
+            L.or_rigid_register.argtypes = [dpp, dpp, ipp, ipp, ctypes.POINTER(_Cfg), dp, dp,
+                                            ctypes.POINTER(_Stats)]
+            L.or_regulariser.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+            L.or_regulariser.restype = ctypes.c_double
+            L.or_nonrigid_energy.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp,
+                                             ctypes.c_double, dp, dp, dp]
+            L.or_nonrigid_energy.restype = ctypes.c_int
+            L.or_nonrigid_compose.argtypes = [dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp]
+            L.or_prolong.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int]
+            L.or_restrict.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+            L.or_nonrigid_register.argtypes = [dpp, dpp, ipp, ipp, ctypes.POINTER(_Cfg), dp, dp,
+                                               dp, dp, ctypes.POINTER(_Stats)]
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# configuration (readings of the paper's unstated constants)
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Config:
+    levels: int = 3
+    max_iter: int = 500
+    max_rejects: int = 30
+    tol_grad: float = 1e-4
+    tol_rel_e: float = 1e-10
+    armijo_c: float = 1e-4
+    tau0: float = 1.0
+    step_cap: float = 0.5
+    lam: float = 1.0
+    mode: str = "rigid"           # "rigid" (paper, Def. 2.1) or "nonrigid" (extension)
+
+    def c(self) -> _Cfg:
+        return _Cfg(self.levels, self.max_iter, self.max_rejects, self.tol_grad, self.tol_rel_e,
+                    self.armijo_c, self.tau0, self.step_cap, self.lam)
+
+
+@dataclasses.dataclass
+class Stats:
+    iters: List[int]
+    evals: List[int]
+    stop: List[int]
+    rejects: int
+    energy: float
+
+    @staticmethod
+    def of(s: _Stats, L: int) -> "Stats":
+        return Stats(list(s.iters[:L]), list(s.evals[:L]), list(s.stop[:L]), s.rejects, s.energy)
+
+
+# --------------------------------------------------------------------------
+# building blocks
+# --------------------------------------------------------------------------
+def downsample(img) -> np.ndarray:
+    img = _f64(img)
+    H, W = img.shape
+    out = np.empty(((H + 1) // 2, (W + 1) // 2), dtype=np.float64)
+    lib().or_downsample(_dp(img), W, H, _dp(out))
+    return out
+
+
+def pyramid(img, levels: int) -> List[np.ndarray]:
+    """Level 0 = the frame itself (as float64); level l+1 = 2x2 box average of level l."""
+    p = [_f64(img)]
+    for _ in range(levels - 1):
+        p.append(downsample(p[-1]))
+    return p
+
+
+def sample(T, px: float, py: float):
+    T = _f64(T)
+    H, W = T.shape
+    out = np.empty(3, dtype=np.float64)
+    lib().or_sample(_dp(T), W, H, px, py, _dp(out))
+    return out
+
+
+def rigid_energy(R, T, theta, grad: bool = True):
+    R, T, th = _f64(R), _f64(T), _f64(theta)
+    H, W = R.shape
+    E = np.zeros(1)
+    g = np.zeros(3)
+    lib().or_rigid_energy(_dp(R), _dp(T), W, H, _dp(th), _dp(E), _dp(g) if grad else None)
+    return (float(E[0]), g) if grad else float(E[0])
+
+
+def nonrigid_energy(R, T, u, lam: float, grad: bool = True):
+    R, T = _f64(R), _f64(T)
+    ux, uy = _f64(u[0]), _f64(u[1])
+    H, W = R.shape
+    E = np.zeros(1)
+    if grad:
+        gx = np.zeros((H, W)); gy = np.zeros((H, W))
+        lib().or_nonrigid_energy(_dp(R), _dp(T), W, H, _dp(ux), _dp(uy), lam, _dp(E), _dp(gx), _dp(gy))
+        return float(E[0]), np.stack([gx, gy])
+    lib().or_nonrigid_energy(_dp(R), _dp(T), W, H, _dp(ux), _dp(uy), lam, _dp(E), None, None)
+    return float(E[0])
+
+
+def regulariser(u, lam: float) -> float:
+    ux, uy = _f64(u[0]), _f64(u[1])
+    H, W = ux.shape
+    return float(lib().or_regulariser(_dp(ux), _dp(uy), W, H, lam))
+
+
+def compose_rigid(a, b) -> np.ndarray:
+    """phi_b o phi_a (apply a first): B's initial guess phi_jk o phi_ij (Sec. 2.1.2)."""
+    a, b = _f64(a), _f64(b)
+    out = np.zeros(3)
+    lib().or_rigid_compose(_dp(a), _dp(b), _dp(out))
+    return out
+
+
+def compose_nonrigid(u1, u2) -> np.ndarray:
+    u1, u2 = _f64(u1), _f64(u2)
+    _, H, W = u1.shape
+    ox = np.zeros((H, W)); oy = np.zeros((H, W))
+    a0, a1, b0, b1 = (np.ascontiguousarray(v) for v in (u1[0], u1[1], u2[0], u2[1]))
+    lib().or_nonrigid_compose(_dp(a0), _dp(a1), _dp(b0), _dp(b1), W, H, _dp(ox), _dp(oy))
+    return np.stack([ox, oy])
+
+
+def prolong(u_coarse, H: int, W: int) -> np.ndarray:
+    src = _f64(u_coarse)
+    Hc, Wc = src.shape
+    out = np.zeros((H, W))
+    lib().or_prolong(_dp(src), Wc, Hc, _dp(out), W, H)
+    return out
+
+
+def restrict(u) -> np.ndarray:
+    src = _f64(u)
+    H, W = src.shape
+    out = np.zeros(((H + 1) // 2, (W + 1) // 2))
+    lib().or_restrict(_dp(src), W, H, _dp(out))
+    return out
+
+
+def _pyr_args(pyr: Sequence[np.ndarray]):
+    L = len(pyr)
+    arr = (ctypes.POINTER(ctypes.c_double) * L)(*[_dp(p) for p in pyr])
+    Ws = (ctypes.c_int * L)(*[p.shape[1] for p in pyr])
+    Hs = (ctypes.c_int * L)(*[p.shape[0] for p in pyr])
+    return arr, Ws, Hs
+
+
+def register_rigid(Rpyr, Tpyr, init, cfg: Config):
+    """Multilevel gradient-flow registration of T onto R, rigid map (Def. 2.1)."""
+    assert len(Rpyr) == cfg.levels == len(Tpyr)
+    ra, Ws, Hs = _pyr_args(Rpyr)
+    ta, _, _ = _pyr_args(Tpyr)
+    init = _f64(init)
+    out = np.zeros(3)
+    st = _Stats()
+    c = cfg.c()
+    lib().or_rigid_register(ra, ta, Ws, Hs, ctypes.byref(c), _dp(init), _dp(out), ctypes.byref(st))
+    return out, Stats.of(st, cfg.levels)
+
+
+def register_nonrigid(Rpyr, Tpyr, init_u, cfg: Config):
+    assert len(Rpyr) == cfg.levels == len(Tpyr)
+    ra, Ws, Hs = _pyr_args(Rpyr)
+    ta, _, _ = _pyr_args(Tpyr)
+    H, W = Rpyr[0].shape
+    ox = np.zeros((H, W)); oy = np.zeros((H, W))
+    st = _Stats()
+    c = cfg.c()
+    if init_u is None:
+        lib().or_nonrigid_register(ra, ta, Ws, Hs, ctypes.byref(c), None, None, _dp(ox), _dp(oy),
+                                   ctypes.byref(st))
+    else:
+        ix, iy = _f64(init_u[0]), _f64(init_u[1])
+        lib().or_nonrigid_register(ra, ta, Ws, Hs, ctypes.byref(c), _dp(ix), _dp(iy), _dp(ox), _dp(oy),
+                                   ctypes.byref(st))
+    return np.stack([ox, oy]), Stats.of(st, cfg.levels)
+
+
+# --------------------------------------------------------------------------
+# scan elements and the operators A and B (Sec. 2.1.1-2.1.2)
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Elem:
+    i: int                        # reference frame index
+    k: int                        # template frame index
+    phi: np.ndarray               # rigid: (alpha, Gx, Gy); nonrigid: [2, H, W] displacement
+    stats: Optional[Stats] = None
+
+
+def identity(mode: str, H: int, W: int) -> np.ndarray:
+    return np.zeros(3) if mode == "rigid" else np.zeros((2, H, W))
+
+
+def register(Rpyr, Tpyr, init, cfg: Config):
+    if cfg.mode == "rigid":
+        return register_rigid(Rpyr, Tpyr, init, cfg)
+    return register_nonrigid(Rpyr, Tpyr, init, cfg)
+
+
+def op_A(pyrs, i: int, k: int, cfg: Config) -> Elem:
+    """A(f_i, f_k): register from the identity (neighbouring frames)."""
+    H, W = pyrs[i][0].shape
+    phi, st = register(pyrs[i], pyrs[k], identity(cfg.mode, H, W), cfg)
+    return Elem(i, k, phi, st)
+
+
+def op_B(e1: Elem, e2: Elem, pyrs, cfg: Config) -> Elem:
+    """B(phi_ij, phi_jk) = register f_k onto f_i from phi_jk o phi_ij (Sec. 2.1.2)."""
+    if e1.k != e2.i:
+        raise ValueError(f"B needs adjacent elements, got ({e1.i},{e1.k}) and ({e2.i},{e2.k})")
+    init = compose_rigid(e1.phi, e2.phi) if cfg.mode == "rigid" else compose_nonrigid(e1.phi, e2.phi)
+    phi, st = register(pyrs[e1.i], pyrs[e2.k], init, cfg)
+    return Elem(e1.i, e2.k, phi, st)
+
+
+# --------------------------------------------------------------------------
+# scan DAGs (Sec. 3, Table 1).  SSA form: leaves 0..n-1 are the inputs x_0..x_{n-1};
+# op j creates node n+j = node[l] (.) node[r]; out[i] holds x_0 (.) ... (.) x_i.
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Dag:
+    name: str
+    n: int
+    ops: List[tuple]
+    out: List[int]
+    exclusive: bool = False
+
+    def work(self) -> int:
+        return len(self.ops)
+
+    def depth(self) -> int:
+        d = [0] * (self.n + len(self.ops))
+        for j, (l, r) in enumerate(self.ops):
+            d[self.n + j] = 1 + max(d[l] if l >= 0 else 0, d[r] if r >= 0 else 0)
+        return max(d) if d else 0
+
+
+class _Builder:
+    def __init__(self, n):
+        self.n = n
+        self.ops = []
+
+    def op(self, l, r):
+        self.ops.append((l, r))
+        return self.n + len(self.ops) - 1
+
+
+def dag_sequential(n: int) -> Dag:
+    """Left fold y_i = y_{i-1} (.) x_i: depth and work n-1 (Table 1)."""
+    b = _Builder(n)
+    cur = list(range(n))
+    for i in range(1, n):
+        cur[i] = b.op(cur[i - 1], cur[i])
+    return Dag("sequential", n, b.ops, cur)
+
+
+def dag_brent_kung(n: int) -> Dag:
+    """Tree scan: up-sweep over strides 1,2,4,..., then the down-sweep fills the gaps."""
+    b = _Builder(n)
+    cur = list(range(n))
+    d = 1
+    while d < n:
+        for i in range(2 * d - 1, n, 2 * d):
+            cur[i] = b.op(cur[i - d], cur[i])
+        d *= 2
+    d = 1 << max(0, (n.bit_length() - 2)) if n > 1 else 1
+    while d >= 1:
+        for i in range(3 * d - 1, n, 2 * d):
+            cur[i] = b.op(cur[i - d], cur[i])
+        d //= 2
+    return Dag("brent_kung", n, b.ops, cur)
+
+
+def dag_dissemination(n: int) -> Dag:
+    """Recursive doubling: round r combines elements 2^r apart (Fig. 2)."""
+    b = _Builder(n)
+    cur = list(range(n))
+    d = 1
+    while d < n:
+        prev = list(cur)
+        for i in range(d, n):
+            cur[i] = b.op(prev[i - d], prev[i])
+        d *= 2
+    return Dag("dissemination", n, b.ops, cur)
+
+
+def dag_ladner_fischer(n: int, k: int = 0) -> Dag:
+    """Ladner-Fischer family P_k.  P_0(n): P_1 on the left half, P_0 on the right half,
+    then the left total is combined into every right output (n/2 ops).  P_k(n), k >= 1:
+    pairwise combine, P_{k-1} on the n/2 pair sums, then fill the even positions."""
+    b = _Builder(n)
+
+    def rec(xs, k):
+        m = len(xs)
+        if m == 1:
+            return list(xs)
+        if m == 2:
+            return [xs[0], b.op(xs[0], xs[1])]
+        if k == 0:
+            h = (m + 1) // 2
+            left = rec(xs[:h], 1)
+            right = rec(xs[h:], 0)
+            return left + [b.op(left[-1], r) for r in right]
+        pairs = [b.op(xs[2 * i], xs[2 * i + 1]) for i in range(m // 2)]
+        sub = rec(pairs, k - 1)
+        out = [xs[0]]
+        for i in range(1, m):
+            if i % 2 == 1:
+                out.append(sub[i // 2])
+            else:
+                out.append(b.op(sub[i // 2 - 1], xs[i]))
+        return out
+
+    out = rec(list(range(n)), k)
+    return Dag(f"ladner_fischer{k}", n, b.ops, out)
+
+
+def dag_blelloch(n: int) -> Dag:
+    """Exclusive tree scan (up-sweep, then down-sweep from the identity, node -1).
+    Counted with its identity applications: work 2(n-1), depth 2 log2 n (Table 1)."""
+    b = _Builder(n)
+    cur = list(range(n))
+    d = 1
+    while d < n:
+        for i in range(2 * d - 1, n, 2 * d):
+            cur[i] = b.op(cur[i - d], cur[i])
+        d *= 2
+    cur[n - 1] = -1
+    d //= 2
+    while d >= 1:
+        for i in range(2 * d - 1, n, 2 * d):
+            left = cur[i - d]
+            cur[i - d] = cur[i]
+            cur[i] = b.op(cur[i], left)
+        d //= 2
+    return Dag("blelloch", n, b.ops, cur, exclusive=True)
+
+
+DAGS = {"sequential": dag_sequential, "brent_kung": dag_brent_kung,
+        "dissemination": dag_dissemination, "ladner_fischer": dag_ladner_fischer}
+
+
+def scan(frames, cfg: Config, dag: Optional[Dag] = None, leaves: Optional[List[Elem]] = None,
+         pyrs=None) -> List[Elem]:
+    """Register every frame to frame 0: leaves A(f_{i-1}, f_i), then B along ``dag``.
+    Returns [phi_{0,1}, ..., phi_{0,N-1}] (inclusive scan of Sec. 3)."""
+    N = len(frames)
+    n = N - 1
+    if pyrs is None:
+        pyrs = [pyramid(np.asarray(f), cfg.levels) for f in frames]
+    if dag is None:
+        dag = dag_sequential(n)
+    assert dag.n == n and not dag.exclusive
+    nodes: List[Elem] = list(leaves) if leaves is not None else [op_A(pyrs, i, i + 1, cfg) for i in range(n)]
+    for (l, r) in dag.ops:
+        nodes.append(op_B(nodes[l], nodes[r], pyrs, cfg))
+    return [nodes[o] for o in dag.out]
+
+
+# --------------------------------------------------------------------------
+# comparisons
+# --------------------------------------------------------------------------
+def rigid_displacement(theta, H: int, W: int) -> np.ndarray:
+    """phi(x) - x on the pixel grid, [2, H, W] (for pixel-error comparisons)."""
+    th = _f64(theta)
+    cx, cy = 0.5 * (W - 1), 0.5 * (H - 1)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    xc, yc = x - cx, y - cy
+    ca, sa = math.cos(th[0]), math.sin(th[0])
+    px = ca * xc - sa * yc + cx + th[1]
+    py = sa * xc + ca * yc + cy + th[2]
+    return np.stack([px - x, py - y])
+
+
+def max_px_error(phi_a, phi_b, H: int, W: int, mode: str) -> float:
+    """max over pixels of |phi_a(x) - phi_b(x)|_2."""
+    if mode == "rigid":
+        d = rigid_displacement(phi_a, H, W) - rigid_displacement(phi_b, H, W)
+    else:
+        d = _f64(phi_a) - _f64(phi_b)
+    return float(np.sqrt((d ** 2).sum(axis=0)).max())

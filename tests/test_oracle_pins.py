@@ -1,0 +1,361 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/scan_work.json), closed forms, invariants, library
+routines (numpy's corrcoef), brute-force search and exactness properties of
+bilinear interpolation.  A dropped term, a wrong sign, a transposed operand or
+a wrong index in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2010_12478_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "scan_work.json")
+
+
+def rand_img(H, W, seed):
+    return np.random.default_rng(seed).uniform(0.0, 1.0, size=(H, W))
+
+
+# ---------------------------------------------------------------- pyramid
+def test_downsample_by_hand_with_odd_clamp():
+    a = np.arange(15, dtype=np.float64).reshape(3, 5)       # rows 0..2, cols 0..4
+    d = O.downsample(a)
+    assert d.shape == (2, 3)
+    # (0,0): rows 0-1, cols 0-1 ; (0,2): cols 4,4 (clamped) ; (1,*): rows 2,2 (clamped)
+    exp = np.array([[(0 + 1 + 5 + 6) / 4, (2 + 3 + 7 + 8) / 4, (4 + 4 + 9 + 9) / 4],
+                    [(10 + 11 + 10 + 11) / 4, (12 + 13 + 12 + 13) / 4, (14 + 14 + 14 + 14) / 4]])
+    np.testing.assert_array_equal(d, exp)
+
+
+def test_pyramid_of_linear_ramp_is_centre_consistent():
+    # f(x, y) = 3x - 2y + 1 on an even grid: the box average of level l sits at
+    # x_l = 2 x_{l+1} + 0.5, i.e. level l+1 equals f(2x + 0.5, 2y + 0.5).
+    H, W = 16, 24
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    p = O.pyramid(3 * x - 2 * y + 1, 3)
+    y1, x1 = np.mgrid[0:H // 2, 0:W // 2].astype(np.float64)
+    np.testing.assert_allclose(p[1], 3 * (2 * x1 + 0.5) - 2 * (2 * y1 + 0.5) + 1, atol=1e-12)
+    y2, x2 = np.mgrid[0:H // 4, 0:W // 4].astype(np.float64)
+    np.testing.assert_allclose(p[2], 3 * (4 * x2 + 1.5) - 2 * (4 * y2 + 1.5) + 1, atol=1e-12)
+
+
+# ---------------------------------------------------------------- sampling
+def test_sample_exact_at_pixels_and_on_bilinear_functions():
+    H, W = 7, 9
+    T = rand_img(H, W, 1)
+    for r in range(H):
+        for c in range(W):
+            assert O.sample(T, c, r)[0] == T[r, c]
+    # bilinear interpolation reproduces span{1, x, y, xy} exactly, with exact derivatives
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    F = 0.5 + 2.0 * x - 3.0 * y + 0.25 * x * y
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        px, py = rng.uniform(0, W - 1), rng.uniform(0, H - 1)
+        v, dx, dy = O.sample(F, px, py)
+        assert v == pytest.approx(0.5 + 2 * px - 3 * py + 0.25 * px * py, abs=1e-12)
+        assert dx == pytest.approx(2.0 + 0.25 * py, abs=1e-12)
+        assert dy == pytest.approx(-3.0 + 0.25 * px, abs=1e-12)
+
+
+def test_sample_clamps_to_edge_with_zero_derivative_along_clamped_axis():
+    H, W = 5, 6
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    F = 1.0 + x + 10.0 * y
+    v, dx, dy = O.sample(F, -3.0, 2.5)          # x clamped to 0
+    assert (v, dx, dy) == (pytest.approx(1 + 25.0), 0.0, pytest.approx(10.0))
+    v, dx, dy = O.sample(F, 2.25, H + 4.0)      # y clamped to H-1
+    assert (v, dx, dy) == (pytest.approx(1 + 2.25 + 40.0), pytest.approx(1.0), 0.0)
+    v, dx, dy = O.sample(F, W - 1.0, H - 1.0)   # exactly on the last pixel: not clamped
+    assert v == F[-1, -1] and dx == pytest.approx(1.0) and dy == pytest.approx(10.0)
+
+
+# ---------------------------------------------------------------- NCC energy
+def test_ncc_energy_equals_corrcoef_at_identity():
+    R, T = rand_img(12, 10, 3), rand_img(12, 10, 4)
+    E = O.rigid_energy(R, T, [0.0, 0.0, 0.0], grad=False)
+    assert E == pytest.approx(1.0 - np.corrcoef(R.ravel(), T.ravel())[0, 1], abs=1e-13)
+    u = np.zeros((2, 12, 10))
+    assert O.nonrigid_energy(R, T, u, 5.0, grad=False) == pytest.approx(E, abs=1e-13)
+
+
+def test_ncc_by_hand_on_2x2():
+    R = np.array([[0.0, 1.0], [2.0, 3.0]])
+    T = np.array([[1.0, 0.0], [3.0, 2.0]])
+    # centred: r = (-1.5, -0.5, 0.5, 1.5), t = (-0.5, -1.5, 1.5, 0.5); r.t = 0.75+0.75+0.75+0.75 = 3
+    # |r|^2 = |t|^2 = 5  ->  NCC = 3/5
+    assert O.rigid_energy(R, T, [0, 0, 0], grad=False) == pytest.approx(1.0 - 0.6, abs=1e-15)
+
+
+def test_ncc_invariances_and_self_match():
+    R, T = rand_img(16, 16, 5), rand_img(16, 16, 6)
+    th = [0.02, 0.3, -0.4]
+    E = O.rigid_energy(R, T, th, grad=False)
+    assert O.rigid_energy(R, 3.0 * T + 7.0, th, grad=False) == pytest.approx(E, abs=1e-12)
+    assert O.rigid_energy(0.5 * R - 2.0, T, th, grad=False) == pytest.approx(E, abs=1e-12)
+    assert O.rigid_energy(R, R, [0, 0, 0], grad=False) == 0.0
+    assert O.rigid_energy(R, -R, [0, 0, 0], grad=False) == pytest.approx(2.0, abs=1e-13)
+
+
+def test_constant_image_is_degenerate():
+    R = np.full((8, 8), 0.3)
+    E, g = O.rigid_energy(R, rand_img(8, 8, 7), [0, 0.1, 0.2])
+    assert E == 1.0 and not g.any()
+
+
+# ---------------------------------------------------------------- gradients
+def test_rigid_gradient_matches_central_differences():
+    R, T = synth.rigid_pair(48, 40, 0.01, (0.6, -0.9), noise_snr=8.0, seed=11)
+    th = np.array([0.013, 0.37, -0.61])
+    E, g = O.rigid_energy(R, T, th)
+    h = 1e-6
+    for k in range(3):
+        e = np.zeros(3); e[k] = h
+        fd = (O.rigid_energy(R, T, th + e, grad=False) - O.rigid_energy(R, T, th - e, grad=False)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-9), k
+
+
+def test_nonrigid_gradient_matches_central_differences():
+    H, W = 20, 18
+    R, T = synth.translated_pair(H, W, (0.4, -0.3), noise_snr=8.0, seed=12)
+    rng = np.random.default_rng(13)
+    u = rng.uniform(-0.4, 0.4, size=(2, H, W)) + np.array([0.3, -0.2])[:, None, None]
+    lam = 3.0
+    E, g = O.nonrigid_energy(R, T, u, lam)
+    h = 1e-6
+    pts = [(0, 0, 0), (1, 5, 7), (0, H - 1, W - 1), (1, 0, W - 1), (0, 11, 3), (1, H - 1, 4)]
+    for (cmp, r, c) in pts:
+        up, um = u.copy(), u.copy()
+        up[cmp, r, c] += h; um[cmp, r, c] -= h
+        fd = (O.nonrigid_energy(R, T, up, lam, grad=False) - O.nonrigid_energy(R, T, um, lam, grad=False)) / (2 * h)
+        assert g[cmp, r, c] == pytest.approx(fd, rel=1e-5, abs=1e-10), (cmp, r, c)
+
+
+def test_regulariser_closed_form_on_ramp():
+    # u_x = a * column, u_y = b * row: every horizontal edge of u_x differs by a,
+    # every vertical edge of u_y by b; the other differences vanish.
+    H, W, a, b, lam = 6, 9, 0.3, -0.7, 2.5
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    u = np.stack([a * x, b * y])
+    P = H * W
+    exp = 0.5 * lam / P * (a * a * (W - 1) * H + b * b * (H - 1) * W)
+    assert O.regulariser(u, lam) == pytest.approx(exp, rel=1e-14)
+
+
+# ---------------------------------------------------------------- identical frames
+@pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
+def test_identical_frames_give_exact_identity(mode):
+    R, _ = synth.translated_pair(64, 64, (0, 0), noise_snr=10.0, seed=21)
+    cfg = O.Config(levels=2, mode=mode)
+    p = O.pyramid(R, 2)
+    phi, st = O.register(p, p, O.identity(mode, 64, 64), cfg)
+    assert not np.any(phi)
+    assert st.iters == [0, 0] and st.energy == 0.0
+
+
+# ---------------------------------------------------------------- known shifts
+@pytest.mark.parametrize("seed", range(6))
+def test_recovers_known_translation(seed):
+    rng = np.random.default_rng(100 + seed)
+    s = rng.uniform(-3.4, 3.4, size=2)
+    R, T = synth.translated_pair(96, 96, s, seed=seed, noise_snr=None if seed % 2 else 10.0)
+    th, st = O.register_rigid(O.pyramid(R, 2), O.pyramid(T, 2), np.zeros(3), O.Config(levels=2))
+    assert abs(th[1] - s[0]) <= 0.05 and abs(th[2] - s[1]) <= 0.05, (th, s)
+    assert abs(th[0]) <= 1e-3
+
+
+@pytest.mark.parametrize("alpha", [0.01, -0.015])
+def test_recovers_known_rotation(alpha):
+    R, T = synth.rigid_pair(128, 128, alpha, (1.2, -0.7), noise_snr=None, seed=5)
+    th, _ = O.register_rigid(O.pyramid(R, 2), O.pyramid(T, 2), np.zeros(3), O.Config(levels=2))
+    assert abs(th[0] - alpha) <= 1e-4
+    assert abs(th[1] - 1.2) <= 0.05 and abs(th[2] + 0.7) <= 0.05
+
+
+def test_nonrigid_recovers_smooth_field():
+    ser = synth.make_series(synth.SeriesSpec(2, 96, 96, step=2.0, field_amp=1.0, snr=(10, 10),
+                                             field_rate=(0.8, 1.2), seed=31))
+    F = ser.frames.numpy()
+    cfg = O.Config(levels=2, mode="nonrigid", lam=4.0)
+    u, st = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, cfg)
+    err = (u - ser.truth_field(1))[:, 12:-12, 12:-12]
+    assert np.sqrt((err ** 2).sum(0).mean()) <= 0.1
+    # and the field moved away from a pure translation where the truth does
+    assert np.abs(ser.truth_field(1) - ser.truth_field(1).mean(axis=(1, 2), keepdims=True)).max() > 0.1
+
+
+# ---------------------------------------------------------------- brute force
+def test_gradient_flow_lands_on_brute_force_minimiser():
+    R, T = synth.rigid_pair(32, 32, 0.0, (0.63, -0.41), noise_snr=6.0, seed=41)
+    cfg = O.Config(levels=2, tol_grad=1e-7)
+    th, _ = O.register_rigid(O.pyramid(R, 2), O.pyramid(T, 2), np.zeros(3), cfg)
+
+    def best(center, half, step):
+        grid = np.arange(-half, half + 1e-12, step)
+        bestE, arg = np.inf, None
+        for gx in center[0] + grid:
+            for gy in center[1] + grid:
+                E = O.rigid_energy(R, T, [th[0], gx, gy], grad=False)
+                if E < bestE:
+                    bestE, arg = E, (gx, gy)
+        return np.array(arg), bestE
+
+    coarse, _ = best((0.63, -0.41), 1.0, 0.05)
+    fine, Ebf = best(coarse, 0.05, 0.005)
+    assert np.abs(fine - th[1:]).max() <= 0.01, (fine, th)
+    assert O.rigid_energy(R, T, th, grad=False) <= Ebf + 1e-9
+    # alpha: 1-D search at the returned translation
+    al = th[0] + np.arange(-2e-3, 2e-3 + 1e-12, 2e-5)
+    Es = [O.rigid_energy(R, T, [a, th[1], th[2]], grad=False) for a in al]
+    assert abs(al[int(np.argmin(Es))] - th[0]) <= 4e-5
+
+
+# ---------------------------------------------------------------- composition
+def _rigid_map(th, pts, W, H):
+    cx, cy = 0.5 * (W - 1), 0.5 * (H - 1)
+    ca, sa = math.cos(th[0]), math.sin(th[0])
+    x, y = pts[:, 0] - cx, pts[:, 1] - cy
+    return np.stack([ca * x - sa * y + cx + th[1], sa * x + ca * y + cy + th[2]], axis=1)
+
+
+def test_rigid_composition_matches_pointwise_composition():
+    rng = np.random.default_rng(51)
+    a, b = np.array([0.1, 2.0, -1.0]), np.array([-0.3, 0.5, 4.0])
+    pts = rng.uniform(0, 100, size=(20, 2))
+    direct = _rigid_map(b, _rigid_map(a, pts, 101, 77), 101, 77)
+    np.testing.assert_allclose(_rigid_map(O.compose_rigid(a, b), pts, 101, 77), direct, atol=1e-12)
+
+
+def test_rigid_composition_associative_with_identity():
+    rng = np.random.default_rng(52)
+    a, b, c = (rng.uniform(-1, 1, 3) for _ in range(3))
+    l = O.compose_rigid(O.compose_rigid(a, b), c)
+    r = O.compose_rigid(a, O.compose_rigid(b, c))
+    np.testing.assert_allclose(l, r, atol=1e-12)
+    np.testing.assert_array_equal(O.compose_rigid(a, np.zeros(3)), a)
+    np.testing.assert_allclose(O.compose_rigid(np.zeros(3), a), a, atol=0)
+
+
+def test_nonrigid_composition_of_translations_and_linear_fields():
+    H, W = 10, 12
+    t1 = np.broadcast_to(np.array([0.7, -1.2])[:, None, None], (2, H, W)).copy()
+    t2 = np.broadcast_to(np.array([-0.2, 0.4])[:, None, None], (2, H, W)).copy()
+    np.testing.assert_allclose(O.compose_nonrigid(t1, t2), t1 + t2, atol=1e-14)
+    # u2 linear in x: u2(p) = (0.1 px, 0): composition gives u1 + 0.1 (x + u1_x) where in range
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    u2 = np.stack([0.1 * x, np.zeros_like(x)])
+    c = O.compose_nonrigid(t1 * 0.5, u2)
+    inside = (x + 0.35 <= W - 1)
+    np.testing.assert_allclose(c[0][inside], (0.35 + 0.1 * (x + 0.35))[inside], atol=1e-12)
+
+
+def test_prolong_and_restrict_on_affine_fields():
+    Hc, Wc = 6, 7
+    y, x = np.mgrid[0:Hc, 0:Wc].astype(np.float64)
+    uc = 0.3 * x - 0.2 * y + 1.0
+    f = O.prolong(uc, 2 * Hc, 2 * Wc)
+    Y, X = np.mgrid[0:2 * Hc, 0:2 * Wc].astype(np.float64)
+    exp = 2.0 * (0.3 * (X - 0.5) / 2 - 0.2 * (Y - 0.5) / 2 + 1.0)
+    interior = (X >= 1) & (X <= 2 * Wc - 2) & (Y >= 1) & (Y <= 2 * Hc - 2)
+    np.testing.assert_allclose(f[interior], exp[interior], atol=1e-12)
+    # restriction of the prolonged affine field returns the coarse field (halved twice-doubled)
+    back = O.restrict(f)
+    np.testing.assert_allclose(back[1:-1, 1:-1], uc[1:-1, 1:-1], atol=1e-12)
+
+
+# ---------------------------------------------------------------- scan DAGs
+def _concat_check(d):
+    vals = [f"{i}," for i in range(d.n)]
+    for (l, r) in d.ops:
+        vals.append(("" if l < 0 else vals[l]) + ("" if r < 0 else vals[r]))
+    return vals
+
+
+@pytest.mark.parametrize("name", list(O.DAGS))
+def test_dag_computes_inclusive_prefixes(name):
+    for n in range(1, 70):
+        d = O.DAGS[name](n)
+        vals = _concat_check(d)
+        for i, o in enumerate(d.out):
+            assert vals[o] == "".join(f"{j}," for j in range(i + 1)), (name, n, i)
+
+
+def test_blelloch_is_exclusive_and_one_shift_from_inclusive():
+    # Sec. 1: an exclusive result becomes inclusive by one shift plus one operator application
+    for n in (1, 2, 4, 8, 32):
+        d = O.dag_blelloch(n)
+        vals = _concat_check(d)
+        excl = ["" if o < 0 else vals[o] for o in d.out]
+        for i in range(n):
+            assert excl[i] == "".join(f"{j}," for j in range(i))
+            assert excl[i] + f"{i}," == "".join(f"{j}," for j in range(i + 1))
+
+
+def test_dag_work_and_depth_match_table1_and_fig2():
+    g = json.load(open(GOLDEN))
+    for N in (2, 4, 8, 16, 64, 256, 4096):
+        lg = int(math.log2(N))
+        assert O.dag_sequential(N).work() == N - 1 and O.dag_sequential(N).depth() == N - 1
+        assert O.dag_blelloch(N).work() == 2 * (N - 1)
+        assert O.dag_dissemination(N).work() == N * lg - N + 1
+        assert O.dag_dissemination(N).depth() == lg
+        assert O.dag_ladner_fischer(N).work() < 4 * N - 5
+        assert O.dag_ladner_fischer(N).depth() == lg
+        assert O.dag_brent_kung(N).work() == 2 * N - 2 - lg
+    f2 = g["fig2_dissemination_n8"]
+    d = O.dag_dissemination(f2["N"])
+    assert d.work() == f2["work"] and d.depth() == f2["rounds"]
+
+
+def test_table5_work_counts():
+    # full registration on P ranks: N preprocessing A's, N-P local reduction steps,
+    # the global scan over P elements, N steps in the last local phase (Sec. 4.1, Table 5)
+    g = json.load(open(GOLDEN))["table5_work"]
+    N = g["N"]
+    assert g["serial"] == N + (N - 1) == O.dag_sequential(N).work() + N
+    for P, wd, wl in zip(g["P"], g["dissemination"], g["ladner_fischer"]):
+        assert N + (N - P) + O.dag_dissemination(P).work() + N == wd
+        assert N + (N - P) + O.dag_ladner_fischer(P).work() + N == wl
+
+
+# ---------------------------------------------------------------- operator / scan
+@pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
+def test_operator_associativity_on_tiny_series(mode):
+    spec = synth.SeriesSpec(4, 64, 64, step=1.5, field_amp=0.5, snr=(10, 10), seed=61)
+    F = synth.make_series(spec).frames.numpy()
+    cfg = O.Config(levels=2, mode=mode, lam=4.0)
+    pyrs = [O.pyramid(f, 2) for f in F]
+    a, b, c = (O.op_A(pyrs, i, i + 1, cfg) for i in range(3))
+    left = O.op_B(O.op_B(a, b, pyrs, cfg), c, pyrs, cfg)
+    right = O.op_B(a, O.op_B(b, c, pyrs, cfg), pyrs, cfg)
+    assert (left.i, left.k) == (right.i, right.k) == (0, 3)
+    assert O.max_px_error(left.phi, right.phi, 64, 64, mode) <= 0.02
+
+
+def test_operator_B_rejects_non_adjacent_elements():
+    e1 = O.Elem(0, 1, np.zeros(3))
+    e2 = O.Elem(2, 3, np.zeros(3))
+    with pytest.raises(ValueError):
+        O.op_B(e1, e2, None, O.Config())
+
+
+@pytest.mark.parametrize("dag", ["brent_kung", "dissemination", "ladner_fischer"])
+def test_parallel_scan_equals_sequential_recursion(dag):
+    spec = synth.spec_c1()
+    spec.n_frames = 9
+    F = synth.make_series(spec).frames.numpy()
+    cfg = O.Config(levels=2)
+    pyrs = [O.pyramid(f, 2) for f in F]
+    leaves = [O.op_A(pyrs, i, i + 1, cfg) for i in range(len(F) - 1)]
+    seq = O.scan(F, cfg, O.dag_sequential(len(F) - 1), leaves=leaves, pyrs=pyrs)
+    par = O.scan(F, cfg, O.DAGS[dag](len(F) - 1), leaves=leaves, pyrs=pyrs)
+    for i, (s, p) in enumerate(zip(seq, par)):
+        assert (s.i, s.k) == (p.i, p.k) == (0, i + 1)
+        assert O.max_px_error(s.phi, p.phi, 128, 128, "rigid") <= 0.02
