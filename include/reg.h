@@ -1,0 +1,235 @@
+/*
+ * reg.h - C ABI of the GB300 registration-scan library (libreg.so).
+ *
+ * The library registers every frame f_1..f_{N-1} of an image series to the
+ * first frame f_0 by an inclusive prefix scan with the operator
+ *
+ *     phi_ij (.)_B phi_jk = B(phi_ij, phi_jk)                 [Sec. 3]
+ *
+ * where B composes the two known deformations into an initial guess
+ * phi_jk o phi_ij and then minimises the normalised-cross-correlation
+ * distance D(f_i, f_k o phi) by gradient flow on a coarse-to-fine pyramid
+ * [Sec. 2.1.1, Sec. 2.1.2, Def. 2.1].  The neighbour registrations
+ * A(f_{i-1}, f_i) start from the identity.
+ *
+ * Deformation models:
+ *   REG_RIGID     phi(x) = Rot(alpha) (x - c) + c + G, c = ((W-1)/2, (H-1)/2),
+ *                 pixel (r, c) at x = (c, r)                         [Def. 2.1]
+ *   REG_NONRIGID  phi(x) = x + u(x), u a dense 2-channel field, energy
+ *                 1 - NCC + lambda/(2P) sum_edges |u(a) - u(b)|^2 (an extension:
+ *                 the paper's deformation is rigid)
+ *
+ * Conventions common to every entry point:
+ *   - Return value: REG_OK (0) or a negative REG_E* code; reg_strerror()
+ *     names it and reg_last_error_message() gives the detail of the last
+ *     failure on the calling thread.  Non-convergence is not an error: it is
+ *     reported in reg_stats_t.stop[].
+ *   - Pointers are host or device memory as stated per argument; where
+ *     "host or device" is allowed the library detects the kind.
+ *   - Caller-owned buffers are only borrowed for the duration of the call
+ *     (the call returns after its work on `stream` has completed).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).
+ *   - All computation runs in the library's CUDA kernels (sm_103a); there is
+ *     no CPU fallback.  Without a usable GPU every compute entry point
+ *     returns REG_ECUDA.
+ */
+#ifndef REG_H
+#define REG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define REG_OK        0
+#define REG_EINVAL   -1   /* bad argument (size, pointer, mode, adjacency of B's inputs) */
+#define REG_ENOMEM   -2   /* device or host allocation failed */
+#define REG_EBUDGET  -3   /* stream admission refused: memory budget or slots full; retry later */
+#define REG_ETIMEOUT -4   /* a bounded wait gave up (device queue or host poll) */
+#define REG_ECUDA    -5   /* CUDA runtime error, or no usable GPU */
+#define REG_ESTATE   -6   /* object used in the wrong state */
+
+/* ---- enums ------------------------------------------------------------ */
+#define REG_RIGID    0
+#define REG_NONRIGID 1
+
+#define REG_F32  0        /* pyramid storage type; arithmetic is always FP32 */
+#define REG_BF16 1
+#define REG_F16  2
+
+#define REG_SCHED_SEQ           0   /* left fold phi_{0,i} = phi_{0,i-1} (.) phi_{i-1,i}   [Sec. 3] */
+#define REG_SCHED_BRENT_KUNG    1   /* work-efficient tree scan                        [Table 1] */
+#define REG_SCHED_DISSEMINATION 2   /* recursive doubling, depth log2 N                [Table 1, Fig. 2] */
+#define REG_SCHED_LADNER_FISCHER 3  /* Ladner-Fischer P_0                              [Table 1] */
+
+#define REG_EXEC_PLAIN      0   /* one operator per kernel launch, DAG order on a stream pool */
+#define REG_EXEC_LEVEL      1   /* one launch per DAG depth, all its operators batched */
+#define REG_EXEC_PERSISTENT 2   /* one persistent launch, device ready-queue over the DAG */
+
+#define REG_MAX_LEVELS 8
+
+/* why a level stopped (reg_stats_t.stop) */
+#define REG_STOP_GRAD    0   /* metric gradient norm below tol_grad */
+#define REG_STOP_REL     1   /* accepted step lowered E by less than tol_rel_e * |E| */
+#define REG_STOP_LS      2   /* line search exhausted max_rejects halvings */
+#define REG_STOP_MAXIT   3   /* max_iter accepted steps */
+
+/* ---- data types --------------------------------------------------------- */
+
+/* Scan element: deformation plus indices, 20 bytes [Sec. 5: "20 bytes of
+ * deformation data and indices"].  Rigid parameters (alpha in radians, G in
+ * pixels of the finest level).  For REG_NONRIGID the field lives in a separate
+ * buffer and alpha/gx/gy hold the field's mean displacement (alpha = 0). */
+typedef struct {
+    int32_t i, k;        /* phi_{i,k}: f_k o phi ~ f_i */
+    float alpha, gx, gy;
+} reg_elem_t;
+
+typedef struct {
+    int    mode;          /* REG_RIGID or REG_NONRIGID */
+    int    levels;        /* pyramid levels, 1..REG_MAX_LEVELS */
+    int    max_iter;      /* accepted gradient-flow steps per level */
+    int    max_rejects;   /* Armijo halvings per step */
+    double tol_grad;      /* stop: metric norm of the descent direction */
+    double tol_rel_e;     /* stop: relative energy decrease of an accepted step */
+    double armijo_c;      /* sufficient-decrease constant */
+    double tau0;          /* first trial step of each level */
+    double step_cap;      /* largest step, pixels of the current level */
+    double lambda;        /* regulariser weight (REG_NONRIGID) */
+    int    storage;       /* REG_F32, REG_BF16 or REG_F16 pyramid storage */
+    int    cluster;       /* CTAs cooperating on one operator (1,2,4,8,16); 0 = auto */
+    int    workers;       /* persistent executor: operator slots in flight; 0 = auto */
+    size_t mem_budget;    /* stream service: device bytes it may hold; 0 = unlimited */
+} reg_config_t;
+
+typedef struct {
+    int32_t i, k;                      /* the element this operator produced */
+    int32_t iters[REG_MAX_LEVELS];     /* accepted steps per level, index 0 = finest */
+    int32_t evals[REG_MAX_LEVELS];     /* energy evaluations per level */
+    int32_t stop[REG_MAX_LEVELS];      /* REG_STOP_* per level */
+    int32_t rejects;                   /* Armijo rejections, all levels */
+    int32_t status;                    /* REG_OK, or a device-side error code */
+    double  energy;                    /* energy at the result, finest level */
+    double  theta[3];                  /* the result: rigid (alpha, Gx, Gy) in FP64; nonrigid
+                                          (0, mean u_x, mean u_y) */
+} reg_stats_t;
+
+typedef struct reg_ctx reg_ctx_t;
+typedef struct reg_stream reg_stream_t;
+
+typedef struct {
+    uint64_t frame_id;     /* id given at submit */
+    reg_elem_t elem;       /* phi_{0,i} of that frame (i = its position in the stream) */
+    double submit_us;      /* host clock (us) at submit */
+    double done_us;        /* host clock (us) when the result was seen complete */
+    int32_t status;
+} reg_result_t;
+
+/* ---- configuration and context ----------------------------------------- */
+
+/* Fill *cfg with the defaults (rigid, 2 levels, FP32 storage, auto tiles). */
+void reg_config_default(reg_config_t *cfg);
+
+/* Create a context on CUDA device `device`.  The context owns its pyramids,
+ * queues and workspaces; destroy it with reg_ctx_destroy.  Errors: REG_EINVAL
+ * (bad config), REG_ECUDA (no device / no sm_103a GPU), REG_ENOMEM. */
+int reg_ctx_create(const reg_config_t *cfg, int device, reg_ctx_t **out);
+void reg_ctx_destroy(reg_ctx_t *ctx);
+
+/* ---- the operators ------------------------------------------------------ */
+
+/* Register template T onto reference R (A when init == NULL, else the
+ * minimisation of B from `init`) [Sec. 2.1.1].
+ *   R, T       fp32 images, H rows of `pitch` elements (pitch >= W), host or device.
+ *   init       rigid initial deformation (host), NULL = identity.
+ *   field_in   REG_NONRIGID initial field [2][H][W] fp32 (x plane then y), host or
+ *              device, NULL = identity.
+ *   out        result (host), i = 0, k = 1.
+ *   field_out  REG_NONRIGID result field [2][H][W] (host or device); may be NULL
+ *              for REG_RIGID.
+ *   stats      optional (host).
+ * Errors: REG_EINVAL (W or H < 2 at the coarsest level, pitch < W, NULL R/T/out). */
+int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int W, int H, int pitch,
+                 const reg_elem_t *init, const float *field_in,
+                 reg_elem_t *out, float *field_out, reg_stats_t *stats, void *stream);
+
+/* Register all frames to f_0 by the scan [Sec. 3]: the N-1 neighbour
+ * operators A(f_{i-1}, f_i), then B along the DAG of `schedule`.
+ *   frames     fp32 [N][H][pitch], host or device (host frames are copied in).
+ *   out        N-1 elements phi_{0,1}..phi_{0,N-1} (host or device).
+ *   fields_out REG_NONRIGID: [N-1][2][H][W] fp32 (host or device); NULL for rigid.
+ *   per_op     optional host array of (N-1) + (#B operators of the schedule)
+ *              stats, leaves first, then the B operators in DAG order
+ *              (reg_scan_work() gives the count).
+ * Errors: REG_EINVAL, REG_ENOMEM, REG_ECUDA, REG_ETIMEOUT (persistent queue). */
+int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch,
+             int schedule, int exec, reg_elem_t *out, float *fields_out,
+             reg_stats_t *per_op, void *stream);
+
+/* Number of B applications the schedule uses for n = N-1 elements (host only,
+ * no GPU needed).  Returns -1 for an unknown schedule. */
+int reg_scan_work(int schedule, int n);
+
+/* Write the schedule's DAG in SSA form (host only): op j creates node n+j =
+ * node[left[j]] (.) node[right[j]]; out_node[i] holds x_0 (.) ... (.) x_i.
+ * Arrays sized by reg_scan_work() and n.  Returns the op count or -1. */
+int reg_scan_dag(int schedule, int n, int32_t *left, int32_t *right, int32_t *out_node);
+
+/* ---- kernel-level entry points (one hot-path step each) ------------------- */
+
+/* Pyramid build [Sec. 2.1.1, multilevel scheme]: 2x2 box average per level,
+ * odd last row/column clamped.  frame: device fp32 [H][pitch].  out: device,
+ * levels packed level 0 first, each W_l x H_l contiguous, in `storage` type
+ * (4 or 2 bytes per pixel).  Returns REG_EINVAL for levels outside 1..8. */
+int reg_pyramid(reg_ctx_t *ctx, const float *frame, int W, int H, int pitch,
+                int levels, int storage, void *out, void *stream);
+
+/* Energy and gradient at a given deformation (one fused warp+reduction pass,
+ * as used inside the iteration) [Sec. 2.1.1].  R, T device fp32 [H][W].
+ *   REG_RIGID:    theta[3] (host) = (alpha, Gx, Gy); grad[3] (host, optional).
+ *   REG_NONRIGID: field [2][H][W] device; grad_field [2][H][W] device optional
+ *                 (dE/du per pixel).  lambda from the context configuration.
+ *   energy (host): E. */
+int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W, int H,
+               const double *theta, const float *field, double *energy,
+               double *grad, float *grad_field, void *stream);
+
+/* Nonrigid composition (B's initial guess, Sec. 2.1.2):
+ * out(x) = u1(x) + u2(x + u1(x)), bilinear with clamp. Device [2][H][W] each. */
+int reg_compose_field(reg_ctx_t *ctx, const float *u1, const float *u2, int W, int H,
+                      float *out, void *stream);
+
+/* ---- streaming service ----------------------------------------------------- */
+
+/* Open an acquisition stream of W x H fp32 frames.  The first submitted frame
+ * is f_0; each later frame f_i yields phi_{0,i} via A(f_{i-1}, f_i) and
+ * B(phi_{0,i-1}, phi_{i-1,i}), run on the device while other frames and other
+ * streams are in flight.  Errors: REG_EBUDGET if the stream's resident state
+ * does not fit the context's memory budget. */
+int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out);
+
+/* Submit one frame (host or device, [H][W] fp32; copied before return).
+ * REG_EBUDGET: no slot or memory free right now; retry after polling. */
+int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t frame_id);
+
+/* Collect up to `max` finished results in submission order; waits up to
+ * timeout_us for at least one (0 = do not wait).  *n_out = number written.
+ * REG_ETIMEOUT if none finished in time (n_out = 0). */
+int reg_stream_poll(reg_stream_t *s, reg_result_t *out, int max, int *n_out, int timeout_us);
+
+/* Finish all submitted frames and release the stream. */
+int reg_stream_close(reg_stream_t *s);
+
+/* ---- diagnostics ----------------------------------------------------------- */
+const char *reg_strerror(int code);
+const char *reg_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REG_H */

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libreg (the C ABI of include/reg.h).
+
+Argument marshalling only: every step of the registration runs in the
+library's CUDA kernels.  Arrays are torch tensors (device or host) or numpy
+arrays (host); the binding passes their data pointers.  If libreg.so has not
+been built, importing the symbols raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libreg.so")
+
+REG_OK, REG_EINVAL, REG_ENOMEM, REG_EBUDGET, REG_ETIMEOUT, REG_ECUDA, REG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+RIGID, NONRIGID = 0, 1
+F32, BF16, F16 = 0, 1, 2
+SCHEDULES = {"sequential": 0, "brent_kung": 1, "dissemination": 2, "ladner_fischer": 3}
+EXECS = {"plain": 0, "level": 1, "persistent": 2}
+STORAGES = {"f32": F32, "bf16": BF16, "f16": F16}
+MAX_LEVELS = 8
+
+# every symbol include/reg.h declares
+EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairwise", "reg_scan",
+           "reg_scan_work", "reg_scan_dag", "reg_pyramid", "reg_energy", "reg_compose_field",
+           "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
+           "reg_strerror", "reg_last_error_message"]
+
+
+class RegError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+class reg_elem_t(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int32), ("k", ctypes.c_int32), ("alpha", ctypes.c_float),
+                ("gx", ctypes.c_float), ("gy", ctypes.c_float)]
+
+
+class reg_config_t(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("levels", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("max_rejects", ctypes.c_int), ("tol_grad", ctypes.c_double), ("tol_rel_e", ctypes.c_double),
+                ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double), ("step_cap", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("storage", ctypes.c_int), ("cluster", ctypes.c_int),
+                ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t)]
+
+
+class reg_stats_t(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int32), ("k", ctypes.c_int32), ("iters", ctypes.c_int32 * MAX_LEVELS),
+                ("evals", ctypes.c_int32 * MAX_LEVELS), ("stop", ctypes.c_int32 * MAX_LEVELS),
+                ("rejects", ctypes.c_int32), ("status", ctypes.c_int32), ("energy", ctypes.c_double),
+                ("theta", ctypes.c_double * 3)]
+
+
+class reg_result_t(ctypes.Structure):
+    _fields_ = [("frame_id", ctypes.c_uint64), ("elem", reg_elem_t), ("submit_us", ctypes.c_double),
+                ("done_us", ctypes.c_double), ("status", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libreg.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libreg.so is not built ({LIB_PATH}); run paper_2010_12478_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp, fp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+        L.reg_config_default.argtypes = [ctypes.POINTER(reg_config_t)]
+        L.reg_ctx_create.argtypes = [ctypes.POINTER(reg_config_t), ip, ctypes.POINTER(vp)]
+        L.reg_ctx_destroy.argtypes = [vp]
+        L.reg_pairwise.argtypes = [vp, fp, fp, ip, ip, ip, ctypes.POINTER(reg_elem_t), fp,
+                                   ctypes.POINTER(reg_elem_t), fp, ctypes.POINTER(reg_stats_t), vp]
+        L.reg_scan.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, vp, fp, ctypes.POINTER(reg_stats_t), vp]
+        L.reg_scan_work.argtypes = [ip, ip]
+        L.reg_scan_dag.argtypes = [ip, ip, vp, vp, vp]
+        L.reg_pyramid.argtypes = [vp, fp, ip, ip, ip, ip, ip, vp, vp]
+        L.reg_energy.argtypes = [vp, fp, fp, ip, ip, dp, fp, dp, dp, fp, vp]
+        L.reg_compose_field.argtypes = [vp, fp, fp, ip, ip, fp, vp]
+        L.reg_stream_open.argtypes = [vp, ip, ip, ctypes.POINTER(vp)]
+        L.reg_stream_submit.argtypes = [vp, fp, ctypes.c_uint64]
+        L.reg_stream_poll.argtypes = [vp, ctypes.POINTER(reg_result_t), ip, ctypes.POINTER(ctypes.c_int), ip]
+        L.reg_stream_close.argtypes = [vp]
+        L.reg_strerror.argtypes = [ip]
+        L.reg_strerror.restype = ctypes.c_char_p
+        L.reg_last_error_message.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(code: int, where: str):
+    if code != REG_OK:
+        msg = lib().reg_last_error_message().decode(errors="replace")
+        raise RegError(code, where, f"{lib().reg_strerror(code).decode()}: {msg}")
+
+
+def _ptr(a) -> Optional[int]:
+    """Data pointer of a torch tensor or numpy array (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+@dataclasses.dataclass
+class Config:
+    mode: str = "rigid"
+    levels: int = 2
+    max_iter: int = 500
+    max_rejects: int = 30
+    tol_grad: float = 1e-4
+    tol_rel_e: float = 1e-10
+    armijo_c: float = 1e-4
+    tau0: float = 1.0
+    step_cap: float = 0.5
+    lam: float = 4.0
+    storage: str = "f32"
+    cluster: int = 0
+    workers: int = 0
+    mem_budget: int = 0
+
+    def c(self) -> reg_config_t:
+        return reg_config_t(RIGID if self.mode == "rigid" else NONRIGID, self.levels, self.max_iter,
+                            self.max_rejects, self.tol_grad, self.tol_rel_e, self.armijo_c, self.tau0,
+                            self.step_cap, self.lam, STORAGES[self.storage], self.cluster, self.workers,
+                            self.mem_budget)
+
+
+def stats_dict(s: reg_stats_t, levels: int) -> dict:
+    return dict(i=s.i, k=s.k, iters=list(s.iters[:levels]), evals=list(s.evals[:levels]),
+                stop=list(s.stop[:levels]), rejects=s.rejects, status=s.status, energy=s.energy,
+                theta=list(s.theta))
+
+
+def scan_work(schedule: str, n: int) -> int:
+    return lib().reg_scan_work(SCHEDULES[schedule], n)
+
+
+def scan_dag(schedule: str, n: int):
+    m = scan_work(schedule, n)
+    left = np.zeros(max(m, 1), np.int32)
+    right = np.zeros(max(m, 1), np.int32)
+    out = np.zeros(max(n, 1), np.int32)
+    lib().reg_scan_dag(SCHEDULES[schedule], n, left.ctypes.data, right.ctypes.data, out.ctypes.data)
+    return list(zip(left[:m].tolist(), right[:m].tolist())), out[:n].tolist()
+
+
+class Context:
+    """A libreg context on one GPU (owns pyramids, queues and workspaces)."""
+
+    def __init__(self, cfg: Optional[Config] = None, device: int = 0):
+        self.cfg = cfg or Config()
+        self._c = self.cfg.c()
+        h = ctypes.c_void_p()
+        check(lib().reg_ctx_create(ctypes.byref(self._c), device, ctypes.byref(h)), "reg_ctx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().reg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- operators
+    def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,
+                 stream=None):
+        H, W = R.shape[-2], R.shape[-1]
+        out = reg_elem_t()
+        st = reg_stats_t()
+        ini = None
+        if init is not None:
+            ini = reg_elem_t(0, 1, float(init[0]), float(init[1]), float(init[2]))
+        check(lib().reg_pairwise(self.h, _ptr(R), _ptr(T), W, H, W, ctypes.byref(ini) if ini else None,
+                                 _ptr(field_in), ctypes.byref(out), _ptr(field_out), ctypes.byref(st),
+                                 _stream(stream)), "reg_pairwise")
+        return (out.i, out.k, out.alpha, out.gx, out.gy), stats_dict(st, self.cfg.levels)
+
+    def scan(self, frames, schedule: str = "brent_kung", exec: str = "level", fields_out=None,
+             out_elems=None, want_stats: bool = True, stream=None):
+        N, H, W = frames.shape
+        n = N - 1
+        m = scan_work(schedule, n)
+        elems = (reg_elem_t * n)() if out_elems is None else None
+        stats = (reg_stats_t * (n + m))() if want_stats else None
+        out_ptr = ctypes.addressof(elems) if elems is not None else _ptr(out_elems)
+        check(lib().reg_scan(self.h, _ptr(frames), N, W, H, W, SCHEDULES[schedule], EXECS[exec], out_ptr,
+                             _ptr(fields_out), stats, _stream(stream)), "reg_scan")
+        el = [(e.i, e.k, e.alpha, e.gx, e.gy) for e in elems] if elems is not None else None
+        st = [stats_dict(s, self.cfg.levels) for s in stats] if stats is not None else None
+        return el, st
+
+    # ---- kernel-level steps
+    def pyramid(self, frame, levels: int, storage: str, out):
+        H, W = frame.shape
+        check(lib().reg_pyramid(self.h, _ptr(frame), W, H, W, levels, STORAGES[storage], _ptr(out), None),
+              "reg_pyramid")
+
+    def energy_rigid(self, R, T, theta):
+        H, W = R.shape
+        th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+        E = ctypes.c_double()
+        g = (ctypes.c_double * 3)()
+        check(lib().reg_energy(self.h, _ptr(R), _ptr(T), W, H, th, None, ctypes.byref(E), g, None, None),
+              "reg_energy")
+        return E.value, np.array(list(g))
+
+    def energy_field(self, R, T, field, grad_field=None):
+        H, W = R.shape
+        E = ctypes.c_double()
+        check(lib().reg_energy(self.h, _ptr(R), _ptr(T), W, H, None, _ptr(field), ctypes.byref(E), None,
+                               _ptr(grad_field), None), "reg_energy")
+        return E.value
+
+    def compose_field(self, u1, u2, out):
+        _, H, W = u1.shape
+        check(lib().reg_compose_field(self.h, _ptr(u1), _ptr(u2), W, H, _ptr(out), None), "reg_compose_field")
+
+
+class Stream:
+    """An acquisition stream of the serving API (reg_stream_*)."""
+
+    def __init__(self, ctx: Context, W: int, H: int):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        check(lib().reg_stream_open(ctx.h, W, H, ctypes.byref(h)), "reg_stream_open")
+        self.h = h
+
+    def submit(self, frame, frame_id: int) -> int:
+        return lib().reg_stream_submit(self.h, _ptr(frame), frame_id)
+
+    def poll(self, max_results: int = 64, timeout_us: int = 0) -> List[dict]:
+        buf = (reg_result_t * max_results)()
+        n = ctypes.c_int()
+        rc = lib().reg_stream_poll(self.h, buf, max_results, ctypes.byref(n), timeout_us)
+        if rc not in (REG_OK, REG_ETIMEOUT):
+            check(rc, "reg_stream_poll")
+        return [dict(frame_id=r.frame_id, elem=(r.elem.i, r.elem.k, r.elem.alpha, r.elem.gx, r.elem.gy),
+                     submit_us=r.submit_us, done_us=r.done_us, status=r.status) for r in buf[:n.value]]
+
+    def close(self):
+        if self.h:
+            check(lib().reg_stream_close(self.h), "reg_stream_close")
+            self.h = None

@@ -1,0 +1,884 @@
+// Host side of libreg: the C ABI declared in include/reg.h, the scan DAG
+// builders, the executors and device memory management.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "reg_internal.h"
+
+using namespace reg;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? REG_ENOMEM : REG_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+#define CHECK(expr)                \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != REG_OK) return r_; \
+    } while (0)
+
+extern "C" const char *reg_strerror(int code)
+{
+    switch (code) {
+    case REG_OK: return "ok";
+    case REG_EINVAL: return "invalid argument";
+    case REG_ENOMEM: return "out of memory";
+    case REG_EBUDGET: return "memory budget or slots exhausted";
+    case REG_ETIMEOUT: return "bounded wait timed out";
+    case REG_ECUDA: return "CUDA error";
+    case REG_ESTATE: return "invalid state";
+    }
+    return "unknown error";
+}
+
+extern "C" const char *reg_last_error_message(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------ device buffers
+namespace {
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    int reserve(size_t n)
+    {
+        if (n <= bytes) return REG_OK;
+        release();
+        size_t want = std::max(n, (size_t)256);
+        cudaError_t e = cudaMalloc(&ptr, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ptr = nullptr;
+            return fail(REG_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+        }
+        bytes = want;
+        return REG_OK;
+    }
+    template <typename T> T *as() const { return (T *)ptr; }
+};
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t storage_bytes(int storage) { return storage == REG_F32 ? 4 : 2; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ scan DAGs
+// SSA form: leaves 0..n-1 are x_0..x_{n-1}; op j makes node n+j = node[l] (.) node[r].
+namespace {
+
+struct Dag {
+    std::vector<int> left, right, out;
+};
+
+struct DagBuilder {
+    int n;
+    Dag d;
+    explicit DagBuilder(int n_) : n(n_) {}
+    int op(int l, int r)
+    {
+        d.left.push_back(l);
+        d.right.push_back(r);
+        return n + (int)d.left.size() - 1;
+    }
+};
+
+// Sequential recursion phi_{0,i} = phi_{0,i-1} (.) phi_{i-1,i} (Sec. 3).
+Dag dag_seq(int n)
+{
+    DagBuilder b(n);
+    std::vector<int> cur(n);
+    for (int i = 0; i < n; ++i) cur[i] = i;
+    for (int i = 1; i < n; ++i) cur[i] = b.op(cur[i - 1], cur[i]);
+    b.d.out = cur;
+    return b.d;
+}
+
+// Brent-Kung: reduction tree over strides 1, 2, 4, ..., then a reverse tree
+// that completes the prefixes between the tree nodes (Table 1 family).
+Dag dag_brent_kung(int n)
+{
+    DagBuilder b(n);
+    std::vector<int> cur(n);
+    for (int i = 0; i < n; ++i) cur[i] = i;
+    int stride = 1;
+    for (; stride < n; stride *= 2)
+        for (int i = 2 * stride - 1; i < n; i += 2 * stride) cur[i] = b.op(cur[i - stride], cur[i]);
+    int top = 1;
+    while (top * 4 <= n) top *= 2;   // largest stride whose reverse step can apply
+    for (int s = top; s >= 1; s /= 2)
+        for (int i = 3 * s - 1; i < n; i += 2 * s) cur[i] = b.op(cur[i - s], cur[i]);
+    b.d.out = cur;
+    return b.d;
+}
+
+// Dissemination: in round r every element combines with the one 2^r before it (Fig. 2).
+Dag dag_dissemination(int n)
+{
+    DagBuilder b(n);
+    std::vector<int> cur(n), prev;
+    for (int i = 0; i < n; ++i) cur[i] = i;
+    for (int s = 1; s < n; s *= 2) {
+        prev = cur;
+        for (int i = s; i < n; ++i) cur[i] = b.op(prev[i - s], prev[i]);
+    }
+    b.d.out = cur;
+    return b.d;
+}
+
+// Ladner-Fischer P_k recursion (Table 1): P_0 = P_1 on the left half, P_0 on the
+// right half, then the left total applied to every right prefix; P_k (k >= 1)
+// pairs neighbours, recurses with P_{k-1} on the pairs and fills even positions.
+std::vector<int> lf_rec(DagBuilder &b, const std::vector<int> &xs, int k)
+{
+    const int m = (int)xs.size();
+    if (m == 1) return xs;
+    if (m == 2) return {xs[0], b.op(xs[0], xs[1])};
+    std::vector<int> res;
+    if (k == 0) {
+        int h = (m + 1) / 2;
+        std::vector<int> L = lf_rec(b, std::vector<int>(xs.begin(), xs.begin() + h), 1);
+        std::vector<int> R = lf_rec(b, std::vector<int>(xs.begin() + h, xs.end()), 0);
+        res = L;
+        for (int r : R) res.push_back(b.op(L.back(), r));
+        return res;
+    }
+    std::vector<int> pairs;
+    for (int i = 0; i + 1 < m; i += 2) pairs.push_back(b.op(xs[i], xs[i + 1]));
+    std::vector<int> sub = lf_rec(b, pairs, k - 1);
+    res.push_back(xs[0]);
+    for (int i = 1; i < m; ++i) res.push_back(i % 2 ? sub[i / 2] : b.op(sub[i / 2 - 1], xs[i]));
+    return res;
+}
+
+Dag dag_ladner_fischer(int n)
+{
+    DagBuilder b(n);
+    std::vector<int> xs(n);
+    for (int i = 0; i < n; ++i) xs[i] = i;
+    b.d.out = n > 0 ? lf_rec(b, xs, 0) : std::vector<int>();
+    return b.d;
+}
+
+bool make_dag(int schedule, int n, Dag &d)
+{
+    switch (schedule) {
+    case REG_SCHED_SEQ: d = dag_seq(n); return true;
+    case REG_SCHED_BRENT_KUNG: d = dag_brent_kung(n); return true;
+    case REG_SCHED_DISSEMINATION: d = dag_dissemination(n); return true;
+    case REG_SCHED_LADNER_FISCHER: d = dag_ladner_fischer(n); return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" int reg_scan_work(int schedule, int n)
+{
+    if (n < 0) return -1;
+    Dag d;
+    if (!make_dag(schedule, n, d)) return -1;
+    return (int)d.left.size();
+}
+
+extern "C" int reg_scan_dag(int schedule, int n, int32_t *left, int32_t *right, int32_t *out_node)
+{
+    if (n < 0) return -1;
+    Dag d;
+    if (!make_dag(schedule, n, d)) return -1;
+    for (size_t j = 0; j < d.left.size(); ++j) {
+        if (left) left[j] = d.left[j];
+        if (right) right[j] = d.right[j];
+    }
+    if (out_node)
+        for (int i = 0; i < n; ++i) out_node[i] = d.out[i];
+    return (int)d.left.size();
+}
+
+// ------------------------------------------------------------------ context
+struct reg_ctx {
+    reg_config_t cfg;
+    int device = 0;
+    int num_sms = 0;
+    std::mutex mu;
+    // workspaces
+    DevBuf frames_dev;      // host-supplied frames staged on the device
+    DevBuf pyr[kMaxLevels]; // pyramid levels of all frames
+    DevBuf means, level_tab, ops, stats, node_theta, node_field, scratch, status;
+    DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr;
+    DevBuf tmp;
+    cudaStream_t pool[16] = {};
+    cudaEvent_t ev_pool_done[16] = {};
+    std::vector<cudaEvent_t> op_events;
+    bool pool_ready = false;
+};
+
+extern "C" void reg_config_default(reg_config_t *c)
+{
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->mode = REG_RIGID;
+    c->levels = 2;
+    c->max_iter = 500;
+    c->max_rejects = 30;
+    c->tol_grad = 1e-4;
+    c->tol_rel_e = 1e-10;
+    c->armijo_c = 1e-4;
+    c->tau0 = 1.0;
+    c->step_cap = 0.5;
+    c->lambda = 4.0;
+    c->storage = REG_F32;
+    c->cluster = 0;
+    c->workers = 0;
+    c->mem_budget = 0;
+}
+
+static int validate_cfg(const reg_config_t &c)
+{
+    if (c.mode != REG_RIGID && c.mode != REG_NONRIGID) return fail(REG_EINVAL, "mode %d", c.mode);
+    if (c.levels < 1 || c.levels > kMaxLevels) return fail(REG_EINVAL, "levels %d not in 1..%d", c.levels, kMaxLevels);
+    if (c.max_iter < 0 || c.max_rejects < 0) return fail(REG_EINVAL, "negative iteration limits");
+    if (!(c.tau0 > 0) || !(c.step_cap > 0) || !(c.armijo_c > 0 && c.armijo_c < 1))
+        return fail(REG_EINVAL, "tau0/step_cap/armijo_c out of range");
+    if (c.storage != REG_F32 && c.storage != REG_BF16 && c.storage != REG_F16)
+        return fail(REG_EINVAL, "storage %d", c.storage);
+    if (c.cluster != 0 && c.cluster != 1 && c.cluster != 2 && c.cluster != 4 && c.cluster != 8 && c.cluster != 16)
+        return fail(REG_EINVAL, "cluster %d not in {0,1,2,4,8,16}", c.cluster);
+    if (c.lambda < 0) return fail(REG_EINVAL, "lambda < 0");
+    return REG_OK;
+}
+
+extern "C" int reg_ctx_create(const reg_config_t *cfg, int device, reg_ctx_t **out)
+{
+    if (!out) return fail(REG_EINVAL, "out is NULL");
+    *out = nullptr;
+    reg_config_t c;
+    if (cfg) c = *cfg;
+    else reg_config_default(&c);
+    CHECK(validate_cfg(c));
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= device || device < 0) {
+        cudaGetLastError();
+        return fail(REG_ECUDA, "no CUDA device %d (count %d)", device, n);
+    }
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(REG_ECUDA, "device %d is sm_%d%d; this build targets sm_103a (GB300)", device, prop.major,
+                    prop.minor);
+    CU(cudaSetDevice(device));
+    reg_ctx *ctx = new reg_ctx();
+    ctx->cfg = c;
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    *out = ctx;
+    return REG_OK;
+}
+
+extern "C" void reg_ctx_destroy(reg_ctx_t *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->pool_ready) {
+        for (int i = 0; i < 16; ++i) {
+            cudaStreamDestroy(ctx->pool[i]);
+            cudaEventDestroy(ctx->ev_pool_done[i]);
+        }
+    }
+    for (cudaEvent_t e : ctx->op_events) cudaEventDestroy(e);
+    delete ctx;
+}
+
+// ------------------------------------------------------------------ shared pieces
+namespace {
+
+struct Geometry {
+    int W[kMaxLevels], H[kMaxLevels], levels;
+};
+
+int geometry(int W, int H, int levels, Geometry &g)
+{
+    g.levels = levels;
+    int w = W, h = H;
+    for (int l = 0; l < levels; ++l) {
+        if (w < 2 || h < 2)
+            return fail(REG_EINVAL, "level %d of a %dx%d frame is %dx%d; every level needs >= 2x2", l, W, H, w, h);
+        g.W[l] = w;
+        g.H[l] = h;
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    return REG_OK;
+}
+
+Config dev_config(const reg_config_t &c)
+{
+    Config d;
+    d.mode = c.mode;
+    d.levels = c.levels;
+    d.max_iter = c.max_iter;
+    d.max_rejects = c.max_rejects;
+    d.tol_grad = c.tol_grad;
+    d.tol_rel_e = c.tol_rel_e;
+    d.armijo_c = c.armijo_c;
+    d.tau0 = c.tau0;
+    d.step_cap = c.step_cap;
+    d.lambda = c.lambda;
+    return d;
+}
+
+// Build the pyramids of `nf` frames (device fp32, frame f at frames + f*fstride,
+// rows of `pitch`) into ctx->pyr starting at frame slot `first`, and fill the
+// level table rows of those frames.  `total` frames are reserved.
+int build_pyramids(reg_ctx *ctx, const Geometry &g, const float *frames, int nf, size_t fstride, int pitch,
+                   int first, int total, cudaStream_t s)
+{
+    const int L = g.levels;
+    const size_t sb = storage_bytes(ctx->cfg.storage);
+    void *base[kMaxLevels];
+    size_t stride[kMaxLevels];
+    for (int l = 0; l < L; ++l) {
+        stride[l] = (size_t)g.W[l] * g.H[l];
+        CHECK(ctx->pyr[l].reserve(stride[l] * sb * total));
+        base[l] = (char *)ctx->pyr[l].ptr + stride[l] * sb * first;
+    }
+    CHECK(ctx->means.reserve(sizeof(float) * (size_t)total * L));
+    CU(launch_pyramid(frames, nf, fstride, g.W[0], g.H[0], pitch, L, ctx->cfg.storage, base, stride,
+                      ctx->means.as<float>() + (size_t)first * L, s));
+    return REG_OK;
+}
+
+// Level table for `total` frames (means are read on the device side via a copy).
+int build_level_table(reg_ctx *ctx, const Geometry &g, int total, cudaStream_t s)
+{
+    const int L = g.levels;
+    const size_t sb = storage_bytes(ctx->cfg.storage);
+    std::vector<float> means((size_t)total * L);
+    CU(cudaMemcpyAsync(means.data(), ctx->means.ptr, sizeof(float) * means.size(), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    std::vector<LevelDesc> tab((size_t)total * L);
+    for (int f = 0; f < total; ++f)
+        for (int l = 0; l < L; ++l) {
+            LevelDesc &d = tab[(size_t)f * L + l];
+            d.ptr = (const char *)ctx->pyr[l].ptr + (size_t)g.W[l] * g.H[l] * sb * f;
+            d.W = g.W[l];
+            d.H = g.H[l];
+            d.pitch = g.W[l];
+            d.mean = means[(size_t)f * L + l];
+        }
+    CHECK(ctx->level_tab.reserve(sizeof(LevelDesc) * tab.size()));
+    CU(cudaMemcpyAsync(ctx->level_tab.ptr, tab.data(), sizeof(LevelDesc) * tab.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    return REG_OK;
+}
+
+int pow2_floor(int v)
+{
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// CTAs per operator for a launch of `n_ops` concurrent operators: enough to fill
+// the GPU twice over (two CTAs per SM), at most 8, unless fixed by the config.
+int auto_cluster(const reg_ctx *ctx, int n_ops)
+{
+    if (ctx->cfg.cluster > 0) return ctx->cfg.cluster;
+    int slots = 2 * ctx->num_sms;
+    int c = pow2_floor(std::max(1, slots / std::max(1, n_ops)));
+    return std::min(8, c);
+}
+
+struct ScanPlan {
+    std::vector<OpDesc> ops;       // execution order (grouped by depth)
+    std::vector<int> user_index;   // execution index -> index in the user's stats order
+    std::vector<int> depth_start;  // ops[depth_start[d] .. depth_start[d+1]) have depth d
+    std::vector<int> node_i, node_k;
+    std::vector<int> out_nodes;
+    int n_nodes = 0;
+};
+
+int plan_scan(int N, const Dag &d, ScanPlan &p)
+{
+    const int n = N - 1, m = (int)d.left.size();
+    p.n_nodes = n + m;
+    p.node_i.assign(p.n_nodes, 0);
+    p.node_k.assign(p.n_nodes, 0);
+    std::vector<OpDesc> user(n + m);
+    std::vector<int> depth(p.n_nodes, 0), op_depth(n + m, 0);
+    for (int i = 0; i < n; ++i) {
+        p.node_i[i] = i;
+        p.node_k[i] = i + 1;
+        user[i] = OpDesc{i, i + 1, -1, -1, i, -1};
+    }
+    for (int j = 0; j < m; ++j) {
+        int l = d.left[j], r = d.right[j], o = n + j;
+        if (l < 0 || r < 0 || l >= o || r >= o) return fail(REG_EINVAL, "malformed DAG");
+        if (p.node_k[l] != p.node_i[r])
+            return fail(REG_EINVAL, "B needs adjacent elements: (%d,%d) (.) (%d,%d)", p.node_i[l], p.node_k[l],
+                        p.node_i[r], p.node_k[r]);
+        p.node_i[o] = p.node_i[l];
+        p.node_k[o] = p.node_k[r];
+        depth[o] = 1 + std::max(depth[l], depth[r]);
+        user[n + j] = OpDesc{p.node_i[l], p.node_k[r], l, r, o, -1};
+        op_depth[n + j] = depth[o];
+    }
+    int maxd = 0;
+    for (int v : op_depth) maxd = std::max(maxd, v);
+    p.depth_start.assign(maxd + 2, 0);
+    for (int v : op_depth) p.depth_start[v + 1]++;
+    for (int q = 0; q <= maxd; ++q) p.depth_start[q + 1] += p.depth_start[q];
+    std::vector<int> fill(p.depth_start.begin(), p.depth_start.end() - 1);
+    p.ops.resize(n + m);
+    p.user_index.resize(n + m);
+    for (int u = 0; u < n + m; ++u) {
+        int e = fill[op_depth[u]]++;
+        p.ops[e] = user[u];
+        p.user_index[e] = u;
+    }
+    p.out_nodes = d.out;
+    return REG_OK;
+}
+
+int ensure_pool(reg_ctx *ctx)
+{
+    if (ctx->pool_ready) return REG_OK;
+    for (int i = 0; i < 16; ++i) {
+        CU(cudaStreamCreateWithFlags(&ctx->pool[i], cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ctx->ev_pool_done[i], cudaEventDisableTiming));
+    }
+    ctx->pool_ready = true;
+    return REG_OK;
+}
+
+int ensure_op_events(reg_ctx *ctx, size_t n)
+{
+    while (ctx->op_events.size() < n) {
+        cudaEvent_t e;
+        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->op_events.push_back(e);
+    }
+    return REG_OK;
+}
+
+// Allocate node storage, stats and nonrigid scratch; fill Params.
+int prepare_params(reg_ctx *ctx, const Geometry &g, int n_frames, int n_nodes, int n_ops, int slots, Params &p,
+                   cudaStream_t s)
+{
+    memset(&p, 0, sizeof(p));
+    p.cfg = dev_config(ctx->cfg);
+    p.levels = ctx->level_tab.as<LevelDesc>();
+    p.n_frames = n_frames;
+    p.n_ops = n_ops;
+    p.n_nodes = n_nodes;
+    CHECK(ctx->ops.reserve(sizeof(OpDesc) * std::max(1, n_ops)));
+    p.ops = ctx->ops.as<OpDesc>();
+    CHECK(ctx->stats.reserve(sizeof(OpStats) * std::max(1, n_ops)));
+    p.stats = ctx->stats.as<OpStats>();
+    CHECK(ctx->node_theta.reserve(sizeof(double) * 3 * std::max(1, n_nodes)));
+    p.node_theta = ctx->node_theta.as<double>();
+    CHECK(ctx->status.reserve(sizeof(int) * 4));
+    p.status = ctx->status.as<int>();
+    CU(cudaMemsetAsync(p.status, 0, sizeof(int) * 4, s));
+    CU(cudaMemsetAsync(p.stats, 0, sizeof(OpStats) * std::max(1, n_ops), s));
+    if (ctx->cfg.mode == REG_NONRIGID) {
+        const size_t P0 = (size_t)g.W[0] * g.H[0];
+        CHECK(ctx->node_field.reserve(sizeof(float) * 2 * P0 * std::max(1, n_nodes)));
+        p.node_field = ctx->node_field.as<float>();
+        p.scratch_floats = scratch_floats_per_slot(g.W, g.H, g.levels);
+        CHECK(ctx->scratch.reserve(sizeof(float) * p.scratch_floats * std::max(1, slots)));
+        p.scratch = ctx->scratch.as<float>();
+    }
+    return REG_OK;
+}
+
+int check_device_status(reg_ctx *ctx, cudaStream_t s)
+{
+    int st[4];
+    CU(cudaMemcpyAsync(st, ctx->status.ptr, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (st[0] == kDevQueueTimeout) return fail(REG_ETIMEOUT, "device ready-queue wait timed out");
+    if (st[0] != 0) return fail(REG_EINVAL, "device rejected an operator descriptor (code %d)", st[0]);
+    return REG_OK;
+}
+
+// Execute the planned operators.
+int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_t s)
+{
+    const int n_ops = (int)plan.ops.size();
+    const int storage = ctx->cfg.storage;
+    const bool nonrigid = ctx->cfg.mode == REG_NONRIGID;
+    const int n_depth = (int)plan.depth_start.size() - 1;
+    if (exec == REG_EXEC_LEVEL) {
+        for (int dpt = 0; dpt < n_depth; ++dpt) {
+            int b = plan.depth_start[dpt], e = plan.depth_start[dpt + 1];
+            int C = auto_cluster(ctx, e - b);
+            int chunk = nonrigid ? (int)(ctx->scratch.bytes / (sizeof(float) * p.scratch_floats)) : (e - b);
+            chunk = std::max(1, chunk);
+            for (int q = b; q < e; q += chunk) {
+                p.op_base = q;
+                CU(launch_ops(p, storage, C, std::min(chunk, e - q), s));
+            }
+        }
+        return REG_OK;
+    }
+    if (exec == REG_EXEC_PLAIN) {
+        CHECK(ensure_pool(ctx));
+        CHECK(ensure_op_events(ctx, n_ops));
+        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 8;
+        std::vector<int> node_op(p.n_nodes, -1);
+        for (int e = 0; e < n_ops; ++e) node_op[plan.ops[e].out] = e;
+        CU(cudaEventRecord(ctx->ev_pool_done[0], s));
+        for (int i = 0; i < 16; ++i) CU(cudaStreamWaitEvent(ctx->pool[i], ctx->ev_pool_done[0], 0));
+        for (int e = 0; e < n_ops; ++e) {
+            const int lane = e % 16;
+            cudaStream_t ls = ctx->pool[lane];
+            const OpDesc &op = plan.ops[e];
+            if (op.left >= 0) {
+                CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.left]], 0));
+                CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.right]], 0));
+            }
+            Params q = p;
+            q.op_base = e;
+            // one scratch slot per pool stream: operators on a stream run in order
+            q.scratch = p.scratch ? p.scratch + (size_t)lane * p.scratch_floats : nullptr;
+            CU(launch_ops(q, storage, C, 1, ls));
+            CU(cudaEventRecord(ctx->op_events[e], ls));
+        }
+        for (int i = 0; i < 16; ++i) {
+            CU(cudaEventRecord(ctx->ev_pool_done[i], ctx->pool[i]));
+            CU(cudaStreamWaitEvent(s, ctx->ev_pool_done[i], 0));
+        }
+        return REG_OK;
+    }
+    if (exec == REG_EXEC_PERSISTENT) {
+        // consumers (CSR by node) and pending counts
+        std::vector<int> pending(n_ops, 0), cstart(p.n_nodes + 1, 0), cons;
+        std::vector<int> ready;
+        for (int e = 0; e < n_ops; ++e) {
+            const OpDesc &op = plan.ops[e];
+            if (op.left >= 0) {
+                pending[e] = 2;
+                cstart[op.left + 1]++;
+                cstart[op.right + 1]++;
+            } else {
+                ready.push_back(e);
+            }
+        }
+        for (int v = 0; v < p.n_nodes; ++v) cstart[v + 1] += cstart[v];
+        cons.assign(std::max(1, cstart[p.n_nodes]), 0);
+        std::vector<int> fillp(cstart.begin(), cstart.end() - 1);
+        for (int e = 0; e < n_ops; ++e) {
+            const OpDesc &op = plan.ops[e];
+            if (op.left >= 0) {
+                cons[fillp[op.left]++] = e;
+                cons[fillp[op.right]++] = e;
+            }
+        }
+        std::vector<int> slots(n_ops, -1);
+        for (size_t i = 0; i < ready.size(); ++i) slots[i] = ready[i];
+        CHECK(ctx->q_slots.reserve(sizeof(int) * std::max(1, n_ops)));
+        CHECK(ctx->q_pending.reserve(sizeof(int) * std::max(1, n_ops)));
+        CHECK(ctx->q_cons.reserve(sizeof(int) * cons.size()));
+        CHECK(ctx->q_cons_start.reserve(sizeof(int) * cstart.size()));
+        CHECK(ctx->q_ctr.reserve(sizeof(int) * 4));
+        CU(cudaMemcpyAsync(ctx->q_slots.ptr, slots.data(), sizeof(int) * n_ops, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ctx->q_pending.ptr, pending.data(), sizeof(int) * n_ops, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ctx->q_cons.ptr, cons.data(), sizeof(int) * cons.size(), cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ctx->q_cons_start.ptr, cstart.data(), sizeof(int) * cstart.size(), cudaMemcpyHostToDevice,
+                           s));
+        int ctr[4] = {0, (int)ready.size(), 0, 0};
+        CU(cudaMemcpyAsync(ctx->q_ctr.ptr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s));
+        p.queue.head = ctx->q_ctr.as<int>();
+        p.queue.tail = ctx->q_ctr.as<int>() + 1;
+        p.queue.done = ctx->q_ctr.as<int>() + 2;
+        p.queue.slots = ctx->q_slots.as<int>();
+        p.queue.pending = ctx->q_pending.as<int>();
+        p.queue.consumers = ctx->q_cons.as<int>();
+        p.queue.cons_start = ctx->q_cons_start.as<int>();
+        p.queue.timeout_ns = 20LL * 1000 * 1000 * 1000;
+        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 2;
+        int workers = ctx->cfg.workers > 0 ? ctx->cfg.workers : std::max(1, 2 * ctx->num_sms / C);
+        if (nonrigid) workers = std::min(workers, (int)(ctx->scratch.bytes / (sizeof(float) * p.scratch_floats)));
+        workers = std::max(1, std::min(workers, n_ops));
+        p.op_base = 0;
+        CU(launch_persistent(p, storage, C, workers, s));
+        return REG_OK;
+    }
+    return fail(REG_EINVAL, "exec %d", exec);
+}
+
+int copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (!dst) return REG_OK;
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    return REG_OK;
+}
+
+int scratch_slots_for(reg_ctx *ctx, int exec, int n_ops)
+{
+    if (ctx->cfg.mode != REG_NONRIGID) return 0;
+    if (exec == REG_EXEC_PLAIN) return 16;
+    int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 2;
+    int cap = exec == REG_EXEC_PERSISTENT ? (ctx->cfg.workers > 0 ? ctx->cfg.workers : 2 * ctx->num_sms / C)
+                                          : 4 * ctx->num_sms;
+    return std::max(1, std::min(n_ops, cap));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ reg_scan
+extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch, int schedule, int exec,
+                        reg_elem_t *out, float *fields_out, reg_stats_t *per_op, void *stream)
+{
+    if (!ctx) return fail(REG_EINVAL, "ctx is NULL");
+    if (!frames || !out) return fail(REG_EINVAL, "frames/out is NULL");
+    if (N < 2) return fail(REG_EINVAL, "need N >= 2 frames, got %d", N);
+    if (pitch < W) return fail(REG_EINVAL, "pitch %d < W %d", pitch, W);
+    if (exec != REG_EXEC_PLAIN && exec != REG_EXEC_LEVEL && exec != REG_EXEC_PERSISTENT)
+        return fail(REG_EINVAL, "exec %d", exec);
+    if (ctx->cfg.mode == REG_NONRIGID && !fields_out) return fail(REG_EINVAL, "fields_out is NULL for nonrigid");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry g;
+    CHECK(geometry(W, H, ctx->cfg.levels, g));
+    Dag dag;
+    if (!make_dag(schedule, N - 1, dag)) return fail(REG_EINVAL, "schedule %d", schedule);
+    ScanPlan plan;
+    CHECK(plan_scan(N, dag, plan));
+
+    const float *dframes = frames;
+    if (!is_device_ptr(frames)) {
+        size_t bytes = sizeof(float) * (size_t)N * H * pitch;
+        CHECK(ctx->frames_dev.reserve(bytes));
+        CU(cudaMemcpyAsync(ctx->frames_dev.ptr, frames, bytes, cudaMemcpyHostToDevice, s));
+        dframes = ctx->frames_dev.as<float>();
+    }
+    CHECK(build_pyramids(ctx, g, dframes, N, (size_t)H * pitch, pitch, 0, N, s));
+    CHECK(build_level_table(ctx, g, N, s));
+
+    const int n_ops = (int)plan.ops.size();
+    Params p;
+    CHECK(prepare_params(ctx, g, N, plan.n_nodes, n_ops, scratch_slots_for(ctx, exec, n_ops), p, s));
+    CU(cudaMemcpyAsync(ctx->ops.ptr, plan.ops.data(), sizeof(OpDesc) * n_ops, cudaMemcpyHostToDevice, s));
+    CHECK(execute(ctx, plan, p, exec, s));
+    CU(cudaGetLastError());
+    CHECK(check_device_status(ctx, s));
+
+    // results
+    const int n = N - 1;
+    std::vector<double> th((size_t)3 * plan.n_nodes);
+    CU(cudaMemcpyAsync(th.data(), p.node_theta, sizeof(double) * th.size(), cudaMemcpyDeviceToHost, s));
+    std::vector<OpStats> st(n_ops);
+    CU(cudaMemcpyAsync(st.data(), p.stats, sizeof(OpStats) * n_ops, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    std::vector<reg_elem_t> el(n);
+    for (int i = 0; i < n; ++i) {
+        int node = plan.out_nodes[i];
+        el[i].i = plan.node_i[node];
+        el[i].k = plan.node_k[node];
+        el[i].alpha = (float)th[3 * node];
+        el[i].gx = (float)th[3 * node + 1];
+        el[i].gy = (float)th[3 * node + 2];
+    }
+    CHECK(copy_out(out, el.data(), sizeof(reg_elem_t) * n, s));
+    if (ctx->cfg.mode == REG_NONRIGID) {
+        const size_t fb = sizeof(float) * 2 * (size_t)W * H;
+        for (int i = 0; i < n; ++i)
+            CHECK(copy_out((char *)fields_out + fb * i, (const char *)p.node_field + fb * plan.out_nodes[i], fb, s));
+    }
+    if (per_op) {
+        for (int e = 0; e < n_ops; ++e) memcpy(&per_op[plan.user_index[e]], &st[e], sizeof(reg_stats_t));
+    }
+    CU(cudaStreamSynchronize(s));
+    for (int e = 0; e < n_ops; ++e)
+        if (st[e].status != kDevOk) return fail(REG_EINVAL, "operator %d failed on the device (%d)", e, st[e].status);
+    return REG_OK;
+}
+
+// ------------------------------------------------------------------ reg_pairwise
+extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int W, int H, int pitch,
+                            const reg_elem_t *init, const float *field_in, reg_elem_t *out, float *field_out,
+                            reg_stats_t *stats, void *stream)
+{
+    if (!ctx) return fail(REG_EINVAL, "ctx is NULL");
+    if (!R || !T || !out) return fail(REG_EINVAL, "R/T/out is NULL");
+    if (pitch < W) return fail(REG_EINVAL, "pitch %d < W %d", pitch, W);
+    const bool nonrigid = ctx->cfg.mode == REG_NONRIGID;
+    if (nonrigid && !field_out) return fail(REG_EINVAL, "field_out is NULL for nonrigid");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry g;
+    CHECK(geometry(W, H, ctx->cfg.levels, g));
+    const size_t fbytes = sizeof(float) * (size_t)H * pitch;
+    CHECK(ctx->frames_dev.reserve(2 * fbytes));
+    float *stage = ctx->frames_dev.as<float>();
+    const float *src[2] = {R, T};
+    for (int f = 0; f < 2; ++f) {
+        CU(cudaMemcpyAsync((char *)stage + f * fbytes, src[f], fbytes, cudaMemcpyDefault, s));
+    }
+    CHECK(build_pyramids(ctx, g, stage, 2, (size_t)H * pitch, pitch, 0, 2, s));
+    CHECK(build_level_table(ctx, g, 2, s));
+    Params p;
+    CHECK(prepare_params(ctx, g, 2, 2, 1, 1, p, s));
+    const bool has_init = nonrigid ? field_in != nullptr : init != nullptr;
+    OpDesc op{0, 1, -1, -1, 0, has_init ? 1 : -1};
+    CU(cudaMemcpyAsync(ctx->ops.ptr, &op, sizeof(op), cudaMemcpyHostToDevice, s));
+    if (has_init) {
+        if (nonrigid) {
+            const size_t fb = sizeof(float) * 2 * (size_t)W * H;
+            CU(cudaMemcpyAsync((char *)p.node_field + fb, field_in, fb, cudaMemcpyDefault, s));
+        } else {
+            double th[3] = {init->alpha, init->gx, init->gy};
+            CU(cudaMemcpyAsync(p.node_theta + 3, th, sizeof(th), cudaMemcpyHostToDevice, s));
+            CU(cudaStreamSynchronize(s));
+        }
+    }
+    int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 8;
+    p.op_base = 0;
+    CU(launch_ops(p, ctx->cfg.storage, C, 1, s));
+    CU(cudaGetLastError());
+    CHECK(check_device_status(ctx, s));
+    double th[3];
+    OpStats st;
+    CU(cudaMemcpyAsync(th, p.node_theta, sizeof(th), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&st, p.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+    if (nonrigid) CHECK(copy_out(field_out, p.node_field, sizeof(float) * 2 * (size_t)W * H, s));
+    CU(cudaStreamSynchronize(s));
+    out->i = 0;
+    out->k = 1;
+    out->alpha = (float)th[0];
+    out->gx = (float)th[1];
+    out->gy = (float)th[2];
+    if (stats) memcpy(stats, &st, sizeof(st));
+    if (st.status != kDevOk) return fail(REG_EINVAL, "operator failed on the device (%d)", st.status);
+    return REG_OK;
+}
+
+// ------------------------------------------------------------------ kernel-level entry points
+extern "C" int reg_pyramid(reg_ctx_t *ctx, const float *frame, int W, int H, int pitch, int levels, int storage,
+                           void *out, void *stream)
+{
+    if (!ctx || !frame || !out) return fail(REG_EINVAL, "NULL argument");
+    if (levels < 1 || levels > kMaxLevels) return fail(REG_EINVAL, "levels %d", levels);
+    if (storage != REG_F32 && storage != REG_BF16 && storage != REG_F16) return fail(REG_EINVAL, "storage");
+    if (pitch < W) return fail(REG_EINVAL, "pitch < W");
+    if (!is_device_ptr(frame) || !is_device_ptr(out)) return fail(REG_EINVAL, "frame and out must be device memory");
+    Geometry g;
+    CHECK(geometry(W, H, levels, g));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    void *base[kMaxLevels];
+    size_t stride[kMaxLevels];
+    size_t off = 0;
+    for (int l = 0; l < levels; ++l) {
+        stride[l] = (size_t)g.W[l] * g.H[l];
+        base[l] = (char *)out + off;
+        off += stride[l] * storage_bytes(storage);
+    }
+    CU(launch_pyramid(frame, 1, (size_t)H * pitch, W, H, pitch, levels, storage, base, stride, nullptr, s));
+    CU(cudaStreamSynchronize(s));
+    return REG_OK;
+}
+
+extern "C" int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W, int H, const double *theta,
+                          const float *field, double *energy, double *grad, float *grad_field, void *stream)
+{
+    if (!ctx || !R || !T || !energy) return fail(REG_EINVAL, "NULL argument");
+    const bool nonrigid = ctx->cfg.mode == REG_NONRIGID;
+    if (nonrigid ? !field : !theta) return fail(REG_EINVAL, "deformation is NULL");
+    if (W < 2 || H < 2) return fail(REG_EINVAL, "W, H >= 2");
+    if (grad_field && !is_device_ptr(grad_field)) return fail(REG_EINVAL, "grad_field must be device memory");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CU(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    reg_config_t saved = ctx->cfg;
+    ctx->cfg.levels = 1;
+    ctx->cfg.storage = REG_F32;
+    Geometry g;
+    int rc = geometry(W, H, 1, g);
+    const size_t fbytes = sizeof(float) * (size_t)W * H;
+    Params p;
+    if (rc == REG_OK) rc = ctx->frames_dev.reserve(2 * fbytes);
+    if (rc == REG_OK) {
+        float *stage = ctx->frames_dev.as<float>();
+        cudaMemcpyAsync(stage, R, fbytes, cudaMemcpyDefault, s);
+        cudaMemcpyAsync((char *)stage + fbytes, T, fbytes, cudaMemcpyDefault, s);
+        rc = build_pyramids(ctx, g, stage, 2, (size_t)W * H, W, 0, 2, s);
+    }
+    if (rc == REG_OK) rc = build_level_table(ctx, g, 2, s);
+    if (rc == REG_OK) rc = prepare_params(ctx, g, 2, 1, 1, 1, p, s);
+    if (rc == REG_OK) rc = ctx->tmp.reserve(sizeof(double) * 8);
+    if (rc == REG_OK) {
+        double *dv = ctx->tmp.as<double>();
+        if (!nonrigid) cudaMemcpyAsync(dv + 4, theta, sizeof(double) * 3, cudaMemcpyHostToDevice, s);
+        else cudaMemcpyAsync(p.scratch, field, 2 * fbytes, cudaMemcpyDefault, s);   // U_0 of slot 0, level 0
+        cudaError_t e = launch_energy(p, REG_F32, dv + 4, field, dv, grad_field, s);
+        double res[4] = {0, 0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(res, dv, sizeof(res), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(REG_ECUDA, "energy kernel: %s", cudaGetErrorString(e));
+        else {
+            *energy = res[0];
+            if (grad && !nonrigid) { grad[0] = res[1]; grad[1] = res[2]; grad[2] = res[3]; }
+        }
+    }
+    ctx->cfg = saved;
+    return rc;
+}
+
+extern "C" int reg_compose_field(reg_ctx_t *ctx, const float *u1, const float *u2, int W, int H, float *out,
+                                 void *stream)
+{
+    if (!ctx || !u1 || !u2 || !out) return fail(REG_EINVAL, "NULL argument");
+    if (W < 2 || H < 2) return fail(REG_EINVAL, "W, H >= 2");
+    if (!is_device_ptr(u1) || !is_device_ptr(u2) || !is_device_ptr(out))
+        return fail(REG_EINVAL, "u1, u2 and out must be device memory");
+    CU(cudaSetDevice(ctx->device));
+    CU(launch_compose(u1, u2, W, H, out, (cudaStream_t)stream));
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    return REG_OK;
+}

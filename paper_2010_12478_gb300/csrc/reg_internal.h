@@ -1,0 +1,101 @@
+// Internal declarations shared by the kernel and host translation units of libreg.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/reg.h"
+
+namespace reg {
+
+constexpr int kMaxLevels = REG_MAX_LEVELS;
+constexpr int kThreads = 256;          // threads per CTA of the operator kernels
+
+// One pyramid level of one frame, as the operator kernels read it.
+struct LevelDesc {
+    const void *ptr;   // storage-typed pixels, row-major
+    int W, H, pitch;   // pitch in elements
+    float mean;        // level mean (FP32 shift constant of the moment sums)
+};
+
+// One operator application.  left < 0: A(f_ref, f_tmpl) from the identity (or
+// from `init_node` when >= 0); otherwise B(node[left], node[right]).
+struct OpDesc {
+    int ref, tmpl;     // frame indices
+    int left, right;   // input nodes of B, -1 for A
+    int out;           // node written
+    int init_node;     // A only: node holding the initial deformation, -1 = identity
+};
+
+// Per-operator record written by the device (mirrors reg_stats_t).
+struct OpStats {
+    int32_t i, k;
+    int32_t iters[kMaxLevels], evals[kMaxLevels], stop[kMaxLevels];
+    int32_t rejects, status;
+    double energy;
+    double theta[3];
+};
+static_assert(sizeof(OpStats) == sizeof(reg_stats_t), "stats layout");
+
+// Device-side error codes in OpStats::status and the kernel status word.
+enum DevStatus : int32_t {
+    kDevOk = 0,
+    kDevBadOp = 1,       // operator descriptor out of range / non-adjacent
+    kDevQueueTimeout = 2 // bounded wait on the ready queue gave up
+};
+
+struct Config {
+    int mode, levels, max_iter, max_rejects;
+    double tol_grad, tol_rel_e, armijo_c, tau0, step_cap, lambda;
+};
+
+// Ready-queue state of the persistent executor (device memory).
+struct Queue {
+    int *head;         // next slot to claim
+    int *tail;         // next slot to fill
+    int *slots;        // op indices in ready order, -1 = not yet filled
+    int *pending;      // per op: inputs not yet produced
+    int *consumers;    // CSR list of ops consuming each node
+    int *cons_start;   // [n_nodes + 1]
+    int *done;         // number of finished ops
+    long long timeout_ns;
+};
+
+struct Params {
+    Config cfg;
+    const LevelDesc *levels;   // [n_frames][cfg.levels]
+    int n_frames;
+    const OpDesc *ops;
+    int n_ops;
+    int op_base;               // first op of this launch (batched launches)
+    double *node_theta;        // rigid: [n_nodes][3] (alpha, Gx, Gy)
+    float *node_field;         // nonrigid: [n_nodes][2][H0][W0]
+    int n_nodes;
+    float *scratch;            // nonrigid per-slot work buffers
+    size_t scratch_floats;     // floats per slot
+    OpStats *stats;            // [n_ops]
+    int *status;               // kernel status word (first device error)
+    Queue queue;               // persistent executor only
+};
+
+// Host launchers (reg_kernels.cu).
+// Pyramids of N frames: level l of frame f at level_base[l] + f * level_stride[l] (elements,
+// storage-typed); means[f * levels + l] = mean of that level.
+cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, int H, int pitch, int levels,
+                           int storage, void *const *level_base, const size_t *level_stride, float *means,
+                           cudaStream_t s);
+cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_ops,
+                       cudaStream_t s);
+cudaError_t launch_persistent(const Params &p, int storage, int cluster, int workers,
+                              cudaStream_t s);
+cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
+                          const float *field, double *out_dev, float *grad_field,
+                          cudaStream_t s);
+cudaError_t launch_compose(const float *u1, const float *u2, int W, int H, float *out,
+                           cudaStream_t s);
+size_t scratch_floats_per_slot(const int *W, const int *H, int levels);
+int max_cluster_size();
+
+}  // namespace reg

@@ -1,0 +1,296 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: |phi_gpu(x) - phi_oracle(x)| <= 0.02 px at every finest-level pixel and
+relative energy error <= 1e-5 for FP32 storage; <= 0.1 px for BF16/FP16
+storage.  Kernel-level steps (pyramid, energy/gradient, composition) are
+compared element by element with tolerances derived from FP32 arithmetic.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2010_12478_gb300 import binding as B
+from paper_2010_12478_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PX_TOL = 0.02
+E_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2010_12478_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def ctx_of(**kw):
+    return B.Context(B.Config(**kw))
+
+
+def ocfg(cfg: B.Config) -> O.Config:
+    return O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
+                    tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
+                    lam=cfg.lam, mode=cfg.mode)
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-12)
+
+
+# ------------------------------------------------------------------ kernel-level steps
+@pytest.mark.parametrize("shape", [(64, 64), (45, 67), (3, 5)])
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_pyramid_matches_oracle(shape, storage):
+    H, W = shape
+    levels = 2 if min(H, W) < 8 else 3
+    img = np.random.default_rng(1).uniform(0, 1, size=(H, W)).astype(np.float32)
+    ctx = ctx_of()
+    sizes = []
+    h, w = H, W
+    for _ in range(levels):
+        sizes.append((h, w))
+        h, w = (h + 1) // 2, (w + 1) // 2
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[storage]
+    out = torch.zeros(sum(a * b for a, b in sizes), dtype=dt, device="cuda")
+    ctx.pyramid(torch.from_numpy(img).cuda(), levels, storage, out)
+    got = out.float().cpu().numpy()
+    levels_got, off = [], 0
+    for (h, w) in sizes:
+        levels_got.append(got[off:off + h * w].reshape(h, w).astype(np.float64))
+        off += h * w
+    tol = {"f32": 3e-7, "bf16": 8e-3, "f16": 1e-3}[storage]
+    np.testing.assert_allclose(levels_got[0], img.astype(np.float64), rtol=tol, atol=tol)
+    for l in range(1, levels):
+        # the oracle's box average of the GPU's previous level as stored (storage rounding is part of the path)
+        np.testing.assert_allclose(levels_got[l], O.downsample(levels_got[l - 1]), rtol=tol, atol=tol)
+
+
+def test_rigid_energy_and_gradient_match_oracle():
+    R, T = synth.rigid_pair(97, 131, 0.01, (1.3, -0.8), noise_snr=8.0, seed=3)
+    ctx = ctx_of()
+    for th in ([0.0, 0.0, 0.0], [0.012, 1.1, -0.7], [-0.02, 2.5, 3.1], [0.0, 0.25, 0.5]):
+        Eg, gg = ctx.energy_rigid(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda(), th)
+        Eo, go = O.rigid_energy(R, T, th)
+        assert rel(Eg, Eo) <= 1e-6
+        assert np.abs(gg - go).max() <= 1e-4 * max(1.0, np.abs(go).max()), (gg, go)
+
+
+def test_field_energy_and_gradient_match_oracle():
+    H, W = 53, 71
+    R, T = synth.translated_pair(H, W, (0.7, -0.4), noise_snr=8.0, seed=4)
+    u = np.random.default_rng(5).uniform(-0.5, 0.5, size=(2, H, W)).astype(np.float32) + 0.3
+    ctx = ctx_of(mode="nonrigid", lam=3.0)
+    gf = torch.zeros((2, H, W), device="cuda")
+    Eg = ctx.energy_field(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(u).cuda(), gf)
+    Eo, go = O.nonrigid_energy(R, T, u.astype(np.float64), 3.0)
+    assert rel(Eg, Eo) <= 1e-6
+    scale = np.abs(go).max()
+    np.testing.assert_allclose(gf.cpu().numpy(), go, atol=2e-4 * scale)
+
+
+def test_compose_field_matches_oracle():
+    H, W = 40, 33
+    rng = np.random.default_rng(6)
+    u1 = rng.uniform(-2, 2, size=(2, H, W)).astype(np.float32)
+    u2 = rng.uniform(-2, 2, size=(2, H, W)).astype(np.float32)
+    ctx = ctx_of(mode="nonrigid")
+    out = torch.zeros((2, H, W), device="cuda")
+    ctx.compose_field(torch.from_numpy(u1).cuda(), torch.from_numpy(u2).cuda(), out)
+    ref = O.compose_nonrigid(u1.astype(np.float64), u2.astype(np.float64))
+    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=2e-5)
+
+
+# ------------------------------------------------------------------ operators
+@pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
+def test_identical_frames_give_exact_identity(mode):
+    R, _ = synth.translated_pair(96, 80, (0, 0), noise_snr=10.0, seed=7)
+    cfg = B.Config(mode=mode)
+    ctx = B.Context(cfg)
+    Rt = torch.from_numpy(R).cuda()
+    fo = torch.full((2, 96, 80), 7.0, device="cuda")
+    (i, k, a, gx, gy), st = ctx.pairwise(Rt, Rt.clone(), field_out=fo)
+    assert (a, gx, gy) == (0.0, 0.0, 0.0)
+    assert st["iters"] == [0, 0] and st["energy"] == 0.0
+    if mode == "nonrigid":
+        assert not fo.any()
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+@pytest.mark.parametrize("case", range(4))
+def test_pairwise_rigid_matches_oracle(cluster, case):
+    rng = np.random.default_rng(20 + case)
+    H, W = [(128, 128), (97, 131), (64, 200), (33, 47)][case]
+    s = rng.uniform(-3, 3, 2)
+    R, T = synth.rigid_pair(H, W, rng.uniform(-0.01, 0.01), s, noise_snr=[None, 10.0, 5.0, 10.0][case], seed=case)
+    cfg = B.Config(cluster=cluster)
+    ctx = B.Context(cfg)
+    (i, k, a, gx, gy), st = ctx.pairwise(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda())
+    th_o, st_o = O.register_rigid(O.pyramid(R, 2), O.pyramid(T, 2), np.zeros(3), ocfg(cfg))
+    err = O.max_px_error(np.array(st["theta"]), th_o, H, W, "rigid")
+    assert err <= PX_TOL, (st, st_o, th_o)
+    assert rel(st["energy"], st_o.energy) <= E_TOL
+
+
+def test_pairwise_rigid_with_initial_guess_matches_oracle():
+    R, T = synth.rigid_pair(128, 96, 0.004, (9.7, -6.2), noise_snr=10.0, seed=9)
+    cfg = B.Config()
+    ctx = B.Context(cfg)
+    init = [0.002, 8.9, -5.5]
+    _, st = ctx.pairwise(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda(), init=init)
+    th_o, st_o = O.register_rigid(O.pyramid(R, 2), O.pyramid(T, 2), np.array(init, np.float32).astype(np.float64),
+                                  ocfg(cfg))
+    assert O.max_px_error(np.array(st["theta"]), th_o, 128, 96, "rigid") <= PX_TOL
+
+
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_pairwise_nonrigid_matches_oracle(cluster):
+    ser = synth.make_series(synth.SeriesSpec(2, 96, 112, step=2.0, field_amp=1.0, snr=(10, 10),
+                                             field_rate=(0.8, 1.2), seed=11))
+    F = ser.frames.numpy()
+    cfg = B.Config(mode="nonrigid", cluster=cluster)
+    ctx = B.Context(cfg)
+    fo = torch.zeros((2, 96, 112), device="cuda")
+    _, st = ctx.pairwise(torch.from_numpy(F[0]).cuda(), torch.from_numpy(F[1]).cuda(), field_out=fo)
+    u_o, st_o = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, ocfg(cfg))
+    err = O.max_px_error(fo.cpu().numpy(), u_o, 96, 112, "nonrigid")
+    assert err <= PX_TOL, (err, st, st_o)
+    assert rel(st["energy"], st_o.energy) <= E_TOL
+
+
+# ------------------------------------------------------------------ scans
+def c1_frames(n=16, seed=1410):
+    spec = synth.spec_c1(seed)
+    spec.n_frames = n
+    return synth.make_series(spec).frames.numpy()
+
+
+def oracle_scan(F, cfg, schedule):
+    oc = ocfg(cfg)
+    return O.scan(F, oc, O.DAGS[schedule](len(F) - 1))
+
+
+@pytest.mark.parametrize("schedule", ["sequential", "brent_kung", "dissemination", "ladner_fischer"])
+@pytest.mark.parametrize("exec_", ["plain", "level", "persistent"])
+def test_scan_rigid_c1_matches_oracle(schedule, exec_):
+    F = c1_frames()
+    cfg = B.Config()
+    ctx = B.Context(cfg)
+    els, st = ctx.scan(torch.from_numpy(F).cuda(), schedule=schedule, exec=exec_)
+    ref = oracle_scan(F, cfg, schedule)
+    for i, (e, o) in enumerate(zip(els, ref)):
+        assert (e[0], e[1]) == (o.i, o.k) == (0, i + 1)
+        err = O.max_px_error(np.array(e[2:]), o.phi, 128, 128, "rigid")
+        assert err <= PX_TOL, (i, e, o.phi)
+    # every operator's energy (leaves first, then B in DAG order)
+    n = len(F) - 1
+    leaves = [O.op_A([O.pyramid(f, 2) for f in F], j, j + 1, ocfg(cfg)) for j in range(2)]
+    for j in range(2):
+        assert rel(st[j]["energy"], leaves[j].stats.energy) <= E_TOL
+    assert len(st) == n + B.scan_work(schedule, n)
+
+
+def test_scan_host_frames_equal_device_frames():
+    F = c1_frames(9)
+    ctx = B.Context(B.Config())
+    a, _ = ctx.scan(torch.from_numpy(F).cuda())
+    b, _ = ctx.scan(np.ascontiguousarray(F))
+    assert a == b
+
+
+def test_scan_is_deterministic_and_independent_of_executor():
+    F = c1_frames(12)
+    ctx = B.Context(B.Config(cluster=2))
+    runs = [ctx.scan(torch.from_numpy(F).cuda(), exec=e)[0] for e in ("level", "level", "plain", "persistent")]
+    assert runs[0] == runs[1] == runs[2] == runs[3]
+
+
+@pytest.mark.parametrize("exec_", ["level", "persistent"])
+def test_scan_nonrigid_c1_matches_oracle(exec_):
+    F = c1_frames(6)
+    cfg = B.Config(mode="nonrigid")
+    ctx = B.Context(cfg)
+    n = len(F) - 1
+    fo = torch.zeros((n, 2, 128, 128), device="cuda")
+    els, st = ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung", exec=exec_, fields_out=fo)
+    ref = oracle_scan(F, cfg, "brent_kung")
+    got = fo.cpu().numpy()
+    for i, o in enumerate(ref):
+        err = O.max_px_error(got[i], o.phi, 128, 128, "nonrigid")
+        assert err <= PX_TOL, (i, err)
+
+
+def test_scan_two_frames():
+    F = c1_frames(2)
+    ctx = B.Context(B.Config())
+    els, st = ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung")
+    o = oracle_scan(F, B.Config(), "brent_kung")[0]
+    assert len(els) == 1 and O.max_px_error(np.array(els[0][2:]), o.phi, 128, 128, "rigid") <= PX_TOL
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_reduced_precision_storage_within_tenth_pixel(storage):
+    F = c1_frames(8)
+    cfg = B.Config(storage=storage)
+    ctx = B.Context(cfg)
+    els, _ = ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung")
+    ref = oracle_scan(F, B.Config(), "brent_kung")
+    for e, o in zip(els, ref):
+        assert O.max_px_error(np.array(e[2:]), o.phi, 128, 128, "rigid") <= 0.1
+
+
+def test_invalid_arguments_are_rejected():
+    ctx = B.Context(B.Config(levels=3))
+    F = torch.zeros((3, 6, 6), device="cuda")
+    els, st = ctx.scan(F)   # 6x6 at 3 levels has a 2x2 coarsest level: allowed (constant frames: E = 1)
+    assert all(s["energy"] == 1.0 for s in st)
+    F = torch.zeros((3, 5, 5), device="cuda")   # 5 -> 3 -> 2 is fine, 3 levels of 3x3 are not
+    F = torch.zeros((3, 3, 3), device="cuda")
+    with pytest.raises(B.RegError) as e:
+        ctx.scan(F)
+    assert e.value.code == B.REG_EINVAL
+
+
+# ------------------------------------------------------------------ full size (256 x 512^2), sampled
+def test_c2_full_size_sampled_operators_match_oracle():
+    spec = synth.spec_c2()
+    ser = synth.make_series(spec, device="cuda")
+    frames = ser.frames
+    cfg = B.Config()
+    ctx = B.Context(cfg)
+    n = spec.n_frames - 1
+    els, st = ctx.scan(frames, schedule="brent_kung", exec="level")
+    ops, out = B.scan_dag("brent_kung", n)
+    Fh = frames.cpu().numpy()
+    oc = ocfg(cfg)
+    pyr = {}
+
+    def P(i):
+        if i not in pyr:
+            pyr[i] = O.pyramid(Fh[i], cfg.levels)
+        return pyr[i]
+
+    node = [None] * (n + len(ops))
+    for j in range(n):
+        node[j] = O.Elem(st[j]["i"], st[j]["k"], np.array(st[j]["theta"]))
+    for j, (l, r) in enumerate(ops):
+        node[n + j] = O.Elem(st[n + j]["i"], st[n + j]["k"], np.array(st[n + j]["theta"]))
+    rng = np.random.default_rng(1410)
+    # leaves: A from the frames; B: from the GPU's exact input elements
+    for j in rng.choice(n, 2, replace=False):
+        th, so = O.register_rigid(P(j), P(j + 1), np.zeros(3), oc)
+        assert O.max_px_error(node[j].phi, th, 512, 512, "rigid") <= PX_TOL
+        assert rel(st[j]["energy"], so.energy) <= E_TOL
+    for j in rng.choice(len(ops), 3, replace=False):
+        l, r = ops[j]
+        e = O.op_B(node[l], node[r], {node[l].i: P(node[l].i), node[r].k: P(node[r].k)}, oc)
+        assert O.max_px_error(node[n + j].phi, e.phi, 512, 512, "rigid") <= PX_TOL
+        assert rel(st[n + j]["energy"], e.stats.energy) <= E_TOL
+    # the prefixes are the sequential recursion at sampled points (Sec. 3)
+    for i in rng.choice(n - 1, 2, replace=False):
+        a = O.op_A({i + 1: P(i + 1), i + 2: P(i + 2)}, i + 1, i + 2, oc)
+        prev = O.Elem(0, i + 1, np.array(els[i][2:], dtype=np.float64))
+        e = O.op_B(prev, a, {0: P(0), i + 2: P(i + 2)}, oc)
+        assert O.max_px_error(np.array(els[i + 1][2:], dtype=np.float64), e.phi, 512, 512, "rigid") <= PX_TOL

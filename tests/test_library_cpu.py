@@ -1,0 +1,81 @@
+"""Host-side checks of libreg that need no GPU: the library loads, exports every
+symbol include/reg.h declares, and its scan DAGs (host C++) equal the oracle's
+independently written generators and the paper's work counts."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+import oracle as O
+from paper_2010_12478_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2010_12478_gb300 import build
+    build.build()
+    return B.lib()
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "reg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(reg_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = header_symbols()
+    assert len(syms) >= 16
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(B.EXPORTS) == syms
+
+
+def test_struct_layouts_match_header(lib):
+    assert ctypes.sizeof(B.reg_elem_t) == 20          # 20-byte scan element (Sec. 5)
+    assert ctypes.sizeof(B.reg_stats_t) == 144
+    cfg = B.reg_config_t()
+    lib.reg_config_default(ctypes.byref(cfg))
+    assert cfg.levels == 2 and cfg.mode == B.RIGID and cfg.storage == B.F32
+
+
+def test_errors_without_gpu_are_reported_not_crashing(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    h = ctypes.c_void_p()
+    rc = lib.reg_ctx_create(None, 0, ctypes.byref(h))
+    assert rc == B.REG_ECUDA and not h.value
+    assert lib.reg_strerror(rc) == b"CUDA error"
+    bad = B.reg_config_t()
+    lib.reg_config_default(ctypes.byref(bad))
+    bad.levels = 9
+    assert lib.reg_ctx_create(ctypes.byref(bad), 0, ctypes.byref(h)) == B.REG_EINVAL
+    assert b"levels" in lib.reg_last_error_message()
+
+
+@pytest.mark.parametrize("name", ["sequential", "brent_kung", "dissemination", "ladner_fischer"])
+def test_library_dag_equals_oracle_dag(lib, name):
+    for n in list(range(1, 40)) + [255, 256, 1000, 4095]:
+        ops, out = B.scan_dag(name, n)
+        ref = O.DAGS[name](n)
+        assert ops == [tuple(o) for o in ref.ops], (name, n)
+        assert out == ref.out, (name, n)
+
+
+def test_library_work_counts_match_paper(lib):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "scan_work.json")))
+    assert B.scan_work("dissemination", 8) == g["fig2_dissemination_n8"]["work"]
+    t5 = g["table5_work"]
+    N = t5["N"]
+    for P, wd, wl in zip(t5["P"], t5["dissemination"], t5["ladner_fischer"]):
+        assert N + (N - P) + B.scan_work("dissemination", P) + N == wd
+        assert N + (N - P) + B.scan_work("ladner_fischer", P) + N == wl
+    assert B.scan_work("sequential", N) + N == t5["serial"]
+    for n in (2, 16, 256, 4096):
+        assert B.scan_work("brent_kung", n) == 2 * n - 2 - n.bit_length() + 1
+    assert lib.reg_scan_work(99, 10) == -1
