@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark: registered frames/s of the registration scan on one GB300.
+
+Workload (default ``c2``): a synthetic 256-frame series of 512x512 fp32 lattice
+frames (random-walk drift U(+-1) px/frame per axis, smooth field <= 1.5 px,
+SNR 10, seed 1410), registered to frame 0 by the Brent-Kung scan of the
+operator B, leaves A(f_{i-1}, f_i); 2-level pyramid; FP32 arithmetic with
+float-float/FP64 reductions and FP64 step control.  One step = pyramid build
++ all operators + results back on the host, through reg_scan.
+
+``value``: frames/s with the frames resident in HBM, executor ``plain`` (one
+operator per kernel launch, the workload's stated form).  ``batched`` gives
+the same workload through the persistent device-queue executor.  ``e2e``:
+the same call with pinned HOST frames (host->device copy of the series and
+device->host copy of the results inside the timed region).
+
+Run ``python bench.py --impl reference`` for the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "registered frames/s and operator applications/s at <=0.02 px vs FP64 oracle; stream p50/p99"
+UNIT = "frames/s"
+
+
+def workload_spec(name: str, rank: int):
+    from paper_2010_12478_gb300 import synth
+    if name == "c1":
+        spec = synth.spec_c1(seed=synth.DEFAULT_SEED + rank)
+    elif name == "c2":
+        spec = synth.spec_c2(seed=synth.DEFAULT_SEED + rank)
+    elif name == "c3":
+        spec = synth.spec_c3(seed=synth.DEFAULT_SEED + rank)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return spec
+
+
+WORKLOAD_TEXT = {
+    "c1": "16 frames 128x128 fp32 lattice series, sequential-recursion workload size",
+    "c2": "256 frames 512x512 fp32 lattice series (random-walk drift +-1 px/frame, field <=1.5 px, SNR 10), "
+          "Brent-Kung scan of B over A leaves",
+    "c3": "4096 frames 512x512 fp32 lattice series (SNR 3-20, 5% jumps <=8 px), Brent-Kung scan",
+}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smmax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swpc=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sms = sorted(r["sm"] for r in rows)
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swpc", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": rows[0]["smmax"], "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(stats, H, W, levels, storage_bytes, mode):
+    """Bytes the method must move per step in the operator kernels: every energy
+    evaluation reads the reference and template level once (2 s P_l bytes)."""
+    total = 0.0
+    sizes = []
+    h, w = H, W
+    for _ in range(levels):
+        sizes.append(h * w)
+        h, w = (h + 1) // 2, (w + 1) // 2
+    for s in stats:
+        for l, ev in enumerate(s["evals"]):
+            total += ev * 2 * storage_bytes * sizes[l]
+    return total
+
+
+def profile_traffic(kernel_src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    p = os.path.join(ROOT, "profiles", "op_kernel_c2_rigid.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m = re.search(r"kernel source sha256: ([0-9a-f]{12})", text)
+    t = re.search(r"dram bytes per launch \(scaled\): ([0-9.e+]+)", text)
+    if not m or not t or m.group(1) != kernel_src_hash:
+        return None
+    return float(t.group(1))
+
+
+def kernel_hash():
+    p = os.path.join(ROOT, "paper_2010_12478_gb300", "csrc", "reg_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_sample(frames_np, cfg_bind, budget_s: float):
+    """Time the FP64 oracle on a bounded sample of the workload's operators:
+    leaves A(f_i, f_{i+1}) then B over consecutive pairs of them, until the budget."""
+    import numpy as np
+    import oracle as O
+    oc = O.Config(levels=cfg_bind.levels, max_iter=cfg_bind.max_iter, max_rejects=cfg_bind.max_rejects,
+                  tol_grad=cfg_bind.tol_grad, tol_rel_e=cfg_bind.tol_rel_e, armijo_c=cfg_bind.armijo_c,
+                  tau0=cfg_bind.tau0, step_cap=cfg_bind.step_cap, lam=cfg_bind.lam, mode=cfg_bind.mode)
+    t0 = time.perf_counter()
+    pyr = {}
+    ops = 0
+    leaves = []
+    i = 0
+    N = frames_np.shape[0]
+    while time.perf_counter() - t0 < budget_s and i + 1 < N:
+        for j in (i, i + 1):
+            if j not in pyr:
+                pyr[j] = O.pyramid(frames_np[j], oc.levels)
+        leaves.append(O.op_A(pyr, i, i + 1, oc))
+        ops += 1
+        if len(leaves) % 2 == 0:
+            O.op_B(leaves[-2], leaves[-1], pyr, oc)
+            ops += 1
+        i += 1
+    dt = time.perf_counter() - t0
+    return ops, dt, f"{ops} operators ({len(leaves)} A leaves + {ops - len(leaves)} B) on frames 0..{i}"
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--mode", default="rigid", choices=["rigid", "nonrigid"])
+    ap.add_argument("--exec", dest="exec_", default="plain", choices=["plain", "level", "persistent"])
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--oracle-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="main timed region only (for profiler captures)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import numpy as np
+    import torch
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2010_12478_gb300 import binding as B
+    from paper_2010_12478_gb300 import build, synth
+    build.build()
+
+    spec = workload_spec(args.workload, rank)
+    ser = synth.make_series(spec, device=dev)
+    frames = ser.frames
+    N, H, W = frames.shape
+    cfg = B.Config(mode=args.mode, cluster=args.cluster)
+    ctx = B.Context(cfg, device=local)
+    ctx.set_timing(True)
+    fields = torch.empty((N - 1, 2, H, W), device=dev) if args.mode == "nonrigid" else None
+
+    def step(src, exec_):
+        return ctx.scan(src, schedule="brent_kung", exec=exec_, fields_out=fields)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def timed(src, exec_, steps, warmup):
+        for _ in range(warmup):
+            step(src, exec_)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        st_list, tim = [], []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            _, st = step(src, exec_)
+            st_list.append(st)
+            tim.append(ctx.last_timing())
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, st_list, tim
+
+    # ---- main timed region (device-resident frames, the workload's stated executor)
+    with ClockSampler(local) as clk:
+        ms, st_list, tim = timed(frames, args.exec_, args.steps, args.warmup)
+    clocks = clk.summary()
+    n_ops = len(st_list[0])
+    value = world * (N - 1) / (ms / 1e3)
+    ops_per_s = world * n_ops / (ms / 1e3)
+
+    # roofline of the operator kernel
+    sb = 4 if cfg.storage == "f32" else 2
+    alg = sum(algorithmic_bytes(st, H, W, cfg.levels, sb, cfg.mode) for st in st_list) / len(st_list)
+    kms = sum(t["op_kernel_ms"] for t in tim) / len(tim)
+    launches = sum(t["op_launches"] for t in tim) / len(tim)
+    peak, peak_src = peaks()
+    achieved = alg / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    traffic = profile_traffic(kernel_hash())
+    gpu_launches = int(sum(t["op_launches"] + t["pyramid_launches"] for t in tim))
+
+    levels = cfg.levels
+    batched = e2e = None
+    if not args.quick:
+        # ---- batched executor on the same workload
+        bms, bst, btim = timed(frames, "persistent", max(3, args.steps // 2), 2)
+        batched = {"exec": "persistent", "value": round(world * (N - 1) / (bms / 1e3), 2), "unit": UNIT,
+                   "ms_per_step": round(bms, 3),
+                   "op_kernel_ms": round(sum(t["op_kernel_ms"] for t in btim) / len(btim), 3)}
+        # ---- end to end: pinned host frames through the C ABI, copies inside the timed region
+        host = frames.cpu().pin_memory()
+        ems, _, _ = timed(host, args.exec_, max(3, args.steps // 2), 1)
+        n_nodes = (N - 1) + B.scan_work("brent_kung", N - 1)
+        d2h = 4 * N * levels + 16 + 24 * n_nodes + 144 * n_ops + 20 * (N - 1)
+        e2e = {"value": round(world * (N - 1) / (ems / 1e3), 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(N * H * W * 4), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- accuracy bookkeeping: iterations per operator (uneven counts drive the load balance)
+    ev = np.array([sum(s["evals"]) for s in st_list[0]])
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and not args.quick and world == 1:
+        fr = frames.cpu().numpy()
+        ops, dt, sample = oracle_sample(fr, cfg, args.oracle_budget)
+        ops_s = ops / dt
+        cpu = {"value": round(ops_s * (N - 1) / n_ops, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": sample + f"; {dt:.1f} s single-threaded FP64 C; frames/s = operators/s x "
+                                  f"{N - 1}/{n_ops} (operators per registered frame of this scan)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "frames": N, "H": H,
+                       "W": W, "mode": args.mode, "levels": levels, "schedule": "brent_kung",
+                       "exec": args.exec_, "cluster": args.cluster or "auto",
+                       "l2": "inputs larger than L2 (frames %d MiB > 129 MB L2)" % (N * H * W * 4 >> 20),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "ops_per_s": round(ops_per_s, 2), "operators_per_step": n_ops,
+            "evals_per_operator": {"mean": round(float(ev.mean()), 2), "max": int(ev.max())},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                         else "fallback 6.8 TB/s",
+                         "kernel": "op_kernel (operator kernel)", "algorithmic_bytes_per_step": alg,
+                         "kernel_ms_per_step": round(kms, 3), "launches_per_step": launches},
+            "batched": batched,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": gpu_launches,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    import torch
+    from paper_2010_12478_gb300 import binding as B
+    from paper_2010_12478_gb300 import synth
+    spec = workload_spec(args.workload, 0)
+    ser = synth.make_series(spec, device="cpu")
+    fr = ser.frames.numpy()
+    N = fr.shape[0]
+    n_ops = (N - 1) + len(__import__("oracle").dag_brent_kung(N - 1).ops)
+    cfg = B.Config(mode=args.mode)
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(fr, cfg, budget)
+    tot_ops, tot_dt = 0, 0.0
+    sample = ""
+    for _ in range(args.steps):
+        ops, dt, sample = oracle_sample(fr, cfg, budget)
+        tot_ops += ops
+        tot_dt += dt
+    ops_s = tot_ops / tot_dt
+    value = ops_s * (N - 1) / n_ops
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * tot_dt / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "mode": args.mode,
+                       "levels": cfg.levels, "schedule": "brent_kung"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {sample} (about {budget:.0f} s); frames/s = operators/s x "
+                                       f"{N - 1}/{n_ops}"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -224,6 +224,25 @@ int reg_stream_poll(reg_stream_t *s, reg_result_t *out, int max, int *n_out, int
 /* Finish all submitted frames and release the stream. */
 int reg_stream_close(reg_stream_t *s);
 
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Device-side accounting of the last reg_scan / reg_pairwise call on a context. */
+typedef struct {
+    int32_t op_launches;       /* operator-kernel launches */
+    int32_t pyramid_launches;  /* pyramid-build launches (level copy, box averages, level means) */
+    double  op_kernel_ms;      /* device time of the operator kernels: CUDA events recorded on the
+                                  launching stream around each launch (per-DAG-depth executor) or
+                                  around the whole operator phase (stream-pool and persistent
+                                  executors); 0 unless timing is enabled */
+    double  pyramid_ms;        /* device time of the pyramid build, same method */
+} reg_timing_t;
+
+/* Enable (1) or disable (0) event timing of the kernels launched by later calls. */
+int reg_ctx_set_timing(reg_ctx_t *ctx, int enable);
+
+/* Copy the accounting of the last call into *out (host). */
+int reg_ctx_last_timing(reg_ctx_t *ctx, reg_timing_t *out);
+
 /* ---- diagnostics ----------------------------------------------------------- */
 const char *reg_strerror(int code);
 const char *reg_last_error_message(void);

@@ -103,10 +103,10 @@ def _f64(a) -> np.ndarray:
 # --------------------------------------------------------------------------
 @dataclasses.dataclass
 class Config:
-    levels: int = 3
+    levels: int = 2
     max_iter: int = 500
     max_rejects: int = 30
-    tol_grad: float = 1e-4
+    tol_grad: float = 1e-5
     tol_rel_e: float = 1e-10
     armijo_c: float = 1e-4
     tau0: float = 1.0

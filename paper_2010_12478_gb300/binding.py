@@ -29,7 +29,7 @@ MAX_LEVELS = 8
 EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairwise", "reg_scan",
            "reg_scan_work", "reg_scan_dag", "reg_pyramid", "reg_energy", "reg_compose_field",
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
-           "reg_strerror", "reg_last_error_message"]
+           "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message"]
 
 
 class RegError(RuntimeError):
@@ -56,6 +56,11 @@ class reg_stats_t(ctypes.Structure):
                 ("evals", ctypes.c_int32 * MAX_LEVELS), ("stop", ctypes.c_int32 * MAX_LEVELS),
                 ("rejects", ctypes.c_int32), ("status", ctypes.c_int32), ("energy", ctypes.c_double),
                 ("theta", ctypes.c_double * 3)]
+
+
+class reg_timing_t(ctypes.Structure):
+    _fields_ = [("op_launches", ctypes.c_int32), ("pyramid_launches", ctypes.c_int32),
+                ("op_kernel_ms", ctypes.c_double), ("pyramid_ms", ctypes.c_double)]
 
 
 class reg_result_t(ctypes.Structure):
@@ -89,6 +94,8 @@ def lib() -> ctypes.CDLL:
         L.reg_stream_submit.argtypes = [vp, fp, ctypes.c_uint64]
         L.reg_stream_poll.argtypes = [vp, ctypes.POINTER(reg_result_t), ip, ctypes.POINTER(ctypes.c_int), ip]
         L.reg_stream_close.argtypes = [vp]
+        L.reg_ctx_set_timing.argtypes = [vp, ip]
+        L.reg_ctx_last_timing.argtypes = [vp, ctypes.POINTER(reg_timing_t)]
         L.reg_strerror.argtypes = [ip]
         L.reg_strerror.restype = ctypes.c_char_p
         L.reg_last_error_message.restype = ctypes.c_char_p
@@ -125,7 +132,7 @@ class Config:
     levels: int = 2
     max_iter: int = 500
     max_rejects: int = 30
-    tol_grad: float = 1e-4
+    tol_grad: float = 1e-5
     tol_rel_e: float = 1e-10
     armijo_c: float = 1e-4
     tau0: float = 1.0
@@ -182,6 +189,15 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_timing(self, enable: bool = True):
+        check(lib().reg_ctx_set_timing(self.h, int(enable)), "reg_ctx_set_timing")
+
+    def last_timing(self) -> dict:
+        t = reg_timing_t()
+        check(lib().reg_ctx_last_timing(self.h, ctypes.byref(t)), "reg_ctx_last_timing")
+        return dict(op_launches=t.op_launches, pyramid_launches=t.pyramid_launches,
+                    op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms)
 
     # ---- operators
     def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,

@@ -250,6 +250,12 @@ struct reg_ctx {
     cudaEvent_t ev_pool_done[16] = {};
     std::vector<cudaEvent_t> op_events;
     bool pool_ready = false;
+    // measurement
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;   // timing events, used in pairs
+    size_t tev_used = 0;
+    std::vector<std::pair<int, int>> op_pairs, pyr_pairs;
+    reg_timing_t last = {};
 };
 
 extern "C" void reg_config_default(reg_config_t *c)
@@ -260,7 +266,7 @@ extern "C" void reg_config_default(reg_config_t *c)
     c->levels = 2;
     c->max_iter = 500;
     c->max_rejects = 30;
-    c->tol_grad = 1e-4;
+    c->tol_grad = 1e-5;
     c->tol_rel_e = 1e-10;
     c->armijo_c = 1e-4;
     c->tau0 = 1.0;
@@ -326,11 +332,50 @@ extern "C" void reg_ctx_destroy(reg_ctx_t *ctx)
         }
     }
     for (cudaEvent_t e : ctx->op_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     delete ctx;
 }
 
 // ------------------------------------------------------------------ shared pieces
 namespace {
+
+// Timing: event pairs recorded on the launching stream, resolved after the call.
+void timing_reset(reg_ctx *ctx)
+{
+    ctx->tev_used = 0;
+    ctx->op_pairs.clear();
+    ctx->pyr_pairs.clear();
+    memset(&ctx->last, 0, sizeof(ctx->last));
+}
+
+int timing_mark(reg_ctx *ctx, cudaStream_t s)
+{
+    if (!ctx->timing) return -1;
+    if (ctx->tev_used == ctx->tev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        ctx->tev.push_back(e);
+    }
+    int id = (int)ctx->tev_used++;
+    if (cudaEventRecord(ctx->tev[id], s) != cudaSuccess) return -1;
+    return id;
+}
+
+void timing_resolve(reg_ctx *ctx)
+{
+    if (!ctx->timing) return;
+    auto sum = [&](const std::vector<std::pair<int, int>> &v) {
+        double t = 0.0;
+        for (auto &pr : v) {
+            float ms = 0.f;
+            if (pr.first >= 0 && pr.second >= 0 && cudaEventElapsedTime(&ms, ctx->tev[pr.first], ctx->tev[pr.second]) == cudaSuccess)
+                t += ms;
+        }
+        return t;
+    };
+    ctx->last.op_kernel_ms = sum(ctx->op_pairs);
+    ctx->last.pyramid_ms = sum(ctx->pyr_pairs);
+}
 
 struct Geometry {
     int W[kMaxLevels], H[kMaxLevels], levels;
@@ -383,8 +428,11 @@ int build_pyramids(reg_ctx *ctx, const Geometry &g, const float *frames, int nf,
         base[l] = (char *)ctx->pyr[l].ptr + stride[l] * sb * first;
     }
     CHECK(ctx->means.reserve(sizeof(float) * (size_t)total * L));
+    int e0 = timing_mark(ctx, s);
     CU(launch_pyramid(frames, nf, fstride, g.W[0], g.H[0], pitch, L, ctx->cfg.storage, base, stride,
                       ctx->means.as<float>() + (size_t)first * L, s));
+    ctx->pyr_pairs.push_back({e0, timing_mark(ctx, s)});
+    ctx->last.pyramid_launches += 2 * L;
     return REG_OK;
 }
 
@@ -557,7 +605,10 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
             chunk = std::max(1, chunk);
             for (int q = b; q < e; q += chunk) {
                 p.op_base = q;
+                int e0 = timing_mark(ctx, s);
                 CU(launch_ops(p, storage, C, std::min(chunk, e - q), s));
+                ctx->op_pairs.push_back({e0, timing_mark(ctx, s)});
+                ctx->last.op_launches += 1;
             }
         }
         return REG_OK;
@@ -568,6 +619,7 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
         const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 8;
         std::vector<int> node_op(p.n_nodes, -1);
         for (int e = 0; e < n_ops; ++e) node_op[plan.ops[e].out] = e;
+        const int t0 = timing_mark(ctx, s);
         CU(cudaEventRecord(ctx->ev_pool_done[0], s));
         for (int i = 0; i < 16; ++i) CU(cudaStreamWaitEvent(ctx->pool[i], ctx->ev_pool_done[0], 0));
         for (int e = 0; e < n_ops; ++e) {
@@ -584,11 +636,13 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
             q.scratch = p.scratch ? p.scratch + (size_t)lane * p.scratch_floats : nullptr;
             CU(launch_ops(q, storage, C, 1, ls));
             CU(cudaEventRecord(ctx->op_events[e], ls));
+            ctx->last.op_launches += 1;
         }
         for (int i = 0; i < 16; ++i) {
             CU(cudaEventRecord(ctx->ev_pool_done[i], ctx->pool[i]));
             CU(cudaStreamWaitEvent(s, ctx->ev_pool_done[i], 0));
         }
+        ctx->op_pairs.push_back({t0, timing_mark(ctx, s)});
         return REG_OK;
     }
     if (exec == REG_EXEC_PERSISTENT) {
@@ -642,7 +696,10 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
         if (nonrigid) workers = std::min(workers, (int)(ctx->scratch.bytes / (sizeof(float) * p.scratch_floats)));
         workers = std::max(1, std::min(workers, n_ops));
         p.op_base = 0;
+        int e0 = timing_mark(ctx, s);
         CU(launch_persistent(p, storage, C, workers, s));
+        ctx->op_pairs.push_back({e0, timing_mark(ctx, s)});
+        ctx->last.op_launches += 1;
         return REG_OK;
     }
     return fail(REG_EINVAL, "exec %d", exec);
@@ -687,6 +744,7 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     if (!make_dag(schedule, N - 1, dag)) return fail(REG_EINVAL, "schedule %d", schedule);
     ScanPlan plan;
     CHECK(plan_scan(N, dag, plan));
+    timing_reset(ctx);
 
     const float *dframes = frames;
     if (!is_device_ptr(frames)) {
@@ -732,6 +790,7 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
         for (int e = 0; e < n_ops; ++e) memcpy(&per_op[plan.user_index[e]], &st[e], sizeof(reg_stats_t));
     }
     CU(cudaStreamSynchronize(s));
+    timing_resolve(ctx);
     for (int e = 0; e < n_ops; ++e)
         if (st[e].status != kDevOk) return fail(REG_EINVAL, "operator %d failed on the device (%d)", e, st[e].status);
     return REG_OK;
@@ -752,6 +811,7 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     cudaStream_t s = (cudaStream_t)stream;
     Geometry g;
     CHECK(geometry(W, H, ctx->cfg.levels, g));
+    timing_reset(ctx);
     const size_t fbytes = sizeof(float) * (size_t)H * pitch;
     CHECK(ctx->frames_dev.reserve(2 * fbytes));
     float *stage = ctx->frames_dev.as<float>();
@@ -778,7 +838,10 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     }
     int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 8;
     p.op_base = 0;
+    int e0 = timing_mark(ctx, s);
     CU(launch_ops(p, ctx->cfg.storage, C, 1, s));
+    ctx->op_pairs.push_back({e0, timing_mark(ctx, s)});
+    ctx->last.op_launches += 1;
     CU(cudaGetLastError());
     CHECK(check_device_status(ctx, s));
     double th[3];
@@ -787,6 +850,7 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     CU(cudaMemcpyAsync(&st, p.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
     if (nonrigid) CHECK(copy_out(field_out, p.node_field, sizeof(float) * 2 * (size_t)W * H, s));
     CU(cudaStreamSynchronize(s));
+    timing_resolve(ctx);
     out->i = 0;
     out->k = 1;
     out->alpha = (float)th[0];
@@ -880,5 +944,20 @@ extern "C" int reg_compose_field(reg_ctx_t *ctx, const float *u1, const float *u
     CU(cudaSetDevice(ctx->device));
     CU(launch_compose(u1, u2, W, H, out, (cudaStream_t)stream));
     CU(cudaStreamSynchronize((cudaStream_t)stream));
+    return REG_OK;
+}
+
+// ------------------------------------------------------------------ measurement
+extern "C" int reg_ctx_set_timing(reg_ctx_t *ctx, int enable)
+{
+    if (!ctx) return fail(REG_EINVAL, "ctx is NULL");
+    ctx->timing = enable != 0;
+    return REG_OK;
+}
+
+extern "C" int reg_ctx_last_timing(reg_ctx_t *ctx, reg_timing_t *out)
+{
+    if (!ctx || !out) return fail(REG_EINVAL, "NULL argument");
+    *out = ctx->last;
     return REG_OK;
 }

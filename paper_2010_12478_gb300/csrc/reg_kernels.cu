@@ -199,39 +199,49 @@ __device__ __forceinline__ void for_pixels(int W, int r0, int r1, F &&f, G &&flu
     }
 }
 
-// Bilinear sample of T (storage S, pitch Tp) at (px, py) with clamp-to-edge.
-// Returns the value; derivative along a clamped axis is 0.
+// Bilinear sample of T (storage S, pitch Tp) at p = (xi + vx, yi + vy) with clamp-to-edge,
+// where (xi, yi) is an integer pixel and (vx, vy) a small FP32 offset.  Splitting the
+// position keeps the FP32 fractional part exact to the precision of the offset, not
+// of the absolute coordinate.  Cell choice and clamping follow floor(p) clamped to
+// [0, W-2]; the derivative along a clamped axis (p < 0 or p > W-1) is 0.
 template <typename S, bool DERIV>
-__device__ __forceinline__ float bilinear(const S *T, int W, int H, int Tp, float px, float py,
-                                          float &dtx, float &dty)
+__device__ __forceinline__ float sample_at(const S *T, int W, int H, int Tp, int xi, int yi, float vx, float vy,
+                                           float &dtx, float &dty)
 {
-    float qx = fminf(fmaxf(px, 0.f), (float)(W - 1));
-    float qy = fminf(fmaxf(py, 0.f), (float)(H - 1));
-    int x0 = min((int)qx, W - 2), y0 = min((int)qy, H - 2);
-    float fx = qx - (float)x0, fy = qy - (float)y0;
-    const S *row = T + (size_t)y0 * Tp + x0;
+    vx = fminf(fmaxf(vx, -1.0e6f), 1.0e6f);   // also maps NaN into range: every access stays in bounds
+    vy = fminf(fmaxf(vy, -1.0e6f), 1.0e6f);
+    const float flx = floorf(vx), fly = floorf(vy);
+    int x = xi + (int)flx, y = yi + (int)fly;
+    float fx = vx - flx, fy = vy - fly;
+    bool clx = false, cly = false;
+    if (x < 0) { x = 0; fx = 0.f; clx = true; }
+    else if (x > W - 2) { clx = (x > W - 1) || (fx > 0.f); x = W - 2; fx = 1.f; }
+    if (y < 0) { y = 0; fy = 0.f; cly = true; }
+    else if (y > H - 2) { cly = (y > H - 1) || (fy > 0.f); y = H - 2; fy = 1.f; }
+    const S *row = T + (size_t)y * Tp + x;
     float t00 = ldS<S>(row), t01 = ldS<S>(row + 1);
     float t10 = ldS<S>(row + Tp), t11 = ldS<S>(row + Tp + 1);
     float gx = 1.f - fx, gy = 1.f - fy;
     float top = fmaf(fx, t01, gx * t00);
     float bot = fmaf(fx, t11, gx * t10);
     if (DERIV) {
-        bool inx = (px >= 0.f) && (px <= (float)(W - 1));
-        bool iny = (py >= 0.f) && (py <= (float)(H - 1));
-        dtx = inx ? fmaf(fy, t11 - t10, gy * (t01 - t00)) : 0.f;
-        dty = iny ? (bot - top) : 0.f;
+        dtx = clx ? 0.f : fmaf(fy, t11 - t10, gy * (t01 - t00));
+        dty = cly ? 0.f : (bot - top);
     }
     return fmaf(fy, bot, gy * top);
 }
 
-// Plain (storage-independent) fp32 bilinear for displacement fields read through L2.
-__device__ __forceinline__ float bilinear_cg(const float *F, int W, int H, float px, float py)
+// Bilinear value (no derivative) of an fp32 field read through L2, at (xi + vx, yi + vy).
+__device__ __forceinline__ float sample_cg(const float *F, int W, int H, int xi, int yi, float vx, float vy)
 {
-    float qx = fminf(fmaxf(px, 0.f), (float)(W - 1));
-    float qy = fminf(fmaxf(py, 0.f), (float)(H - 1));
-    int x0 = min((int)qx, W - 2), y0 = min((int)qy, H - 2);
-    float fx = qx - (float)x0, fy = qy - (float)y0;
-    const float *row = F + (size_t)y0 * W + x0;
+    vx = fminf(fmaxf(vx, -1.0e6f), 1.0e6f);
+    vy = fminf(fmaxf(vy, -1.0e6f), 1.0e6f);
+    const float flx = floorf(vx), fly = floorf(vy);
+    int x = xi + (int)flx, y = yi + (int)fly;
+    float fx = vx - flx, fy = vy - fly;
+    if (x < 0) { x = 0; fx = 0.f; } else if (x > W - 2) { x = W - 2; fx = 1.f; }
+    if (y < 0) { y = 0; fy = 0.f; } else if (y > H - 2) { y = H - 2; fy = 1.f; }
+    const float *row = F + (size_t)y * W + x;
     float t00 = __ldcg(row), t01 = __ldcg(row + 1), t10 = __ldcg(row + W), t11 = __ldcg(row + W + 1);
     float gx = 1.f - fx;
     float top = fmaf(fx, t01, gx * t00);
@@ -245,7 +255,9 @@ template <typename S, int NM, bool GRAD>
 __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &sm, int &buf,
                            const cg::cluster_group &cl)
 {
-    const float ca = pm[0], sa = pm[1], cxg = pm[2], cyg = pm[3];
+    // pm: cos(alpha) - 1, sin(alpha), fractional translation (x, y), integer translation (x, y)
+    const float cm1 = pm[0], sa = pm[1], gfx = pm[2], gfy = pm[3];
+    const int gix = (int)pm[4], giy = (int)pm[5];
     const float cx = 0.5f * (float)(L.W - 1), cy = 0.5f * (float)(L.H - 1);
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     float hi[NM], lo[NM], a[NM];
@@ -255,10 +267,11 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
         L.W, r0, r1,
         [&](int r, int c) {
             float xc = (float)c - cx, yc = (float)r - cy;
-            float px = fmaf(ca, xc, fmaf(-sa, yc, cxg));
-            float py = fmaf(sa, xc, fmaf(ca, yc, cyg));
+            // phi(x) - x - integer translation: small, so FP32 keeps it to ~1e-7 relative
+            float vx = fmaf(cm1, xc, fmaf(-sa, yc, gfx));
+            float vy = fmaf(sa, xc, fmaf(cm1, yc, gfy));
             float dtx, dty;
-            float tw = bilinear<S, GRAD>(T, L.W, L.H, L.Tp, px, py, dtx, dty);
+            float tw = sample_at<S, GRAD>(T, L.W, L.H, L.Tp, c + gix, r + giy, vx, vy, dtx, dty);
             float rv = ldS<S>(R + (size_t)r * L.Rp + c) - L.cR;
             float tv = tw - L.cR;
             a[0] += tv;
@@ -269,8 +282,9 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
                 a[4] = fmaf(rv, rv, a[4]);
             }
             if constexpr (GRAD) {
-                // g_alpha = dT . dphi/dalpha, dphi/dalpha = (-(py - cyg), px - cxg)
-                float g0 = fmaf(dty, px - cxg, -dtx * (py - cyg));
+                // g_alpha = dT . dphi/dalpha, dphi/dalpha = Rot'(alpha) (x - c)
+                const float ca = 1.f + cm1;
+                float g0 = fmaf(dty, fmaf(ca, xc, -sa * yc), -dtx * fmaf(sa, xc, ca * yc));
                 a[5] = fmaf(rv, g0, a[5]);
                 a[6] = fmaf(rv, dtx, a[6]);
                 a[7] = fmaf(rv, dty, a[7]);
@@ -299,12 +313,16 @@ struct RigidCtl {
 
 __device__ void rigid_params(const RigidCtl &k, const double *th, float *pm)
 {
-    float s, c;
-    sincosf((float)th[0], &s, &c);
-    pm[0] = c;
-    pm[1] = s;
-    pm[2] = (float)(k.cx + th[1]);
-    pm[3] = (float)(k.cy + th[2]);
+    const float a = (float)th[0];
+    const float h = sinf(0.5f * a);
+    pm[0] = -2.f * h * h;            // cos(a) - 1 without cancellation
+    pm[1] = sinf(a);
+    const double ix = rint(th[1]), iy = rint(th[2]);
+    pm[2] = (float)(th[1] - ix);
+    pm[3] = (float)(th[2] - iy);
+    pm[4] = (float)fmax(-4.0e6, fmin(4.0e6, ix));
+    pm[5] = (float)fmax(-4.0e6, fmin(4.0e6, iy));
+    (void)k;
 }
 
 // Thread-0 controller step after a GRAD (first == true: the level's first) or TRIAL pass.
@@ -423,7 +441,7 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
             __syncthreads();
             const int act = sm.action;
             if (act == kActDone) break;
-            float pm[4] = {sm.pm[0], sm.pm[1], sm.pm[2], sm.pm[3]};
+            float pm[6] = {sm.pm[0], sm.pm[1], sm.pm[2], sm.pm[3], sm.pm[4], sm.pm[5]};
             if (act == kActGrad) {
                 eval_rigid<S, 14, true>(L, r0, r1, pm, sm, buf, cl);
             } else {
@@ -510,7 +528,7 @@ __device__ void eval_field_energy(const Lvl &L, const FieldLvl &F, int b, float 
             size_t i = (size_t)r * W + c;
             float2 u = u_at(F, b, i, tau);
             float dtx, dty;
-            float tw = bilinear<S, false>(T, W, H, L.Tp, (float)c + u.x, (float)r + u.y, dtx, dty);
+            float tw = sample_at<S, false>(T, W, H, L.Tp, c, r, u.x, u.y, dtx, dty);
             float rv = ldS<S>(R + (size_t)r * L.Rp + c) - L.cR;
             float tv = tw - L.cR;
             a[0] += tv;
@@ -562,7 +580,7 @@ __device__ void eval_field_grad(const Lvl &L, const FieldLvl &F, int b, const fl
             if (r > 0)     { float2 v = u_at(F, b, i - W, tau); lx += u.x - v.x; ly += u.y - v.y; }
             if (r + 1 < H) { float2 v = u_at(F, b, i + W, tau); lx += u.x - v.x; ly += u.y - v.y; }
             float dtx, dty;
-            float tw = bilinear<S, true>(T, W, H, L.Tp, (float)c + u.x, (float)r + u.y, dtx, dty);
+            float tw = sample_at<S, true>(T, W, H, L.Tp, c, r, u.x, u.y, dtx, dty);
             float rv = ldS<S>(R + (size_t)r * L.Rp + c) - L.cR;
             float tv = tw - L.cR;
             // fP = P * dE_data/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
@@ -670,9 +688,8 @@ __device__ void field_compose(const float *u1, const float *u2, const FieldLvl &
         [&](int r, int c) {
             size_t i = (size_t)r * W + c;
             float ax = __ldcg(u1 + i), ay = __ldcg(u1 + P + i);
-            float px = (float)c + ax, py = (float)r + ay;
-            __stcg(F.U(0, 0) + i, ax + bilinear_cg(u2, W, H, px, py));
-            __stcg(F.U(0, 1) + i, ay + bilinear_cg(u2 + P, W, H, px, py));
+            __stcg(F.U(0, 0) + i, ax + sample_cg(u2, W, H, c, r, ax, ay));
+            __stcg(F.U(0, 1) + i, ay + sample_cg(u2 + P, W, H, c, r, ax, ay));
         },
         []() {});
 }
@@ -972,7 +989,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
         memset(&k, 0, sizeof(k));
         k.cx = 0.5 * (L.W - 1);
         k.cy = 0.5 * (L.H - 1);
-        float pm[4];
+        float pm[6];
         rigid_params(k, theta, pm);
         eval_rigid<S, 14, true>(L, 0, L.H, pm, sm, buf, cl);
         if (tid == 0) {
@@ -1072,9 +1089,8 @@ __global__ void compose_kernel(const float *u1, const float *u2, int W, int H, f
     if (c >= W || r >= H) return;
     const size_t P = (size_t)W * H, i = (size_t)r * W + c;
     float ax = u1[i], ay = u1[P + i];
-    float px = (float)c + ax, py = (float)r + ay;
-    out[i] = ax + bilinear_cg(u2, W, H, px, py);
-    out[P + i] = ay + bilinear_cg(u2 + P, W, H, px, py);
+    out[i] = ax + sample_cg(u2, W, H, c, r, ax, ay);
+    out[P + i] = ay + sample_cg(u2 + P, W, H, c, r, ax, ay);
 }
 
 // ================================================================== host launchers
