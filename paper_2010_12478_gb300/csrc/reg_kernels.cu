@@ -178,9 +178,11 @@ __device__ __forceinline__ void strip_rows(int H, int rank, int C, int &r0, int 
     r1 = min(H, r0 + per);
 }
 
-// Iterate the pixels of rows [r0, r1) in chunks; f(r, c) per pixel, flush() after each chunk.
-template <typename F, typename G>
-__device__ __forceinline__ void for_pixels(int W, int r0, int r1, F &&f, G &&flush)
+// Iterate the pixels of rows [r0, r1): f(r, c) per pixel; flush_fast() after every
+// kFast pixels of this thread and flush() after every kChunk pixels (and at the end).
+constexpr int kFast = 8;
+template <typename F, typename G, typename Q>
+__device__ __forceinline__ void for_pixels2(int W, int r0, int r1, F &&f, Q &&flush_fast, G &&flush)
 {
     const int tid = threadIdx.x;
     int i = r0 * W + tid;
@@ -189,14 +191,24 @@ __device__ __forceinline__ void for_pixels(int W, int r0, int r1, F &&f, G &&flu
     const int dr = kThreads / W, dc = kThreads - dr * W;
     while (i < end) {
 #pragma unroll 1
-        for (int k = 0; k < kChunk && i < end; ++k) {
-            f(r, c);
-            i += kThreads;
-            c += dc; r += dr;
-            if (c >= W) { c -= W; r += 1; }
+        for (int q = 0; q < kChunk / kFast && i < end; ++q) {
+#pragma unroll 1
+            for (int k = 0; k < kFast && i < end; ++k) {
+                f(r, c);
+                i += kThreads;
+                c += dc; r += dr;
+                if (c >= W) { c -= W; r += 1; }
+            }
+            flush_fast();
         }
         flush();
     }
+}
+
+template <typename F, typename G>
+__device__ __forceinline__ void for_pixels(int W, int r0, int r1, F &&f, G &&flush)
+{
+    for_pixels2(W, r0, r1, f, []() {}, flush);
 }
 
 // Bilinear sample of T (storage S, pitch Tp) at p = (xi + vx, yi + vy) with clamp-to-edge,
@@ -263,7 +275,7 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
     float hi[NM], lo[NM], a[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
-    for_pixels(
+    for_pixels2(
         L.W, r0, r1,
         [&](int r, int c) {
             float xc = (float)c - cx, yc = (float)r - cy;
@@ -297,8 +309,13 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
             }
         },
         [&]() {
+            // energy moments: short FP32 runs keep 1 - NCC accurate to ~1e-9
 #pragma unroll
-            for (int m = 0; m < NM; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+            for (int m = 0; m < (NM < 5 ? NM : 5); ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+        },
+        [&]() {
+#pragma unroll
+            for (int m = 5; m < NM; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
         });
     cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
 }
@@ -522,7 +539,7 @@ __device__ void eval_field_energy(const Lvl &L, const FieldLvl &F, int b, float 
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
     const int W = L.W, H = L.H;
-    for_pixels(
+    for_pixels2(
         W, r0, r1,
         [&](int r, int c) {
             size_t i = (size_t)r * W + c;
@@ -551,8 +568,9 @@ __device__ void eval_field_energy(const Lvl &L, const FieldLvl &F, int b, float 
         },
         [&]() {
 #pragma unroll
-            for (int m = 0; m < NM; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
-        });
+            for (int m = 0; m < 5; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+        },
+        [&]() { ff_acc(hi[5], lo[5], a[5]); a[5] = 0.f; });
     cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
 }
 
