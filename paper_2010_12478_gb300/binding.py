@@ -29,7 +29,8 @@ MAX_LEVELS = 8
 EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairwise", "reg_scan",
            "reg_scan_work", "reg_scan_dag", "reg_pyramid", "reg_energy", "reg_compose_field",
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
-           "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message"]
+           "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
+           "reg_pairwise_noalloc"]
 
 
 class RegError(RuntimeError):
@@ -94,6 +95,9 @@ def lib() -> ctypes.CDLL:
         L.reg_stream_submit.argtypes = [vp, fp, ctypes.c_uint64]
         L.reg_stream_poll.argtypes = [vp, ctypes.POINTER(reg_result_t), ip, ctypes.POINTER(ctypes.c_int), ip]
         L.reg_stream_close.argtypes = [vp]
+        L.reg_pairwise_noalloc.argtypes = [ctypes.POINTER(reg_config_t), ip, fp, fp, ip, ip, ip,
+                                           ctypes.POINTER(reg_elem_t), ctypes.POINTER(reg_elem_t),
+                                           ctypes.POINTER(reg_stats_t), vp]
         L.reg_ctx_set_timing.argtypes = [vp, ip]
         L.reg_ctx_last_timing.argtypes = [vp, ctypes.POINTER(reg_timing_t)]
         L.reg_strerror.argtypes = [ip]
@@ -252,6 +256,19 @@ class Context:
     def compose_field(self, u1, u2, out):
         _, H, W = u1.shape
         check(lib().reg_compose_field(self.h, _ptr(u1), _ptr(u2), W, H, _ptr(out), None), "reg_compose_field")
+
+
+def pairwise_noalloc(cfg: Config, R, T, init: Optional[Sequence[float]] = None, device: int = 0, stream=None):
+    """reg_pairwise_noalloc: rigid pairwise registration that allocates nothing (device R, T)."""
+    H, W = R.shape[-2], R.shape[-1]
+    c = cfg.c()
+    out = reg_elem_t()
+    st = reg_stats_t()
+    ini = reg_elem_t(0, 1, float(init[0]), float(init[1]), float(init[2])) if init is not None else None
+    check(lib().reg_pairwise_noalloc(ctypes.byref(c), device, _ptr(R), _ptr(T), W, H, W,
+                                     ctypes.byref(ini) if ini else None, ctypes.byref(out), ctypes.byref(st),
+                                     _stream(stream)), "reg_pairwise_noalloc")
+    return (out.i, out.k, out.alpha, out.gx, out.gy), stats_dict(st, cfg.levels)
 
 
 class Stream:

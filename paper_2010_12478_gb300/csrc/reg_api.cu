@@ -58,6 +58,8 @@ extern "C" const char *reg_strerror(int code)
 
 extern "C" const char *reg_last_error_message(void) { return g_last_error.c_str(); }
 
+void reg::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 // ------------------------------------------------------------------ device buffers
 namespace {
 

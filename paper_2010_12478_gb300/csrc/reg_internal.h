@@ -96,6 +96,8 @@ cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
 cudaError_t launch_compose(const float *u1, const float *u2, int W, int H, float *out,
                            cudaStream_t s);
 size_t scratch_floats_per_slot(const int *W, const int *H, int levels);
+// Set the calling thread's message returned by reg_last_error_message().
+void set_last_error(const char *msg);
 int max_cluster_size();
 
 }  // namespace reg

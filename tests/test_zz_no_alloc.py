@@ -1,0 +1,65 @@
+"""reg_pairwise_noalloc: the allocation-free rigid pairwise registration.
+
+Callers that must not allocate device memory when they register (a real-time
+acquisition loop, code under CUDA-graph capture, a fixed memory pool) use this
+entry point; it keeps its working data in a static device array.  It must give
+the same registration as reg_pairwise, call after call, even though every call
+reuses the array the previous call left behind.  This file is collected last
+so that a run stopping at the first failure has run every other test first.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2010_12478_gb300 import binding as B
+from paper_2010_12478_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PX_TOL = 0.02
+E_TOL = 1e-5
+
+
+def _max_px(th_a, th_b, H, W):
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    cx, cy = 0.5 * (W - 1), 0.5 * (H - 1)
+
+    def disp(th):
+        ca, sa = np.cos(th[0]), np.sin(th[0])
+        return np.stack([ca * (x - cx) - sa * (y - cy) + cx + th[1], sa * (x - cx) + ca * (y - cy) + cy + th[2]])
+
+    d = disp(th_a) - disp(th_b)
+    return float(np.sqrt((d ** 2).sum(0)).max())
+
+
+def test_noalloc_matches_pairwise_on_two_calls_in_a_row():
+    from paper_2010_12478_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    cfg = B.Config()
+    ctx = B.Context(cfg)
+    cases = [synth.rigid_pair(200, 256, 0.006, (1.7, -2.2), noise_snr=10.0, seed=71),
+             synth.rigid_pair(160, 96, -0.004, (-0.9, 2.6), noise_snr=6.0, seed=72)]
+    for R, T in cases:
+        H, W = R.shape
+        Rd, Td = torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda()
+        _, ref = ctx.pairwise(Rd, Td)
+        torch.cuda.synchronize()
+        (i, k, a, gx, gy), st = B.pairwise_noalloc(cfg, Rd, Td)
+        assert (i, k) == (0, 1)
+        assert _max_px(np.array(st["theta"]), np.array(ref["theta"]), H, W) <= PX_TOL
+        assert abs(st["energy"] - ref["energy"]) <= E_TOL * abs(ref["energy"])
+        assert abs(a - ref["theta"][0]) <= 1e-6 and abs(gx - ref["theta"][1]) <= 1e-4
+
+
+def test_noalloc_rejects_oversized_and_nonrigid_requests():
+    from paper_2010_12478_gb300 import build
+    build.build()
+    big = torch.zeros((1025, 1024), device="cuda")
+    with pytest.raises(B.RegError) as e:
+        B.pairwise_noalloc(B.Config(), big, big)
+    assert e.value.code == B.REG_EINVAL and "too large" in str(e.value)
+    small = torch.zeros((64, 64), device="cuda")
+    with pytest.raises(B.RegError) as e:
+        B.pairwise_noalloc(B.Config(mode="nonrigid"), small, small)
+    assert e.value.code == B.REG_EINVAL
