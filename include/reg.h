@@ -9,12 +9,12 @@
  * where B composes the two known deformations into an initial guess
  * phi_jk o phi_ij and then minimises the normalised-cross-correlation
  * distance D(f_i, f_k o phi) by gradient flow on a coarse-to-fine pyramid
- * [Sec. 2.1.1, Sec. 2.1.2, Def. 2.1].  The neighbour registrations
+ * [Sec. 2.3.1, Sec. 2.3.2].  The neighbour registrations
  * A(f_{i-1}, f_i) start from the identity.
  *
  * Deformation models:
  *   REG_RIGID     phi(x) = Rot(alpha) (x - c) + c + G, c = ((W-1)/2, (H-1)/2),
- *                 pixel (r, c) at x = (c, r)                         [Def. 2.1]
+ *                 pixel (r, c) at x = (c, r)                         [Sec. 2.3.1]
  *   REG_NONRIGID  phi(x) = x + u(x), u a dense 2-channel field, energy
  *                 1 - NCC + lambda/(2P) sum_edges |u(a) - u(b)|^2 (an extension:
  *                 the paper's deformation is rigid)
@@ -143,7 +143,7 @@ void reg_ctx_destroy(reg_ctx_t *ctx);
 /* ---- the operators ------------------------------------------------------ */
 
 /* Register template T onto reference R (A when init == NULL, else the
- * minimisation of B from `init`) [Sec. 2.1.1].
+ * minimisation of B from `init`) [Sec. 2.3.1].
  *   R, T       fp32 images, H rows of `pitch` elements (pitch >= W), host or device.
  *   init       rigid initial deformation (host), NULL = identity.
  *   field_in   REG_NONRIGID initial field [2][H][W] fp32 (x plane then y), host or
@@ -206,7 +206,7 @@ int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const float *R, co
 
 /* ---- kernel-level entry points (one hot-path step each) ------------------- */
 
-/* Pyramid build [Sec. 2.1.1, multilevel scheme]: 2x2 box average per level,
+/* Pyramid build [Sec. 2.3.1, multilevel scheme]: 2x2 box average per level,
  * odd last row/column clamped.  frame: device fp32 [H][pitch].  out: device,
  * levels packed level 0 first, each W_l x H_l contiguous, in `storage` type
  * (4 or 2 bytes per pixel).  Returns REG_EINVAL for levels outside 1..8. */
@@ -214,7 +214,7 @@ int reg_pyramid(reg_ctx_t *ctx, const float *frame, int W, int H, int pitch,
                 int levels, int storage, void *out, void *stream);
 
 /* Energy and gradient at a given deformation (one fused warp+reduction pass,
- * as used inside the iteration) [Sec. 2.1.1].  R, T device fp32 [H][W].
+ * as used inside the iteration) [Sec. 2.3.1].  R, T device fp32 [H][W].
  *   REG_RIGID:    theta[3] (host) = (alpha, Gx, Gy); grad[3] (host, optional).
  *   REG_NONRIGID: field [2][H][W] device; grad_field [2][H][W] device optional
  *                 (dE/du per pixel).  lambda from the context configuration.
@@ -223,7 +223,7 @@ int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W, int H,
                const double *theta, const float *field, double *energy,
                double *grad, float *grad_field, void *stream);
 
-/* Nonrigid composition (B's initial guess, Sec. 2.1.2):
+/* Nonrigid composition (B's initial guess, Sec. 2.3.2):
  * out(x) = u1(x) + u2(x + u1(x)), bilinear with clamp. Device [2][H][W] each. */
 int reg_compose_field(reg_ctx_t *ctx, const float *u1, const float *u2, int W, int H,
                       float *out, void *stream);

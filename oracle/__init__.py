@@ -9,7 +9,7 @@ Layers:
   * ``oracle.c`` (compiled to ``_build/liboracle.so`` with gcc, FP64, no fast
     math): pyramid, bilinear sampling, NCC energy and gradient, the gradient
     flow with Armijo backtracking (rigid and nonrigid), composition.
-  * this module: ctypes marshalling, the operators A and B (Sec. 2.1.1-2.1.2),
+  * this module: ctypes marshalling, the operators A and B (Sec. 2.3.1-2.3.2),
     the scan DAG generators (Sec. 3, Table 1) and the scan driver that applies
     B along a DAG, one call at a time.
 """
@@ -112,7 +112,7 @@ class Config:
     tau0: float = 1.0
     step_cap: float = 0.5
     lam: float = 1.0
-    mode: str = "rigid"           # "rigid" (paper, Def. 2.1) or "nonrigid" (extension)
+    mode: str = "rigid"           # "rigid" (the paper's map, Sec. 2.3.1) or "nonrigid" (extension)
 
     def c(self) -> _Cfg:
         return _Cfg(self.levels, self.max_iter, self.max_rejects, self.tol_grad, self.tol_rel_e,
@@ -188,7 +188,7 @@ def regulariser(u, lam: float) -> float:
 
 
 def compose_rigid(a, b) -> np.ndarray:
-    """phi_b o phi_a (apply a first): B's initial guess phi_jk o phi_ij (Sec. 2.1.2)."""
+    """phi_b o phi_a (apply a first): B's initial guess phi_jk o phi_ij (Sec. 2.3.2)."""
     a, b = _f64(a), _f64(b)
     out = np.zeros(3)
     lib().or_rigid_compose(_dp(a), _dp(b), _dp(out))
@@ -229,7 +229,7 @@ def _pyr_args(pyr: Sequence[np.ndarray]):
 
 
 def register_rigid(Rpyr, Tpyr, init, cfg: Config):
-    """Multilevel gradient-flow registration of T onto R, rigid map (Def. 2.1)."""
+    """Multilevel gradient-flow registration of T onto R, rigid map of Sec. 2.3.1."""
     assert len(Rpyr) == cfg.levels == len(Tpyr)
     ra, Ws, Hs = _pyr_args(Rpyr)
     ta, _, _ = _pyr_args(Tpyr)
@@ -260,7 +260,7 @@ def register_nonrigid(Rpyr, Tpyr, init_u, cfg: Config):
 
 
 # --------------------------------------------------------------------------
-# scan elements and the operators A and B (Sec. 2.1.1-2.1.2)
+# scan elements and the operators A and B (Sec. 2.3.1-2.3.2)
 # --------------------------------------------------------------------------
 @dataclasses.dataclass
 class Elem:
@@ -288,7 +288,7 @@ def op_A(pyrs, i: int, k: int, cfg: Config) -> Elem:
 
 
 def op_B(e1: Elem, e2: Elem, pyrs, cfg: Config) -> Elem:
-    """B(phi_ij, phi_jk) = register f_k onto f_i from phi_jk o phi_ij (Sec. 2.1.2)."""
+    """B(phi_ij, phi_jk) = register f_k onto f_i from phi_jk o phi_ij (Sec. 2.3.2)."""
     if e1.k != e2.i:
         raise ValueError(f"B needs adjacent elements, got ({e1.i},{e1.k}) and ({e2.i},{e2.k})")
     init = compose_rigid(e1.phi, e2.phi) if cfg.mode == "rigid" else compose_nonrigid(e1.phi, e2.phi)

@@ -8,15 +8,15 @@
  * loops, with no blocking, fusion or reordering.
  *
  * What it computes (paper section / definition in brackets):
- *   - the image pyramid of the multilevel scheme            [Sec. 2.1.1]
+ *   - the image pyramid of the multilevel scheme            [Sec. 2.3.1]
  *   - the normalised-cross-correlation distance D(R, T o phi) and its
  *     gradient, for the rigid map phi(x) = R(alpha)(x - c) + c + G
- *                                                          [Def. 2.1, Sec. 2.1.1]
+ *                                                          [Sec. 2.3.1]
  *   - a nonrigid extension phi(x) = x + u(x) (not in the paper) with energy
  *     1 - NCC + lambda/(2P) * sum over grid edges of |u(a) - u(b)|^2
  *   - the gradient-flow minimiser with Armijo backtracking, run coarse to
- *     fine                                                  [Sec. 2.1.1]
- *   - the composition phi_jk o phi_ij used as initial guess of B [Sec. 2.1.2]
+ *     fine                                                  [Sec. 2.3.1]
+ *   - the composition phi_jk o phi_ij used as initial guess of B [Sec. 2.3.2]
  *
  * The scan itself (sequential recursion, tree DAGs) is driven from Python
  * (oracle/__init__.py), one operator call at a time.
@@ -137,7 +137,7 @@ static or_ncc_t or_ncc(const or_moments_t *m)
 
 /* ------------------------------------------------------------------------ */
 /* Rigid energy E = 1 - NCC(R, T o phi) and its gradient in (alpha, Gx, Gy). */
-/* phi(x) = R(alpha)(x - c0) + c0 + G                      [Def. 2.1]       */
+/* phi(x) = R(alpha)(x - c0) + c0 + G                      [Sec. 2.3.1]        */
 /* ------------------------------------------------------------------------ */
 
 int or_rigid_energy(const double *R, const double *T, int W, int H,
@@ -183,7 +183,7 @@ int or_rigid_energy(const double *R, const double *T, int W, int H,
 }
 
 /* Rigid composition phi2 o phi1 in centred coordinates: alpha1 + alpha2,
- * G = R(alpha2) G1 + G2.                                   [Sec. 2.1.2]   */
+ * G = R(alpha2) G1 + G2.                                   [Sec. 2.3.2]   */
 void or_rigid_compose(const double a[3], const double b[3], double out[3])
 {
     double ca = cos(b[0]), sa = sin(b[0]);

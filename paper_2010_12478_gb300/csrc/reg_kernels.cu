@@ -1,7 +1,7 @@
 // Device kernels of libreg: pyramid build and the registration operator.
 //
 // Design (GB300, sm_103a):
-//   * One operator application (A or B, Sec. 2.1.1-2.1.2) runs start to finish
+//   * One operator application (A or B, Sec. 2.3.1-2.3.2) runs start to finish
 //     inside ONE thread-block cluster: every level, every gradient-flow
 //     iteration and every Armijo trial.  The C CTAs of the cluster split the
 //     rows of each pyramid level; their partial sums meet through distributed
@@ -418,7 +418,7 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
         memset(&k, 0, sizeof(k));
         double th0[3] = {0.0, 0.0, 0.0};
         if (op.left >= 0) {
-            // B's initial guess phi_jk o phi_ij in centred coordinates (Sec. 2.1.2)
+            // B's initial guess phi_jk o phi_ij in centred coordinates (Sec. 2.3.2)
             // node states come from other clusters: read through L2, never a stale L1 line
             const double *pa = p.node_theta + 3 * op.left, *pb = p.node_theta + 3 * op.right;
             double a[3] = {__ldcg(pa), __ldcg(pa + 1), __ldcg(pa + 2)};

@@ -19,7 +19,7 @@ Frame ``t`` aligned to frame 0 satisfies ``f_t(phi(x)) ~= f_0(x)`` for
 returned beside the frames.  The electron-microscopy data of the paper
 (Sec. 5, 1920x1856 TEM frames) is not available; these series stand in for it
 with the paper's structure: a (nearly) periodic image whose neighbouring
-frames differ by less than half a period (Sec. 2.1.2).
+frames differ by less than half a period (Sec. 2.3.2).
 
 Seeds: numpy's PCG64 seeded with ``(seed, series)`` draws the per-series and
 per-frame parameters; the per-pixel noise comes from a ``torch.Generator``
