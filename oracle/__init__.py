@@ -54,6 +54,11 @@ class _Cfg(ctypes.Structure):
                 ("step_cap", ctypes.c_double), ("lambda_", ctypes.c_double)]
 
 
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("s", ctypes.c_int), ("W0", ctypes.c_int),
+                ("H0", ctypes.c_int)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * MAX_LEVELS), ("evals", ctypes.c_int * MAX_LEVELS),
                 ("stop", ctypes.c_int * MAX_LEVELS), ("rejects", ctypes.c_int),
@@ -75,16 +80,17 @@ def lib():
             L.or_rigid_compose.argtypes = [dp, dp, dp]
             L.or_rigid_register.argtypes = [dpp, dpp, ipp, ipp, ctypes.POINTER(_Cfg), dp, dp,
                                             ctypes.POINTER(_Stats)]
-            L.or_regulariser.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
-            L.or_regulariser.restype = ctypes.c_double
-            L.or_nonrigid_energy.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp,
-                                             ctypes.c_double, dp, dp, dp]
-            L.or_nonrigid_energy.restype = ctypes.c_int
-            L.or_nonrigid_compose.argtypes = [dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp]
-            L.or_prolong.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int]
-            L.or_restrict.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
-            L.or_nonrigid_register.argtypes = [dpp, dpp, ipp, ipp, ctypes.POINTER(_Cfg), dp, dp,
-                                               dp, dp, ctypes.POINTER(_Stats)]
+            gp = ctypes.POINTER(_Grid)
+            L.or_grid_regulariser.argtypes = [gp, dp, dp, ctypes.c_double, ctypes.c_double]
+            L.or_grid_regulariser.restype = ctypes.c_double
+            L.or_grid_energy.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, gp, dp, dp,
+                                         ctypes.c_double, dp, dp, dp]
+            L.or_grid_energy.restype = ctypes.c_int
+            L.or_grid_register.argtypes = [dpp, dpp, ipp, ipp, ctypes.POINTER(_Cfg), gp, dp, dp, dp, dp,
+                                           ctypes.POINTER(_Stats)]
+            L.or_grid_compose.argtypes = [gp, dp, dp, dp, dp, dp, dp]
+            L.or_grid_dense.argtypes = [gp, dp, dp, dp, dp]
+            L.or_grid_level_dense.argtypes = [gp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
             _lib = L
     return _lib
 
@@ -111,7 +117,8 @@ class Config:
     armijo_c: float = 1e-4
     tau0: float = 1.0
     step_cap: float = 0.5
-    lam: float = 1.0
+    lam: float = 2.0
+    grid: int = 0                 # control-grid spacing of the nonrigid field (finest px), 0 = auto
     mode: str = "rigid"           # "rigid" (the paper's map, Sec. 2.3.1) or "nonrigid" (extension)
 
     def c(self) -> _Cfg:
@@ -168,23 +175,76 @@ def rigid_energy(R, T, theta, grad: bool = True):
     return (float(E[0]), g) if grad else float(E[0])
 
 
-def nonrigid_energy(R, T, u, lam: float, grad: bool = True):
+@dataclasses.dataclass
+class Grid:
+    """Control grid of the nonrigid field: points (jx*s, jy*s), jx < nx, jy < ny (finest px)."""
+    nx: int
+    ny: int
+    s: int
+    W0: int
+    H0: int
+
+    def c(self) -> _Grid:
+        return _Grid(self.nx, self.ny, self.s, self.W0, self.H0)
+
+
+def grid_for(W0: int, H0: int, spacing: int = 0) -> Grid:
+    """Spacing 16 px, doubled until the grid has at most 65 points per axis (spacing 0),
+    or the given spacing."""
+    s = spacing if spacing > 0 else 16
+    if spacing <= 0:
+        while (W0 - 1 + s - 1) // s + 1 > 65 or (H0 - 1 + s - 1) // s + 1 > 65:
+            s *= 2
+    return Grid((W0 - 1 + s - 1) // s + 1, (H0 - 1 + s - 1) // s + 1, s, W0, H0)
+
+
+def grid_energy(R, T, level: int, g: Grid, c, lam: float, grad: bool = True):
+    """Energy of the level-``level`` images for control values c [2, ny, nx] in pixels of that level."""
     R, T = _f64(R), _f64(T)
-    ux, uy = _f64(u[0]), _f64(u[1])
+    cx, cy = _f64(c[0]), _f64(c[1])
     H, W = R.shape
     E = np.zeros(1)
+    gc = g.c()
     if grad:
-        gx = np.zeros((H, W)); gy = np.zeros((H, W))
-        lib().or_nonrigid_energy(_dp(R), _dp(T), W, H, _dp(ux), _dp(uy), lam, _dp(E), _dp(gx), _dp(gy))
+        gx = np.zeros((g.ny, g.nx)); gy = np.zeros((g.ny, g.nx))
+        lib().or_grid_energy(_dp(R), _dp(T), W, H, level, ctypes.byref(gc), _dp(cx), _dp(cy), lam, _dp(E),
+                             _dp(gx), _dp(gy))
         return float(E[0]), np.stack([gx, gy])
-    lib().or_nonrigid_energy(_dp(R), _dp(T), W, H, _dp(ux), _dp(uy), lam, _dp(E), None, None)
+    lib().or_grid_energy(_dp(R), _dp(T), W, H, level, ctypes.byref(gc), _dp(cx), _dp(cy), lam, _dp(E), None, None)
     return float(E[0])
 
 
-def regulariser(u, lam: float) -> float:
-    ux, uy = _f64(u[0]), _f64(u[1])
-    H, W = ux.shape
-    return float(lib().or_regulariser(_dp(ux), _dp(uy), W, H, lam))
+def grid_regulariser(g: Grid, c, lam: float, P: float) -> float:
+    cx, cy = _f64(c[0]), _f64(c[1])
+    gc = g.c()
+    return float(lib().or_grid_regulariser(ctypes.byref(gc), _dp(cx), _dp(cy), lam, P))
+
+
+def grid_dense(g: Grid, c) -> np.ndarray:
+    """Dense finest-level field [2, H0, W0] of control values c (finest px)."""
+    cx, cy = _f64(c[0]), _f64(c[1])
+    ux = np.zeros((g.H0, g.W0)); uy = np.zeros((g.H0, g.W0))
+    gc = g.c()
+    lib().or_grid_dense(ctypes.byref(gc), _dp(cx), _dp(cy), _dp(ux), _dp(uy))
+    return np.stack([ux, uy])
+
+
+def grid_level_dense(g: Grid, c, level: int, H: int, W: int) -> np.ndarray:
+    """Field [2, H, W] on the pixels of pyramid level ``level`` for control values in that level's px."""
+    cx, cy = _f64(c[0]), _f64(c[1])
+    ux = np.zeros((H, W)); uy = np.zeros((H, W))
+    gc = g.c()
+    lib().or_grid_level_dense(ctypes.byref(gc), _dp(cx), _dp(cy), level, W, H, _dp(ux), _dp(uy))
+    return np.stack([ux, uy])
+
+
+def compose_grid(g: Grid, c1, c2) -> np.ndarray:
+    """Control values of phi_2 o phi_1 at the control points (B's initial guess, Sec. 2.3.2)."""
+    a0, a1, b0, b1 = (_f64(v) for v in (c1[0], c1[1], c2[0], c2[1]))
+    ox = np.zeros((g.ny, g.nx)); oy = np.zeros((g.ny, g.nx))
+    gc = g.c()
+    lib().or_grid_compose(ctypes.byref(gc), _dp(a0), _dp(a1), _dp(b0), _dp(b1), _dp(ox), _dp(oy))
+    return np.stack([ox, oy])
 
 
 def compose_rigid(a, b) -> np.ndarray:
@@ -192,31 +252,6 @@ def compose_rigid(a, b) -> np.ndarray:
     a, b = _f64(a), _f64(b)
     out = np.zeros(3)
     lib().or_rigid_compose(_dp(a), _dp(b), _dp(out))
-    return out
-
-
-def compose_nonrigid(u1, u2) -> np.ndarray:
-    u1, u2 = _f64(u1), _f64(u2)
-    _, H, W = u1.shape
-    ox = np.zeros((H, W)); oy = np.zeros((H, W))
-    a0, a1, b0, b1 = (np.ascontiguousarray(v) for v in (u1[0], u1[1], u2[0], u2[1]))
-    lib().or_nonrigid_compose(_dp(a0), _dp(a1), _dp(b0), _dp(b1), W, H, _dp(ox), _dp(oy))
-    return np.stack([ox, oy])
-
-
-def prolong(u_coarse, H: int, W: int) -> np.ndarray:
-    src = _f64(u_coarse)
-    Hc, Wc = src.shape
-    out = np.zeros((H, W))
-    lib().or_prolong(_dp(src), Wc, Hc, _dp(out), W, H)
-    return out
-
-
-def restrict(u) -> np.ndarray:
-    src = _f64(u)
-    H, W = src.shape
-    out = np.zeros(((H + 1) // 2, (W + 1) // 2))
-    lib().or_restrict(_dp(src), W, H, _dp(out))
     return out
 
 
@@ -241,21 +276,24 @@ def register_rigid(Rpyr, Tpyr, init, cfg: Config):
     return out, Stats.of(st, cfg.levels)
 
 
-def register_nonrigid(Rpyr, Tpyr, init_u, cfg: Config):
+def register_nonrigid(Rpyr, Tpyr, init_c, cfg: Config):
+    """Multilevel registration of the control-grid field; init_c and the result in finest px."""
     assert len(Rpyr) == cfg.levels == len(Tpyr)
     ra, Ws, Hs = _pyr_args(Rpyr)
     ta, _, _ = _pyr_args(Tpyr)
     H, W = Rpyr[0].shape
-    ox = np.zeros((H, W)); oy = np.zeros((H, W))
+    g = grid_for(W, H, cfg.grid)
+    gc = g.c()
+    ox = np.zeros((g.ny, g.nx)); oy = np.zeros((g.ny, g.nx))
     st = _Stats()
     c = cfg.c()
-    if init_u is None:
-        lib().or_nonrigid_register(ra, ta, Ws, Hs, ctypes.byref(c), None, None, _dp(ox), _dp(oy),
-                                   ctypes.byref(st))
+    if init_c is None:
+        lib().or_grid_register(ra, ta, Ws, Hs, ctypes.byref(c), ctypes.byref(gc), None, None, _dp(ox), _dp(oy),
+                               ctypes.byref(st))
     else:
-        ix, iy = _f64(init_u[0]), _f64(init_u[1])
-        lib().or_nonrigid_register(ra, ta, Ws, Hs, ctypes.byref(c), _dp(ix), _dp(iy), _dp(ox), _dp(oy),
-                                   ctypes.byref(st))
+        ix, iy = _f64(init_c[0]), _f64(init_c[1])
+        lib().or_grid_register(ra, ta, Ws, Hs, ctypes.byref(c), ctypes.byref(gc), _dp(ix), _dp(iy), _dp(ox),
+                               _dp(oy), ctypes.byref(st))
     return np.stack([ox, oy]), Stats.of(st, cfg.levels)
 
 
@@ -266,12 +304,15 @@ def register_nonrigid(Rpyr, Tpyr, init_u, cfg: Config):
 class Elem:
     i: int                        # reference frame index
     k: int                        # template frame index
-    phi: np.ndarray               # rigid: (alpha, Gx, Gy); nonrigid: [2, H, W] displacement
+    phi: np.ndarray               # rigid: (alpha, Gx, Gy); nonrigid: control values [2, ny, nx] (finest px)
     stats: Optional[Stats] = None
 
 
-def identity(mode: str, H: int, W: int) -> np.ndarray:
-    return np.zeros(3) if mode == "rigid" else np.zeros((2, H, W))
+def identity(mode: str, H: int, W: int, grid: int = 0) -> np.ndarray:
+    if mode == "rigid":
+        return np.zeros(3)
+    g = grid_for(W, H, grid)
+    return np.zeros((2, g.ny, g.nx))
 
 
 def register(Rpyr, Tpyr, init, cfg: Config):
@@ -283,7 +324,7 @@ def register(Rpyr, Tpyr, init, cfg: Config):
 def op_A(pyrs, i: int, k: int, cfg: Config) -> Elem:
     """A(f_i, f_k): register from the identity (neighbouring frames)."""
     H, W = pyrs[i][0].shape
-    phi, st = register(pyrs[i], pyrs[k], identity(cfg.mode, H, W), cfg)
+    phi, st = register(pyrs[i], pyrs[k], identity(cfg.mode, H, W, cfg.grid), cfg)
     return Elem(i, k, phi, st)
 
 
@@ -291,7 +332,11 @@ def op_B(e1: Elem, e2: Elem, pyrs, cfg: Config) -> Elem:
     """B(phi_ij, phi_jk) = register f_k onto f_i from phi_jk o phi_ij (Sec. 2.3.2)."""
     if e1.k != e2.i:
         raise ValueError(f"B needs adjacent elements, got ({e1.i},{e1.k}) and ({e2.i},{e2.k})")
-    init = compose_rigid(e1.phi, e2.phi) if cfg.mode == "rigid" else compose_nonrigid(e1.phi, e2.phi)
+    if cfg.mode == "rigid":
+        init = compose_rigid(e1.phi, e2.phi)
+    else:
+        H, W = pyrs[e1.i][0].shape
+        init = compose_grid(grid_for(W, H, cfg.grid), e1.phi, e2.phi)
     phi, st = register(pyrs[e1.i], pyrs[e2.k], init, cfg)
     return Elem(e1.i, e2.k, phi, st)
 
@@ -455,10 +500,14 @@ def rigid_displacement(theta, H: int, W: int) -> np.ndarray:
     return np.stack([px - x, py - y])
 
 
-def max_px_error(phi_a, phi_b, H: int, W: int, mode: str) -> float:
-    """max over pixels of |phi_a(x) - phi_b(x)|_2."""
+def max_px_error(phi_a, phi_b, H: int, W: int, mode: str, grid: int = 0) -> float:
+    """max over finest-level pixels of |phi_a(x) - phi_b(x)|_2 (nonrigid: control values,
+    or dense [2, H, W] fields)."""
     if mode == "rigid":
         d = rigid_displacement(phi_a, H, W) - rigid_displacement(phi_b, H, W)
     else:
-        d = _f64(phi_a) - _f64(phi_b)
+        g = grid_for(W, H, grid)
+        a = _f64(phi_a) if np.shape(phi_a)[1:] == (H, W) else grid_dense(g, phi_a)
+        b = _f64(phi_b) if np.shape(phi_b)[1:] == (H, W) else grid_dense(g, phi_b)
+        d = a - b
     return float(np.sqrt((d ** 2).sum(axis=0)).max())

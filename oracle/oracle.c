@@ -251,35 +251,73 @@ void or_rigid_register(const double *const *Rp, const double *const *Tp,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Nonrigid extension: phi(x) = x + u(x), u = (ux, uy) on the pixel grid.   */
-/* E = 1 - NCC(R, T o phi) + lambda/(2P) sum |forward differences of u|^2   */
+/* Nonrigid extension (not in the paper): phi(x) = x + u(x) with u a         */
+/* free-form field, bilinear in control displacements c_j on a grid of       */
+/* spacing s (finest-level pixels), points X_j = (jx s, jy s),               */
+/* jx = 0..nx-1, jy = 0..ny-1, nx = ceil((W0-1)/s) + 1.                      */
+/* At level l, pixel x of the level sits at finest coordinate                */
+/* X = 2^l x + (2^l - 1)/2 and the level's control values are c / 2^l        */
+/* (displacements in pixels of that level).                                  */
+/* E = 1 - NCC(R, T o phi) + lambda/(2 P_l) sum over control-grid edges of   */
+/* |c_a - c_b|^2  (c in pixels of the level).                                */
 /* ------------------------------------------------------------------------ */
 
-double or_regulariser(const double *ux, const double *uy, int W, int H, double lambda)
+typedef struct {
+    int nx, ny, s;      /* control grid and spacing (finest pixels) */
+    int W0, H0;         /* finest level size */
+} or_grid_t;
+
+/* Cell and bilinear weights of the finest-level coordinate (X, Y), clamped to the grid. */
+static void or_grid_cell(const or_grid_t *g, double X, double Y, int *jx, int *jy, double *wx, double *wy)
+{
+    double gx = clampd(X / g->s, 0.0, (double)(g->nx - 1));
+    double gy = clampd(Y / g->s, 0.0, (double)(g->ny - 1));
+    int ix = (int)floor(gx), iy = (int)floor(gy);
+    if (ix > g->nx - 2) ix = g->nx - 2;
+    if (iy > g->ny - 2) iy = g->ny - 2;
+    *jx = ix; *jy = iy;
+    *wx = gx - ix; *wy = gy - iy;
+}
+
+/* u at finest coordinate (X, Y) from control values cx, cy ([ny][nx]). */
+static void or_grid_eval(const or_grid_t *g, const double *cx, const double *cy, double X, double Y,
+                         double *ux, double *uy)
+{
+    int jx, jy;
+    double wx, wy;
+    or_grid_cell(g, X, Y, &jx, &jy, &wx, &wy);
+    int i = jy * g->nx + jx;
+    double w00 = (1 - wx) * (1 - wy), w01 = wx * (1 - wy), w10 = (1 - wx) * wy, w11 = wx * wy;
+    *ux = w00 * cx[i] + w01 * cx[i + 1] + w10 * cx[i + g->nx] + w11 * cx[i + g->nx + 1];
+    *uy = w00 * cy[i] + w01 * cy[i + 1] + w10 * cy[i + g->nx] + w11 * cy[i + g->nx + 1];
+}
+
+double or_grid_regulariser(const or_grid_t *g, const double *cx, const double *cy, double lambda, double P)
 {
     double s = 0.0;
-    for (int r = 0; r < H; ++r) {
-        for (int c = 0; c < W; ++c) {
-            int i = r * W + c;
-            if (c + 1 < W) {
-                double ax = ux[i + 1] - ux[i], ay = uy[i + 1] - uy[i];
-                s += ax * ax + ay * ay;
+    for (int jy = 0; jy < g->ny; ++jy) {
+        for (int jx = 0; jx < g->nx; ++jx) {
+            int i = jy * g->nx + jx;
+            if (jx + 1 < g->nx) {
+                double a = cx[i + 1] - cx[i], b = cy[i + 1] - cy[i];
+                s += a * a + b * b;
             }
-            if (r + 1 < H) {
-                double bx = ux[i + W] - ux[i], by = uy[i + W] - uy[i];
-                s += bx * bx + by * by;
+            if (jy + 1 < g->ny) {
+                double a = cx[i + g->nx] - cx[i], b = cy[i + g->nx] - cy[i];
+                s += a * a + b * b;
             }
         }
     }
-    return 0.5 * lambda * s / ((double)W * H);
+    return 0.5 * lambda * s / P;
 }
 
-/* E and, if gx/gy are given, dE/du(x) per pixel. */
-int or_nonrigid_energy(const double *R, const double *T, int W, int H,
-                       const double *ux, const double *uy, double lambda,
-                       double *E, double *gx, double *gy)
+/* Energy at level l (images R, T of that level, W x H) for control values c
+ * given in pixels of that level; gradient dE/dc (same units) if gx/gy given. */
+int or_grid_energy(const double *R, const double *T, int W, int H, int l, const or_grid_t *g,
+                   const double *cx, const double *cy, double lambda, double *E, double *gx, double *gy)
 {
-    const int P = W * H;
+    const int P = W * H, Nc = g->nx * g->ny;
+    const double scale = ldexp(1.0, l), off = 0.5 * (scale - 1.0);
     or_moments_t m = {(double)P, 0, 0, 0, 0, 0};
     double *tw = NULL, *dtx = NULL, *dty = NULL;
     if (gx) {
@@ -290,30 +328,45 @@ int or_nonrigid_energy(const double *R, const double *T, int W, int H,
     for (int r = 0; r < H; ++r) {
         for (int c = 0; c < W; ++c) {
             int i = r * W + c;
-            double s[3];
-            or_sample(T, W, H, c + ux[i], r + uy[i], s);
+            double ux, uy, s[3];
+            or_grid_eval(g, cx, cy, scale * c + off, scale * r + off, &ux, &uy);
+            or_sample(T, W, H, c + ux, r + uy, s);
             double rv = R[i], tv = s[0];
             m.sR += rv; m.sT += tv; m.sRR += rv * rv; m.sTT += tv * tv; m.sRT += rv * tv;
             if (gx) { tw[i] = tv; dtx[i] = s[1]; dty[i] = s[2]; }
         }
     }
     or_ncc_t n = or_ncc(&m);
-    double Ed = n.degenerate ? 1.0 : 1.0 - n.ncc;
-    *E = Ed + or_regulariser(ux, uy, W, H, lambda);
+    *E = (n.degenerate ? 1.0 : 1.0 - n.ncc) + or_grid_regulariser(g, cx, cy, lambda, (double)P);
     if (gx) {
+        for (int j = 0; j < Nc; ++j) { gx[j] = 0.0; gy[j] = 0.0; }
+        if (!n.degenerate) {
+            for (int r = 0; r < H; ++r) {
+                for (int c = 0; c < W; ++c) {
+                    int i = r * W + c, jx, jy;
+                    double wx, wy;
+                    or_grid_cell(g, scale * c + off, scale * r + off, &jx, &jy, &wx, &wy);
+                    double f = -(n.a * (R[i] - n.rbar) - n.b * (tw[i] - n.tbar));
+                    double ax = f * dtx[i], ay = f * dty[i];
+                    int j = jy * g->nx + jx;
+                    double w[4] = {(1 - wx) * (1 - wy), wx * (1 - wy), (1 - wx) * wy, wx * wy};
+                    int idx[4] = {j, j + 1, j + g->nx, j + g->nx + 1};
+                    for (int q = 0; q < 4; ++q) { gx[idx[q]] += w[q] * ax; gy[idx[q]] += w[q] * ay; }
+                }
+            }
+        }
+        /* d/dc_j of lambda/(2P) sum over grid edges |c_a - c_b|^2 */
         const double k = lambda / (double)P;
-        for (int r = 0; r < H; ++r) {
-            for (int c = 0; c < W; ++c) {
-                int i = r * W + c;
-                double f = n.degenerate ? 0.0 : -(n.a * (R[i] - n.rbar) - n.b * (tw[i] - n.tbar));
-                /* d/du(x) of lambda/(2P) sum over grid edges (u(a)-u(b))^2 */
+        for (int jy = 0; jy < g->ny; ++jy) {
+            for (int jx = 0; jx < g->nx; ++jx) {
+                int j = jy * g->nx + jx;
                 double lx = 0.0, ly = 0.0;
-                if (c > 0)     { lx += ux[i] - ux[i - 1]; ly += uy[i] - uy[i - 1]; }
-                if (c + 1 < W) { lx += ux[i] - ux[i + 1]; ly += uy[i] - uy[i + 1]; }
-                if (r > 0)     { lx += ux[i] - ux[i - W]; ly += uy[i] - uy[i - W]; }
-                if (r + 1 < H) { lx += ux[i] - ux[i + W]; ly += uy[i] - uy[i + W]; }
-                gx[i] = f * dtx[i] + k * lx;
-                gy[i] = f * dty[i] + k * ly;
+                if (jx > 0)         { lx += cx[j] - cx[j - 1];     ly += cy[j] - cy[j - 1]; }
+                if (jx + 1 < g->nx) { lx += cx[j] - cx[j + 1];     ly += cy[j] - cy[j + 1]; }
+                if (jy > 0)         { lx += cx[j] - cx[j - g->nx]; ly += cy[j] - cy[j - g->nx]; }
+                if (jy + 1 < g->ny) { lx += cx[j] - cx[j + g->nx]; ly += cy[j] - cy[j + g->nx]; }
+                gx[j] += k * lx;
+                gy[j] += k * ly;
             }
         }
         free(tw); free(dtx); free(dty);
@@ -321,131 +374,113 @@ int or_nonrigid_energy(const double *R, const double *T, int W, int H,
     return n.degenerate;
 }
 
-/* Composition of displacement fields: (phi2 o phi1)(x) = x + u1(x) + u2(x + u1(x)). */
-void or_nonrigid_compose(const double *u1x, const double *u1y,
-                         const double *u2x, const double *u2y, int W, int H,
-                         double *ox, double *oy)
+/* One level of gradient flow for the control values (pixels of level l).
+ * Metric: the mean over control points, <v, w> = (1/Nc) sum v.w, so the
+ * descent direction is d = -Nc dE/dc and tau |d_j| is a move in pixels.    */
+static void or_grid_level(const double *R, const double *T, int W, int H, int l, const or_grid_t *g,
+                          const or_cfg_t *cfg, double *cx, double *cy, or_stats_t *st)
 {
-    for (int r = 0; r < H; ++r) {
-        for (int c = 0; c < W; ++c) {
-            int i = r * W + c;
-            double px = c + u1x[i], py = r + u1y[i], sx[3], sy[3];
-            or_sample(u2x, W, H, px, py, sx);
-            or_sample(u2y, W, H, px, py, sy);
-            ox[i] = u1x[i] + sx[0];
-            oy[i] = u1y[i] + sy[0];
-        }
-    }
-}
-
-/* Coarse-to-fine transfer: a coarse pixel (rc, cc) covers fine pixels 2rc, 2rc+1,
- * so fine pixel (r, c) sits at coarse coordinate ((c - 0.5)/2, (r - 0.5)/2);
- * displacements double.                                                      */
-void or_prolong(const double *src, int Wc, int Hc, double *dst, int W, int H)
-{
-    for (int r = 0; r < H; ++r) {
-        for (int c = 0; c < W; ++c) {
-            double s[3];
-            or_sample(src, Wc, Hc, 0.5 * (c - 0.5), 0.5 * (r - 0.5), s);
-            dst[r * W + c] = 2.0 * s[0];
-        }
-    }
-}
-
-/* Fine-to-coarse transfer of an initial displacement: box average, halved. */
-void or_restrict(const double *src, int W, int H, double *dst)
-{
-    int w2 = (W + 1) / 2, h2 = (H + 1) / 2;
-    or_downsample(src, W, H, dst);
-    for (int i = 0; i < w2 * h2; ++i) dst[i] *= 0.5;
-}
-
-/* One level of gradient flow for the field u.  Metric: the mean-L2 product
- * <v, w> = (1/P) sum v.w, so the descent direction is d = -P dE/du and a
- * step tau moves pixel x by tau |d(x)| pixels.                             */
-static void or_nonrigid_level(const double *R, const double *T, int W, int H,
-                              const or_cfg_t *cfg, double *ux, double *uy,
-                              or_stats_t *st, int lvl)
-{
-    const int P = W * H;
-    double *gx = (double *)malloc(sizeof(double) * P), *gy = (double *)malloc(sizeof(double) * P);
-    double *dx = (double *)malloc(sizeof(double) * P), *dy = (double *)malloc(sizeof(double) * P);
-    double *tx = (double *)malloc(sizeof(double) * P), *ty = (double *)malloc(sizeof(double) * P);
+    const int Nc = g->nx * g->ny;
+    double *gx = (double *)malloc(sizeof(double) * Nc), *gy = (double *)malloc(sizeof(double) * Nc);
+    double *dx = (double *)malloc(sizeof(double) * Nc), *dy = (double *)malloc(sizeof(double) * Nc);
+    double *tx = (double *)malloc(sizeof(double) * Nc), *ty = (double *)malloc(sizeof(double) * Nc);
     double E, Et = 0.0;
-    or_nonrigid_energy(R, T, W, H, ux, uy, cfg->lambda, &E, gx, gy);
-    st->evals[lvl] += 1;
+    or_grid_energy(R, T, W, H, l, g, cx, cy, cfg->lambda, &E, gx, gy);
+    st->evals[l] += 1;
     double tau = cfg->tau0;
     int stop = OR_STOP_MAXIT;
     for (int it = 0; it < cfg->max_iter; ++it) {
         double ss = 0.0, dmax = 0.0;
-        for (int i = 0; i < P; ++i) {
-            dx[i] = -(double)P * gx[i];
-            dy[i] = -(double)P * gy[i];
-            double q = dx[i] * dx[i] + dy[i] * dy[i];
+        for (int j = 0; j < Nc; ++j) {
+            dx[j] = -(double)Nc * gx[j];
+            dy[j] = -(double)Nc * gy[j];
+            double q = dx[j] * dx[j] + dy[j] * dy[j];
             ss += q;
             if (q > dmax) dmax = q;
         }
         dmax = sqrt(dmax);
-        double slope = -ss / (double)P;       /* dE/du . d */
-        double gn = sqrt(ss / (double)P);      /* metric norm of d */
+        double slope = -ss / (double)Nc;
+        double gn = sqrt(ss / (double)Nc);
         if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
         if (tau * dmax > cfg->step_cap) tau = cfg->step_cap / dmax;
         int accepted = 0;
         for (int rej = 0; rej <= cfg->max_rejects; ++rej) {
-            for (int i = 0; i < P; ++i) { tx[i] = ux[i] + tau * dx[i]; ty[i] = uy[i] + tau * dy[i]; }
-            or_nonrigid_energy(R, T, W, H, tx, ty, cfg->lambda, &Et, NULL, NULL);
-            st->evals[lvl] += 1;
+            for (int j = 0; j < Nc; ++j) { tx[j] = cx[j] + tau * dx[j]; ty[j] = cy[j] + tau * dy[j]; }
+            or_grid_energy(R, T, W, H, l, g, tx, ty, cfg->lambda, &Et, NULL, NULL);
+            st->evals[l] += 1;
             if (Et <= E + cfg->armijo_c * tau * slope) { accepted = 1; break; }
             st->rejects += 1;
             tau *= 0.5;
         }
         if (!accepted) { stop = OR_STOP_LS; break; }
-        memcpy(ux, tx, sizeof(double) * P);
-        memcpy(uy, ty, sizeof(double) * P);
-        st->iters[lvl] += 1;
+        memcpy(cx, tx, sizeof(double) * Nc);
+        memcpy(cy, ty, sizeof(double) * Nc);
+        st->iters[l] += 1;
         double Eold = E;
         E = Et;
         tau *= 2.0;
         if (Eold - Et <= cfg->tol_rel_e * fabs(Eold)) { stop = OR_STOP_REL; break; }
-        or_nonrigid_energy(R, T, W, H, ux, uy, cfg->lambda, &E, gx, gy);
-        st->evals[lvl] += 1;
+        or_grid_energy(R, T, W, H, l, g, cx, cy, cfg->lambda, &E, gx, gy);
+        st->evals[l] += 1;
     }
-    st->stop[lvl] = stop;
-    if (lvl == 0) st->energy = E;
+    st->stop[l] = stop;
+    if (l == 0) st->energy = E;
     free(gx); free(gy); free(dx); free(dy); free(tx); free(ty);
 }
 
-/* Multilevel nonrigid registration.  init_x/init_y: finest-level initial
- * displacement (NULL = identity); it is restricted to the coarsest level,
- * and each level's result is prolonged to start the next finer level.     */
-void or_nonrigid_register(const double *const *Rp, const double *const *Tp,
-                          const int *Ws, const int *Hs, const or_cfg_t *cfg,
-                          const double *init_x, const double *init_y,
-                          double *out_x, double *out_y, or_stats_t *st)
+/* Multilevel nonrigid registration on the control grid.  init (finest-level
+ * pixels, NULL = identity) is scaled to the coarsest level by 2^-(L-1); each
+ * finer level starts from twice the coarser result (same grid, exact).     */
+void or_grid_register(const double *const *Rp, const double *const *Tp, const int *Ws, const int *Hs,
+                      const or_cfg_t *cfg, const or_grid_t *g, const double *init_x, const double *init_y,
+                      double *out_x, double *out_y, or_stats_t *st)
 {
-    int L = cfg->levels;
+    const int L = cfg->levels, Nc = g->nx * g->ny;
     memset(st, 0, sizeof(*st));
-    double *ux[OR_MAX_LEVELS] = {0}, *uy[OR_MAX_LEVELS] = {0};
-    for (int l = 0; l < L; ++l) {
-        ux[l] = (double *)calloc((size_t)Ws[l] * Hs[l], sizeof(double));
-        uy[l] = (double *)calloc((size_t)Ws[l] * Hs[l], sizeof(double));
-    }
+    double *cx = (double *)calloc(Nc, sizeof(double)), *cy = (double *)calloc(Nc, sizeof(double));
     if (init_x) {
-        memcpy(ux[0], init_x, sizeof(double) * Ws[0] * Hs[0]);
-        memcpy(uy[0], init_y, sizeof(double) * Ws[0] * Hs[0]);
-        for (int l = 1; l < L; ++l) {
-            or_restrict(ux[l - 1], Ws[l - 1], Hs[l - 1], ux[l]);
-            or_restrict(uy[l - 1], Ws[l - 1], Hs[l - 1], uy[l]);
-        }
+        for (int j = 0; j < Nc; ++j) { cx[j] = ldexp(init_x[j], -(L - 1)); cy[j] = ldexp(init_y[j], -(L - 1)); }
     }
     for (int l = L - 1; l >= 0; --l) {
-        or_nonrigid_level(Rp[l], Tp[l], Ws[l], Hs[l], cfg, ux[l], uy[l], st, l);
-        if (l > 0) {
-            or_prolong(ux[l], Ws[l], Hs[l], ux[l - 1], Ws[l - 1], Hs[l - 1]);
-            or_prolong(uy[l], Ws[l], Hs[l], uy[l - 1], Ws[l - 1], Hs[l - 1]);
+        or_grid_level(Rp[l], Tp[l], Ws[l], Hs[l], l, g, cfg, cx, cy, st);
+        if (l > 0)
+            for (int j = 0; j < Nc; ++j) { cx[j] *= 2.0; cy[j] *= 2.0; }
+    }
+    memcpy(out_x, cx, sizeof(double) * Nc);
+    memcpy(out_y, cy, sizeof(double) * Nc);
+    free(cx); free(cy);
+}
+
+/* Composition at the control points (B's initial guess, Sec. 2.3.2):
+ * c(X_j) = c1_j + u2(X_j + c1_j), u2 the field of c2 (finest-level pixels). */
+void or_grid_compose(const or_grid_t *g, const double *c1x, const double *c1y, const double *c2x,
+                     const double *c2y, double *ox, double *oy)
+{
+    for (int jy = 0; jy < g->ny; ++jy) {
+        for (int jx = 0; jx < g->nx; ++jx) {
+            int j = jy * g->nx + jx;
+            double ux, uy;
+            or_grid_eval(g, c2x, c2y, jx * (double)g->s + c1x[j], jy * (double)g->s + c1y[j], &ux, &uy);
+            ox[j] = c1x[j] + ux;
+            oy[j] = c1y[j] + uy;
         }
     }
-    memcpy(out_x, ux[0], sizeof(double) * Ws[0] * Hs[0]);
-    memcpy(out_y, uy[0], sizeof(double) * Ws[0] * Hs[0]);
-    for (int l = 0; l < L; ++l) { free(ux[l]); free(uy[l]); }
+}
+
+/* Field of level l (W x H pixels of that level) for control values in pixels of that level. */
+void or_grid_level_dense(const or_grid_t *g, const double *cx, const double *cy, int l, int W, int H,
+                         double *ux, double *uy)
+{
+    const double scale = ldexp(1.0, l), off = 0.5 * (scale - 1.0);
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c)
+            or_grid_eval(g, cx, cy, scale * c + off, scale * r + off, &ux[r * W + c], &uy[r * W + c]);
+}
+
+/* Dense finest-level field of the control values. */
+void or_grid_dense(const or_grid_t *g, const double *cx, const double *cy, double *ux, double *uy)
+{
+    for (int r = 0; r < g->H0; ++r)
+        for (int c = 0; c < g->W0; ++c)
+            or_grid_eval(g, cx, cy, (double)c, (double)r, &ux[r * g->W0 + c], &uy[r * g->W0 + c]);
 }

@@ -82,8 +82,8 @@ def test_ncc_energy_equals_corrcoef_at_identity():
     R, T = rand_img(12, 10, 3), rand_img(12, 10, 4)
     E = O.rigid_energy(R, T, [0.0, 0.0, 0.0], grad=False)
     assert E == pytest.approx(1.0 - np.corrcoef(R.ravel(), T.ravel())[0, 1], abs=1e-13)
-    u = np.zeros((2, 12, 10))
-    assert O.nonrigid_energy(R, T, u, 5.0, grad=False) == pytest.approx(E, abs=1e-13)
+    g = O.grid_for(10, 12, 4)
+    assert O.grid_energy(R, T, 0, g, np.zeros((2, g.ny, g.nx)), 5.0, grad=False) == pytest.approx(E, abs=1e-13)
 
 
 def test_ncc_by_hand_on_2x2():
@@ -122,31 +122,56 @@ def test_rigid_gradient_matches_central_differences():
         assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-9), k
 
 
-def test_nonrigid_gradient_matches_central_differences():
-    H, W = 20, 18
-    R, T = synth.translated_pair(H, W, (0.4, -0.3), noise_snr=8.0, seed=12)
+@pytest.mark.parametrize("level", [0, 1])
+def test_grid_gradient_matches_central_differences(level):
+    R0, T0 = synth.translated_pair(40, 36, (0.4, -0.3), noise_snr=8.0, seed=12)
+    pr, pt = O.pyramid(R0, 2), O.pyramid(T0, 2)
+    R, T = pr[level], pt[level]
+    g = O.grid_for(36, 40, 8)
     rng = np.random.default_rng(13)
-    u = rng.uniform(-0.4, 0.4, size=(2, H, W)) + np.array([0.3, -0.2])[:, None, None]
+    c = rng.uniform(-0.4, 0.4, size=(2, g.ny, g.nx)) + np.array([0.3, -0.2])[:, None, None]
     lam = 3.0
-    E, g = O.nonrigid_energy(R, T, u, lam)
+    E, gr = O.grid_energy(R, T, level, g, c, lam)
     h = 1e-6
-    pts = [(0, 0, 0), (1, 5, 7), (0, H - 1, W - 1), (1, 0, W - 1), (0, 11, 3), (1, H - 1, 4)]
-    for (cmp, r, c) in pts:
-        up, um = u.copy(), u.copy()
-        up[cmp, r, c] += h; um[cmp, r, c] -= h
-        fd = (O.nonrigid_energy(R, T, up, lam, grad=False) - O.nonrigid_energy(R, T, um, lam, grad=False)) / (2 * h)
-        assert g[cmp, r, c] == pytest.approx(fd, rel=1e-5, abs=1e-10), (cmp, r, c)
+    for (cmp, jy, jx) in [(0, 0, 0), (1, 2, 3), (0, g.ny - 1, g.nx - 1), (1, 0, g.nx - 1), (0, 3, 1)]:
+        cp, cm = c.copy(), c.copy()
+        cp[cmp, jy, jx] += h; cm[cmp, jy, jx] -= h
+        fd = (O.grid_energy(R, T, level, g, cp, lam, grad=False) - O.grid_energy(R, T, level, g, cm, lam, grad=False)) / (2 * h)
+        assert gr[cmp, jy, jx] == pytest.approx(fd, rel=1e-5, abs=1e-10), (cmp, jy, jx)
 
 
-def test_regulariser_closed_form_on_ramp():
-    # u_x = a * column, u_y = b * row: every horizontal edge of u_x differs by a,
-    # every vertical edge of u_y by b; the other differences vanish.
-    H, W, a, b, lam = 6, 9, 0.3, -0.7, 2.5
-    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
-    u = np.stack([a * x, b * y])
-    P = H * W
-    exp = 0.5 * lam / P * (a * a * (W - 1) * H + b * b * (H - 1) * W)
-    assert O.regulariser(u, lam) == pytest.approx(exp, rel=1e-14)
+def test_grid_regulariser_closed_form_on_ramp():
+    # c_x = a * jx, c_y = b * jy: every horizontal edge of c_x differs by a, every vertical edge of c_y by b
+    g = O.grid_for(57, 41, 8)
+    a, b, lam, P = 0.3, -0.7, 2.5, 57 * 41
+    jy, jx = np.mgrid[0:g.ny, 0:g.nx].astype(np.float64)
+    c = np.stack([a * jx, b * jy])
+    exp = 0.5 * lam / P * (a * a * (g.nx - 1) * g.ny + b * b * (g.ny - 1) * g.nx)
+    assert O.grid_regulariser(g, c, lam, P) == pytest.approx(exp, rel=1e-14)
+
+
+def test_grid_field_interpolates_control_points_and_affine_fields():
+    g = O.grid_for(50, 34, 8)           # points at 0, 8, .., 56 > 49: the last cell extends past the frame
+    rng = np.random.default_rng(14)
+    c = rng.uniform(-1, 1, size=(2, g.ny, g.nx))
+    u = O.grid_dense(g, c)
+    for jy in range(g.ny):
+        for jx in range(g.nx):
+            if jy * 8 < 34 and jx * 8 < 50:
+                np.testing.assert_allclose(u[:, jy * 8, jx * 8], c[:, jy, jx], atol=1e-14)
+    # affine field u(X) = A X + b is reproduced exactly, at level 0 and at level 1 where pixel x sits at
+    # X = 2x + 1/2 and the level's values are halved
+    A = np.array([[0.01, -0.02], [0.03, 0.005]]); bb = np.array([0.7, -1.1])
+    jy, jx = np.mgrid[0:g.ny, 0:g.nx].astype(np.float64)
+    ca = np.stack([A[0, 0] * 8 * jx + A[0, 1] * 8 * jy + bb[0], A[1, 0] * 8 * jx + A[1, 1] * 8 * jy + bb[1]])
+    Y, X = np.mgrid[0:34, 0:50].astype(np.float64)
+    np.testing.assert_allclose(O.grid_dense(g, ca), np.stack([A[0, 0] * X + A[0, 1] * Y + bb[0],
+                                                              A[1, 0] * X + A[1, 1] * Y + bb[1]]), atol=1e-12)
+    y1, x1 = np.mgrid[0:17, 0:25].astype(np.float64)
+    X1, Y1 = 2 * x1 + 0.5, 2 * y1 + 0.5
+    lvl = O.grid_level_dense(g, ca / 2, 1, 17, 25)
+    np.testing.assert_allclose(lvl, 0.5 * np.stack([A[0, 0] * X1 + A[0, 1] * Y1 + bb[0],
+                                                    A[1, 0] * X1 + A[1, 1] * Y1 + bb[1]]), atol=1e-12)
 
 
 # ---------------------------------------------------------------- identical frames
@@ -183,12 +208,14 @@ def test_nonrigid_recovers_smooth_field():
     ser = synth.make_series(synth.SeriesSpec(2, 96, 96, step=2.0, field_amp=1.0, snr=(10, 10),
                                              field_rate=(0.8, 1.2), seed=31))
     F = ser.frames.numpy()
-    cfg = O.Config(levels=2, mode="nonrigid", lam=4.0)
-    u, st = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, cfg)
+    cfg = O.Config(levels=2, mode="nonrigid")
+    c, st = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, cfg)
+    u = O.grid_dense(O.grid_for(96, 96), c)
     err = (u - ser.truth_field(1))[:, 12:-12, 12:-12]
     assert np.sqrt((err ** 2).sum(0).mean()) <= 0.1
     # and the field moved away from a pure translation where the truth does
-    assert np.abs(ser.truth_field(1) - ser.truth_field(1).mean(axis=(1, 2), keepdims=True)).max() > 0.1
+    tf = ser.truth_field(1)
+    assert np.abs(tf - tf.mean(axis=(1, 2), keepdims=True)).max() > 0.1
 
 
 # ---------------------------------------------------------------- brute force
@@ -243,31 +270,17 @@ def test_rigid_composition_associative_with_identity():
     np.testing.assert_allclose(O.compose_rigid(np.zeros(3), a), a, atol=0)
 
 
-def test_nonrigid_composition_of_translations_and_linear_fields():
-    H, W = 10, 12
-    t1 = np.broadcast_to(np.array([0.7, -1.2])[:, None, None], (2, H, W)).copy()
-    t2 = np.broadcast_to(np.array([-0.2, 0.4])[:, None, None], (2, H, W)).copy()
-    np.testing.assert_allclose(O.compose_nonrigid(t1, t2), t1 + t2, atol=1e-14)
-    # u2 linear in x: u2(p) = (0.1 px, 0): composition gives u1 + 0.1 (x + u1_x) where in range
-    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
-    u2 = np.stack([0.1 * x, np.zeros_like(x)])
-    c = O.compose_nonrigid(t1 * 0.5, u2)
-    inside = (x + 0.35 <= W - 1)
-    np.testing.assert_allclose(c[0][inside], (0.35 + 0.1 * (x + 0.35))[inside], atol=1e-12)
-
-
-def test_prolong_and_restrict_on_affine_fields():
-    Hc, Wc = 6, 7
-    y, x = np.mgrid[0:Hc, 0:Wc].astype(np.float64)
-    uc = 0.3 * x - 0.2 * y + 1.0
-    f = O.prolong(uc, 2 * Hc, 2 * Wc)
-    Y, X = np.mgrid[0:2 * Hc, 0:2 * Wc].astype(np.float64)
-    exp = 2.0 * (0.3 * (X - 0.5) / 2 - 0.2 * (Y - 0.5) / 2 + 1.0)
-    interior = (X >= 1) & (X <= 2 * Wc - 2) & (Y >= 1) & (Y <= 2 * Hc - 2)
-    np.testing.assert_allclose(f[interior], exp[interior], atol=1e-12)
-    # restriction of the prolonged affine field returns the coarse field (halved twice-doubled)
-    back = O.restrict(f)
-    np.testing.assert_allclose(back[1:-1, 1:-1], uc[1:-1, 1:-1], atol=1e-12)
+def test_grid_composition_of_translations_and_linear_fields():
+    g = O.grid_for(40, 33, 8)
+    t1 = np.broadcast_to(np.array([0.7, -1.2])[:, None, None], (2, g.ny, g.nx)).copy()
+    t2 = np.broadcast_to(np.array([-0.2, 0.4])[:, None, None], (2, g.ny, g.nx)).copy()
+    np.testing.assert_allclose(O.compose_grid(g, t1, t2), t1 + t2, atol=1e-14)
+    # u2(X) = (0.1 X, 0): composition at control point X_j is c1_j + 0.1 (X_j + c1_jx) inside the grid
+    jy, jx = np.mgrid[0:g.ny, 0:g.nx].astype(np.float64)
+    u2 = np.stack([0.1 * 8 * jx, np.zeros_like(jx)])
+    c = O.compose_grid(g, 0.5 * t1, u2)
+    inside = (8 * jx + 0.35 <= 8 * (g.nx - 1))
+    np.testing.assert_allclose(c[0][inside], (0.35 + 0.1 * (8 * jx + 0.35))[inside], atol=1e-12)
 
 
 # ---------------------------------------------------------------- scan DAGs
@@ -330,7 +343,7 @@ def test_table5_work_counts():
 def test_operator_associativity_on_tiny_series(mode):
     spec = synth.SeriesSpec(4, 64, 64, step=1.5, field_amp=0.5, snr=(10, 10), seed=61)
     F = synth.make_series(spec).frames.numpy()
-    cfg = O.Config(levels=2, mode=mode, lam=4.0)
+    cfg = O.Config(levels=2, mode=mode)
     pyrs = [O.pyramid(f, 2) for f in F]
     a, b, c = (O.op_A(pyrs, i, i + 1, cfg) for i in range(3))
     left = O.op_B(O.op_B(a, b, pyrs, cfg), c, pyrs, cfg)
