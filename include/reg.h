@@ -15,9 +15,12 @@
  * Deformation models:
  *   REG_RIGID     phi(x) = Rot(alpha) (x - c) + c + G, c = ((W-1)/2, (H-1)/2),
  *                 pixel (r, c) at x = (c, r)                         [Sec. 2.3.1]
- *   REG_NONRIGID  phi(x) = x + u(x), u a dense 2-channel field, energy
- *                 1 - NCC + lambda/(2P) sum_edges |u(a) - u(b)|^2 (an extension:
- *                 the paper's deformation is rigid)
+ *   REG_NONRIGID  phi(x) = x + u(x), u bilinear in control displacements c_j on
+ *                 a grid of spacing s (finest pixels) at points (jx s, jy s),
+ *                 jx < nx = ceil((W-1)/s) + 1; energy 1 - NCC + lambda/(2P) sum over
+ *                 control-grid edges |c_a - c_b|^2 (an extension: the paper's
+ *                 deformation is rigid).  Control values are stored as (x, y) float
+ *                 pairs, row-major [ny][nx]; dense fields as planes [2][H][W].
  *
  * Conventions common to every entry point:
  *   - Return value: REG_OK (0) or a negative REG_E* code; reg_strerror()
@@ -104,6 +107,8 @@ typedef struct {
     int    cluster;       /* CTAs cooperating on one operator (1,2,4,8,16); 0 = auto */
     int    workers;       /* persistent executor: operator slots in flight; 0 = auto */
     size_t mem_budget;    /* stream service: device bytes it may hold; 0 = unlimited */
+    int    grid;          /* REG_NONRIGID control-grid spacing in finest pixels; 0 = auto (16,
+                             doubled until at most 65 points per axis); a multiple of 2^(levels-1) */
 } reg_config_t;
 
 typedef struct {
@@ -214,19 +219,23 @@ int reg_pyramid(reg_ctx_t *ctx, const float *frame, int W, int H, int pitch,
                 int levels, int storage, void *out, void *stream);
 
 /* Energy and gradient at a given deformation (one fused warp+reduction pass,
- * as used inside the iteration) [Sec. 2.3.1].  R, T device fp32 [H][W].
+ * as used inside the iteration) [Sec. 2.3.1].  R, T device or host fp32 [H][W].
  *   REG_RIGID:    theta[3] (host) = (alpha, Gx, Gy); grad[3] (host, optional).
- *   REG_NONRIGID: field [2][H][W] device; grad_field [2][H][W] device optional
- *                 (dE/du per pixel).  lambda from the context configuration.
+ *   REG_NONRIGID: grid_values: control values [ny][nx] (x, y) pairs, device;
+ *                 grad_values: dE/dc in the same layout, device, optional.
+ *                 lambda and grid spacing from the context configuration.
  *   energy (host): E. */
 int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W, int H,
-               const double *theta, const float *field, double *energy,
-               double *grad, float *grad_field, void *stream);
+               const double *theta, const float *grid_values, double *energy,
+               double *grad, float *grad_values, void *stream);
 
-/* Nonrigid composition (B's initial guess, Sec. 2.3.2):
- * out(x) = u1(x) + u2(x + u1(x)), bilinear with clamp. Device [2][H][W] each. */
-int reg_compose_field(reg_ctx_t *ctx, const float *u1, const float *u2, int W, int H,
-                      float *out, void *stream);
+/* Control grid of a W x H frame for spacing `grid` (0 = auto) and `levels` (host only). */
+int reg_grid_dims(int W, int H, int grid, int levels, int *nx, int *ny, int *spacing);
+
+/* Nonrigid composition at the control points (B's initial guess, Sec. 2.3.2):
+ * out_j = q1_j + u2(X_j + q1_j), u2 the field of q2.  Device [ny][nx] (x, y) pairs. */
+int reg_compose_grid(reg_ctx_t *ctx, const float *q1, const float *q2, int W, int H,
+                     float *out, void *stream);
 
 /* ---- streaming service ----------------------------------------------------- */
 

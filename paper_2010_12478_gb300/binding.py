@@ -27,7 +27,7 @@ MAX_LEVELS = 8
 
 # every symbol include/reg.h declares
 EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairwise", "reg_scan",
-           "reg_scan_work", "reg_scan_dag", "reg_pyramid", "reg_energy", "reg_compose_field",
+           "reg_scan_work", "reg_scan_dag", "reg_pyramid", "reg_energy", "reg_compose_grid", "reg_grid_dims",
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
            "reg_pairwise_noalloc"]
@@ -49,7 +49,7 @@ class reg_config_t(ctypes.Structure):
                 ("max_rejects", ctypes.c_int), ("tol_grad", ctypes.c_double), ("tol_rel_e", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double), ("step_cap", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("storage", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t)]
+                ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("grid", ctypes.c_int)]
 
 
 class reg_stats_t(ctypes.Structure):
@@ -90,7 +90,8 @@ def lib() -> ctypes.CDLL:
         L.reg_scan_dag.argtypes = [ip, ip, vp, vp, vp]
         L.reg_pyramid.argtypes = [vp, fp, ip, ip, ip, ip, ip, vp, vp]
         L.reg_energy.argtypes = [vp, fp, fp, ip, ip, dp, fp, dp, dp, fp, vp]
-        L.reg_compose_field.argtypes = [vp, fp, fp, ip, ip, fp, vp]
+        L.reg_compose_grid.argtypes = [vp, fp, fp, ip, ip, fp, vp]
+        L.reg_grid_dims.argtypes = [ip, ip, ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
         L.reg_stream_open.argtypes = [vp, ip, ip, ctypes.POINTER(vp)]
         L.reg_stream_submit.argtypes = [vp, fp, ctypes.c_uint64]
         L.reg_stream_poll.argtypes = [vp, ctypes.POINTER(reg_result_t), ip, ctypes.POINTER(ctypes.c_int), ip]
@@ -141,17 +142,18 @@ class Config:
     armijo_c: float = 1e-4
     tau0: float = 1.0
     step_cap: float = 0.5
-    lam: float = 4.0
+    lam: float = 2.0
     storage: str = "f32"
     cluster: int = 0
     workers: int = 0
     mem_budget: int = 0
+    grid: int = 0
 
     def c(self) -> reg_config_t:
         return reg_config_t(RIGID if self.mode == "rigid" else NONRIGID, self.levels, self.max_iter,
                             self.max_rejects, self.tol_grad, self.tol_rel_e, self.armijo_c, self.tau0,
                             self.step_cap, self.lam, STORAGES[self.storage], self.cluster, self.workers,
-                            self.mem_budget)
+                            self.mem_budget, self.grid)
 
 
 def stats_dict(s: reg_stats_t, levels: int) -> dict:
@@ -246,16 +248,23 @@ class Context:
               "reg_energy")
         return E.value, np.array(list(g))
 
-    def energy_field(self, R, T, field, grad_field=None):
+    def energy_grid(self, R, T, values, grad_values=None):
+        """E (and dE/dc into grad_values) at control values [ny, nx, 2] (device)."""
         H, W = R.shape
         E = ctypes.c_double()
-        check(lib().reg_energy(self.h, _ptr(R), _ptr(T), W, H, None, _ptr(field), ctypes.byref(E), None,
-                               _ptr(grad_field), None), "reg_energy")
+        check(lib().reg_energy(self.h, _ptr(R), _ptr(T), W, H, None, _ptr(values), ctypes.byref(E), None,
+                               _ptr(grad_values), None), "reg_energy")
         return E.value
 
-    def compose_field(self, u1, u2, out):
-        _, H, W = u1.shape
-        check(lib().reg_compose_field(self.h, _ptr(u1), _ptr(u2), W, H, _ptr(out), None), "reg_compose_field")
+    def compose_grid(self, q1, q2, W: int, H: int, out):
+        check(lib().reg_compose_grid(self.h, _ptr(q1), _ptr(q2), W, H, _ptr(out), None), "reg_compose_grid")
+
+
+def grid_dims(W: int, H: int, grid: int = 0, levels: int = 2):
+    nx, ny, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().reg_grid_dims(W, H, grid, levels, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(sp)),
+          "reg_grid_dims")
+    return nx.value, ny.value, sp.value
 
 
 def pairwise_noalloc(cfg: Config, R, T, init: Optional[Sequence[float]] = None, device: int = 0, stream=None):

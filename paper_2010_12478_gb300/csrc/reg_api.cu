@@ -245,7 +245,7 @@ struct reg_ctx {
     // workspaces
     DevBuf frames_dev;      // host-supplied frames staged on the device
     DevBuf pyr[kMaxLevels]; // pyramid levels of all frames
-    DevBuf means, level_tab, ops, stats, node_theta, node_field, scratch, status;
+    DevBuf means, level_tab, ops, stats, node_theta, node_grid, status, node_ids;
     DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr;
     DevBuf tmp;
     cudaStream_t pool[16] = {};
@@ -273,7 +273,8 @@ extern "C" void reg_config_default(reg_config_t *c)
     c->armijo_c = 1e-4;
     c->tau0 = 1.0;
     c->step_cap = 0.5;
-    c->lambda = 4.0;
+    c->lambda = 2.0;
+    c->grid = 0;
     c->storage = REG_F32;
     c->cluster = 0;
     c->workers = 0;
@@ -292,6 +293,7 @@ static int validate_cfg(const reg_config_t &c)
     if (c.cluster != 0 && c.cluster != 1 && c.cluster != 2 && c.cluster != 4 && c.cluster != 8 && c.cluster != 16)
         return fail(REG_EINVAL, "cluster %d not in {0,1,2,4,8,16}", c.cluster);
     if (c.lambda < 0) return fail(REG_EINVAL, "lambda < 0");
+    if (c.grid < 0) return fail(REG_EINVAL, "grid < 0");
     return REG_OK;
 }
 
@@ -395,6 +397,29 @@ int geometry(int W, int H, int levels, Geometry &g)
         w = (w + 1) / 2;
         h = (h + 1) / 2;
     }
+    return REG_OK;
+}
+
+struct GridDims {
+    int nx, ny, s;
+};
+
+// Control grid of the nonrigid field: spacing 16 finest pixels doubled until at most 65 points per
+// axis (grid == 0), or the configured spacing; every level needs a spacing of at least one pixel.
+int grid_dims(int W, int H, int grid, int levels, GridDims &g)
+{
+    if (grid < 0) return fail(REG_EINVAL, "grid spacing %d < 0", grid);
+    int sp = grid > 0 ? grid : 16;
+    if (grid == 0)
+        while ((W - 1 + sp - 1) / sp + 1 > 65 || (H - 1 + sp - 1) / sp + 1 > 65) sp *= 2;
+    g.s = sp;
+    g.nx = (W - 1 + sp - 1) / sp + 1;
+    g.ny = (H - 1 + sp - 1) / sp + 1;
+    if (g.nx < 2 || g.ny < 2) return fail(REG_EINVAL, "control grid needs >= 2x2 points");
+    if ((sp >> (levels - 1)) < 1 || (sp & ((1 << (levels - 1)) - 1)) != 0)
+        return fail(REG_EINVAL, "grid spacing %d must be a multiple of 2^(levels-1)", sp);
+    if ((size_t)g.nx * g.ny * 4 * 8 > 200 * 1024)
+        return fail(REG_EINVAL, "control grid %dx%d does not fit shared memory; use a larger spacing", g.nx, g.ny);
     return REG_OK;
 }
 
@@ -551,9 +576,8 @@ int ensure_op_events(reg_ctx *ctx, size_t n)
     return REG_OK;
 }
 
-// Allocate node storage, stats and nonrigid scratch; fill Params.
-int prepare_params(reg_ctx *ctx, const Geometry &g, int n_frames, int n_nodes, int n_ops, int slots, Params &p,
-                   cudaStream_t s)
+// Allocate node storage and stats; fill Params.
+int prepare_params(reg_ctx *ctx, const Geometry &g, int n_frames, int n_nodes, int n_ops, Params &p, cudaStream_t s)
 {
     memset(&p, 0, sizeof(p));
     p.cfg = dev_config(ctx->cfg);
@@ -572,12 +596,13 @@ int prepare_params(reg_ctx *ctx, const Geometry &g, int n_frames, int n_nodes, i
     CU(cudaMemsetAsync(p.status, 0, sizeof(int) * 4, s));
     CU(cudaMemsetAsync(p.stats, 0, sizeof(OpStats) * std::max(1, n_ops), s));
     if (ctx->cfg.mode == REG_NONRIGID) {
-        const size_t P0 = (size_t)g.W[0] * g.H[0];
-        CHECK(ctx->node_field.reserve(sizeof(float) * 2 * P0 * std::max(1, n_nodes)));
-        p.node_field = ctx->node_field.as<float>();
-        p.scratch_floats = scratch_floats_per_slot(g.W, g.H, g.levels);
-        CHECK(ctx->scratch.reserve(sizeof(float) * p.scratch_floats * std::max(1, slots)));
-        p.scratch = ctx->scratch.as<float>();
+        GridDims gd;
+        CHECK(grid_dims(g.W[0], g.H[0], ctx->cfg.grid, g.levels, gd));
+        p.gnx = gd.nx;
+        p.gny = gd.ny;
+        p.gs = gd.s;
+        CHECK(ctx->node_grid.reserve(sizeof(float2) * (size_t)gd.nx * gd.ny * std::max(1, n_nodes)));
+        p.node_grid = ctx->node_grid.as<float2>();
     }
     return REG_OK;
 }
@@ -603,8 +628,7 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
         for (int dpt = 0; dpt < n_depth; ++dpt) {
             int b = plan.depth_start[dpt], e = plan.depth_start[dpt + 1];
             int C = auto_cluster(ctx, e - b);
-            int chunk = nonrigid ? (int)(ctx->scratch.bytes / (sizeof(float) * p.scratch_floats)) : (e - b);
-            chunk = std::max(1, chunk);
+            int chunk = std::max(1, e - b);
             for (int q = b; q < e; q += chunk) {
                 p.op_base = q;
                 int e0 = timing_mark(ctx, s);
@@ -634,8 +658,6 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
             }
             Params q = p;
             q.op_base = e;
-            // one scratch slot per pool stream: operators on a stream run in order
-            q.scratch = p.scratch ? p.scratch + (size_t)lane * p.scratch_floats : nullptr;
             CU(launch_ops(q, storage, C, 1, ls));
             CU(cudaEventRecord(ctx->op_events[e], ls));
             ctx->last.op_launches += 1;
@@ -695,7 +717,6 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
         p.queue.timeout_ns = 20LL * 1000 * 1000 * 1000;
         const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 2;
         int workers = ctx->cfg.workers > 0 ? ctx->cfg.workers : std::max(1, 2 * ctx->num_sms / C);
-        if (nonrigid) workers = std::min(workers, (int)(ctx->scratch.bytes / (sizeof(float) * p.scratch_floats)));
         workers = std::max(1, std::min(workers, n_ops));
         p.op_base = 0;
         int e0 = timing_mark(ctx, s);
@@ -712,16 +733,6 @@ int copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
     if (!dst) return REG_OK;
     CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
     return REG_OK;
-}
-
-int scratch_slots_for(reg_ctx *ctx, int exec, int n_ops)
-{
-    if (ctx->cfg.mode != REG_NONRIGID) return 0;
-    if (exec == REG_EXEC_PLAIN) return 16;
-    int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 2;
-    int cap = exec == REG_EXEC_PERSISTENT ? (ctx->cfg.workers > 0 ? ctx->cfg.workers : 2 * ctx->num_sms / C)
-                                          : 4 * ctx->num_sms;
-    return std::max(1, std::min(n_ops, cap));
 }
 
 }  // namespace
@@ -742,6 +753,10 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     cudaStream_t s = (cudaStream_t)stream;
     Geometry g;
     CHECK(geometry(W, H, ctx->cfg.levels, g));
+    if (ctx->cfg.mode == REG_NONRIGID) {
+        GridDims gd;
+        CHECK(grid_dims(W, H, ctx->cfg.grid, ctx->cfg.levels, gd));
+    }
     Dag dag;
     if (!make_dag(schedule, N - 1, dag)) return fail(REG_EINVAL, "schedule %d", schedule);
     ScanPlan plan;
@@ -760,7 +775,7 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
 
     const int n_ops = (int)plan.ops.size();
     Params p;
-    CHECK(prepare_params(ctx, g, N, plan.n_nodes, n_ops, scratch_slots_for(ctx, exec, n_ops), p, s));
+    CHECK(prepare_params(ctx, g, N, plan.n_nodes, n_ops, p, s));
     CU(cudaMemcpyAsync(ctx->ops.ptr, plan.ops.data(), sizeof(OpDesc) * n_ops, cudaMemcpyHostToDevice, s));
     CHECK(execute(ctx, plan, p, exec, s));
     CU(cudaGetLastError());
@@ -784,9 +799,18 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     }
     CHECK(copy_out(out, el.data(), sizeof(reg_elem_t) * n, s));
     if (ctx->cfg.mode == REG_NONRIGID) {
+        // dense finest-level fields of the prefixes, written by one kernel
+        CHECK(ctx->node_ids.reserve(sizeof(int) * n));
+        CU(cudaMemcpyAsync(ctx->node_ids.ptr, plan.out_nodes.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
         const size_t fb = sizeof(float) * 2 * (size_t)W * H;
-        for (int i = 0; i < n; ++i)
-            CHECK(copy_out((char *)fields_out + fb * i, (const char *)p.node_field + fb * plan.out_nodes[i], fb, s));
+        float *dst = (float *)fields_out;
+        const bool direct = is_device_ptr(fields_out);
+        if (!direct) {
+            CHECK(ctx->frames_dev.reserve(fb * n + (size_t)sizeof(float) * N * H * pitch));
+            dst = (float *)((char *)ctx->frames_dev.ptr + (size_t)sizeof(float) * N * H * pitch);
+        }
+        CU(launch_grid_dense(p.node_grid, ctx->node_ids.as<int>(), n, p.gnx, p.gny, p.gs, W, H, dst, s));
+        if (!direct) CU(cudaMemcpyAsync(fields_out, dst, fb * n, cudaMemcpyDeviceToHost, s));
     }
     if (per_op) {
         for (int e = 0; e < n_ops; ++e) memcpy(&per_op[plan.user_index[e]], &st[e], sizeof(reg_stats_t));
@@ -815,7 +839,8 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     CHECK(geometry(W, H, ctx->cfg.levels, g));
     timing_reset(ctx);
     const size_t fbytes = sizeof(float) * (size_t)H * pitch;
-    CHECK(ctx->frames_dev.reserve(2 * fbytes));
+    // staged R and T, then (nonrigid) one dense field for the initial guess or the result
+    CHECK(ctx->frames_dev.reserve(2 * fbytes + (nonrigid ? sizeof(float) * 2 * (size_t)W * H : 0)));
     float *stage = ctx->frames_dev.as<float>();
     const float *src[2] = {R, T};
     for (int f = 0; f < 2; ++f) {
@@ -824,14 +849,17 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     CHECK(build_pyramids(ctx, g, stage, 2, (size_t)H * pitch, pitch, 0, 2, s));
     CHECK(build_level_table(ctx, g, 2, s));
     Params p;
-    CHECK(prepare_params(ctx, g, 2, 2, 1, 1, p, s));
+    CHECK(prepare_params(ctx, g, 2, 2, 1, p, s));
     const bool has_init = nonrigid ? field_in != nullptr : init != nullptr;
     OpDesc op{0, 1, -1, -1, 0, has_init ? 1 : -1};
     CU(cudaMemcpyAsync(ctx->ops.ptr, &op, sizeof(op), cudaMemcpyHostToDevice, s));
     if (has_init) {
         if (nonrigid) {
+            // dense initial field -> control values sampled at the control points (node 1)
             const size_t fb = sizeof(float) * 2 * (size_t)W * H;
-            CU(cudaMemcpyAsync((char *)p.node_field + fb, field_in, fb, cudaMemcpyDefault, s));
+            float *u = (float *)((char *)ctx->frames_dev.ptr + 2 * fbytes);
+            CU(cudaMemcpyAsync(u, field_in, fb, cudaMemcpyDefault, s));
+            CU(launch_grid_from_dense(u, W, H, p.gnx, p.gny, p.gs, p.node_grid + (size_t)p.gnx * p.gny, s));
         } else {
             double th[3] = {init->alpha, init->gx, init->gy};
             CU(cudaMemcpyAsync(p.node_theta + 3, th, sizeof(th), cudaMemcpyHostToDevice, s));
@@ -850,7 +878,14 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     OpStats st;
     CU(cudaMemcpyAsync(th, p.node_theta, sizeof(th), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(&st, p.stats, sizeof(st), cudaMemcpyDeviceToHost, s));
-    if (nonrigid) CHECK(copy_out(field_out, p.node_field, sizeof(float) * 2 * (size_t)W * H, s));
+    if (nonrigid) {
+        const size_t fb = sizeof(float) * 2 * (size_t)W * H;
+        CHECK(ctx->node_ids.reserve(sizeof(int)));
+        CU(cudaMemsetAsync(ctx->node_ids.ptr, 0, sizeof(int), s));
+        float *u = (float *)((char *)ctx->frames_dev.ptr + 2 * fbytes);
+        CU(launch_grid_dense(p.node_grid, ctx->node_ids.as<int>(), 1, p.gnx, p.gny, p.gs, W, H, u, s));
+        CHECK(copy_out(field_out, u, fb, s));
+    }
     CU(cudaStreamSynchronize(s));
     timing_resolve(ctx);
     out->i = 0;
@@ -891,13 +926,14 @@ extern "C" int reg_pyramid(reg_ctx_t *ctx, const float *frame, int W, int H, int
 }
 
 extern "C" int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W, int H, const double *theta,
-                          const float *field, double *energy, double *grad, float *grad_field, void *stream)
+                          const float *grid_values, double *energy, double *grad, float *grad_values, void *stream)
 {
     if (!ctx || !R || !T || !energy) return fail(REG_EINVAL, "NULL argument");
     const bool nonrigid = ctx->cfg.mode == REG_NONRIGID;
-    if (nonrigid ? !field : !theta) return fail(REG_EINVAL, "deformation is NULL");
+    if (nonrigid ? !grid_values : !theta) return fail(REG_EINVAL, "deformation is NULL");
     if (W < 2 || H < 2) return fail(REG_EINVAL, "W, H >= 2");
-    if (grad_field && !is_device_ptr(grad_field)) return fail(REG_EINVAL, "grad_field must be device memory");
+    if (nonrigid && (!is_device_ptr(grid_values) || (grad_values && !is_device_ptr(grad_values))))
+        return fail(REG_EINVAL, "control values and their gradient must be device memory");
     std::lock_guard<std::mutex> lock(ctx->mu);
     CU(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -916,13 +952,12 @@ extern "C" int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W,
         rc = build_pyramids(ctx, g, stage, 2, (size_t)W * H, W, 0, 2, s);
     }
     if (rc == REG_OK) rc = build_level_table(ctx, g, 2, s);
-    if (rc == REG_OK) rc = prepare_params(ctx, g, 2, 1, 1, 1, p, s);
+    if (rc == REG_OK) rc = prepare_params(ctx, g, 2, 1, 1, p, s);
     if (rc == REG_OK) rc = ctx->tmp.reserve(sizeof(double) * 8);
     if (rc == REG_OK) {
         double *dv = ctx->tmp.as<double>();
         if (!nonrigid) cudaMemcpyAsync(dv + 4, theta, sizeof(double) * 3, cudaMemcpyHostToDevice, s);
-        else cudaMemcpyAsync(p.scratch, field, 2 * fbytes, cudaMemcpyDefault, s);   // U_0 of slot 0, level 0
-        cudaError_t e = launch_energy(p, REG_F32, dv + 4, field, dv, grad_field, s);
+        cudaError_t e = launch_energy(p, REG_F32, dv + 4, (const float2 *)grid_values, dv, (float2 *)grad_values, s);
         double res[4] = {0, 0, 0, 0};
         if (e == cudaSuccess) e = cudaMemcpyAsync(res, dv, sizeof(res), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -936,15 +971,29 @@ extern "C" int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W,
     return rc;
 }
 
-extern "C" int reg_compose_field(reg_ctx_t *ctx, const float *u1, const float *u2, int W, int H, float *out,
-                                 void *stream)
+extern "C" int reg_grid_dims(int W, int H, int grid, int levels, int *nx, int *ny, int *spacing)
 {
-    if (!ctx || !u1 || !u2 || !out) return fail(REG_EINVAL, "NULL argument");
+    if (levels < 1 || levels > kMaxLevels) return fail(REG_EINVAL, "levels %d", levels);
+    GridDims g;
+    CHECK(grid_dims(W, H, grid, levels, g));
+    if (nx) *nx = g.nx;
+    if (ny) *ny = g.ny;
+    if (spacing) *spacing = g.s;
+    return REG_OK;
+}
+
+extern "C" int reg_compose_grid(reg_ctx_t *ctx, const float *q1, const float *q2, int W, int H, float *out,
+                                void *stream)
+{
+    if (!ctx || !q1 || !q2 || !out) return fail(REG_EINVAL, "NULL argument");
     if (W < 2 || H < 2) return fail(REG_EINVAL, "W, H >= 2");
-    if (!is_device_ptr(u1) || !is_device_ptr(u2) || !is_device_ptr(out))
-        return fail(REG_EINVAL, "u1, u2 and out must be device memory");
+    if (!is_device_ptr(q1) || !is_device_ptr(q2) || !is_device_ptr(out))
+        return fail(REG_EINVAL, "q1, q2 and out must be device memory");
+    GridDims g;
+    CHECK(grid_dims(W, H, ctx->cfg.grid, ctx->cfg.levels, g));
     CU(cudaSetDevice(ctx->device));
-    CU(launch_compose(u1, u2, W, H, out, (cudaStream_t)stream));
+    CU(launch_grid_compose((const float2 *)q1, (const float2 *)q2, g.nx, g.ny, g.s, (float2 *)out,
+                           (cudaStream_t)stream));
     CU(cudaStreamSynchronize((cudaStream_t)stream));
     return REG_OK;
 }

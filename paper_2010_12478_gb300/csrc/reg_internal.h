@@ -70,11 +70,10 @@ struct Params {
     const OpDesc *ops;
     int n_ops;
     int op_base;               // first op of this launch (batched launches)
-    double *node_theta;        // rigid: [n_nodes][3] (alpha, Gx, Gy)
-    float *node_field;         // nonrigid: [n_nodes][2][H0][W0]
+    double *node_theta;        // [n_nodes][3]: rigid (alpha, Gx, Gy); nonrigid (0, mean c_x, mean c_y)
+    float2 *node_grid;         // nonrigid: [n_nodes][gny * gnx] control values (finest px)
+    int gnx, gny, gs;          // nonrigid control grid: points per axis and spacing (finest px)
     int n_nodes;
-    float *scratch;            // nonrigid per-slot work buffers
-    size_t scratch_floats;     // floats per slot
     OpStats *stats;            // [n_ops]
     int *status;               // kernel status word (first device error)
     Queue queue;               // persistent executor only
@@ -91,11 +90,14 @@ cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_o
 cudaError_t launch_persistent(const Params &p, int storage, int cluster, int workers,
                               cudaStream_t s);
 cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
-                          const float *field, double *out_dev, float *grad_field,
+                          const float2 *grid_dev, double *out_dev, float2 *grad_dev,
                           cudaStream_t s);
-cudaError_t launch_compose(const float *u1, const float *u2, int W, int H, float *out,
-                           cudaStream_t s);
-size_t scratch_floats_per_slot(const int *W, const int *H, int levels);
+cudaError_t launch_grid_compose(const float2 *q1, const float2 *q2, int nx, int ny, int spacing,
+                                float2 *out, cudaStream_t s);
+cudaError_t launch_grid_dense(const float2 *grids, const int *nodes, int n, int nx, int ny,
+                              int spacing, int W, int H, float *out, cudaStream_t s);
+cudaError_t launch_grid_from_dense(const float *u, int W, int H, int nx, int ny, int spacing,
+                                   float2 *out, cudaStream_t s);
 // Set the calling thread's message returned by reg_last_error_message().
 void set_last_error(const char *msg);
 int max_cluster_size();

@@ -493,59 +493,83 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
 }
 
 // ================================================================== nonrigid
-// Work buffers of one slot: per level l, 8 planes of W_l*H_l floats:
-// U0x U0y U1x U1y D0x D0y D1x D1y.
-struct FieldLvl {
-    float *base;
-    int W, H;
-    __device__ float *U(int b, int comp) const { return base + (size_t)(2 * b + comp) * W * H; }
-    __device__ float *D(int b, int comp) const { return base + (size_t)(4 + 2 * b + comp) * W * H; }
+// Free-form field: u(x) bilinear in control values c_j on a grid of spacing s
+// (finest-level pixels), points (jx s, jy s).  At level l a pixel x sits at
+// finest coordinate X = 2^l x + (2^l - 1)/2, and the level works on c in its
+// own pixels (c / 2^l).  Every CTA of the cluster holds the whole grid in
+// shared memory: c (current), d (descent direction), ct (trial values) and gp
+// (this CTA's partial gradient).
+
+struct Grid {
+    int nx, ny, s;   // points per axis, spacing in finest pixels
 };
 
-__device__ __forceinline__ FieldLvl field_level(const Params &p, int slot, int l)
+struct GridLvl {
+    int W, H, l;     // level size and index
+    float scale_inv; // 1 / s in level-coordinate units: g = (2^l x + off) / s
+    float off;       // (2^l - 1) / 2
+    float pl;        // 2^l
+};
+
+// Cell and weights of level pixel (x, y); matches the clamped cell choice of the oracle.
+__device__ __forceinline__ void grid_cell(const Grid &G, const GridLvl &L, int x, int y, int &ix, int &iy,
+                                          float &wx, float &wy)
 {
-    size_t off = 0;
-    int W = 0, H = 0;
-    for (int q = 0; q <= l; ++q) {
-        const LevelDesc &d = p.levels[q];   // frame 0's geometry: every frame has the same size
-        if (q < l) off += (size_t)8 * d.W * d.H;
-        W = d.W; H = d.H;
-    }
-    FieldLvl f;
-    f.base = p.scratch + (size_t)slot * p.scratch_floats + off;
-    f.W = W; f.H = H;
-    return f;
+    float gx = fmaf(L.pl, (float)x, L.off) * L.scale_inv;
+    float gy = fmaf(L.pl, (float)y, L.off) * L.scale_inv;
+    gx = fminf(gx, (float)(G.nx - 1));
+    gy = fminf(gy, (float)(G.ny - 1));
+    ix = min((int)gx, G.nx - 2);
+    iy = min((int)gy, G.ny - 2);
+    wx = gx - (float)ix;
+    wy = gy - (float)iy;
 }
 
-// u(x) = U(x) + tau * D(x) (tau == 0: D is not read)
-__device__ __forceinline__ float2 u_at(const FieldLvl &F, int b, size_t i, float tau)
+__device__ __forceinline__ float2 grid_eval(const float2 *c, int nx, int ix, int iy, float wx, float wy)
 {
-    float ux = __ldcg(F.U(b, 0) + i), uy = __ldcg(F.U(b, 1) + i);
-    if (tau != 0.f) {
-        ux = fmaf(tau, __ldcg(F.D(b, 0) + i), ux);
-        uy = fmaf(tau, __ldcg(F.D(b, 1) + i), uy);
-    }
-    return make_float2(ux, uy);
+    const float2 a = c[iy * nx + ix], b = c[iy * nx + ix + 1], e = c[(iy + 1) * nx + ix], f = c[(iy + 1) * nx + ix + 1];
+    const float gx = 1.f - wx, gy = 1.f - wy;
+    float2 u;
+    u.x = fmaf(wy, fmaf(wx, f.x, gx * e.x), gy * fmaf(wx, b.x, gx * a.x));
+    u.y = fmaf(wy, fmaf(wx, f.y, gx * e.y), gy * fmaf(wx, b.y, gx * a.y));
+    return u;
 }
 
-// Energy of the field U_b + tau D_b: slots 0 St, 1 Stt, 2 Srt, 3 Sr, 4 Srr, 5 sum |forward diff|^2.
+// Rows and band of control-cell rows owned by a CTA: cell rows [k q, (k+1) q), q = ceil((ny-1)/C);
+// level pixel rows of those cells (the last CTA also takes rows clamped into the last cell row).
+__device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int rank, int C, int &cr0, int &cr1,
+                                          int &r0, int &r1)
+{
+    const int cells = G.ny - 1;
+    const int q = (cells + C - 1) / C;
+    cr0 = min(cells, rank * q);
+    cr1 = min(cells, cr0 + q);
+    const int sl = G.s >> L.l;   // cell height in level pixels
+    r0 = min(L.H, cr0 * sl);
+    r1 = (cr1 == cells) ? L.H : min(L.H, cr1 * sl);
+    if (cr0 == cr1) r0 = r1 = L.H;
+}
+
+// Energy moments of the field ct: slots 0 St, 1 Stt, 2 Srt, 3 Sr, 4 Srr, 5 sum over control edges |dct|^2
+// (rank 0 only, so the cluster sum counts it once).
 template <typename S>
-__device__ void eval_field_energy(const Lvl &L, const FieldLvl &F, int b, float tau, int r0, int r1,
-                                  Smem &sm, int &buf, const cg::cluster_group &cl)
+__device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *ct, int r0, int r1,
+                                 Smem &sm, int &buf, const cg::cluster_group &cl)
 {
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     constexpr int NM = 6;
     float hi[NM], lo[NM], a[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
-    const int W = L.W, H = L.H;
     for_pixels2(
-        W, r0, r1,
+        L.W, r0, r1,
         [&](int r, int c) {
-            size_t i = (size_t)r * W + c;
-            float2 u = u_at(F, b, i, tau);
+            int ix, iy;
+            float wx, wy;
+            grid_cell(G, GL, c, r, ix, iy, wx, wy);
+            const float2 u = grid_eval(ct, G.nx, ix, iy, wx, wy);
             float dtx, dty;
-            float tw = sample_at<S, false>(T, W, H, L.Tp, c, r, u.x, u.y, dtx, dty);
+            float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c, r, u.x, u.y, dtx, dty);
             float rv = ldS<S>(R + (size_t)r * L.Rp + c) - L.cR;
             float tv = tw - L.cR;
             a[0] += tv;
@@ -553,80 +577,153 @@ __device__ void eval_field_energy(const Lvl &L, const FieldLvl &F, int b, float 
             a[2] = fmaf(rv, tv, a[2]);
             a[3] += rv;
             a[4] = fmaf(rv, rv, a[4]);
-            float reg = 0.f;
-            if (c + 1 < W) {
-                float2 v = u_at(F, b, i + 1, tau);
-                float ex = v.x - u.x, ey = v.y - u.y;
-                reg = fmaf(ex, ex, fmaf(ey, ey, reg));
-            }
-            if (r + 1 < H) {
-                float2 v = u_at(F, b, i + W, tau);
-                float ex = v.x - u.x, ey = v.y - u.y;
-                reg = fmaf(ex, ex, fmaf(ey, ey, reg));
-            }
-            a[5] += reg;
         },
         [&]() {
 #pragma unroll
             for (int m = 0; m < 5; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
         },
-        [&]() { ff_acc(hi[5], lo[5], a[5]); a[5] = 0.f; });
+        []() {});
+    if (cl.block_rank() == 0) {
+        const int Nc = G.nx * G.ny;
+        float e = 0.f;
+        int k = 0;
+        for (int j = threadIdx.x; j < Nc; j += kThreads) {
+            const int jx = j % G.nx;
+            const float2 v = ct[j];
+            if (jx + 1 < G.nx) {
+                const float2 w = ct[j + 1];
+                e = fmaf(w.x - v.x, w.x - v.x, fmaf(w.y - v.y, w.y - v.y, e));
+            }
+            if (j + G.nx < Nc) {
+                const float2 w = ct[j + G.nx];
+                e = fmaf(w.x - v.x, w.x - v.x, fmaf(w.y - v.y, w.y - v.y, e));
+            }
+            if (++k == kFast) { ff_acc(hi[5], lo[5], e); e = 0.f; k = 0; }
+        }
+        ff_acc(hi[5], lo[5], e);
+    }
     cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
 }
 
-// Field pass: u = U_b + tau D_b materialised into U_{1-b}; descent direction
-// d = -P dE/du = -(fP grad T(x + u) + lambda * sum_nbrs (u(x) - u(y))) into D_{1-b};
-// reduces sum |d|^2 and max |d|^2.  pm: tau, aP, bP, rbar, tbar, lambda.
+// Gradient pass at c: this CTA's cells in four parity phases (no two cells of a phase share a
+// corner, so each corner is updated by one warp at a time, in a fixed order); then every CTA
+// assembles the whole gradient from the (at most two) CTAs whose band holds each control row,
+// and forms d = -(Nc/P) [sum F grad T w + lambda sum_nbrs (c_j - c_k)], F = P dE/dTw.
+// pm: aP, bP, rbar, tbar, lambda.  Returns sum |d|^2 (float-float, in sm.tot[0]) and max |d|^2
+// (sm.tot[1]); identical in every CTA.
 template <typename S>
-__device__ void eval_field_grad(const Lvl &L, const FieldLvl &F, int b, const float *pm, int r0, int r1,
-                                Smem &sm, int &buf, const cg::cluster_group &cl)
+__device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *c, float2 *d,
+                               float2 *gp, const float *pm, int cr0, int cr1, Smem &sm, const cg::cluster_group &cl)
 {
     const S *R = (const S *)L.R, *T = (const S *)L.T;
-    const float tau = pm[0], aP = pm[1], bP = pm[2], rb = pm[3], tb = pm[4], lam = pm[5];
-    constexpr int NM = 2;
-    float hi[NM] = {0.f, 0.f}, lo[NM] = {0.f, 0.f}, a[NM] = {0.f, 0.f};
-    const int W = L.W, H = L.H;
-    const int nb = 1 - b;
-    for_pixels(
-        W, r0, r1,
-        [&](int r, int c) {
-            size_t i = (size_t)r * W + c;
-            float2 u = u_at(F, b, i, tau);
-            float lx = 0.f, ly = 0.f;
-            if (c > 0)     { float2 v = u_at(F, b, i - 1, tau); lx += u.x - v.x; ly += u.y - v.y; }
-            if (c + 1 < W) { float2 v = u_at(F, b, i + 1, tau); lx += u.x - v.x; ly += u.y - v.y; }
-            if (r > 0)     { float2 v = u_at(F, b, i - W, tau); lx += u.x - v.x; ly += u.y - v.y; }
-            if (r + 1 < H) { float2 v = u_at(F, b, i + W, tau); lx += u.x - v.x; ly += u.y - v.y; }
-            float dtx, dty;
-            float tw = sample_at<S, true>(T, W, H, L.Tp, c, r, u.x, u.y, dtx, dty);
-            float rv = ldS<S>(R + (size_t)r * L.Rp + c) - L.cR;
-            float tv = tw - L.cR;
-            // fP = P * dE_data/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
-            float fP = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
-            float dx = -fmaf(fP, dtx, lam * lx);
-            float dy = -fmaf(fP, dty, lam * ly);
-            __stcg(F.U(nb, 0) + i, u.x);
-            __stcg(F.U(nb, 1) + i, u.y);
-            __stcg(F.D(nb, 0) + i, dx);
-            __stcg(F.D(nb, 1) + i, dy);
-            float q = fmaf(dx, dx, dy * dy);
-            a[0] += q;
-            a[1] = fmaxf(a[1], q);
-        },
-        [&]() {
-            ff_acc(hi[0], lo[0], a[0]);
-            a[0] = 0.f;
-            hi[1] = fmaxf(hi[1], a[1]);
-        });
-    cluster_reduce<NM, true>(hi, lo, sm, buf, cl, true);
+    const float aP = pm[0], bP = pm[1], rb = pm[2], tb = pm[3], lam = pm[4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Nc = G.nx * G.ny, ncx = G.nx - 1, ncy = G.ny - 1;
+    const int sl = G.s >> GL.l;
+    for (int j = tid; j < Nc; j += kThreads) gp[j] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int phase = 0; phase < 4; ++phase) {
+        const int px = phase & 1, py = phase >> 1;
+        const int first_row = cr0 + ((py - cr0) % 2 + 2) % 2;
+        const int rows = first_row < cr1 ? (cr1 - first_row + 1) / 2 : 0;
+        const int cols = (ncx - px + 1) / 2;
+        const int ncell = rows * cols;
+        for (int q = warp; q < ncell; q += kWarps) {
+            const int cyy = first_row + 2 * (q / cols), cxx = px + 2 * (q % cols);
+            const int x0 = cxx * sl, x1 = (cxx == ncx - 1) ? L.W : min(L.W, x0 + sl);
+            const int y0 = cyy * sl, y1 = (cyy == ncy - 1) ? L.H : min(L.H, y0 + sl);
+            const int w = x1 - x0, npx = w * (y1 - y0);
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int i = lane; i < npx; i += 32) {
+                const int y = y0 + i / w, x = x0 + i % w;
+                int ix, iy;
+                float wx, wy;
+                grid_cell(G, GL, x, y, ix, iy, wx, wy);
+                const float2 u = grid_eval(c, G.nx, ix, iy, wx, wy);
+                float dtx, dty;
+                const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, x, y, u.x, u.y, dtx, dty);
+                const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
+                const float tv = tw - L.cR;
+                // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
+                const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
+                const float gx = F * dtx, gy = F * dty;
+                const float w00 = (1.f - wx) * (1.f - wy), w01 = wx * (1.f - wy), w10 = (1.f - wx) * wy, w11 = wx * wy;
+                acc[0] = fmaf(w00, gx, acc[0]); acc[1] = fmaf(w00, gy, acc[1]);
+                acc[2] = fmaf(w01, gx, acc[2]); acc[3] = fmaf(w01, gy, acc[3]);
+                acc[4] = fmaf(w10, gx, acc[4]); acc[5] = fmaf(w10, gy, acc[5]);
+                acc[6] = fmaf(w11, gx, acc[6]); acc[7] = fmaf(w11, gy, acc[7]);
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], off);
+            if (lane == 0) {
+                const int j = cyy * G.nx + cxx;
+                gp[j].x += acc[0]; gp[j].y += acc[1];
+                gp[j + 1].x += acc[2]; gp[j + 1].y += acc[3];
+                gp[j + G.nx].x += acc[4]; gp[j + G.nx].y += acc[5];
+                gp[j + G.nx + 1].x += acc[6]; gp[j + G.nx + 1].y += acc[7];
+            }
+        }
+        __syncthreads();
+    }
+    cl.sync();   // every CTA's partial gradient is complete and visible in the cluster
+    const int C = cl.num_blocks();
+    const int q = (ncy + C - 1) / C;
+    const float scale = -(float)Nc / ((float)L.W * (float)L.H);
+    float ssh = 0.f, ssl = 0.f, mx = 0.f, run = 0.f;
+    int k = 0;
+    for (int j = tid; j < Nc; j += kThreads) {
+        const int jy = j / G.nx, jx = j - jy * G.nx;
+        // bands: rank r owns cell rows [r q, (r+1) q) and so control rows [r q, (r+1) q]
+        const int rlo = jy > 0 ? min(C - 1, (jy - 1) / max(q, 1)) : 0;
+        const int rhi = min(C - 1, jy / max(q, 1));
+        float2 g = make_float2(0.f, 0.f);
+        for (int r = rlo; r <= rhi; ++r) {
+            const float2 v = *cl.map_shared_rank(gp + j, r);
+            g.x += v.x;
+            g.y += v.y;
+        }
+        const float2 cj = c[j];
+        float lx = 0.f, ly = 0.f;
+        if (jx > 0)        { const float2 v = c[j - 1];    lx += cj.x - v.x; ly += cj.y - v.y; }
+        if (jx + 1 < G.nx) { const float2 v = c[j + 1];    lx += cj.x - v.x; ly += cj.y - v.y; }
+        if (jy > 0)        { const float2 v = c[j - G.nx]; lx += cj.x - v.x; ly += cj.y - v.y; }
+        if (jy + 1 < G.ny) { const float2 v = c[j + G.nx]; lx += cj.x - v.x; ly += cj.y - v.y; }
+        float2 dj;
+        dj.x = scale * fmaf(lam, lx, g.x);
+        dj.y = scale * fmaf(lam, ly, g.y);
+        d[j] = dj;
+        const float qd = fmaf(dj.x, dj.x, dj.y * dj.y);
+        run += qd;
+        mx = fmaxf(mx, qd);
+        if (++k == kFast) { ff_acc(ssh, ssl, run); run = 0.f; k = 0; }
+    }
+    ff_acc(ssh, ssl, run);
+    // block reduction (identical in every CTA: same inputs, same order)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        float h2 = __shfl_xor_sync(0xffffffffu, ssh, off), l2 = __shfl_xor_sync(0xffffffffu, ssl, off);
+        ff_add(ssh, ssl, h2, l2);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if (lane == 0) { sm.warp[warp][0] = make_float2(ssh, ssl); sm.warp[warp][1] = make_float2(mx, 0.f); }
+    __syncthreads();
+    if (tid == 0) {
+        float h = 0.f, l = 0.f, m = 0.f;
+        for (int w2 = 0; w2 < kWarps; ++w2) { ff_add(h, l, sm.warp[w2][0].x, sm.warp[w2][0].y); m = fmaxf(m, sm.warp[w2][1].x); }
+        sm.tot[0] = (double)h + (double)l;
+        sm.tot[1] = (double)m;
+    }
+    __syncthreads();
 }
 
 struct FieldCtl {
-    double E, tau, tau_pend, slope, P, sr, srr;
+    double E, tau, tau_pend, slope, P, Nc, sr, srr;
     double a, b, rbar, tbar;      // NCC terms at the current field
     double ta, tb, trbar, ttbar;  // at the trial field
     int degen, tdegen;
-    int nrej, iters, evals, stop, rejects, cur;
+    int nrej, iters, evals, stop, rejects;
 };
 
 __device__ double field_energy(FieldCtl &k, const Config &cfg, const double *tot, bool trial)
@@ -639,35 +736,32 @@ __device__ double field_energy(FieldCtl &k, const Config &cfg, const double *tot
     return E;
 }
 
-__device__ void field_params(const FieldCtl &k, const Config &cfg, float tau, float *pm)
+// Gradient-pass parameters from the current NCC terms: aP, bP, rbar, tbar, lambda.
+__device__ void field_grad_params(const FieldCtl &k, const Config &cfg, float *pm)
 {
-    pm[0] = tau;
-    pm[1] = (float)(k.a * k.P);
-    pm[2] = (float)(k.b * k.P);
-    pm[3] = (float)k.rbar;
-    pm[4] = (float)k.tbar;
-    pm[5] = (float)cfg.lambda;
+    pm[0] = (float)(k.a * k.P);
+    pm[1] = (float)(k.b * k.P);
+    pm[2] = (float)k.rbar;
+    pm[3] = (float)k.tbar;
+    pm[4] = (float)cfg.lambda;
 }
 
-// Thread-0 controller of the nonrigid level loop; mirrors rigid_step with the
-// field passes (ENERGY at level start, FIELD = gradient, TRIAL = Armijo trial).
+// Thread-0 controller of the nonrigid level loop (same rules as the rigid one): ENERGY at level
+// start, GRAD = gradient pass, TRIAL = Armijo trial at c + tau d.  pm[0] of a trial is tau.
 __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int action, float *pm)
 {
     if (action == kActEnergy) {
         k.sr = tot[3]; k.srr = tot[4];
         k.E = field_energy(k, cfg, tot, false);
-        k.tau_pend = 0.0;
-        field_params(k, cfg, 0.f, pm);
-        return kActField;
+        field_grad_params(k, cfg, pm);
+        return kActGrad;
     }
-    if (action == kActField) {
+    if (action == kActGrad) {
         k.evals += 1;
-        k.cur ^= 1;
-        k.tau_pend = 0.0;
         if (k.iters >= cfg.max_iter) { k.stop = REG_STOP_MAXIT; return kActDone; }
-        double ss = tot[0], dmax = sqrt(tot[1]);
-        k.slope = -ss / k.P;
-        double gn = sqrt(ss / k.P);
+        const double ss = tot[0], dmax = sqrt(tot[1]);
+        k.slope = -ss / k.Nc;
+        const double gn = sqrt(ss / k.Nc);
         if (!(gn >= cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
         if (k.tau * dmax > cfg.step_cap) k.tau = cfg.step_cap / dmax;
         k.nrej = 0;
@@ -675,209 +769,148 @@ __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int
         return kActTrial;
     }
     // trial
-    double Et = field_energy(k, cfg, tot, true);
+    const double Et = field_energy(k, cfg, tot, true);
     k.evals += 1;
     if (Et <= k.E + cfg.armijo_c * k.tau * k.slope) {
         k.iters += 1;
-        double Eold = k.E;
+        const double Eold = k.E;
         k.E = Et;
         k.a = k.ta; k.b = k.tb; k.rbar = k.trbar; k.tbar = k.ttbar; k.degen = k.tdegen;
-        k.tau_pend = (double)(float)k.tau;   // the step the trial pass applied
+        k.tau_pend = (double)(float)k.tau;
         k.tau *= 2.0;
         if (Eold - Et <= cfg.tol_rel_e * fabs(Eold)) { k.stop = REG_STOP_REL; return kActDone; }
-        field_params(k, cfg, (float)k.tau_pend, pm);
-        return kActField;
+        field_grad_params(k, cfg, pm);
+        return kActGrad;   // c is advanced to ct before the gradient pass
     }
     k.rejects += 1;
     k.nrej += 1;
     k.tau *= 0.5;
+    k.tau_pend = 0.0;
     if (k.nrej > cfg.max_rejects) { k.stop = REG_STOP_LS; return kActDone; }
     pm[0] = (float)k.tau;
     return kActTrial;
 }
 
-// Composition (B's initial guess) into U_0 of level 0: u1(x) + u2(x + u1(x)).
-__device__ void field_compose(const float *u1, const float *u2, const FieldLvl &F, int r0, int r1)
+// FFD value of the grid q (finest-pixel values) at finest coordinate (X, Y), read through L2.
+__device__ __forceinline__ float2 grid_eval_global(const float2 *q, const Grid &G, float X, float Y)
 {
-    const int W = F.W, H = F.H;
-    const size_t P = (size_t)W * H;
-    for_pixels(
-        W, r0, r1,
-        [&](int r, int c) {
-            size_t i = (size_t)r * W + c;
-            float ax = __ldcg(u1 + i), ay = __ldcg(u1 + P + i);
-            __stcg(F.U(0, 0) + i, ax + sample_cg(u2, W, H, c, r, ax, ay));
-            __stcg(F.U(0, 1) + i, ay + sample_cg(u2 + P, W, H, c, r, ax, ay));
-        },
-        []() {});
-}
-
-// Restriction of an initial field, level l -> l+1: box average, halved.
-__device__ void field_restrict(const FieldLvl &Ff, const FieldLvl &Fc, int r0, int r1)
-{
-    for_pixels(
-        Fc.W, r0, r1,
-        [&](int r, int c) {
-            int ra = 2 * r, rb = min(2 * r + 1, Ff.H - 1), ca = 2 * c, cb = min(2 * c + 1, Ff.W - 1);
-            for (int comp = 0; comp < 2; ++comp) {
-                const float *s = Ff.U(0, comp);
-                float v = (__ldcg(s + (size_t)ra * Ff.W + ca) + __ldcg(s + (size_t)ra * Ff.W + cb)) +
-                          (__ldcg(s + (size_t)rb * Ff.W + ca) + __ldcg(s + (size_t)rb * Ff.W + cb));
-                __stcg(Fc.U(0, comp) + (size_t)r * Fc.W + c, 0.125f * v);
-            }
-        },
-        []() {});
-}
-
-// Prolongation, level l+1 -> l: u_l(x) = 2 bilinear(u_{l+1}, ((c - 0.5)/2, (r - 0.5)/2)),
-// u_{l+1} = U_b + tau D_b of the coarse level.
-__device__ void field_prolong(const FieldLvl &Fc, int b, float tau, const FieldLvl &Ff, int r0, int r1)
-{
-    for_pixels(
-        Ff.W, r0, r1,
-        [&](int r, int c) {
-            float px = 0.5f * ((float)c - 0.5f), py = 0.5f * ((float)r - 0.5f);
-            float qx = fminf(fmaxf(px, 0.f), (float)(Fc.W - 1));
-            float qy = fminf(fmaxf(py, 0.f), (float)(Fc.H - 1));
-            int x0 = min((int)qx, Fc.W - 2), y0 = min((int)qy, Fc.H - 2);
-            float fx = qx - (float)x0, fy = qy - (float)y0;
-            size_t i00 = (size_t)y0 * Fc.W + x0;
-            float2 t00 = u_at(Fc, b, i00, tau), t01 = u_at(Fc, b, i00 + 1, tau);
-            float2 t10 = u_at(Fc, b, i00 + Fc.W, tau), t11 = u_at(Fc, b, i00 + Fc.W + 1, tau);
-            float gx = 1.f - fx, gy = 1.f - fy;
-            float topx = fmaf(fx, t01.x, gx * t00.x), botx = fmaf(fx, t11.x, gx * t10.x);
-            float topy = fmaf(fx, t01.y, gx * t00.y), boty = fmaf(fx, t11.y, gx * t10.y);
-            size_t i = (size_t)r * Ff.W + c;
-            __stcg(Ff.U(0, 0) + i, 2.f * fmaf(fy, botx, gy * topx));
-            __stcg(Ff.U(0, 1) + i, 2.f * fmaf(fy, boty, gy * topy));
-        },
-        []() {});
+    float gx = fminf(fmaxf(X / (float)G.s, 0.f), (float)(G.nx - 1));
+    float gy = fminf(fmaxf(Y / (float)G.s, 0.f), (float)(G.ny - 1));
+    int ix = min((int)gx, G.nx - 2), iy = min((int)gy, G.ny - 2);
+    float wx = gx - (float)ix, wy = gy - (float)iy;
+    const float2 *p = q + iy * G.nx + ix;
+    float2 a = __ldcg(p), b = __ldcg(p + 1), e = __ldcg(p + G.nx), f = __ldcg(p + G.nx + 1);
+    float hx = 1.f - wx, hy = 1.f - wy;
+    float2 u;
+    u.x = fmaf(wy, fmaf(wx, f.x, hx * e.x), hy * fmaf(wx, b.x, hx * a.x));
+    u.y = fmaf(wy, fmaf(wx, f.y, hx * e.y), hy * fmaf(wx, b.y, hx * a.y));
+    return u;
 }
 
 template <typename S>
-__device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, int slot, Smem &sm,
+__device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Smem &sm, float2 *gbuf,
                              const cg::cluster_group &cl)
 {
     const int tid = threadIdx.x;
     const int C = cl.num_blocks(), rank = cl.block_rank();
     const Config &cfg = p.cfg;
     const int Lc = cfg.levels;
+    const Grid G{p.gnx, p.gny, p.gs};
+    const int Nc = G.nx * G.ny;
+    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
     int buf = 0;
-    const FieldLvl F0 = field_level(p, slot, 0);
-    const size_t P0 = (size_t)F0.W * F0.H;
-    // initial field at level 0 (U_0), then restricted down to the coarsest level
+    // initial control values (finest px), scaled to the coarsest level
     {
-        int r0, r1;
-        strip_rows(F0.H, rank, C, r0, r1);
-        bool have_init = true;
+        const float sc = ldexpf(1.f, -(Lc - 1));
         if (op.left >= 0) {
-            field_compose(p.node_field + 2 * P0 * op.left, p.node_field + 2 * P0 * op.right, F0, r0, r1);
+            // B's initial guess phi_jk o phi_ij at the control points (Sec. 2.3.2)
+            const float2 *q1 = p.node_grid + (size_t)Nc * op.left, *q2 = p.node_grid + (size_t)Nc * op.right;
+            for (int j = tid; j < Nc; j += kThreads) {
+                const int jy = j / G.nx, jx = j - jy * G.nx;
+                const float2 a = __ldcg(q1 + j);
+                const float2 u = grid_eval_global(q2, G, (float)(jx * G.s) + a.x, (float)(jy * G.s) + a.y);
+                c[j] = make_float2(sc * (a.x + u.x), sc * (a.y + u.y));
+            }
         } else if (op.init_node >= 0) {
-            const float *src = p.node_field + 2 * P0 * op.init_node;
-            for_pixels(F0.W, r0, r1, [&](int r, int c) {
-                size_t i = (size_t)r * F0.W + c;
-                __stcg(F0.U(0, 0) + i, __ldcg(src + i));
-                __stcg(F0.U(0, 1) + i, __ldcg(src + P0 + i));
-            }, []() {});
-        } else {
-            have_init = false;
-        }
-        if (have_init) {
-            for (int l = 0; l + 1 < Lc; ++l) {
-                cluster_barrier(cl);
-                FieldLvl Ff = field_level(p, slot, l), Fc = field_level(p, slot, l + 1);
-                int q0, q1;
-                strip_rows(Fc.H, rank, C, q0, q1);
-                field_restrict(Ff, Fc, q0, q1);
+            const float2 *q = p.node_grid + (size_t)Nc * op.init_node;
+            for (int j = tid; j < Nc; j += kThreads) {
+                const float2 a = __ldcg(q + j);
+                c[j] = make_float2(sc * a.x, sc * a.y);
             }
         } else {
-            FieldLvl Fc = field_level(p, slot, Lc - 1);
-            int q0, q1;
-            strip_rows(Fc.H, rank, C, q0, q1);
-            for_pixels(Fc.W, q0, q1, [&](int r, int c) {
-                size_t i = (size_t)r * Fc.W + c;
-                __stcg(Fc.U(0, 0) + i, 0.f);
-                __stcg(Fc.U(0, 1) + i, 0.f);
-            }, []() {});
+            for (int j = tid; j < Nc; j += kThreads) c[j] = make_float2(0.f, 0.f);
         }
-        cluster_barrier(cl);
     }
     FieldCtl k;
-    if (tid == 0) memset(&k, 0, sizeof(k));
+    if (tid == 0) {
+        memset(&k, 0, sizeof(k));
+        k.Nc = (double)Nc;
+    }
     int stops[kMaxLevels], iters[kMaxLevels], evals[kMaxLevels];
-    int cur = 0;
-    float tau_pend = 0.f;
     for (int l = Lc - 1; l >= 0; --l) {
         const Lvl L = level_of(p, op.ref, op.tmpl, l);
-        const FieldLvl F = field_level(p, slot, l);
-        int r0, r1;
-        strip_rows(L.H, rank, C, r0, r1);
+        GridLvl GL;
+        GL.W = L.W; GL.H = L.H; GL.l = l;
+        GL.pl = ldexpf(1.f, l);
+        GL.off = 0.5f * (GL.pl - 1.f);
+        GL.scale_inv = 1.f / (float)G.s;
+        int cr0, cr1, r0, r1;
+        grid_rows(G, GL, rank, C, cr0, cr1, r0, r1);
         if (tid == 0) {
             k.P = (double)L.W * (double)L.H;
             k.tau = cfg.tau0;
+            k.tau_pend = 0.0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
-            k.cur = 0;
             sm.action = kActEnergy;
-            sm.pm[0] = 0.f;
-            sm.idata[0] = 0;
         }
         for (;;) {
             __syncthreads();
             const int act = sm.action;
             if (act == kActDone) break;
-            float pm[6];
+            float pm[5];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) pm[q] = sm.pm[q];
-            cur = sm.idata[0];
-            if (act == kActEnergy) eval_field_energy<S>(L, F, 0, 0.f, r0, r1, sm, buf, cl);
-            else if (act == kActTrial) eval_field_energy<S>(L, F, cur, pm[0], r0, r1, sm, buf, cl);
-            else eval_field_grad<S>(L, F, cur, pm, r0, r1, sm, buf, cl);
+            for (int q = 0; q < 5; ++q) pm[q] = sm.pm[q];
+            if (act == kActEnergy) {
+                grid_energy_pass<S>(L, G, GL, c, r0, r1, sm, buf, cl);
+            } else if (act == kActTrial) {
+                for (int j = tid; j < Nc; j += kThreads) {
+                    const float2 a = c[j], b = d[j];
+                    ct[j] = make_float2(fmaf(pm[0], b.x, a.x), fmaf(pm[0], b.y, a.y));
+                }
+                __syncthreads();
+                grid_energy_pass<S>(L, G, GL, ct, r0, r1, sm, buf, cl);
+            } else {
+                grid_grad_pass<S>(L, G, GL, c, d, gp, pm, cr0, cr1, sm, cl);
+            }
             if (tid == 0) {
-                sm.action = field_step(k, cfg, sm.tot, act, sm.pm);
-                sm.idata[0] = k.cur;
-                sm.pm[8] = (float)k.tau_pend;
+                const int next = field_step(k, cfg, sm.tot, act, sm.pm);
+                sm.action = next;
+                sm.idata[0] = (act == kActTrial && k.tau_pend != 0.0) ? 1 : 0;   // accepted: c <- ct
+            }
+            __syncthreads();
+            if (sm.idata[0]) {
+                for (int j = tid; j < Nc; j += kThreads) c[j] = ct[j];
+                __syncthreads();
+                if (tid == 0) { sm.idata[0] = 0; k.tau_pend = 0.0; }
             }
         }
-        cur = sm.idata[0];
-        tau_pend = sm.pm[8];
         if (tid == 0) { stops[l] = k.stop; iters[l] = k.iters; evals[l] = k.evals; }
         if (l > 0) {
-            const FieldLvl Ff = field_level(p, slot, l - 1);
-            int q0, q1;
-            strip_rows(Ff.H, rank, C, q0, q1);
-            field_prolong(F, cur, tau_pend, Ff, q0, q1);
-            cluster_barrier(cl);
-            if (tid == 0) { sm.idata[0] = 0; sm.pm[8] = 0.f; }
-            __syncthreads();
+            for (int j = tid; j < Nc; j += kThreads) c[j] = make_float2(2.f * c[j].x, 2.f * c[j].y);
         }
+        __syncthreads();
     }
-    // output: node field = U_cur + tau_pend D_cur at level 0; mean displacement reduced
-    {
-        int r0, r1;
-        strip_rows(F0.H, rank, C, r0, r1);
-        float *o = p.node_field + 2 * P0 * op.out;
-        float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f}, a[2] = {0.f, 0.f};
-        for_pixels(
-            F0.W, r0, r1,
-            [&](int r, int c) {
-                size_t i = (size_t)r * F0.W + c;
-                float2 u = u_at(F0, cur, i, tau_pend);
-                __stcg(o + i, u.x);
-                __stcg(o + P0 + i, u.y);
-                a[0] += u.x;
-                a[1] += u.y;
-            },
-            [&]() {
-                ff_acc(hi[0], lo[0], a[0]); ff_acc(hi[1], lo[1], a[1]);
-                a[0] = a[1] = 0.f;
-            });
-        cluster_reduce<2, false>(hi, lo, sm, buf, cl, true);
+    if (rank == 0) {
+        float2 *o = p.node_grid + (size_t)Nc * op.out;
+        for (int j = tid; j < Nc; j += kThreads) __stcg(o + j, c[j]);
     }
     if (tid == 0 && rank == 0) {
+        double mx = 0.0, my = 0.0;
+        for (int j = 0; j < Nc; ++j) { mx += c[j].x; my += c[j].y; }
         double *o = p.node_theta + 3 * op.out;
         o[0] = 0.0;
-        o[1] = sm.tot[0] / (double)P0;
-        o[2] = sm.tot[1] / (double)P0;
+        o[1] = mx / Nc;
+        o[2] = my / Nc;
         OpStats &st = p.stats[op_index];
         st.i = op.ref;
         st.k = op.tmpl;
@@ -906,7 +939,7 @@ __device__ bool op_valid(const Params &p, const OpDesc &op)
 }
 
 template <int MODE, typename S>
-__device__ void run_op(const Params &p, int op_index, int slot, Smem &sm, const cg::cluster_group &cl)
+__device__ void run_op(const Params &p, int op_index, Smem &sm, float2 *gbuf, const cg::cluster_group &cl)
 {
     const OpDesc op = p.ops[op_index];
     if (!op_valid(p, op)) {
@@ -917,7 +950,7 @@ __device__ void run_op(const Params &p, int op_index, int slot, Smem &sm, const 
         return;
     }
     if constexpr (MODE == REG_RIGID) run_rigid<S>(p, op, op_index, sm, cl);
-    else run_nonrigid<S>(p, op, op_index, slot, sm, cl);
+    else run_nonrigid<S>(p, op, op_index, sm, gbuf, cl);
 }
 
 // Batched launch: cluster q of the grid runs operator op_base + q.
@@ -925,9 +958,10 @@ template <int MODE, typename S>
 __global__ void __launch_bounds__(kThreads, 2) op_kernel(Params p)
 {
     __shared__ Smem sm;
+    extern __shared__ float2 gbuf[];   // nonrigid: control grid c, d, ct, gp
     cg::cluster_group cl = cg::this_cluster();
     const int q = blockIdx.x / cl.num_blocks();
-    run_op<MODE, S>(p, p.op_base + q, q, sm, cl);
+    run_op<MODE, S>(p, p.op_base + q, sm, gbuf, cl);
     cl.sync();   // no CTA leaves while a peer may still read its shared memory
 }
 
@@ -937,8 +971,8 @@ template <int MODE, typename S>
 __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(Params p)
 {
     __shared__ Smem sm;
+    extern __shared__ float2 gbuf[];
     cg::cluster_group cl = cg::this_cluster();
-    const int worker = blockIdx.x / cl.num_blocks();
     const bool leader = cl.block_rank() == 0 && threadIdx.x == 0;
     for (;;) {
         if (leader) {
@@ -972,7 +1006,7 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(Params p)
         const int op = *cl.map_shared_rank(&sm.idata[1], 0);
         cl.sync();
         if (op < 0) break;
-        run_op<MODE, S>(p, op, worker, sm, cl);
+        run_op<MODE, S>(p, op, sm, gbuf, cl);
         cl.sync();
         if (leader) {
             // publish the produced node and release its consumers
@@ -993,11 +1027,14 @@ __global__ void __launch_bounds__(kThreads, 2) persistent_kernel(Params p)
 }
 
 // Energy/gradient at a given deformation for a single pair (one cluster of 1 CTA).
+// Rigid: theta (device) -> out[0] = E, out[1..3] = dE/dtheta.  Nonrigid: control values cgrid
+// (finest px, level 0) -> out[0] = E and grad_c = dE/dc.
 template <int MODE, typename S>
-__global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double *theta, const float *field,
-                                                          double *out, float *grad_field)
+__global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double *theta, const float2 *cgrid,
+                                                          double *out, float2 *grad_c)
 {
     __shared__ Smem sm;
+    extern __shared__ float2 gbuf[];
     cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x;
     int buf = 0;
@@ -1021,32 +1058,35 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
             }
         }
     } else {
-        // field energy at U_0 of slot 0 (the caller's field is staged there by the host)
-        const FieldLvl F = field_level(p, 0, 0);
-        eval_field_energy<S>(L, F, 0, 0.f, 0, L.H, sm, buf, cl);
+        const Grid G{p.gnx, p.gny, p.gs};
+        const int Nc = G.nx * G.ny;
+        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc;
+        for (int j = tid; j < Nc; j += kThreads) c[j] = cgrid[j];
+        __syncthreads();
+        GridLvl GL;
+        GL.W = L.W; GL.H = L.H; GL.l = 0; GL.pl = 1.f; GL.off = 0.f; GL.scale_inv = 1.f / (float)G.s;
+        int cr0, cr1, r0, r1;
+        grid_rows(G, GL, 0, 1, cr0, cr1, r0, r1);
+        grid_energy_pass<S>(L, G, GL, c, r0, r1, sm, buf, cl);
         FieldCtl k;
         if (tid == 0) {
             memset(&k, 0, sizeof(k));
             k.P = (double)L.W * L.H;
+            k.Nc = Nc;
             k.sr = sm.tot[3]; k.srr = sm.tot[4];
             out[0] = field_energy(k, p.cfg, sm.tot, false);
-            field_params(k, p.cfg, 0.f, sm.pm);
+            field_grad_params(k, p.cfg, sm.pm);
         }
         __syncthreads();
-        if (grad_field) {
-            float pm[6];
-            for (int q = 0; q < 6; ++q) pm[q] = sm.pm[q];
-            eval_field_grad<S>(L, F, 0, pm, 0, L.H, sm, buf, cl);
-            // D_1 holds d = -P dE/du; report dE/du
-            const size_t P = (size_t)L.W * L.H;
-            const float s = -1.f / (float)P;
-            for (size_t i = tid; i < P; i += kThreads) {
-                grad_field[i] = s * __ldcg(F.D(1, 0) + i);
-                grad_field[P + i] = s * __ldcg(F.D(1, 1) + i);
-            }
+        if (grad_c) {
+            float pm[5];
+            for (int q = 0; q < 5; ++q) pm[q] = sm.pm[q];
+            grid_grad_pass<S>(L, G, GL, c, d, gp, pm, cr0, cr1, sm, cl);
+            // d = -Nc dE/dc
+            const float s = -1.f / (float)Nc;
+            for (int j = tid; j < Nc; j += kThreads) grad_c[j] = make_float2(s * d[j].x, s * d[j].y);
         }
     }
-    (void)field;
 }
 
 // ================================================================== pyramid
@@ -1100,15 +1140,50 @@ __global__ void __launch_bounds__(kThreads) level_mean(const S *img, size_t stri
     }
 }
 
-// Nonrigid composition of two fields (standalone entry point).
-__global__ void compose_kernel(const float *u1, const float *u2, int W, int H, float *out)
+// Composition of two control grids at the control points (standalone entry point).
+__global__ void grid_compose_kernel(const float2 *q1, const float2 *q2, Grid G, float2 *out)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-    if (c >= W || r >= H) return;
-    const size_t P = (size_t)W * H, i = (size_t)r * W + c;
-    float ax = u1[i], ay = u1[P + i];
-    out[i] = ax + sample_cg(u2, W, H, c, r, ax, ay);
-    out[P + i] = ay + sample_cg(u2 + P, W, H, c, r, ax, ay);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= G.nx * G.ny) return;
+    const int jy = j / G.nx, jx = j - jy * G.nx;
+    const float2 a = q1[j];
+    const float2 u = grid_eval_global(q2, G, (float)(jx * G.s) + a.x, (float)(jy * G.s) + a.y);
+    out[j] = make_float2(a.x + u.x, a.y + u.y);
+}
+
+// Dense finest-level fields [2][H][W] of control grids (grid nodes[blockIdx.z]), four pixels per
+// thread written with one float4 store per plane where the row allows it.
+__global__ void grid_dense_kernel(const float2 *grids, const int *nodes, Grid G, int W, int H, float *out)
+{
+    const int Nc = G.nx * G.ny;
+    const float2 *q = grids + (size_t)Nc * nodes[blockIdx.z];
+    float *ox = out + (size_t)blockIdx.z * 2 * W * H, *oy = ox + (size_t)W * H;
+    const int r = blockIdx.y, c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (c0 >= W) return;
+    float vx[4], vy[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float2 u = grid_eval_global(q, G, (float)min(c0 + t, W - 1), (float)r);
+        vx[t] = u.x;
+        vy[t] = u.y;
+    }
+    const size_t i = (size_t)r * W + c0;
+    if (c0 + 3 < W && (((size_t)(ox + i) | (size_t)(oy + i)) & 15) == 0) {
+        __stcs((float4 *)(ox + i), make_float4(vx[0], vx[1], vx[2], vx[3]));
+        __stcs((float4 *)(oy + i), make_float4(vy[0], vy[1], vy[2], vy[3]));
+    } else {
+        for (int t = 0; t < 4 && c0 + t < W; ++t) { ox[i + t] = vx[t]; oy[i + t] = vy[t]; }
+    }
+}
+
+// Control values sampled from a dense finest-level field [2][H][W] (clamped at the border).
+__global__ void grid_from_dense_kernel(const float *u, int W, int H, Grid G, float2 *out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= G.nx * G.ny) return;
+    const int jy = j / G.nx, jx = j - jy * G.nx;
+    const int x = min(jx * G.s, W - 1), y = min(jy * G.s, H - 1);
+    out[j] = make_float2(u[(size_t)y * W + x], u[(size_t)W * H + (size_t)y * W + x]);
 }
 
 // ================================================================== host launchers
@@ -1148,6 +1223,11 @@ cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, in
     return cudaErrorInvalidValue;
 }
 
+static size_t grid_smem(const Params &p)
+{
+    return p.cfg.mode == REG_NONRIGID ? sizeof(float2) * 4 * (size_t)p.gnx * p.gny : 0;
+}
+
 template <typename K>
 static cudaError_t launch_cluster(K kernel, int blocks, int cluster, cudaStream_t s, const Params &p)
 {
@@ -1155,10 +1235,15 @@ static cudaError_t launch_cluster(K kernel, int blocks, int cluster, cudaStream_
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
+    const size_t smem = grid_smem(p);
+    if (smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(blocks);
     lc.blockDim = dim3(kThreads);
-    lc.dynamicSmemBytes = 0;
+    lc.dynamicSmemBytes = smem;
     lc.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1208,13 +1293,15 @@ cudaError_t launch_persistent(const Params &p, int storage, int cluster, int wor
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev, const float *field,
-                          double *out_dev, float *grad_field, cudaStream_t s)
+cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev, const float2 *grid_dev,
+                          double *out_dev, float2 *grad_dev, cudaStream_t s)
 {
     (void)storage;
+    const size_t smem = grid_smem(p);
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(1);
     lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = smem;
     lc.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1224,21 +1311,36 @@ cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
     lc.attrs = attr;
     lc.numAttrs = 1;
     if (p.cfg.mode == REG_RIGID)
-        return cudaLaunchKernelEx(&lc, energy_kernel<REG_RIGID, float>, p, theta_dev, field, out_dev, grad_field);
-    return cudaLaunchKernelEx(&lc, energy_kernel<REG_NONRIGID, float>, p, theta_dev, field, out_dev, grad_field);
+        return cudaLaunchKernelEx(&lc, energy_kernel<REG_RIGID, float>, p, theta_dev, grid_dev, out_dev, grad_dev);
+    cudaError_t e = cudaFuncSetAttribute(energy_kernel<REG_NONRIGID, float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&lc, energy_kernel<REG_NONRIGID, float>, p, theta_dev, grid_dev, out_dev, grad_dev);
 }
 
-cudaError_t launch_compose(const float *u1, const float *u2, int W, int H, float *out, cudaStream_t s)
+cudaError_t launch_grid_compose(const float2 *q1, const float2 *q2, int nx, int ny, int spacing, float2 *out,
+                                cudaStream_t s)
 {
-    compose_kernel<<<dim3((W + 127) / 128, H), 128, 0, s>>>(u1, u2, W, H, out);
+    const int Nc = nx * ny;
+    grid_compose_kernel<<<(Nc + 127) / 128, 128, 0, s>>>(q1, q2, Grid{nx, ny, spacing}, out);
     return cudaGetLastError();
 }
 
-size_t scratch_floats_per_slot(const int *W, const int *H, int levels)
+cudaError_t launch_grid_dense(const float2 *grids, const int *nodes, int n, int nx, int ny, int spacing, int W,
+                              int H, float *out, cudaStream_t s)
 {
-    size_t n = 0;
-    for (int l = 0; l < levels; ++l) n += (size_t)8 * W[l] * H[l];
-    return n;
+    if (n <= 0) return cudaSuccess;
+    dim3 grid((W / 4 + 1 + 63) / 64, H, n);
+    grid_dense_kernel<<<grid, 64, 0, s>>>(grids, nodes, Grid{nx, ny, spacing}, W, H, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_from_dense(const float *u, int W, int H, int nx, int ny, int spacing, float2 *out,
+                                   cudaStream_t s)
+{
+    const int Nc = nx * ny;
+    grid_from_dense_kernel<<<(Nc + 127) / 128, 128, 0, s>>>(u, W, H, Grid{nx, ny, spacing}, out);
+    return cudaGetLastError();
 }
 
 int max_cluster_size() { return 16; }

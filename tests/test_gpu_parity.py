@@ -33,7 +33,7 @@ def ctx_of(**kw):
 def ocfg(cfg: B.Config) -> O.Config:
     return O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
                     tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
-                    lam=cfg.lam, mode=cfg.mode)
+                    lam=cfg.lam, mode=cfg.mode, grid=cfg.grid)
 
 
 def rel(a, b):
@@ -78,29 +78,33 @@ def test_rigid_energy_and_gradient_match_oracle():
         assert np.abs(gg - go).max() <= 1e-4 * max(1.0, np.abs(go).max()), (gg, go)
 
 
-def test_field_energy_and_gradient_match_oracle():
+@pytest.mark.parametrize("grid", [8, 16])
+def test_grid_energy_and_gradient_match_oracle(grid):
     H, W = 53, 71
     R, T = synth.translated_pair(H, W, (0.7, -0.4), noise_snr=8.0, seed=4)
-    u = np.random.default_rng(5).uniform(-0.5, 0.5, size=(2, H, W)).astype(np.float32) + 0.3
-    ctx = ctx_of(mode="nonrigid", lam=3.0)
-    gf = torch.zeros((2, H, W), device="cuda")
-    Eg = ctx.energy_field(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(u).cuda(), gf)
-    Eo, go = O.nonrigid_energy(R, T, u.astype(np.float64), 3.0)
+    g = O.grid_for(W, H, grid)
+    assert B.grid_dims(W, H, grid, 1) == (g.nx, g.ny, g.s)
+    c = np.random.default_rng(5).uniform(-0.5, 0.5, size=(2, g.ny, g.nx)) + 0.3
+    ctx = ctx_of(mode="nonrigid", lam=3.0, grid=grid)
+    cd = torch.from_numpy(np.ascontiguousarray(c.transpose(1, 2, 0)).astype(np.float32)).cuda()
+    gd = torch.zeros((g.ny, g.nx, 2), device="cuda")
+    Eg = ctx.energy_grid(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda(), cd, gd)
+    Eo, go = O.grid_energy(R, T, 0, g, cd.cpu().numpy().transpose(2, 0, 1).astype(np.float64), 3.0)
     assert rel(Eg, Eo) <= 1e-6
-    scale = np.abs(go).max()
-    np.testing.assert_allclose(gf.cpu().numpy(), go, atol=2e-4 * scale)
+    np.testing.assert_allclose(gd.cpu().numpy().transpose(2, 0, 1), go, atol=2e-4 * np.abs(go).max())
 
 
-def test_compose_field_matches_oracle():
+def test_compose_grid_matches_oracle():
     H, W = 40, 33
+    g = O.grid_for(W, H, 8)
     rng = np.random.default_rng(6)
-    u1 = rng.uniform(-2, 2, size=(2, H, W)).astype(np.float32)
-    u2 = rng.uniform(-2, 2, size=(2, H, W)).astype(np.float32)
-    ctx = ctx_of(mode="nonrigid")
-    out = torch.zeros((2, H, W), device="cuda")
-    ctx.compose_field(torch.from_numpy(u1).cuda(), torch.from_numpy(u2).cuda(), out)
-    ref = O.compose_nonrigid(u1.astype(np.float64), u2.astype(np.float64))
-    np.testing.assert_allclose(out.cpu().numpy(), ref, atol=2e-5)
+    c1 = rng.uniform(-3, 3, size=(g.ny, g.nx, 2)).astype(np.float32)
+    c2 = rng.uniform(-3, 3, size=(g.ny, g.nx, 2)).astype(np.float32)
+    ctx = ctx_of(mode="nonrigid", grid=8)
+    out = torch.zeros((g.ny, g.nx, 2), device="cuda")
+    ctx.compose_grid(torch.from_numpy(c1).cuda(), torch.from_numpy(c2).cuda(), W, H, out)
+    ref = O.compose_grid(g, c1.transpose(2, 0, 1), c2.transpose(2, 0, 1))
+    np.testing.assert_allclose(out.cpu().numpy().transpose(2, 0, 1), ref, atol=2e-5)
 
 
 # ------------------------------------------------------------------ operators
@@ -154,8 +158,8 @@ def test_pairwise_nonrigid_matches_oracle(cluster):
     ctx = B.Context(cfg)
     fo = torch.zeros((2, 96, 112), device="cuda")
     _, st = ctx.pairwise(torch.from_numpy(F[0]).cuda(), torch.from_numpy(F[1]).cuda(), field_out=fo)
-    u_o, st_o = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, ocfg(cfg))
-    err = O.max_px_error(fo.cpu().numpy(), u_o, 96, 112, "nonrigid")
+    c_o, st_o = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, ocfg(cfg))
+    err = O.max_px_error(fo.cpu().numpy(), c_o, 96, 112, "nonrigid")
     assert err <= PX_TOL, (err, st, st_o)
     assert rel(st["energy"], st_o.energy) <= E_TOL
 
