@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "reg_internal.h"
+#include "reg_host.h"
 
 using namespace reg;
 
@@ -59,6 +60,17 @@ extern "C" const char *reg_strerror(int code)
 extern "C" const char *reg_last_error_message(void) { return g_last_error.c_str(); }
 
 void reg::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+int reg::host_fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
 
 // ------------------------------------------------------------------ device buffers
 namespace {
@@ -324,9 +336,13 @@ extern "C" int reg_ctx_create(const reg_config_t *cfg, int device, reg_ctx_t **o
     return REG_OK;
 }
 
+reg_config_t reg::host_config(reg_ctx_t *ctx) { return ctx->cfg; }
+int reg::host_device(reg_ctx_t *ctx) { return ctx->device; }
+
 extern "C" void reg_ctx_destroy(reg_ctx_t *ctx)
 {
     if (!ctx) return;
+    stop_stream_service(ctx);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->pool_ready) {

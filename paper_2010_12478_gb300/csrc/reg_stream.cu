@@ -1,15 +1,515 @@
-// Streaming service of libreg (reg_stream_*).
-#include "reg_internal.h"
+// Streaming service of libreg (reg_stream_*): online registration of frames
+// as they arrive, with continuous batching on one GPU.
+//
+// Each acquisition stream registers frame f_i to its first frame f_0 by the
+// sequential recursion of Sec. 3, phi_{0,i} = B(phi_{0,i-1}, A(f_{i-1}, f_i)).
+// A service thread (one per context) launches every operator as soon as its
+// inputs are complete, one operator per launch on a pool of CUDA streams, so
+// the operators of new frames and of other streams run on the device while
+// earlier ones are still in flight (continuous batching: the hardware runs the
+// concurrent launches side by side).  Frames live in a fixed ring of device
+// slots per stream; submit refuses a frame with REG_EBUDGET while every slot is
+// in use, and opening a stream is refused when its resident state would exceed
+// the context's memory budget.  Results come back in submission order.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
 
-extern "C" int reg_stream_open(reg_ctx_t *, int, int, reg_stream_t **out)
+#include "reg_internal.h"
+#include "reg_host.h"
+
+using namespace reg;
+
+namespace {
+
+constexpr int kLanes = 32;          // CUDA streams the service launches operators on
+constexpr int kSlots = 24;          // frame slots per stream (frames in flight)
+constexpr int kStreamCluster = 4;   // CTAs per operator (fixed: results do not depend on load)
+
+double now_us()
 {
-    if (out) *out = nullptr;
-    return REG_ESTATE;
+    return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
-extern "C" int reg_stream_submit(reg_stream_t *, const float *, uint64_t) { return REG_ESTATE; }
-extern "C" int reg_stream_poll(reg_stream_t *, reg_result_t *, int, int *n_out, int)
+
+struct Slot {
+    bool used = false;
+    long long index = -1;       // frame index within the stream (1 ..)
+    uint64_t frame_id = 0;
+    double submit_us = 0.0;
+    cudaEvent_t ready = nullptr; // pyramid built
+    cudaEvent_t a_ev = nullptr, b_ev = nullptr;
+    bool a_launched = false, a_done = false, b_launched = false, b_done = false;
+    bool emitted = false;
+};
+
+}  // namespace
+
+struct reg_stream {
+    reg_ctx_t *ctx = nullptr;
+    int W = 0, H = 0, L = 0, storage = REG_F32, mode = REG_RIGID;
+    int gnx = 0, gny = 0, gs = 0;
+    size_t bytes = 0;
+    // device memory (owned)
+    void *pyr[kMaxLevels] = {};
+    size_t lvl_elems[kMaxLevels] = {};
+    int Wl[kMaxLevels] = {}, Hl[kMaxLevels] = {};
+    float *stage = nullptr;      // one fp32 frame being copied in
+    float *means = nullptr;      // level means of the frame being staged
+    LevelDesc *table = nullptr;  // [kSlots + 1][L]; slot 0 holds f_0
+    OpDesc *ops = nullptr;       // [2 (kSlots + 1)]: A of slot s at 2s, B at 2s + 1
+    OpStats *stats = nullptr;
+    double *theta = nullptr;     // nodes, one per op
+    float2 *grid = nullptr;
+    int *status = nullptr;
+    // pinned host mirrors
+    OpDesc *h_ops = nullptr;
+    double *h_theta = nullptr;
+    OpStats *h_stats = nullptr;
+    cudaStream_t copy = nullptr;
+    // host state (guarded by the service mutex)
+    Slot slots[kSlots + 1];
+    long long submitted = 0;     // frames submitted, f_0 included
+    bool have_f0 = false;
+    cudaEvent_t f0_ready = nullptr;
+    std::deque<reg_result_t> results;
+    bool closing = false;
+    int error = REG_OK;
+};
+
+namespace {
+
+struct Service {
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::thread th;
+    bool stop = false;
+    std::vector<reg_stream *> streams;
+    cudaStream_t lanes[kLanes] = {};
+    int next_lane = 0;
+    int device = 0;
+    size_t used_bytes = 0;
+};
+
+std::mutex g_services_mu;
+std::vector<std::pair<reg_ctx_t *, Service *>> g_services;
+
+Service *service_of(reg_ctx_t *ctx, bool create);
+
+int slot_of(long long index) { return (int)((index - 1) % kSlots) + 1; }
+
+Params stream_params(reg_stream *s)
 {
-    if (n_out) *n_out = 0;
-    return REG_ESTATE;
+    Params p;
+    memset(&p, 0, sizeof(p));
+    reg_config_t c = host_config(s->ctx);
+    p.cfg.mode = c.mode;
+    p.cfg.levels = c.levels;
+    p.cfg.max_iter = c.max_iter;
+    p.cfg.max_rejects = c.max_rejects;
+    p.cfg.tol_grad = c.tol_grad;
+    p.cfg.tol_rel_e = c.tol_rel_e;
+    p.cfg.armijo_c = c.armijo_c;
+    p.cfg.tau0 = c.tau0;
+    p.cfg.step_cap = c.step_cap;
+    p.cfg.lambda = c.lambda;
+    p.levels = s->table;
+    p.n_frames = kSlots + 1;
+    p.ops = s->ops;
+    p.n_ops = 2 * (kSlots + 1);
+    p.node_theta = s->theta;
+    p.node_grid = s->grid;
+    p.gnx = s->gnx;
+    p.gny = s->gny;
+    p.gs = s->gs;
+    p.n_nodes = 2 * (kSlots + 1);
+    p.stats = s->stats;
+    p.status = s->status;
+    return p;
 }
-extern "C" int reg_stream_close(reg_stream_t *) { return REG_ESTATE; }
+
+// Launch one operator (op index e) on a service lane; results to pinned memory; event after.
+int launch_op(Service *sv, reg_stream *s, int e, const OpDesc &op, cudaEvent_t ev)
+{
+    cudaStream_t ls = sv->lanes[sv->next_lane];
+    sv->next_lane = (sv->next_lane + 1) % kLanes;
+    s->h_ops[e] = op;
+    if (cudaMemcpyAsync(s->ops + e, s->h_ops + e, sizeof(OpDesc), cudaMemcpyHostToDevice, ls) != cudaSuccess)
+        return REG_ECUDA;
+    Params p = stream_params(s);
+    p.op_base = e;
+    const int C = host_config(s->ctx).cluster > 0 ? host_config(s->ctx).cluster : kStreamCluster;
+    if (launch_ops(p, s->storage, C, 1, ls) != cudaSuccess) return REG_ECUDA;
+    if (cudaMemcpyAsync(s->h_theta + 3 * e, s->theta + 3 * e, 3 * sizeof(double), cudaMemcpyDeviceToHost, ls) !=
+        cudaSuccess)
+        return REG_ECUDA;
+    if (cudaMemcpyAsync(s->h_stats + e, s->stats + e, sizeof(OpStats), cudaMemcpyDeviceToHost, ls) != cudaSuccess)
+        return REG_ECUDA;
+    if (cudaEventRecord(ev, ls) != cudaSuccess) return REG_ECUDA;
+    return REG_OK;
+}
+
+bool done(cudaEvent_t e)
+{
+    cudaError_t r = cudaEventQuery(e);
+    if (r == cudaErrorNotReady) return false;
+    if (r != cudaSuccess) cudaGetLastError();
+    return true;
+}
+
+void emit(reg_stream *s, Slot &sl, int node, bool identity)
+{
+    reg_result_t r;
+    memset(&r, 0, sizeof(r));
+    r.frame_id = sl.frame_id;
+    r.elem.i = 0;
+    r.elem.k = (int32_t)sl.index;
+    if (!identity) {
+        r.elem.alpha = (float)s->h_theta[3 * node];
+        r.elem.gx = (float)s->h_theta[3 * node + 1];
+        r.elem.gy = (float)s->h_theta[3 * node + 2];
+        r.status = s->h_stats[node].status;
+    }
+    r.submit_us = sl.submit_us;
+    r.done_us = now_us();
+    s->results.push_back(r);
+    sl.emitted = true;
+}
+
+// One pass of the service over a stream: launch ready operators, note completions,
+// emit results in order, free slots.  Called with the service mutex held.
+void advance(Service *sv, reg_stream *s)
+{
+    if (s->error != REG_OK) return;
+    // frames in index order
+    std::vector<Slot *> order;
+    for (int k = 1; k <= kSlots; ++k)
+        if (s->slots[k].used) order.push_back(&s->slots[k]);
+    std::sort(order.begin(), order.end(), [](const Slot *a, const Slot *b) { return a->index < b->index; });
+    for (Slot *sl : order) {
+        const long long i = sl->index;
+        const int si = slot_of(i);
+        const int a_op = 2 * si, b_op = 2 * si + 1;
+        Slot *prev = i > 1 ? &s->slots[slot_of(i - 1)] : nullptr;
+        const bool prev_frame_ready = i == 1 ? done(s->f0_ready) : (prev->used && prev->index == i - 1);
+        // A(f_{i-1}, f_i)
+        if (!sl->a_launched && done(sl->ready) && prev_frame_ready && (i == 1 || done(prev->ready))) {
+            OpDesc op{i == 1 ? 0 : slot_of(i - 1), si, -1, -1, a_op, -1};
+            if (launch_op(sv, s, a_op, op, sl->a_ev) != REG_OK) { s->error = REG_ECUDA; return; }
+            sl->a_launched = true;
+        }
+        if (sl->a_launched && !sl->a_done && done(sl->a_ev)) sl->a_done = true;
+        if (i == 1) {
+            if (sl->a_done && !sl->emitted) emit(s, *sl, a_op, false);
+            continue;
+        }
+        // B(phi_{0,i-1}, phi_{i-1,i}), registering f_i onto f_0
+        const bool prev_result = prev->emitted;
+        if (!sl->b_launched && sl->a_done && prev_result) {
+            const int left = (i - 1 == 1) ? 2 * slot_of(i - 1) : 2 * slot_of(i - 1) + 1;
+            OpDesc op{0, si, left, a_op, b_op, -1};
+            if (launch_op(sv, s, b_op, op, sl->b_ev) != REG_OK) { s->error = REG_ECUDA; return; }
+            sl->b_launched = true;
+        }
+        if (sl->b_launched && !sl->b_done && done(sl->b_ev)) {
+            sl->b_done = true;
+            emit(s, *sl, b_op, false);
+        }
+    }
+    // free slot i-1 once A_i and B_i (which read f_{i-1} and phi_{0,i-1}) are done
+    for (Slot *sl : order) {
+        if (!sl->used || !sl->emitted) continue;
+        const long long i = sl->index;
+        Slot &next = s->slots[slot_of(i + 1)];
+        const bool next_done = next.used && next.index == i + 1 && next.a_done && (next.b_done || i + 1 == 1);
+        if (next_done) sl->used = false;
+    }
+}
+
+void service_loop(Service *sv)
+{
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lock(sv->mu);
+    while (!sv->stop) {
+        for (reg_stream *s : sv->streams) advance(sv, s);
+        sv->done_cv.notify_all();
+        sv->cv.wait_for(lock, std::chrono::microseconds(50));
+    }
+}
+
+Service *service_of(reg_ctx_t *ctx, bool create)
+{
+    std::lock_guard<std::mutex> g(g_services_mu);
+    for (auto &pr : g_services)
+        if (pr.first == ctx) return pr.second;
+    if (!create) return nullptr;
+    Service *sv = new Service();
+    sv->device = host_device(ctx);
+    cudaSetDevice(sv->device);
+    for (int i = 0; i < kLanes; ++i) cudaStreamCreateWithFlags(&sv->lanes[i], cudaStreamNonBlocking);
+    sv->th = std::thread(service_loop, sv);
+    g_services.push_back({ctx, sv});
+    return sv;
+}
+
+void free_stream(reg_stream *s)
+{
+    for (int l = 0; l < kMaxLevels; ++l)
+        if (s->pyr[l]) cudaFree(s->pyr[l]);
+    void *dev[] = {s->stage, s->means, s->table, s->ops, s->stats, s->theta, s->grid, s->status};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (s->h_ops) cudaFreeHost(s->h_ops);
+    if (s->h_theta) cudaFreeHost(s->h_theta);
+    if (s->h_stats) cudaFreeHost(s->h_stats);
+    for (int k = 0; k <= kSlots; ++k) {
+        if (s->slots[k].ready) cudaEventDestroy(s->slots[k].ready);
+        if (s->slots[k].a_ev) cudaEventDestroy(s->slots[k].a_ev);
+        if (s->slots[k].b_ev) cudaEventDestroy(s->slots[k].b_ev);
+    }
+    if (s->f0_ready) cudaEventDestroy(s->f0_ready);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    delete s;
+}
+
+}  // namespace
+
+// Called by reg_ctx_destroy: stop the service thread of the context.
+void reg::stop_stream_service(reg_ctx_t *ctx)
+{
+    Service *sv = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_services_mu);
+        for (size_t i = 0; i < g_services.size(); ++i)
+            if (g_services[i].first == ctx) {
+                sv = g_services[i].second;
+                g_services.erase(g_services.begin() + i);
+                break;
+            }
+    }
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    sv->th.join();
+    for (reg_stream *s : sv->streams) free_stream(s);
+    for (int i = 0; i < kLanes; ++i) cudaStreamDestroy(sv->lanes[i]);
+    delete sv;
+}
+
+extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
+{
+    if (!ctx || !out) return host_fail(REG_EINVAL, "NULL argument");
+    *out = nullptr;
+    const reg_config_t c = host_config(ctx);
+    int Wl[kMaxLevels], Hl[kMaxLevels];
+    {
+        int w = W, h = H;
+        for (int l = 0; l < c.levels; ++l) {
+            if (w < 2 || h < 2) return host_fail(REG_EINVAL, "every pyramid level needs at least 2x2 pixels");
+            Wl[l] = w;
+            Hl[l] = h;
+            w = (w + 1) / 2;
+            h = (h + 1) / 2;
+        }
+    }
+    int gnx = 0, gny = 0, gs = 0;
+    if (c.mode == REG_NONRIGID) {
+        int rc = reg_grid_dims(W, H, c.grid, c.levels, &gnx, &gny, &gs);
+        if (rc != REG_OK) return rc;
+    }
+    const size_t sb = c.storage == REG_F32 ? 4 : 2;
+    size_t pyr_bytes = 0;
+    for (int l = 0; l < c.levels; ++l) pyr_bytes += (size_t)Wl[l] * Hl[l] * sb;
+    const int nops = 2 * (kSlots + 1);
+    const size_t bytes = pyr_bytes * (kSlots + 1) + sizeof(float) * (size_t)W * H + sizeof(LevelDesc) * (kSlots + 1) * c.levels +
+                         (sizeof(OpDesc) + sizeof(OpStats) + 3 * sizeof(double)) * nops +
+                         sizeof(float2) * (size_t)gnx * gny * nops + 4096;
+    Service *sv = service_of(ctx, true);
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        if (c.mem_budget > 0 && sv->used_bytes + bytes > c.mem_budget)
+            return host_fail(REG_EBUDGET, "stream needs %zu bytes; %zu of the %zu-byte budget in use", bytes,
+                             sv->used_bytes, c.mem_budget);
+        sv->used_bytes += bytes;
+    }
+    if (cudaSetDevice(host_device(ctx)) != cudaSuccess) return host_fail(REG_ECUDA, "cudaSetDevice");
+    reg_stream *s = new reg_stream();
+    s->ctx = ctx;
+    s->W = W;
+    s->H = H;
+    s->L = c.levels;
+    s->storage = c.storage;
+    s->mode = c.mode;
+    s->gnx = gnx;
+    s->gny = gny;
+    s->gs = gs;
+    s->bytes = bytes;
+    bool ok = true;
+    for (int l = 0; l < c.levels && ok; ++l) {
+        s->Wl[l] = Wl[l];
+        s->Hl[l] = Hl[l];
+        s->lvl_elems[l] = (size_t)Wl[l] * Hl[l];
+        ok = cudaMalloc(&s->pyr[l], s->lvl_elems[l] * sb * (kSlots + 1)) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&s->stage, sizeof(float) * (size_t)W * H) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->means, sizeof(float) * kMaxLevels) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->table, sizeof(LevelDesc) * (kSlots + 1) * c.levels) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->ops, sizeof(OpDesc) * nops) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->stats, sizeof(OpStats) * nops) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->theta, sizeof(double) * 3 * nops) == cudaSuccess;
+    ok = ok && cudaMalloc(&s->status, sizeof(int) * 4) == cudaSuccess;
+    if (ok && gnx > 0) ok = cudaMalloc(&s->grid, sizeof(float2) * (size_t)gnx * gny * nops) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->h_ops, sizeof(OpDesc) * nops) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->h_theta, sizeof(double) * 3 * nops) == cudaSuccess;
+    ok = ok && cudaMallocHost(&s->h_stats, sizeof(OpStats) * nops) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k <= kSlots && ok; ++k) {
+        ok = cudaEventCreateWithFlags(&s->slots[k].ready, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->slots[k].a_ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->slots[k].b_ev, cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaEventCreateWithFlags(&s->f0_ready, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaMemset(s->status, 0, sizeof(int) * 4) == cudaSuccess &&
+                 cudaMemset(s->stats, 0, sizeof(OpStats) * nops) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_stream(s);
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->used_bytes -= bytes;
+        return host_fail(REG_ENOMEM, "stream allocation failed");
+    }
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->streams.push_back(s);
+    }
+    *out = s;
+    return REG_OK;
+}
+
+extern "C" int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t frame_id)
+{
+    if (!s || !frame) return host_fail(REG_EINVAL, "NULL argument");
+    Service *sv = service_of(s->ctx, false);
+    if (!sv) return host_fail(REG_ESTATE, "stream service is not running");
+    const double t_submit = now_us();
+    long long index;
+    int slot;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        if (s->closing) return host_fail(REG_ESTATE, "stream is closing");
+        if (s->error != REG_OK) return host_fail(s->error, "stream failed earlier");
+        index = s->submitted;
+        slot = index == 0 ? 0 : slot_of(index);
+        if (index > 0 && s->slots[slot].used) return host_fail(REG_EBUDGET, "all %d frame slots are in flight", kSlots);
+    }
+    if (cudaSetDevice(host_device(s->ctx)) != cudaSuccess) return host_fail(REG_ECUDA, "cudaSetDevice");
+    // copy the frame in and build its pyramid (the caller's buffer is free on return)
+    const size_t fb = sizeof(float) * (size_t)s->W * s->H;
+    const size_t sb = s->storage == REG_F32 ? 4 : 2;
+    void *lv[kMaxLevels];
+    size_t stride[kMaxLevels];
+    for (int l = 0; l < s->L; ++l) {
+        lv[l] = (char *)s->pyr[l] + s->lvl_elems[l] * sb * slot;
+        stride[l] = s->lvl_elems[l];
+    }
+    float hmeans[kMaxLevels];
+    cudaError_t e = cudaMemcpyAsync(s->stage, frame, fb, cudaMemcpyDefault, s->copy);
+    if (e == cudaSuccess)
+        e = launch_pyramid(s->stage, 1, (size_t)s->W * s->H, s->W, s->H, s->W, s->L, s->storage, lv, stride, s->means,
+                           s->copy);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmeans, s->means, sizeof(float) * s->L, cudaMemcpyDeviceToHost, s->copy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
+    LevelDesc tab[kMaxLevels];
+    for (int l = 0; l < s->L; ++l) {
+        tab[l].ptr = lv[l];
+        tab[l].W = s->Wl[l];
+        tab[l].H = s->Hl[l];
+        tab[l].pitch = s->Wl[l];
+        tab[l].mean = hmeans[l];
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->table + (size_t)slot * s->L, tab, sizeof(LevelDesc) * s->L, cudaMemcpyHostToDevice,
+                            s->copy);
+    cudaEvent_t ready = index == 0 ? s->f0_ready : s->slots[slot].ready;
+    if (e == cudaSuccess) e = cudaEventRecord(ready, s->copy);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return host_fail(REG_ECUDA, "staging the frame failed: %s", cudaGetErrorString(e));
+    }
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        s->submitted = index + 1;
+        if (index == 0) {
+            s->have_f0 = true;
+            reg_result_t r;
+            memset(&r, 0, sizeof(r));
+            r.frame_id = frame_id;
+            r.submit_us = t_submit;
+            r.done_us = now_us();
+            s->results.push_back(r);   // phi_{0,0} is the identity
+        } else {
+            Slot &sl = s->slots[slot];
+            sl.used = true;
+            sl.index = index;
+            sl.frame_id = frame_id;
+            sl.submit_us = t_submit;
+            sl.a_launched = sl.a_done = sl.b_launched = sl.b_done = sl.emitted = false;
+        }
+    }
+    sv->cv.notify_all();
+    return REG_OK;
+}
+
+extern "C" int reg_stream_poll(reg_stream_t *s, reg_result_t *out, int max, int *n_out, int timeout_us)
+{
+    if (!s || (!out && max > 0) || !n_out) return host_fail(REG_EINVAL, "NULL argument");
+    *n_out = 0;
+    Service *sv = service_of(s->ctx, false);
+    if (!sv) return host_fail(REG_ESTATE, "stream service is not running");
+    std::unique_lock<std::mutex> lock(sv->mu);
+    if (s->results.empty() && timeout_us > 0)
+        sv->done_cv.wait_for(lock, std::chrono::microseconds(timeout_us), [&] { return !s->results.empty() || s->error; });
+    int n = 0;
+    while (n < max && !s->results.empty()) {
+        out[n++] = s->results.front();
+        s->results.pop_front();
+    }
+    *n_out = n;
+    if (s->error != REG_OK) return host_fail(s->error, "stream failed on the device");
+    if (n == 0) return host_fail(REG_ETIMEOUT, "no result within %d us", timeout_us);
+    return REG_OK;
+}
+
+extern "C" int reg_stream_close(reg_stream_t *s)
+{
+    if (!s) return host_fail(REG_EINVAL, "NULL argument");
+    Service *sv = service_of(s->ctx, false);
+    if (!sv) return host_fail(REG_ESTATE, "stream service is not running");
+    int rc = REG_OK;
+    {
+        std::unique_lock<std::mutex> lock(sv->mu);
+        s->closing = true;
+        // every submitted frame finishes; bounded wait
+        auto all_done = [&] {
+            if (s->error != REG_OK) return true;
+            for (int k = 1; k <= kSlots; ++k)
+                if (s->slots[k].used && !s->slots[k].emitted) return false;
+            return true;
+        };
+        if (!sv->done_cv.wait_for(lock, std::chrono::seconds(120), all_done)) rc = REG_ETIMEOUT;
+        sv->streams.erase(std::remove(sv->streams.begin(), sv->streams.end(), s), sv->streams.end());
+        sv->used_bytes -= s->bytes;
+    }
+    cudaSetDevice(host_device(s->ctx));
+    for (int i = 0; i < kLanes; ++i) cudaStreamSynchronize(sv->lanes[i]);
+    free_stream(s);
+    return rc == REG_OK ? REG_OK : host_fail(rc, "stream close timed out waiting for its frames");
+}
