@@ -139,7 +139,7 @@ class Config:
     max_rejects: int = 30
     tol_grad: float = 1e-5
     tol_rel_e: float = 1e-10
-    armijo_c: float = 1e-4
+    armijo_c: float = 0.25
     tau0: float = 1.0
     step_cap: float = 0.5
     lam: float = 2.0

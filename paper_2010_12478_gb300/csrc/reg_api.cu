@@ -282,7 +282,7 @@ extern "C" void reg_config_default(reg_config_t *c)
     c->max_rejects = 30;
     c->tol_grad = 1e-5;
     c->tol_rel_e = 1e-10;
-    c->armijo_c = 1e-4;
+    c->armijo_c = 0.25;
     c->tau0 = 1.0;
     c->step_cap = 0.5;
     c->lambda = 2.0;

@@ -211,6 +211,37 @@ __device__ __forceinline__ void for_pixels(int W, int r0, int r1, F &&f, G &&flu
     for_pixels2(W, r0, r1, f, []() {}, flush);
 }
 
+// Row-major traversal for the fused evaluation passes: warp w walks rows r0 + w, r0 + w + kWarps,
+// ...; in a row, lane l takes columns l + 32 u (u < U) per step, so each thread has U independent
+// samples in flight and a warp's loads stay coalesced.  row(r) runs once per row; px(r, c) per
+// pixel; flush_fast() after every kFast pixels of a thread, flush() after every kChunk (and at
+// the end).  U must divide kFast.
+template <int U, typename RowF, typename PixF, typename Q, typename G>
+__device__ __forceinline__ void for_rows(int W, int r0, int r1, RowF &&row, PixF &&px, Q &&flush_fast, G &&flush)
+{
+    static_assert(kFast % U == 0, "U must divide kFast");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cnt = 0;
+    for (int r = r0 + warp; r < r1; r += kWarps) {
+        row(r);
+        for (int c0 = lane; c0 < W; c0 += 32 * U) {
+            if (c0 + 32 * (U - 1) < W) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) px(r, c0 + 32 * u);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (c0 + 32 * u < W) px(r, c0 + 32 * u);
+            }
+            cnt += U;
+            if ((cnt & (kFast - 1)) == 0) flush_fast();
+            if ((cnt & (kChunk - 1)) == 0) flush();
+        }
+    }
+    flush_fast();
+    flush();
+}
+
 // Bilinear sample of T (storage S, pitch Tp) at p = (xi + vx, yi + vy) with clamp-to-edge,
 // where (xi, yi) is an integer pixel and (vx, vy) a small FP32 offset.  Splitting the
 // position keeps the FP32 fractional part exact to the precision of the offset, not
@@ -270,22 +301,36 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
     // pm: cos(alpha) - 1, sin(alpha), fractional translation (x, y), integer translation (x, y)
     const float cm1 = pm[0], sa = pm[1], gfx = pm[2], gfy = pm[3];
     const int gix = (int)pm[4], giy = (int)pm[5];
+    const float ca = 1.f + cm1;
     const float cx = 0.5f * (float)(L.W - 1), cy = 0.5f * (float)(L.H - 1);
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     float hi[NM], lo[NM], a[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
-    for_pixels2(
+    // per-row terms of phi(x) - x - integer translation (small, so FP32 keeps ~1e-7 relative)
+    float yc = 0.f, bx = 0.f, by = 0.f, gax = 0.f, gay = 0.f;
+    const S *Rrow = R;
+    int yi = 0;
+    for_rows<4>(
         L.W, r0, r1,
+        [&](int r) {
+            yc = (float)r - cy;
+            bx = fmaf(-sa, yc, gfx);
+            by = fmaf(cm1, yc, gfy);
+            gax = -sa * yc;   // d phi_x / d alpha = ca xc - ... (terms in yc)
+            gay = ca * yc;
+            Rrow = R + (size_t)r * L.Rp;
+            yi = r + giy;
+        },
         [&](int r, int c) {
-            float xc = (float)c - cx, yc = (float)r - cy;
-            // phi(x) - x - integer translation: small, so FP32 keeps it to ~1e-7 relative
-            float vx = fmaf(cm1, xc, fmaf(-sa, yc, gfx));
-            float vy = fmaf(sa, xc, fmaf(cm1, yc, gfy));
+            (void)r;
+            const float xc = (float)c - cx;
+            const float vx = fmaf(cm1, xc, bx);
+            const float vy = fmaf(sa, xc, by);
             float dtx, dty;
-            float tw = sample_at<S, GRAD>(T, L.W, L.H, L.Tp, c + gix, r + giy, vx, vy, dtx, dty);
-            float rv = ldS<S>(R + (size_t)r * L.Rp + c) - L.cR;
-            float tv = tw - L.cR;
+            const float tw = sample_at<S, GRAD>(T, L.W, L.H, L.Tp, c + gix, yi, vx, vy, dtx, dty);
+            const float rv = ldS<S>(Rrow + c) - L.cR;
+            const float tv = tw - L.cR;
             a[0] += tv;
             a[1] = fmaf(tv, tv, a[1]);
             a[2] = fmaf(rv, tv, a[2]);
@@ -295,8 +340,7 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
             }
             if constexpr (GRAD) {
                 // g_alpha = dT . dphi/dalpha, dphi/dalpha = Rot'(alpha) (x - c)
-                const float ca = 1.f + cm1;
-                float g0 = fmaf(dty, fmaf(ca, xc, -sa * yc), -dtx * fmaf(sa, xc, ca * yc));
+                const float g0 = fmaf(dty, fmaf(ca, xc, gax), -dtx * fmaf(sa, xc, gay));
                 a[5] = fmaf(rv, g0, a[5]);
                 a[6] = fmaf(rv, dtx, a[6]);
                 a[7] = fmaf(rv, dty, a[7]);
@@ -561,16 +605,23 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     float hi[NM], lo[NM], a[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
-    for_pixels2(
+    const S *Rrow = R;
+    float gyf = 0.f;
+    for_rows<4>(
         L.W, r0, r1,
+        [&](int r) {
+            Rrow = R + (size_t)r * L.Rp;
+            gyf = fminf(fmaf(GL.pl, (float)r, GL.off) * GL.scale_inv, (float)(G.ny - 1));
+        },
         [&](int r, int c) {
-            int ix, iy;
-            float wx, wy;
-            grid_cell(G, GL, c, r, ix, iy, wx, wy);
-            const float2 u = grid_eval(ct, G.nx, ix, iy, wx, wy);
+            const int iy = min((int)gyf, G.ny - 2);
+            const float wy = gyf - (float)iy;
+            const float gxf = fminf(fmaf(GL.pl, (float)c, GL.off) * GL.scale_inv, (float)(G.nx - 1));
+            const int ix = min((int)gxf, G.nx - 2);
+            const float2 u = grid_eval(ct, G.nx, ix, iy, gxf - (float)ix, wy);
             float dtx, dty;
             float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c, r, u.x, u.y, dtx, dty);
-            float rv = ldS<S>(R + (size_t)r * L.Rp + c) - L.cR;
+            float rv = ldS<S>(Rrow + c) - L.cR;
             float tv = tw - L.cR;
             a[0] += tv;
             a[1] = fmaf(tv, tv, a[1]);
