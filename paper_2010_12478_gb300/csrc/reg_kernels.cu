@@ -60,6 +60,15 @@ __device__ __forceinline__ void ff_acc(float &hi, float &lo, float x)
     lo = __fadd_rn(lo, e);
 }
 
+// acc += x*y with the exact rounding error of the product kept in err (the error of a
+// product of two floats is exactly representable: fmaf(x, y, -p)).
+__device__ __forceinline__ void acc_prod(float &acc, float &err, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    err += fmaf(x, y, -p);
+    acc = __fadd_rn(acc, p);
+}
+
 // (hi, lo) += (h2, l2), renormalised.
 __device__ __forceinline__ void ff_add(float &hi, float &lo, float h2, float l2)
 {
@@ -305,6 +314,7 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
     const float cx = 0.5f * (float)(L.W - 1), cy = 0.5f * (float)(L.H - 1);
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     float hi[NM], lo[NM], a[NM];
+    float e1 = 0.f, e2 = 0.f, e4 = 0.f;   // product rounding errors of slots 1, 2, 4
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
     // per-row terms of phi(x) - x - integer translation (small, so FP32 keeps ~1e-7 relative)
@@ -332,11 +342,11 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
             const float rv = ldS<S>(Rrow + c) - L.cR;
             const float tv = tw - L.cR;
             a[0] += tv;
-            a[1] = fmaf(tv, tv, a[1]);
-            a[2] = fmaf(rv, tv, a[2]);
+            acc_prod(a[1], e1, tv, tv);
+            acc_prod(a[2], e2, rv, tv);
             if constexpr (NM > 3) {
                 a[3] += rv;
-                a[4] = fmaf(rv, rv, a[4]);
+                acc_prod(a[4], e4, rv, rv);
             }
             if constexpr (GRAD) {
                 // g_alpha = dT . dphi/dalpha, dphi/dalpha = Rot'(alpha) (x - c)
@@ -353,9 +363,13 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
             }
         },
         [&]() {
-            // energy moments: short FP32 runs keep 1 - NCC accurate to ~1e-9
+            // energy moments: short FP32 runs plus the exact product errors keep 1 - NCC
+            // accurate to ~1e-9 absolute
 #pragma unroll
             for (int m = 0; m < (NM < 5 ? NM : 5); ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+            lo[1] += e1; lo[2] += e2;
+            e1 = 0.f; e2 = 0.f;
+            if constexpr (NM > 4) { lo[4] += e4; e4 = 0.f; }
         },
         [&]() {
 #pragma unroll
@@ -603,6 +617,7 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     constexpr int NM = 6;
     float hi[NM], lo[NM], a[NM];
+    float e1 = 0.f, e2 = 0.f, e4 = 0.f;   // product rounding errors of slots 1, 2, 4
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
     const S *Rrow = R;
@@ -624,14 +639,16 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
             float rv = ldS<S>(Rrow + c) - L.cR;
             float tv = tw - L.cR;
             a[0] += tv;
-            a[1] = fmaf(tv, tv, a[1]);
-            a[2] = fmaf(rv, tv, a[2]);
+            acc_prod(a[1], e1, tv, tv);
+            acc_prod(a[2], e2, rv, tv);
             a[3] += rv;
-            a[4] = fmaf(rv, rv, a[4]);
+            acc_prod(a[4], e4, rv, rv);
         },
         [&]() {
 #pragma unroll
             for (int m = 0; m < 5; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+            lo[1] += e1; lo[2] += e2; lo[4] += e4;
+            e1 = 0.f; e2 = 0.f; e4 = 0.f;
         },
         []() {});
     if (cl.block_rank() == 0) {
