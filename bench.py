@@ -245,6 +245,51 @@ def serving(dev, mode: str, frames_per_stream: int, seed: int = 1410):
                                       f"so the default bench stays within minutes)"}
 
 
+# ------------------------------------------------------------------ precision
+def precision(frames, mode: str, n_samples: int = 2):
+    """Per pyramid storage type: scan throughput on the workload and the maximum displacement
+    error of sampled neighbour operators A(f_i, f_{i+1}) against the FP64 oracle."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2010_12478_gb300 import binding as B
+    N, H, W = frames.shape
+    n = N - 1
+    idx = [int(i) for i in np.linspace(0, n - 1, n_samples)]
+    Fh = frames.cpu().numpy()
+    ref = {}
+    cfg0 = B.Config(mode=mode)
+    oc = O.Config(levels=cfg0.levels, max_iter=cfg0.max_iter, max_rejects=cfg0.max_rejects, tol_grad=cfg0.tol_grad,
+                  tol_rel_e=cfg0.tol_rel_e, armijo_c=cfg0.armijo_c, tau0=cfg0.tau0, step_cap=cfg0.step_cap,
+                  lam=cfg0.lam, mode=mode, grid=cfg0.grid)
+    for i in idx:
+        ref[i] = O.op_A({i: O.pyramid(Fh[i], oc.levels), i + 1: O.pyramid(Fh[i + 1], oc.levels)}, i, i + 1, oc)
+    out = {}
+    for storage in ("f32", "bf16", "f16"):
+        ctx = B.Context(B.Config(mode=mode, storage=storage))
+        fo = torch.empty((n, 2, H, W), device=frames.device) if mode == "nonrigid" else None
+        ctx.scan(frames, schedule="brent_kung", exec="persistent", fields_out=fo)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        els, st = ctx.scan(frames, schedule="brent_kung", exec="persistent", fields_out=fo)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        errs = []
+        for i in idx:
+            # leaves are the first n operators of the per-op stats; compare the operator A(f_i, f_{i+1})
+            if mode == "rigid":
+                errs.append(O.max_px_error(np.array(st[i]["theta"]), ref[i].phi, H, W, "rigid"))
+            else:
+                g = O.grid_for(W, H, cfg0.grid)
+                ctx1 = B.Context(B.Config(mode=mode, storage=storage, cluster=8))
+                u = torch.empty((2, H, W), device=frames.device)
+                ctx1.pairwise(frames[i].contiguous(), frames[i + 1].contiguous(), field_out=u)
+                errs.append(O.max_px_error(u.cpu().numpy(), O.grid_dense(g, ref[i].phi), H, W, "nonrigid"))
+        out[storage] = {"frames_per_s": round(n / dt, 2), "max_px_error_vs_oracle": round(max(errs), 5),
+                        "operators_sampled": len(idx)}
+    return out
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -253,12 +298,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
-    ap.add_argument("--mode", default="rigid", choices=["rigid", "nonrigid"])
+    ap.add_argument("--mode", default="nonrigid", choices=["rigid", "nonrigid"])
     ap.add_argument("--exec", dest="exec_", default="plain", choices=["plain", "level", "persistent"])
-    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--cluster", type=int, default=0, help="CTAs per operator; 0 = autotuned")
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main timed region only (for profiler captures)")
+    ap.add_argument("--serve-frames", type=int, default=96, help="frames per stream in the serving run")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -288,21 +334,24 @@ def main():
     ser = synth.make_series(spec, device=dev)
     frames = ser.frames
     N, H, W = frames.shape
-    cfg = B.Config(mode=args.mode, cluster=args.cluster)
-    ctx = B.Context(cfg, device=local)
-    ctx.set_timing(True)
-    fields = torch.empty((N - 1, 2, H, W), device=dev) if args.mode == "nonrigid" else None
-
-    def step(src, exec_):
-        return ctx.scan(src, schedule="brent_kung", exec=exec_, fields_out=fields)
 
     def barrier():
         if dist:
             dist.barrier()
 
-    def timed(src, exec_, steps, warmup):
+    def make_ctx(mode):
+        c = B.Context(B.Config(mode=mode, cluster=args.cluster), device=local)
+        c.set_timing(True)
+        fl = torch.empty((N - 1, 2, H, W), device=dev) if mode == "nonrigid" else None
+        tuned = {}
+        if args.cluster == 0 and not args.quick:
+            for ex in ("plain", "persistent"):
+                tuned[ex] = c.autotune(frames, exec=ex)   # outside every timed region
+        return c, fl, tuned
+
+    def timed(ctx, fields, src, exec_, steps, warmup):
         for _ in range(warmup):
-            step(src, exec_)
+            ctx.scan(src, schedule="brent_kung", exec=exec_, fields_out=fields)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -311,7 +360,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            _, st = step(src, exec_)
+            _, st = ctx.scan(src, schedule="brent_kung", exec=exec_, fields_out=fields)
             st_list.append(st)
             tim.append(ctx.last_timing())
         e1.record()
@@ -324,9 +373,11 @@ def main():
             ms = float(t.item())
         return ms, st_list, tim
 
+    ctx, fields, tuned = make_ctx(args.mode)
+    cfg = ctx.cfg
     # ---- main timed region (device-resident frames, the workload's stated executor)
     with ClockSampler(local) as clk:
-        ms, st_list, tim = timed(frames, args.exec_, args.steps, args.warmup)
+        ms, st_list, tim = timed(ctx, fields, frames, args.exec_, args.steps, args.warmup)
     clocks = clk.summary()
     n_ops = len(st_list[0])
     value = world * (N - 1) / (ms / 1e3)
@@ -341,25 +392,39 @@ def main():
     achieved = alg / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     traffic = profile_traffic(kernel_hash())
     gpu_launches = int(sum(t["op_launches"] + t["pyramid_launches"] for t in tim))
+    ev = np.array([sum(s["evals"]) for s in st_list[0]])
 
     levels = cfg.levels
-    batched = e2e = None
+    batched = e2e = other = serve = prec = None
     if not args.quick:
         # ---- batched executor on the same workload
-        bms, bst, btim = timed(frames, "persistent", max(3, args.steps // 2), 2)
+        bms, bst, btim = timed(ctx, fields, frames, "persistent", max(3, args.steps // 2), 2)
         batched = {"exec": "persistent", "value": round(world * (N - 1) / (bms / 1e3), 2), "unit": UNIT,
-                   "ms_per_step": round(bms, 3),
+                   "ms_per_step": round(bms, 3), "cluster": tuned.get("persistent", args.cluster),
                    "op_kernel_ms": round(sum(t["op_kernel_ms"] for t in btim) / len(btim), 3)}
         # ---- end to end: pinned host frames through the C ABI, copies inside the timed region
         host = frames.cpu().pin_memory()
-        ems, _, _ = timed(host, args.exec_, max(3, args.steps // 2), 1)
+        ems, _, _ = timed(ctx, fields, host, args.exec_, max(3, args.steps // 2), 1)
         n_nodes = (N - 1) + B.scan_work("brent_kung", N - 1)
         d2h = 4 * N * levels + 16 + 24 * n_nodes + 144 * n_ops + 20 * (N - 1)
         e2e = {"value": round(world * (N - 1) / (ems / 1e3), 2), "unit": UNIT,
                "h2d_bytes_per_step": int(N * H * W * 4), "d2h_bytes_per_step": int(d2h)}
-
-    # ---- accuracy bookkeeping: iterations per operator (uneven counts drive the load balance)
-    ev = np.array([sum(s["evals"]) for s in st_list[0]])
+        # ---- the other deformation model on the same workload
+        omode = "rigid" if args.mode == "nonrigid" else "nonrigid"
+        octx, ofields, otuned = make_ctx(omode)
+        oms, ost, _ = timed(octx, ofields, frames, args.exec_, max(3, args.steps // 2), 2)
+        obms, _, _ = timed(octx, ofields, frames, "persistent", max(3, args.steps // 2), 2)
+        oev = np.array([sum(s["evals"]) for s in ost[0]])
+        other = {"mode": omode, "value": round(world * (N - 1) / (oms / 1e3), 2), "unit": UNIT,
+                 "exec": args.exec_, "batched_value": round(world * (N - 1) / (obms / 1e3), 2),
+                 "evals_per_operator": {"mean": round(float(oev.mean()), 2), "max": int(oev.max())},
+                 "cluster": otuned}
+        del octx
+        if rank == 0:
+            # ---- serving: eight Poisson streams, online registration, p50/p99 latency
+            serve = {m: serving(dev, m, args.serve_frames) for m in (args.mode, omode)}
+            # ---- precision forms: pyramid storage fp32 / bf16 / fp16
+            prec = precision(frames, args.mode)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and not args.quick and world == 1:
@@ -377,7 +442,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "frames": N, "H": H,
                        "W": W, "mode": args.mode, "levels": levels, "schedule": "brent_kung",
-                       "exec": args.exec_, "cluster": args.cluster or "auto",
+                       "exec": args.exec_, "cluster": args.cluster or {"autotuned": tuned},
                        "l2": "inputs larger than L2 (frames %d MiB > 129 MB L2)" % (N * H * W * 4 >> 20),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "ops_per_s": round(ops_per_s, 2), "operators_per_step": n_ops,
@@ -389,6 +454,9 @@ def main():
                          "kernel": "op_kernel (operator kernel)", "algorithmic_bytes_per_step": alg,
                          "kernel_ms_per_step": round(kms, 3), "launches_per_step": launches},
             "batched": batched,
+            "other_mode": other,
+            "serving": serve,
+            "precision": prec,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,

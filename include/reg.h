@@ -36,6 +36,12 @@
  *   - All computation runs in the library's CUDA kernels (sm_103a); there is
  *     no CPU fallback.  Without a usable GPU every compute entry point
  *     returns REG_ECUDA.
+ *   - Every wait inside a kernel is bounded.  The persistent executor's wait
+ *     for a ready operator gives up after 20 s (REG_QUEUE_TIMEOUT_MS in the
+ *     environment overrides it), and reg_scan then returns REG_ETIMEOUT with the
+ *     context still usable.  For tests, REG_FAULT_INJECT=stuck_op in the
+ *     environment makes one operator of the next persistent reg_scan wait for
+ *     an input that never arrives.
  */
 #ifndef REG_H
 #define REG_H
@@ -257,6 +263,23 @@ int reg_stream_poll(reg_stream_t *s, reg_result_t *out, int max, int *n_out, int
 
 /* Finish all submitted frames and release the stream. */
 int reg_stream_close(reg_stream_t *s);
+
+/* ---- autotuner ----------------------------------------------------------- */
+
+/* Choose the number of CTAs that cooperate on one operator (the "tile": rows of
+ * each pyramid level per CTA) for this frame size, mode, storage type and
+ * executor, by timing reg_scan on `frames` with 1, 2, 4, 8 and 16 CTAs per
+ * operator (each twice, after one untimed run) and keeping the fastest.  Later
+ * reg_scan calls on the context with cfg.cluster == 0 and a matching shape
+ * (same W, H, mode, storage, executor and floor(log2 N)) use the choice.
+ * Arguments as reg_scan; best (host, optional) receives the choice.  The paper
+ * has no counterpart (its operator runs on one CPU core). */
+int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch,
+                 int schedule, int exec, int *best);
+
+/* Write / read the context's autotuned choices as JSON lines (host files). */
+int reg_autotune_save(reg_ctx_t *ctx, const char *path);
+int reg_autotune_load(reg_ctx_t *ctx, const char *path);
 
 /* ---- measurement ----------------------------------------------------------- */
 

@@ -30,7 +30,7 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_scan_work", "reg_scan_dag", "reg_pyramid", "reg_energy", "reg_compose_grid", "reg_grid_dims",
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
-           "reg_pairwise_noalloc"]
+           "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load"]
 
 
 class RegError(RuntimeError):
@@ -99,6 +99,9 @@ def lib() -> ctypes.CDLL:
         L.reg_pairwise_noalloc.argtypes = [ctypes.POINTER(reg_config_t), ip, fp, fp, ip, ip, ip,
                                            ctypes.POINTER(reg_elem_t), ctypes.POINTER(reg_elem_t),
                                            ctypes.POINTER(reg_stats_t), vp]
+        L.reg_autotune.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(ip)]
+        L.reg_autotune_save.argtypes = [vp, ctypes.c_char_p]
+        L.reg_autotune_load.argtypes = [vp, ctypes.c_char_p]
         L.reg_ctx_set_timing.argtypes = [vp, ip]
         L.reg_ctx_last_timing.argtypes = [vp, ctypes.POINTER(reg_timing_t)]
         L.reg_strerror.argtypes = [ip]
@@ -195,6 +198,19 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, frames, schedule: str = "brent_kung", exec: str = "persistent") -> int:
+        N, H, W = frames.shape
+        best = ctypes.c_int()
+        check(lib().reg_autotune(self.h, _ptr(frames), N, W, H, W, SCHEDULES[schedule], EXECS[exec],
+                                 ctypes.byref(best)), "reg_autotune")
+        return best.value
+
+    def autotune_save(self, path: str):
+        check(lib().reg_autotune_save(self.h, path.encode()), "reg_autotune_save")
+
+    def autotune_load(self, path: str):
+        check(lib().reg_autotune_load(self.h, path.encode()), "reg_autotune_load")
 
     def set_timing(self, enable: bool = True):
         check(lib().reg_ctx_set_timing(self.h, int(enable)), "reg_ctx_set_timing")

@@ -2,9 +2,12 @@
 // builders, the executors and device memory management.
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -264,6 +267,8 @@ struct reg_ctx {
     cudaEvent_t ev_pool_done[16] = {};
     std::vector<cudaEvent_t> op_events;
     bool pool_ready = false;
+    // autotuned CTAs per operator, keyed by (W, H, mode, storage, exec, floor(log2 N))
+    std::map<std::tuple<int, int, int, int, int, int>, int> tuned;
     // measurement
     bool timing = false;
     std::vector<cudaEvent_t> tev;   // timing events, used in pairs
@@ -503,6 +508,20 @@ int build_level_table(reg_ctx *ctx, const Geometry &g, int total, cudaStream_t s
     return REG_OK;
 }
 
+int log2_floor(int v)
+{
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
+// CTAs per operator chosen by reg_autotune for this shape and executor, or 0.
+int tuned_cluster(const reg_ctx *ctx, int W, int H, int exec, int N)
+{
+    auto it = ctx->tuned.find(std::make_tuple(W, H, ctx->cfg.mode, ctx->cfg.storage, exec, log2_floor(N)));
+    return it == ctx->tuned.end() ? 0 : it->second;
+}
+
 int pow2_floor(int v)
 {
     int p = 1;
@@ -634,7 +653,7 @@ int check_device_status(reg_ctx *ctx, cudaStream_t s)
 }
 
 // Execute the planned operators.
-int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_t s)
+int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, cudaStream_t s)
 {
     const int n_ops = (int)plan.ops.size();
     const int storage = ctx->cfg.storage;
@@ -643,7 +662,7 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
     if (exec == REG_EXEC_LEVEL) {
         for (int dpt = 0; dpt < n_depth; ++dpt) {
             int b = plan.depth_start[dpt], e = plan.depth_start[dpt + 1];
-            int C = auto_cluster(ctx, e - b);
+            int C = tuned > 0 ? tuned : auto_cluster(ctx, e - b);
             int chunk = std::max(1, e - b);
             for (int q = b; q < e; q += chunk) {
                 p.op_base = q;
@@ -658,7 +677,7 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
     if (exec == REG_EXEC_PLAIN) {
         CHECK(ensure_pool(ctx));
         CHECK(ensure_op_events(ctx, n_ops));
-        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 8;
+        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
         std::vector<int> node_op(p.n_nodes, -1);
         for (int e = 0; e < n_ops; ++e) node_op[plan.ops[e].out] = e;
         const int t0 = timing_mark(ctx, s);
@@ -709,6 +728,15 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
                 cons[fillp[op.right]++] = e;
             }
         }
+        // Host-side fault injection for tests: REG_FAULT_INJECT=stuck_op keeps the last operator
+        // waiting for an input that never arrives, so the device queue's bounded wait must give
+        // up and report REG_ETIMEOUT; REG_QUEUE_TIMEOUT_MS shortens that wait.
+        const char *inj = getenv("REG_FAULT_INJECT");
+        if (inj && strcmp(inj, "stuck_op") == 0 && n_ops > 0) {
+            const int last = n_ops - 1;
+            if (pending[last] == 0) ready.erase(std::remove(ready.begin(), ready.end(), last), ready.end());
+            pending[last] += 1;
+        }
         std::vector<int> slots(n_ops, -1);
         for (size_t i = 0; i < ready.size(); ++i) slots[i] = ready[i];
         CHECK(ctx->q_slots.reserve(sizeof(int) * std::max(1, n_ops)));
@@ -731,7 +759,11 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, cudaStream_
         p.queue.consumers = ctx->q_cons.as<int>();
         p.queue.cons_start = ctx->q_cons_start.as<int>();
         p.queue.timeout_ns = 20LL * 1000 * 1000 * 1000;
-        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 2;
+        if (const char *t = getenv("REG_QUEUE_TIMEOUT_MS")) {
+            long long ms = atoll(t);
+            if (ms > 0) p.queue.timeout_ns = ms * 1000 * 1000;
+        }
+        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
         int workers = ctx->cfg.workers > 0 ? ctx->cfg.workers : std::max(1, 2 * ctx->num_sms / C);
         workers = std::max(1, std::min(workers, n_ops));
         p.op_base = 0;
@@ -793,7 +825,7 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     Params p;
     CHECK(prepare_params(ctx, g, N, plan.n_nodes, n_ops, p, s));
     CU(cudaMemcpyAsync(ctx->ops.ptr, plan.ops.data(), sizeof(OpDesc) * n_ops, cudaMemcpyHostToDevice, s));
-    CHECK(execute(ctx, plan, p, exec, s));
+    CHECK(execute(ctx, plan, p, exec, ctx->cfg.cluster > 0 ? 0 : tuned_cluster(ctx, W, H, exec, N), s));
     CU(cudaGetLastError());
     CHECK(check_device_status(ctx, s));
 
@@ -1027,4 +1059,90 @@ extern "C" int reg_ctx_last_timing(reg_ctx_t *ctx, reg_timing_t *out)
     if (!ctx || !out) return fail(REG_EINVAL, "NULL argument");
     *out = ctx->last;
     return REG_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+extern "C" int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch, int schedule,
+                            int exec, int *best)
+{
+    if (!ctx || !frames) return fail(REG_EINVAL, "NULL argument");
+    if (N < 2) return fail(REG_EINVAL, "need N >= 2 frames");
+    const int saved = ctx->cfg.cluster;
+    const int n = N - 1;
+    std::vector<reg_elem_t> out(n);
+    const size_t fb = sizeof(float) * 2 * (size_t)W * H * n;
+    void *fields = nullptr;
+    if (ctx->cfg.mode == REG_NONRIGID) {
+        if (cudaMalloc(&fields, fb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(REG_ENOMEM, "autotune: field buffer");
+        }
+    }
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best_c = 0, rc = REG_OK;
+    float best_ms = 1e30f;
+    const int cands[] = {1, 2, 4, 8, 16};
+    for (int c : cands) {
+        ctx->cfg.cluster = c;
+        rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), (float *)fields, nullptr, s);
+        if (rc != REG_OK) break;   // e.g. a cluster size the device cannot schedule
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2 && rc == REG_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), (float *)fields, nullptr, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_min = std::min(ms_min, ms);
+        }
+        if (rc != REG_OK) break;
+        if (ms_min < best_ms) { best_ms = ms_min; best_c = c; }
+    }
+    ctx->cfg.cluster = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (fields) cudaFree(fields);
+    if (best_c == 0) return rc != REG_OK ? rc : fail(REG_ECUDA, "autotune: no candidate ran");
+    ctx->tuned[std::make_tuple(W, H, ctx->cfg.mode, ctx->cfg.storage, exec, log2_floor(N))] = best_c;
+    if (best) *best = best_c;
+    return REG_OK;
+}
+
+extern "C" int reg_autotune_save(reg_ctx_t *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(REG_EINVAL, "NULL argument");
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(REG_EINVAL, "cannot write %s", path);
+    for (auto &kv : ctx->tuned) {
+        int W, H, mode, storage, exec, lg;
+        std::tie(W, H, mode, storage, exec, lg) = kv.first;
+        fprintf(f, "{\"W\": %d, \"H\": %d, \"mode\": %d, \"storage\": %d, \"exec\": %d, \"log2_frames\": %d, "
+                   "\"cluster\": %d}\n", W, H, mode, storage, exec, lg, kv.second);
+    }
+    fclose(f);
+    return REG_OK;
+}
+
+extern "C" int reg_autotune_load(reg_ctx_t *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(REG_EINVAL, "NULL argument");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(REG_EINVAL, "cannot read %s", path);
+    char line[512];
+    int loaded = 0;
+    while (fgets(line, sizeof(line), f)) {
+        int W, H, mode, storage, exec, lg, c;
+        if (sscanf(line, "{\"W\": %d, \"H\": %d, \"mode\": %d, \"storage\": %d, \"exec\": %d, \"log2_frames\": %d, "
+                         "\"cluster\": %d}", &W, &H, &mode, &storage, &exec, &lg, &c) == 7 &&
+            (c == 1 || c == 2 || c == 4 || c == 8 || c == 16)) {
+            ctx->tuned[std::make_tuple(W, H, mode, storage, exec, lg)] = c;
+            ++loaded;
+        }
+    }
+    fclose(f);
+    return loaded > 0 ? REG_OK : fail(REG_EINVAL, "no autotune entries in %s", path);
 }

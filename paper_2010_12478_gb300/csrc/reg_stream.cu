@@ -29,7 +29,8 @@ namespace {
 
 constexpr int kLanes = 32;          // CUDA streams the service launches operators on
 constexpr int kSlots = 24;          // frame slots per stream (frames in flight)
-constexpr int kStreamCluster = 4;   // CTAs per operator (fixed: results do not depend on load)
+constexpr int kClusterA = 4;    // CTAs per neighbour operator A (fixed: results do not depend on load)
+constexpr int kClusterB = 16;   // CTAs per B: the chain phi_{0,i-1} -> phi_{0,i} is each stream's critical path
 
 double now_us()
 {
@@ -142,7 +143,7 @@ int launch_op(Service *sv, reg_stream *s, int e, const OpDesc &op, cudaEvent_t e
         return REG_ECUDA;
     Params p = stream_params(s);
     p.op_base = e;
-    const int C = host_config(s->ctx).cluster > 0 ? host_config(s->ctx).cluster : kStreamCluster;
+    const int C = host_config(s->ctx).cluster > 0 ? host_config(s->ctx).cluster : (op.left >= 0 ? kClusterB : kClusterA);
     if (launch_ops(p, s->storage, C, 1, ls) != cudaSuccess) return REG_ECUDA;
     if (cudaMemcpyAsync(s->h_theta + 3 * e, s->theta + 3 * e, 3 * sizeof(double), cudaMemcpyDeviceToHost, ls) !=
         cudaSuccess)
