@@ -764,7 +764,12 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
             if (ms > 0) p.queue.timeout_ns = ms * 1000 * 1000;
         }
         const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
-        int workers = ctx->cfg.workers > 0 ? ctx->cfg.workers : std::max(1, 2 * ctx->num_sms / C);
+        int workers = ctx->cfg.workers;
+        if (workers <= 0) {
+            // one worker per cluster slot the device holds at once; extra workers would only wait
+            const int resident = persistent_resident_clusters(p, storage, C);
+            workers = resident > 0 ? resident : std::max(1, 2 * ctx->num_sms / C);
+        }
         workers = std::max(1, std::min(workers, n_ops));
         p.op_base = 0;
         int e0 = timing_mark(ctx, s);

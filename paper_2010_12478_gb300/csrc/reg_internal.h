@@ -89,6 +89,9 @@ cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_o
                        cudaStream_t s);
 cudaError_t launch_persistent(const Params &p, int storage, int cluster, int workers,
                               cudaStream_t s);
+// Clusters of `cluster` CTAs of the persistent kernel that fit on the device at once
+// (occupancy query), or -1 if the query fails.
+int persistent_resident_clusters(const Params &p, int storage, int cluster);
 cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
                           const float2 *grid_dev, double *out_dev, float2 *grad_dev,
                           cudaStream_t s);

@@ -82,6 +82,24 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float h2, float l2)
 }
 
 // ------------------------------------------------------------------ shared state
+// Step-controller state (FP64), used by thread 0 of each CTA only: kept in shared memory so
+// it does not occupy registers of every thread.
+struct RigidCtl {
+    double th[3], tt[3], d[3];
+    double E, tau, slope, sr, srr, m0, P, cx, cy;
+    double a, b, rbar, tbar;       // NCC terms at th
+    double ta, tb, trbar, ttbar;   // at the trial point tt
+    int nrej, iters, evals, stop, rejects;
+};
+
+struct FieldCtl {
+    double E, tau, tau_pend, slope, P, Nc, sr, srr;
+    double a, b, rbar, tbar;      // NCC terms at the current field
+    double ta, tb, trbar, ttbar;  // at the trial field
+    int degen, tdegen;
+    int nrej, iters, evals, stop, rejects;
+};
+
 struct Smem {
     float2 warp[kWarps][kNM];   // per-warp (hi, lo) partials
     double part[2][kNM];        // this CTA's partials, read by the whole cluster
@@ -89,6 +107,10 @@ struct Smem {
     float pm[16];               // pass parameters broadcast by thread 0
     int action;
     int idata[4];
+    union {
+        RigidCtl rctl;
+        FieldCtl fctl;
+    };
 };
 
 // Reduce NM per-thread float-float partials over the cluster into sm.tot.
@@ -302,32 +324,91 @@ __device__ __forceinline__ float sample_cg(const float *F, int W, int H, int xi,
 }
 
 // ================================================================== rigid
-// Moment slots: 0 St, 1 Stt, 2 Srt, 3 Sr, 4 Srr, 5..7 Srg_k, 8..10 Stg_k, 11..13 Sg_k.
-template <typename S, int NM, bool GRAD>
-__device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &sm, int &buf,
-                           const cg::cluster_group &cl)
+// Energy pass moment slots: 0 St, 1 Stt, 2 Srt (t = T(phi(x)) - cR, r = R(x) - cR), and with
+// RSTAT (first pass of a level) 3 Sr, 4 Srr.
+template <typename S, bool RSTAT>
+__device__ void eval_rigid_energy(const Lvl &L, int r0, int r1, const float *pm, Smem &sm, int &buf,
+                                  const cg::cluster_group &cl)
 {
+    constexpr int NM = RSTAT ? 5 : 3;
     // pm: cos(alpha) - 1, sin(alpha), fractional translation (x, y), integer translation (x, y)
     const float cm1 = pm[0], sa = pm[1], gfx = pm[2], gfy = pm[3];
     const int gix = (int)pm[4], giy = (int)pm[5];
-    const float ca = 1.f + cm1;
     const float cx = 0.5f * (float)(L.W - 1), cy = 0.5f * (float)(L.H - 1);
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     float hi[NM], lo[NM], a[NM];
-    float e1 = 0.f, e2 = 0.f, e4 = 0.f;   // product rounding errors of slots 1, 2, 4
+    float e1 = 0.f, e2 = 0.f, e4 = 0.f;   // exact product rounding errors of slots 1, 2, 4
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
     // per-row terms of phi(x) - x - integer translation (small, so FP32 keeps ~1e-7 relative)
-    float yc = 0.f, bx = 0.f, by = 0.f, gax = 0.f, gay = 0.f;
+    float bx = 0.f, by = 0.f;
     const S *Rrow = R;
     int yi = 0;
     for_rows<4>(
         L.W, r0, r1,
         [&](int r) {
-            yc = (float)r - cy;
+            const float yc = (float)r - cy;
             bx = fmaf(-sa, yc, gfx);
             by = fmaf(cm1, yc, gfy);
-            gax = -sa * yc;   // d phi_x / d alpha = ca xc - ... (terms in yc)
+            Rrow = R + (size_t)r * L.Rp;
+            yi = r + giy;
+        },
+        [&](int r, int c) {
+            (void)r;
+            const float xc = (float)c - cx;
+            float dtx, dty;
+            const float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c + gix, yi, fmaf(cm1, xc, bx),
+                                                 fmaf(sa, xc, by), dtx, dty);
+            const float rv = ldS<S>(Rrow + c) - L.cR;
+            const float tv = tw - L.cR;
+            a[0] += tv;
+            acc_prod(a[1], e1, tv, tv);
+            acc_prod(a[2], e2, rv, tv);
+            if constexpr (RSTAT) {
+                a[3] += rv;
+                acc_prod(a[4], e4, rv, rv);
+            }
+        },
+        [&]() {
+            // short FP32 runs plus the exact product errors keep 1 - NCC accurate to ~1e-9
+#pragma unroll
+            for (int m = 0; m < NM; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+            lo[1] += e1; lo[2] += e2;
+            e1 = 0.f; e2 = 0.f;
+            if constexpr (RSTAT) { lo[4] += e4; e4 = 0.f; }
+        },
+        []() {});
+    cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
+}
+
+// Gradient pass at a point whose NCC terms are known (from the energy pass or the accepted
+// trial at the same point): slots k = 0..2 sum F(x) g_k(x), F = P dE/dTw =
+// -(aP (r - rbar) - bP (t - tbar)), g_k = grad T(phi(x)) . dphi/dtheta_k.
+// pm[6..9] = aP, bP, rbar, tbar (rbar, tbar: means of the shifted samples).
+template <typename S>
+__device__ void eval_rigid_grad(const Lvl &L, int r0, int r1, const float *pm, Smem &sm, int &buf,
+                                const cg::cluster_group &cl)
+{
+    constexpr int NM = 3;
+    const float cm1 = pm[0], sa = pm[1], gfx = pm[2], gfy = pm[3];
+    const int gix = (int)pm[4], giy = (int)pm[5];
+    const float aP = pm[6], bP = pm[7], rb = pm[8], tb = pm[9];
+    const float ca = 1.f + cm1;
+    const float cx = 0.5f * (float)(L.W - 1), cy = 0.5f * (float)(L.H - 1);
+    const S *R = (const S *)L.R, *T = (const S *)L.T;
+    float hi[NM], lo[NM], a[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
+    float bx = 0.f, by = 0.f, gax = 0.f, gay = 0.f;
+    const S *Rrow = R;
+    int yi = 0;
+    for_rows<4>(
+        L.W, r0, r1,
+        [&](int r) {
+            const float yc = (float)r - cy;
+            bx = fmaf(-sa, yc, gfx);
+            by = fmaf(cm1, yc, gfy);
+            gax = -sa * yc;   // terms in yc of dphi/dalpha = Rot'(alpha) (x - c)
             gay = ca * yc;
             Rrow = R + (size_t)r * L.Rp;
             yi = r + giy;
@@ -335,58 +416,30 @@ __device__ void eval_rigid(const Lvl &L, int r0, int r1, const float *pm, Smem &
         [&](int r, int c) {
             (void)r;
             const float xc = (float)c - cx;
-            const float vx = fmaf(cm1, xc, bx);
-            const float vy = fmaf(sa, xc, by);
             float dtx, dty;
-            const float tw = sample_at<S, GRAD>(T, L.W, L.H, L.Tp, c + gix, yi, vx, vy, dtx, dty);
+            const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, c + gix, yi, fmaf(cm1, xc, bx),
+                                                fmaf(sa, xc, by), dtx, dty);
             const float rv = ldS<S>(Rrow + c) - L.cR;
             const float tv = tw - L.cR;
-            a[0] += tv;
-            acc_prod(a[1], e1, tv, tv);
-            acc_prod(a[2], e2, rv, tv);
-            if constexpr (NM > 3) {
-                a[3] += rv;
-                acc_prod(a[4], e4, rv, rv);
-            }
-            if constexpr (GRAD) {
-                // g_alpha = dT . dphi/dalpha, dphi/dalpha = Rot'(alpha) (x - c)
-                const float g0 = fmaf(dty, fmaf(ca, xc, gax), -dtx * fmaf(sa, xc, gay));
-                a[5] = fmaf(rv, g0, a[5]);
-                a[6] = fmaf(rv, dtx, a[6]);
-                a[7] = fmaf(rv, dty, a[7]);
-                a[8] = fmaf(tv, g0, a[8]);
-                a[9] = fmaf(tv, dtx, a[9]);
-                a[10] = fmaf(tv, dty, a[10]);
-                a[11] += g0;
-                a[12] += dtx;
-                a[13] += dty;
-            }
+            // no contraction: identical r and t give F == 0 exactly
+            const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
+            const float g0 = fmaf(dty, fmaf(ca, xc, gax), -dtx * fmaf(sa, xc, gay));
+            a[0] = fmaf(F, g0, a[0]);
+            a[1] = fmaf(F, dtx, a[1]);
+            a[2] = fmaf(F, dty, a[2]);
         },
-        [&]() {
-            // energy moments: short FP32 runs plus the exact product errors keep 1 - NCC
-            // accurate to ~1e-9 absolute
-#pragma unroll
-            for (int m = 0; m < (NM < 5 ? NM : 5); ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
-            lo[1] += e1; lo[2] += e2;
-            e1 = 0.f; e2 = 0.f;
-            if constexpr (NM > 4) { lo[4] += e4; e4 = 0.f; }
-        },
+        []() {},
         [&]() {
 #pragma unroll
-            for (int m = 5; m < NM; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+            for (int m = 0; m < NM; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
         });
     cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
 }
 
 enum Action { kActGrad = 0, kActTrial = 1, kActDone = 2, kActEnergy = 3, kActField = 4 };
 
-struct RigidCtl {
-    double th[3], tt[3], d[3];
-    double E, tau, slope, sr, srr, m0, P, cx, cy;
-    int nrej, iters, evals, stop, rejects;
-};
 
-__device__ void rigid_params(const RigidCtl &k, const double *th, float *pm)
+__device__ void rigid_params(const double *th, float *pm)
 {
     const float a = (float)th[0];
     const float h = sinf(0.5f * a);
@@ -397,28 +450,33 @@ __device__ void rigid_params(const RigidCtl &k, const double *th, float *pm)
     pm[3] = (float)(th[2] - iy);
     pm[4] = (float)fmax(-4.0e6, fmin(4.0e6, ix));
     pm[5] = (float)fmax(-4.0e6, fmin(4.0e6, iy));
-    (void)k;
 }
 
-// Thread-0 controller step after a GRAD (first == true: the level's first) or TRIAL pass.
-// Returns the next action and writes the pass parameters.
-__device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int action, bool first,
-                          float *pm)
+__device__ void rigid_grad_params(const RigidCtl &k, float *pm)
 {
+    rigid_params(k.th, pm);
+    pm[6] = (float)(k.a * k.P);
+    pm[7] = (float)(k.b * k.P);
+    pm[8] = (float)k.rbar;
+    pm[9] = (float)k.tbar;
+}
+
+// Thread-0 controller after an ENERGY (level start), GRAD or TRIAL pass.  Returns the next
+// action and writes its parameters.  Same rules as the oracle's level loop.
+__device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int action, float *pm)
+{
+    if (action == kActEnergy) {
+        k.sr = tot[3];
+        k.srr = tot[4];
+        const Ncc n = ncc_terms(k.P, k.sr, tot[0], k.srr, tot[1], tot[2]);
+        k.E = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
+        k.a = n.a; k.b = n.b; k.rbar = n.rbar; k.tbar = n.tbar;
+        rigid_grad_params(k, pm);
+        return kActGrad;
+    }
     if (action == kActGrad) {
-        if (first) { k.sr = tot[3]; k.srr = tot[4]; }
-        Ncc n = ncc_terms(k.P, k.sr, tot[0], k.srr, tot[1], tot[2]);
         double g[3];
-        if (n.degenerate) {
-            k.E = 1.0; g[0] = g[1] = g[2] = 0.0;
-        } else {
-            k.E = __dsub_rn(1.0, n.ncc);
-            for (int q = 0; q < 3; ++q) {
-                double x = __dsub_rn(tot[5 + q], __dmul_rn(n.rbar, tot[11 + q]));
-                double y = __dsub_rn(tot[8 + q], __dmul_rn(n.tbar, tot[11 + q]));
-                g[q] = -__dsub_rn(__dmul_rn(n.a, x), __dmul_rn(n.b, y));
-            }
-        }
+        for (int q = 0; q < 3; ++q) g[q] = tot[q] / k.P;
         k.evals += 1;
         if (k.iters >= cfg.max_iter) { k.stop = REG_STOP_MAXIT; return kActDone; }
         k.d[0] = -g[0] / k.m0; k.d[1] = -g[1]; k.d[2] = -g[2];
@@ -428,21 +486,22 @@ __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int
         if (k.tau * gn > cfg.step_cap) k.tau = cfg.step_cap / gn;
         k.nrej = 0;
         for (int q = 0; q < 3; ++q) k.tt[q] = k.th[q] + k.tau * k.d[q];
-        rigid_params(k, k.tt, pm);
+        rigid_params(k.tt, pm);
         return kActTrial;
     }
     // trial
-    Ncc n = ncc_terms(k.P, k.sr, tot[0], k.srr, tot[1], tot[2]);
-    double Et = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
+    const Ncc n = ncc_terms(k.P, k.sr, tot[0], k.srr, tot[1], tot[2]);
+    const double Et = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
     k.evals += 1;
     if (Et <= k.E + cfg.armijo_c * k.tau * k.slope) {
         for (int q = 0; q < 3; ++q) k.th[q] = k.tt[q];
         k.iters += 1;
-        double Eold = k.E;
+        const double Eold = k.E;
         k.E = Et;
+        k.a = n.a; k.b = n.b; k.rbar = n.rbar; k.tbar = n.tbar;
         k.tau *= 2.0;
         if (Eold - Et <= cfg.tol_rel_e * fabs(Eold)) { k.stop = REG_STOP_REL; return kActDone; }
-        rigid_params(k, k.th, pm);
+        rigid_grad_params(k, pm);
         return kActGrad;
     }
     k.rejects += 1;
@@ -450,7 +509,7 @@ __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int
     k.tau *= 0.5;
     if (k.nrej > cfg.max_rejects) { k.stop = REG_STOP_LS; return kActDone; }
     for (int q = 0; q < 3; ++q) k.tt[q] = k.th[q] + k.tau * k.d[q];
-    rigid_params(k, k.tt, pm);
+    rigid_params(k.tt, pm);
     return kActTrial;
 }
 
@@ -471,7 +530,7 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
     const int C = cl.num_blocks(), rank = cl.block_rank();
     const Config &cfg = p.cfg;
     int buf = 0;
-    RigidCtl k;
+    RigidCtl &k = sm.rctl;
     if (tid == 0) {
         memset(&k, 0, sizeof(k));
         double th0[3] = {0.0, 0.0, 0.0};
@@ -508,22 +567,20 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
             k.m0 = rho * rho;
             k.tau = cfg.tau0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
-            rigid_params(k, k.th, sm.pm);
-            sm.action = kActGrad;
+            rigid_params(k.th, sm.pm);
+            sm.action = kActEnergy;
         }
-        bool first = true;
         for (;;) {
             __syncthreads();
             const int act = sm.action;
             if (act == kActDone) break;
-            float pm[6] = {sm.pm[0], sm.pm[1], sm.pm[2], sm.pm[3], sm.pm[4], sm.pm[5]};
-            if (act == kActGrad) {
-                eval_rigid<S, 14, true>(L, r0, r1, pm, sm, buf, cl);
-            } else {
-                eval_rigid<S, 3, false>(L, r0, r1, pm, sm, buf, cl);
-            }
-            if (tid == 0) sm.action = rigid_step(k, cfg, sm.tot, act, first && act == kActGrad, sm.pm);
-            if (act == kActGrad) first = false;
+            float pm[10];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) pm[q] = sm.pm[q];
+            if (act == kActEnergy) eval_rigid_energy<S, true>(L, r0, r1, pm, sm, buf, cl);
+            else if (act == kActGrad) eval_rigid_grad<S>(L, r0, r1, pm, sm, buf, cl);
+            else eval_rigid_energy<S, false>(L, r0, r1, pm, sm, buf, cl);
+            if (tid == 0) sm.action = rigid_step(k, cfg, sm.tot, act, sm.pm);
         }
         if (tid == 0) {
             stops[l] = k.stop; iters[l] = k.iters; evals[l] = k.evals;
@@ -608,47 +665,61 @@ __device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int r
     if (cr0 == cr1) r0 = r1 = L.H;
 }
 
-// Energy moments of the field ct: slots 0 St, 1 Stt, 2 Srt, 3 Sr, 4 Srr, 5 sum over control edges |dct|^2
-// (rank 0 only, so the cluster sum counts it once).
-template <typename S>
-__device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *ct, int r0, int r1,
-                                 Smem &sm, int &buf, const cg::cluster_group &cl)
+// Energy moments of the field ct: slots 0 St, 1 Stt, 2 Srt, with RSTAT (first pass of a level)
+// 3 Sr, 4 Srr; slot 5 = sum over control edges |dct|^2 (rank 0 only, so the cluster sum counts
+// it once).  Each warp first interpolates the control values of its row along y into crow
+// (nx values), so a pixel only interpolates along x.
+template <typename S, bool RSTAT>
+__device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *ct, float2 *crow_all,
+                                 int r0, int r1, Smem &sm, int &buf, const cg::cluster_group &cl)
 {
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     constexpr int NM = 6;
     float hi[NM], lo[NM], a[NM];
-    float e1 = 0.f, e2 = 0.f, e4 = 0.f;   // product rounding errors of slots 1, 2, 4
+    float e1 = 0.f, e2 = 0.f, e4 = 0.f;   // exact product rounding errors of slots 1, 2, 4
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
+    const int lane = threadIdx.x & 31;
+    float2 *crow = crow_all + (threadIdx.x >> 5) * G.nx;
     const S *Rrow = R;
-    float gyf = 0.f;
     for_rows<4>(
         L.W, r0, r1,
         [&](int r) {
             Rrow = R + (size_t)r * L.Rp;
-            gyf = fminf(fmaf(GL.pl, (float)r, GL.off) * GL.scale_inv, (float)(G.ny - 1));
+            const float gyf = fminf(fmaf(GL.pl, (float)r, GL.off) * GL.scale_inv, (float)(G.ny - 1));
+            const int iy = min((int)gyf, G.ny - 2);
+            const float wy = gyf - (float)iy, hy = 1.f - wy;
+            __syncwarp();
+            for (int j = lane; j < G.nx; j += 32) {
+                const float2 p0 = ct[iy * G.nx + j], p1 = ct[(iy + 1) * G.nx + j];
+                crow[j] = make_float2(fmaf(wy, p1.x, hy * p0.x), fmaf(wy, p1.y, hy * p0.y));
+            }
+            __syncwarp();
         },
         [&](int r, int c) {
-            const int iy = min((int)gyf, G.ny - 2);
-            const float wy = gyf - (float)iy;
             const float gxf = fminf(fmaf(GL.pl, (float)c, GL.off) * GL.scale_inv, (float)(G.nx - 1));
             const int ix = min((int)gxf, G.nx - 2);
-            const float2 u = grid_eval(ct, G.nx, ix, iy, gxf - (float)ix, wy);
+            const float wx = gxf - (float)ix;
+            const float2 p0 = crow[ix], p1 = crow[ix + 1];
+            const float ux = fmaf(wx, p1.x - p0.x, p0.x), uy = fmaf(wx, p1.y - p0.y, p0.y);
             float dtx, dty;
-            float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c, r, u.x, u.y, dtx, dty);
-            float rv = ldS<S>(Rrow + c) - L.cR;
-            float tv = tw - L.cR;
+            const float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c, r, ux, uy, dtx, dty);
+            const float rv = ldS<S>(Rrow + c) - L.cR;
+            const float tv = tw - L.cR;
             a[0] += tv;
             acc_prod(a[1], e1, tv, tv);
             acc_prod(a[2], e2, rv, tv);
-            a[3] += rv;
-            acc_prod(a[4], e4, rv, rv);
+            if constexpr (RSTAT) {
+                a[3] += rv;
+                acc_prod(a[4], e4, rv, rv);
+            }
         },
         [&]() {
 #pragma unroll
-            for (int m = 0; m < 5; ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
-            lo[1] += e1; lo[2] += e2; lo[4] += e4;
-            e1 = 0.f; e2 = 0.f; e4 = 0.f;
+            for (int m = 0; m < (RSTAT ? 5 : 3); ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+            lo[1] += e1; lo[2] += e2;
+            e1 = 0.f; e2 = 0.f;
+            if constexpr (RSTAT) { lo[4] += e4; e4 = 0.f; }
         },
         []() {});
     if (cl.block_rank() == 0) {
@@ -673,6 +744,31 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
 }
 
+// Sum eight per-lane values over the warp by halving exchanges: on return every lane holds the
+// total of value index 4 b4 + 2 b3 + b2 (b_k = bit k of the lane), the same in the four lanes
+// that share those bits.  9 shuffles instead of 40; fixed order, so deterministic.
+__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane)
+{
+    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+    float a4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b4 ? v[k] : v[k + 4], keep = b4 ? v[k + 4] : v[k];
+        a4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float a2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b3 ? a4[k] : a4[k + 2], keep = b3 ? a4[k + 2] : a4[k];
+        a2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const float send = b2 ? a2[0] : a2[1], keep = b2 ? a2[1] : a2[0];
+    float t = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    return t;
+}
+
 // Gradient pass at c: this CTA's cells in four parity phases (no two cells of a phase share a
 // corner, so each corner is updated by one warp at a time, in a fixed order); then every CTA
 // assembles the whole gradient from the (at most two) CTAs whose band holds each control row,
@@ -688,6 +784,8 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Nc = G.nx * G.ny, ncx = G.nx - 1, ncy = G.ny - 1;
     const int sl = G.s >> GL.l;
+    const int lg = 31 - __clz(sl);   // sl is a power of two (the spacing is a multiple of 2^l)
+    float *gpf = (float *)gp;
     for (int j = tid; j < Nc; j += kThreads) gp[j] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int phase = 0; phase < 4; ++phase) {
@@ -701,36 +799,40 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
             const int x0 = cxx * sl, x1 = (cxx == ncx - 1) ? L.W : min(L.W, x0 + sl);
             const int y0 = cyy * sl, y1 = (cyy == ncy - 1) ? L.H : min(L.H, y0 + sl);
             const int w = x1 - x0, npx = w * (y1 - y0);
+            const int j0 = cyy * G.nx + cxx;
+            const float2 c00 = c[j0], c01 = c[j0 + 1], c10 = c[j0 + G.nx], c11 = c[j0 + G.nx + 1];
+            const float2 dtop = make_float2(c01.x - c00.x, c01.y - c00.y);
+            const float2 dbot = make_float2(c11.x - c10.x, c11.y - c10.y);
+            const bool pow2 = (w == sl);
             float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             for (int i = lane; i < npx; i += 32) {
-                const int y = y0 + i / w, x = x0 + i % w;
-                int ix, iy;
-                float wx, wy;
-                grid_cell(G, GL, x, y, ix, iy, wx, wy);
-                const float2 u = grid_eval(c, G.nx, ix, iy, wx, wy);
+                const int y = y0 + (pow2 ? (i >> lg) : i / w), x = x0 + (pow2 ? (i & (sl - 1)) : i % w);
+                const float gxf = fminf(fmaf(GL.pl, (float)x, GL.off) * GL.scale_inv, (float)(G.nx - 1));
+                const float gyf = fminf(fmaf(GL.pl, (float)y, GL.off) * GL.scale_inv, (float)(G.ny - 1));
+                const float wx = gxf - (float)cxx, wy = gyf - (float)cyy;
+                const float tx = fmaf(wx, dtop.x, c00.x), ty = fmaf(wx, dtop.y, c00.y);
+                const float bx = fmaf(wx, dbot.x, c10.x), by = fmaf(wx, dbot.y, c10.y);
+                const float ux = fmaf(wy, bx - tx, tx), uy = fmaf(wy, by - ty, ty);
                 float dtx, dty;
-                const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, x, y, u.x, u.y, dtx, dty);
+                const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, x, y, ux, uy, dtx, dty);
                 const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
                 const float tv = tw - L.cR;
                 // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
                 const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
                 const float gx = F * dtx, gy = F * dty;
-                const float w00 = (1.f - wx) * (1.f - wy), w01 = wx * (1.f - wy), w10 = (1.f - wx) * wy, w11 = wx * wy;
+                const float hx = 1.f - wx, hy = 1.f - wy;
+                const float w00 = hx * hy, w01 = wx * hy, w10 = hx * wy, w11 = wx * wy;
                 acc[0] = fmaf(w00, gx, acc[0]); acc[1] = fmaf(w00, gy, acc[1]);
                 acc[2] = fmaf(w01, gx, acc[2]); acc[3] = fmaf(w01, gy, acc[3]);
                 acc[4] = fmaf(w10, gx, acc[4]); acc[5] = fmaf(w10, gy, acc[5]);
                 acc[6] = fmaf(w11, gx, acc[6]); acc[7] = fmaf(w11, gy, acc[7]);
             }
-#pragma unroll
-            for (int m = 0; m < 8; ++m)
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], off);
-            if (lane == 0) {
-                const int j = cyy * G.nx + cxx;
-                gp[j].x += acc[0]; gp[j].y += acc[1];
-                gp[j + 1].x += acc[2]; gp[j + 1].y += acc[3];
-                gp[j + G.nx].x += acc[4]; gp[j + G.nx].y += acc[5];
-                gp[j + G.nx + 1].x += acc[6]; gp[j + G.nx + 1].y += acc[7];
+            const float tot8 = warp_reduce_scatter8(acc, lane);
+            if ((lane & 3) == 0) {
+                const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                const int corner = vi >> 1;
+                const int jc = j0 + (corner & 1) + (corner >> 1) * G.nx;
+                gpf[2 * jc + (vi & 1)] += tot8;
             }
         }
         __syncthreads();
@@ -785,14 +887,6 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     }
     __syncthreads();
 }
-
-struct FieldCtl {
-    double E, tau, tau_pend, slope, P, Nc, sr, srr;
-    double a, b, rbar, tbar;      // NCC terms at the current field
-    double ta, tb, trbar, ttbar;  // at the trial field
-    int degen, tdegen;
-    int nrej, iters, evals, stop, rejects;
-};
 
 __device__ double field_energy(FieldCtl &k, const Config &cfg, const double *tot, bool trial)
 {
@@ -885,7 +979,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
     const int Lc = cfg.levels;
     const Grid G{p.gnx, p.gny, p.gs};
     const int Nc = G.nx * G.ny;
-    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
+    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc, *crow = gbuf + 4 * Nc;
     int buf = 0;
     // initial control values (finest px), scaled to the coarsest level
     {
@@ -909,7 +1003,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
             for (int j = tid; j < Nc; j += kThreads) c[j] = make_float2(0.f, 0.f);
         }
     }
-    FieldCtl k;
+    FieldCtl &k = sm.fctl;
     if (tid == 0) {
         memset(&k, 0, sizeof(k));
         k.Nc = (double)Nc;
@@ -939,14 +1033,14 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
 #pragma unroll
             for (int q = 0; q < 5; ++q) pm[q] = sm.pm[q];
             if (act == kActEnergy) {
-                grid_energy_pass<S>(L, G, GL, c, r0, r1, sm, buf, cl);
+                grid_energy_pass<S, true>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
             } else if (act == kActTrial) {
                 for (int j = tid; j < Nc; j += kThreads) {
                     const float2 a = c[j], b = d[j];
                     ct[j] = make_float2(fmaf(pm[0], b.x, a.x), fmaf(pm[0], b.y, a.y));
                 }
                 __syncthreads();
-                grid_energy_pass<S>(L, G, GL, ct, r0, r1, sm, buf, cl);
+                grid_energy_pass<S, false>(L, G, GL, ct, crow, r0, r1, sm, buf, cl);
             } else {
                 grid_grad_pass<S>(L, G, GL, c, d, gp, pm, cr0, cr1, sm, cl);
             }
@@ -1023,7 +1117,7 @@ __device__ void run_op(const Params &p, int op_index, Smem &sm, float2 *gbuf, co
 
 // Batched launch: cluster q of the grid runs operator op_base + q.
 template <int MODE, typename S>
-__global__ void __launch_bounds__(kThreads, 2) op_kernel(Params p)
+__global__ void __launch_bounds__(kThreads, MODE == REG_RIGID ? 4 : 3) op_kernel(Params p)
 {
     __shared__ Smem sm;
     extern __shared__ float2 gbuf[];   // nonrigid: control grid c, d, ct, gp
@@ -1036,7 +1130,7 @@ __global__ void __launch_bounds__(kThreads, 2) op_kernel(Params p)
 // Persistent launch: each cluster claims ready operators from the device queue
 // until all n_ops have been claimed.  Every wait is bounded by queue.timeout_ns.
 template <int MODE, typename S>
-__global__ void __launch_bounds__(kThreads, 2) persistent_kernel(Params p)
+__global__ void __launch_bounds__(kThreads, MODE == REG_RIGID ? 4 : 3) persistent_kernel(Params p)
 {
     __shared__ Smem sm;
     extern __shared__ float2 gbuf[];
@@ -1108,35 +1202,35 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
     int buf = 0;
     const Lvl L = level_of(p, 0, 1, 0);
     if constexpr (MODE == REG_RIGID) {
-        RigidCtl k;
-        memset(&k, 0, sizeof(k));
-        k.cx = 0.5 * (L.W - 1);
-        k.cy = 0.5 * (L.H - 1);
-        float pm[6];
-        rigid_params(k, theta, pm);
-        eval_rigid<S, 14, true>(L, 0, L.H, pm, sm, buf, cl);
+        RigidCtl &k = sm.rctl;
+        if (tid == 0) memset(&k, 0, sizeof(k));
+        __syncthreads();
+        k.P = (double)L.W * L.H;
+        k.th[0] = theta[0]; k.th[1] = theta[1]; k.th[2] = theta[2];
+        float pm[10];
+        rigid_params(k.th, pm);
+        eval_rigid_energy<S, true>(L, 0, L.H, pm, sm, buf, cl);
         if (tid == 0) {
-            double P = (double)L.W * L.H;
-            Ncc n = ncc_terms(P, sm.tot[3], sm.tot[0], sm.tot[4], sm.tot[1], sm.tot[2]);
-            out[0] = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
-            for (int q = 0; q < 3; ++q) {
-                double x = __dsub_rn(sm.tot[5 + q], __dmul_rn(n.rbar, sm.tot[11 + q]));
-                double y = __dsub_rn(sm.tot[8 + q], __dmul_rn(n.tbar, sm.tot[11 + q]));
-                out[1 + q] = n.degenerate ? 0.0 : -__dsub_rn(__dmul_rn(n.a, x), __dmul_rn(n.b, y));
-            }
+            rigid_step(k, p.cfg, sm.tot, kActEnergy, sm.pm);
+            out[0] = k.E;
         }
+        __syncthreads();
+        for (int q = 0; q < 10; ++q) pm[q] = sm.pm[q];
+        eval_rigid_grad<S>(L, 0, L.H, pm, sm, buf, cl);
+        if (tid == 0)
+            for (int q = 0; q < 3; ++q) out[1 + q] = sm.tot[q] / k.P;
     } else {
         const Grid G{p.gnx, p.gny, p.gs};
         const int Nc = G.nx * G.ny;
-        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc;
+        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc, *crow = gbuf + 4 * Nc;
         for (int j = tid; j < Nc; j += kThreads) c[j] = cgrid[j];
         __syncthreads();
         GridLvl GL;
         GL.W = L.W; GL.H = L.H; GL.l = 0; GL.pl = 1.f; GL.off = 0.f; GL.scale_inv = 1.f / (float)G.s;
         int cr0, cr1, r0, r1;
         grid_rows(G, GL, 0, 1, cr0, cr1, r0, r1);
-        grid_energy_pass<S>(L, G, GL, c, r0, r1, sm, buf, cl);
-        FieldCtl k;
+        grid_energy_pass<S, true>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
+        FieldCtl &k = sm.fctl;
         if (tid == 0) {
             memset(&k, 0, sizeof(k));
             k.P = (double)L.W * L.H;
@@ -1293,7 +1387,7 @@ cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, in
 
 static size_t grid_smem(const Params &p)
 {
-    return p.cfg.mode == REG_NONRIGID ? sizeof(float2) * 4 * (size_t)p.gnx * p.gny : 0;
+    return p.cfg.mode == REG_NONRIGID ? sizeof(float2) * (4 * (size_t)p.gnx * p.gny + (size_t)kWarps * p.gnx) : 0;
 }
 
 template <typename K>
@@ -1359,6 +1453,50 @@ cudaError_t launch_persistent(const Params &p, int storage, int cluster, int wor
         }
     }
     return cudaErrorInvalidValue;
+}
+
+template <typename K>
+static int resident_clusters(K kernel, int cluster, const Params &p)
+{
+    if (cluster > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return -1;
+    const size_t smem = grid_smem(p);
+    if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cluster);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &lc) != cudaSuccess) return -1;
+    return n;
+}
+
+int persistent_resident_clusters(const Params &p, int storage, int cluster)
+{
+    int n = -1;
+    if (p.cfg.mode == REG_RIGID) {
+        switch (storage) {
+        case REG_F32: n = resident_clusters(persistent_kernel<REG_RIGID, float>, cluster, p); break;
+        case REG_BF16: n = resident_clusters(persistent_kernel<REG_RIGID, __nv_bfloat16>, cluster, p); break;
+        case REG_F16: n = resident_clusters(persistent_kernel<REG_RIGID, __half>, cluster, p); break;
+        }
+    } else {
+        switch (storage) {
+        case REG_F32: n = resident_clusters(persistent_kernel<REG_NONRIGID, float>, cluster, p); break;
+        case REG_BF16: n = resident_clusters(persistent_kernel<REG_NONRIGID, __nv_bfloat16>, cluster, p); break;
+        case REG_F16: n = resident_clusters(persistent_kernel<REG_NONRIGID, __half>, cluster, p); break;
+        }
+    }
+    if (n < 0) cudaGetLastError();
+    return n;
 }
 
 cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev, const float2 *grid_dev,
