@@ -37,7 +37,7 @@ METRIC = "registered frames/s and operator applications/s at <=0.02 px vs FP64 o
 UNIT = "frames/s"
 
 
-def workload_spec(name: str, rank: int):
+def workload_spec(name: str, rank: int, frames: int = 0):
     from paper_2010_12478_gb300 import synth
     if name == "c1":
         spec = synth.spec_c1(seed=synth.DEFAULT_SEED + rank)
@@ -47,6 +47,8 @@ def workload_spec(name: str, rank: int):
         spec = synth.spec_c3(seed=synth.DEFAULT_SEED + rank)
     else:
         raise SystemExit(f"unknown workload {name}")
+    if frames > 0:   # a shorter series of the same kind (profiler captures)
+        spec.n_frames = frames
     return spec
 
 
@@ -299,7 +301,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
     ap.add_argument("--mode", default="nonrigid", choices=["rigid", "nonrigid"])
-    ap.add_argument("--exec", dest="exec_", default="plain", choices=["plain", "level", "persistent"])
+    ap.add_argument("--exec", dest="exec_", default="plain", choices=["plain", "level", "persistent", "graph"])
+    ap.add_argument("--frames", type=int, default=0, help="override the series length (small profiler cases)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per operator; 0 = autotuned")
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -330,7 +333,7 @@ def main():
     from paper_2010_12478_gb300 import build, synth
     build.build()
 
-    spec = workload_spec(args.workload, rank)
+    spec = workload_spec(args.workload, rank, args.frames)
     ser = synth.make_series(spec, device=dev)
     frames = ser.frames
     N, H, W = frames.shape

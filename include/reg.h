@@ -78,6 +78,10 @@ extern "C" {
 #define REG_EXEC_PLAIN      0   /* one operator per kernel launch, DAG order on a stream pool */
 #define REG_EXEC_LEVEL      1   /* one launch per DAG depth, all its operators batched */
 #define REG_EXEC_PERSISTENT 2   /* one persistent launch, device ready-queue over the DAG */
+#define REG_EXEC_GRAPH      3   /* the REG_EXEC_PLAIN launches captured once per plan as a CUDA
+                                   graph and replayed: same kernels, same results, no per-call
+                                   launch cost.  The graph is rebuilt when N, the schedule, the
+                                   frame geometry or a workspace changes. */
 
 #define REG_MAX_LEVELS 8
 
@@ -292,6 +296,9 @@ typedef struct {
                                   around the whole operator phase (stream-pool and persistent
                                   executors); 0 unless timing is enabled */
     double  pyramid_ms;        /* device time of the pyramid build, same method */
+    int32_t graph_captures;    /* REG_EXEC_GRAPH: 1 if this call captured a new graph, 0 if it
+                                  replayed the cached one (always 0 for the other executors) */
+    int32_t reserved;
 } reg_timing_t;
 
 /* Enable (1) or disable (0) event timing of the kernels launched by later calls. */

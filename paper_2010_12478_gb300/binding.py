@@ -21,7 +21,7 @@ REG_OK, REG_EINVAL, REG_ENOMEM, REG_EBUDGET, REG_ETIMEOUT, REG_ECUDA, REG_ESTATE
 RIGID, NONRIGID = 0, 1
 F32, BF16, F16 = 0, 1, 2
 SCHEDULES = {"sequential": 0, "brent_kung": 1, "dissemination": 2, "ladner_fischer": 3}
-EXECS = {"plain": 0, "level": 1, "persistent": 2}
+EXECS = {"plain": 0, "level": 1, "persistent": 2, "graph": 3}
 STORAGES = {"f32": F32, "bf16": BF16, "f16": F16}
 MAX_LEVELS = 8
 
@@ -61,7 +61,8 @@ class reg_stats_t(ctypes.Structure):
 
 class reg_timing_t(ctypes.Structure):
     _fields_ = [("op_launches", ctypes.c_int32), ("pyramid_launches", ctypes.c_int32),
-                ("op_kernel_ms", ctypes.c_double), ("pyramid_ms", ctypes.c_double)]
+                ("op_kernel_ms", ctypes.c_double), ("pyramid_ms", ctypes.c_double),
+                ("graph_captures", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class reg_result_t(ctypes.Structure):
@@ -219,7 +220,7 @@ class Context:
         t = reg_timing_t()
         check(lib().reg_ctx_last_timing(self.h, ctypes.byref(t)), "reg_ctx_last_timing")
         return dict(op_launches=t.op_launches, pyramid_launches=t.pyramid_launches,
-                    op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms)
+                    op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms, graph_captures=t.graph_captures)
 
     # ---- operators
     def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,

@@ -267,6 +267,11 @@ struct reg_ctx {
     cudaEvent_t ev_pool_done[16] = {};
     std::vector<cudaEvent_t> op_events;
     bool pool_ready = false;
+    // REG_EXEC_GRAPH: the captured plain-path launches and the plan they were captured for
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t capture = nullptr;   // graphs are captured here (the caller's stream may be the legacy one)
+    uint64_t graph_key = 0;
+    int graph_captures = 0;
     // autotuned CTAs per operator, keyed by (W, H, mode, storage, exec, floor(log2 N))
     std::map<std::tuple<int, int, int, int, int, int>, int> tuned;
     // measurement
@@ -355,9 +360,11 @@ extern "C" void reg_ctx_destroy(reg_ctx_t *ctx)
             cudaStreamDestroy(ctx->pool[i]);
             cudaEventDestroy(ctx->ev_pool_done[i]);
         }
+        cudaStreamDestroy(ctx->capture);
     }
     for (cudaEvent_t e : ctx->op_events) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     delete ctx;
 }
 
@@ -597,6 +604,7 @@ int ensure_pool(reg_ctx *ctx)
         CU(cudaStreamCreateWithFlags(&ctx->pool[i], cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&ctx->ev_pool_done[i], cudaEventDisableTiming));
     }
+    CU(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
     ctx->pool_ready = true;
     return REG_OK;
 }
@@ -652,6 +660,46 @@ int check_device_status(reg_ctx *ctx, cudaStream_t s)
     return REG_OK;
 }
 
+uint64_t fnv1a(const void *data, size_t n, uint64_t h)
+{
+    const unsigned char *b = (const unsigned char *)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+// One launch per operator on the 16-stream pool, in plan order; an operator waits for the
+// events of the two operators that produce its inputs.  The pool forks from and joins back
+// into s, so the whole sequence can also be captured from s as one graph.
+int launch_plain(reg_ctx *ctx, const ScanPlan &plan, const Params &p, int C, cudaStream_t s)
+{
+    const int n_ops = (int)plan.ops.size();
+    const int storage = ctx->cfg.storage;
+    std::vector<int> node_op(p.n_nodes, -1);
+    for (int e = 0; e < n_ops; ++e) node_op[plan.ops[e].out] = e;
+    CU(cudaEventRecord(ctx->ev_pool_done[0], s));
+    for (int i = 0; i < 16; ++i) CU(cudaStreamWaitEvent(ctx->pool[i], ctx->ev_pool_done[0], 0));
+    for (int e = 0; e < n_ops; ++e) {
+        cudaStream_t ls = ctx->pool[e % 16];
+        const OpDesc &op = plan.ops[e];
+        if (op.left >= 0) {
+            CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.left]], 0));
+            CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.right]], 0));
+        }
+        Params q = p;
+        q.op_base = e;
+        CU(launch_ops(q, storage, C, 1, ls));
+        CU(cudaEventRecord(ctx->op_events[e], ls));
+    }
+    for (int i = 0; i < 16; ++i) {
+        CU(cudaEventRecord(ctx->ev_pool_done[i], ctx->pool[i]));
+        CU(cudaStreamWaitEvent(s, ctx->ev_pool_done[i], 0));
+    }
+    return REG_OK;
+}
+
 // Execute the planned operators.
 int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, cudaStream_t s)
 {
@@ -678,30 +726,53 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
         CHECK(ensure_pool(ctx));
         CHECK(ensure_op_events(ctx, n_ops));
         const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
-        std::vector<int> node_op(p.n_nodes, -1);
-        for (int e = 0; e < n_ops; ++e) node_op[plan.ops[e].out] = e;
         const int t0 = timing_mark(ctx, s);
-        CU(cudaEventRecord(ctx->ev_pool_done[0], s));
-        for (int i = 0; i < 16; ++i) CU(cudaStreamWaitEvent(ctx->pool[i], ctx->ev_pool_done[0], 0));
-        for (int e = 0; e < n_ops; ++e) {
-            const int lane = e % 16;
-            cudaStream_t ls = ctx->pool[lane];
-            const OpDesc &op = plan.ops[e];
-            if (op.left >= 0) {
-                CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.left]], 0));
-                CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.right]], 0));
-            }
-            Params q = p;
-            q.op_base = e;
-            CU(launch_ops(q, storage, C, 1, ls));
-            CU(cudaEventRecord(ctx->op_events[e], ls));
-            ctx->last.op_launches += 1;
-        }
-        for (int i = 0; i < 16; ++i) {
-            CU(cudaEventRecord(ctx->ev_pool_done[i], ctx->pool[i]));
-            CU(cudaStreamWaitEvent(s, ctx->ev_pool_done[i], 0));
-        }
+        CHECK(launch_plain(ctx, plan, p, C, s));
         ctx->op_pairs.push_back({t0, timing_mark(ctx, s)});
+        ctx->last.op_launches += n_ops;
+        return REG_OK;
+    }
+    if (exec == REG_EXEC_GRAPH) {
+        CHECK(ensure_pool(ctx));
+        CHECK(ensure_op_events(ctx, n_ops));
+        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
+        // The graph bakes in the kernel arguments (workspace pointers, config) and the
+        // dependency edges; the descriptors themselves are read from device memory when it runs.
+        p.op_base = 0;
+        uint64_t key = fnv1a(&p, sizeof(p), 1469598103934665603ULL);
+        key = fnv1a(plan.ops.data(), sizeof(OpDesc) * plan.ops.size(), key);
+        int hdr[4] = {C, storage, ctx->cfg.mode, n_ops};
+        key = fnv1a(hdr, sizeof(hdr), key);
+        if (!ctx->graph || ctx->graph_key != key) {
+            if (ctx->graph) {
+                CU(cudaGraphExecDestroy(ctx->graph));
+                ctx->graph = nullptr;
+            }
+            // Relaxed mode: the launcher sets kernel attributes (not stream work) while capturing.
+            CU(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeRelaxed));
+            const int rc = launch_plain(ctx, plan, p, C, ctx->capture);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(ctx->capture, &g);
+            if (rc != REG_OK || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return rc != REG_OK ? rc : fail(REG_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                ctx->graph = nullptr;
+                cudaGetLastError();
+                return fail(REG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+            }
+            ctx->graph_key = key;
+            ctx->graph_captures += 1;
+            ctx->last.graph_captures = 1;
+        }
+        const int t0 = timing_mark(ctx, s);
+        CU(cudaGraphLaunch(ctx->graph, s));
+        ctx->op_pairs.push_back({t0, timing_mark(ctx, s)});
+        ctx->last.op_launches += n_ops;
         return REG_OK;
     }
     if (exec == REG_EXEC_PERSISTENT) {
@@ -798,7 +869,7 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     if (!frames || !out) return fail(REG_EINVAL, "frames/out is NULL");
     if (N < 2) return fail(REG_EINVAL, "need N >= 2 frames, got %d", N);
     if (pitch < W) return fail(REG_EINVAL, "pitch %d < W %d", pitch, W);
-    if (exec != REG_EXEC_PLAIN && exec != REG_EXEC_LEVEL && exec != REG_EXEC_PERSISTENT)
+    if (exec != REG_EXEC_PLAIN && exec != REG_EXEC_LEVEL && exec != REG_EXEC_PERSISTENT && exec != REG_EXEC_GRAPH)
         return fail(REG_EINVAL, "exec %d", exec);
     if (ctx->cfg.mode == REG_NONRIGID && !fields_out) return fail(REG_EINVAL, "fields_out is NULL for nonrigid");
     std::lock_guard<std::mutex> lock(ctx->mu);

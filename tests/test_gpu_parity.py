@@ -177,7 +177,7 @@ def oracle_scan(F, cfg, schedule):
 
 
 @pytest.mark.parametrize("schedule", ["sequential", "brent_kung", "dissemination", "ladner_fischer"])
-@pytest.mark.parametrize("exec_", ["plain", "level", "persistent"])
+@pytest.mark.parametrize("exec_", ["plain", "level", "persistent", "graph"])
 def test_scan_rigid_c1_matches_oracle(schedule, exec_):
     F = c1_frames()
     cfg = B.Config()
@@ -207,11 +207,32 @@ def test_scan_host_frames_equal_device_frames():
 def test_scan_is_deterministic_and_independent_of_executor():
     F = c1_frames(12)
     ctx = B.Context(B.Config(cluster=2))
-    runs = [ctx.scan(torch.from_numpy(F).cuda(), exec=e)[0] for e in ("level", "level", "plain", "persistent")]
-    assert runs[0] == runs[1] == runs[2] == runs[3]
+    runs = [ctx.scan(torch.from_numpy(F).cuda(), exec=e)[0] for e in ("level", "level", "plain", "persistent", "graph")]
+    assert runs[0] == runs[1] == runs[2] == runs[3] == runs[4]
 
 
-@pytest.mark.parametrize("exec_", ["level", "persistent"])
+def test_graph_executor_replays_the_captured_plan():
+    # the first call captures, repeats with the same plan replay; a new N or new frames in the
+    # same buffers give the same results as the one-launch-per-operator path
+    ctx = B.Context(B.Config(cluster=2))
+    ctx.set_timing(True)
+    F = torch.from_numpy(c1_frames(10)).cuda()
+    a, sa = ctx.scan(F, exec="graph")
+    assert ctx.last_timing()["graph_captures"] == 1
+    assert ctx.last_timing()["op_launches"] == len(sa)
+    b, sb = ctx.scan(F, exec="graph")
+    assert ctx.last_timing()["graph_captures"] == 0
+    assert a == b and [s["evals"] for s in sa] == [s["evals"] for s in sb]
+    F2 = torch.flip(F, dims=[0]).contiguous()
+    c, _ = ctx.scan(F2, exec="graph")
+    assert ctx.last_timing()["graph_captures"] == 0   # same plan and workspaces, new frame data
+    assert c == ctx.scan(F2, exec="plain")[0]
+    d, _ = ctx.scan(F[:7].contiguous(), exec="graph")
+    assert ctx.last_timing()["graph_captures"] == 1   # another N: another plan
+    assert d == ctx.scan(F[:7].contiguous(), exec="plain")[0]
+
+
+@pytest.mark.parametrize("exec_", ["level", "persistent", "graph"])
 def test_scan_nonrigid_c1_matches_oracle(exec_):
     F = c1_frames(6)
     cfg = B.Config(mode="nonrigid")
