@@ -91,6 +91,8 @@ def lib():
             L.or_grid_compose.argtypes = [gp, dp, dp, dp, dp, dp, dp]
             L.or_grid_dense.argtypes = [gp, dp, dp, dp, dp]
             L.or_grid_level_dense.argtypes = [gp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+            L.or_warp_rigid.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
+            L.or_warp_grid.argtypes = [gp, dp, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -483,6 +485,38 @@ def scan(frames, cfg: Config, dag: Optional[Dag] = None, leaves: Optional[List[E
     for (l, r) in dag.ops:
         nodes.append(op_B(nodes[l], nodes[r], pyrs, cfg))
     return [nodes[o] for o in dag.out]
+
+
+# --------------------------------------------------------------------------
+# registered series (Sec. 2: frames registered to the first one, then averaged)
+# --------------------------------------------------------------------------
+def warp(T, mode: str, phi, grid: int = 0) -> np.ndarray:
+    """T resampled onto the reference grid: out(x) = T(phi(x)).  Rigid phi = (alpha, gx, gy);
+    nonrigid phi = control values [2, ny, nx] (finest px) of the grid ``grid_for(W, H, grid)``."""
+    T = _f64(T)
+    H, W = T.shape
+    out = np.zeros((H, W))
+    if mode == "rigid":
+        lib().or_warp_rigid(_dp(T), W, H, _dp(_f64(phi)), _dp(out))
+    else:
+        g = grid_for(W, H, grid)
+        c = _f64(phi)
+        gc = g.c()
+        lib().or_warp_grid(ctypes.byref(gc), _dp(T), _dp(_f64(c[0])), _dp(_f64(c[1])), _dp(out))
+    return out
+
+
+def register_series(frames, mode: str, phis, grid: int = 0):
+    """Registered series and its mean: out[0] = f_0, out[k] = f_k o phi_{0,k} for the N-1
+    prefixes ``phis`` of the scan; mean = (1/N) sum_k out[k]."""
+    frames = np.asarray(frames)
+    N = len(frames)
+    assert len(phis) == N - 1
+    out = np.zeros(frames.shape, dtype=np.float64)
+    out[0] = frames[0]
+    for k in range(1, N):
+        out[k] = warp(frames[k], mode, phis[k - 1], grid)
+    return out, out.sum(axis=0) / N
 
 
 # --------------------------------------------------------------------------

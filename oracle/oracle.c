@@ -17,6 +17,8 @@
  *   - the gradient-flow minimiser with Armijo backtracking, run coarse to
  *     fine                                                  [Sec. 2.3.1]
  *   - the composition phi_jk o phi_ij used as initial guess of B [Sec. 2.3.2]
+ *   - the registered frame T o phi on the reference grid, from which the
+ *     registered series and its average are formed            [Sec. 2]
  *
  * The scan itself (sequential recursion, tree DAGs) is driven from Python
  * (oracle/__init__.py), one operator call at a time.
@@ -483,4 +485,32 @@ void or_grid_dense(const or_grid_t *g, const double *cx, const double *cy, doubl
     for (int r = 0; r < g->H0; ++r)
         for (int c = 0; c < g->W0; ++c)
             or_grid_eval(g, cx, cy, (double)c, (double)r, &ux[r * g->W0 + c], &uy[r * g->W0 + c]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Registered frame: T resampled onto the reference grid by phi,            */
+/* out(x) = T(phi(x)), bilinear with clamp-to-edge.  The series is          */
+/* registered to its first frame and then averaged            [Sec. 2].    */
+/* ------------------------------------------------------------------------ */
+void or_warp_rigid(const double *T, int W, int H, const double theta[3], double *out)
+{
+    const double cx = 0.5 * (W - 1), cy = 0.5 * (H - 1);
+    const double ca = cos(theta[0]), sa = sin(theta[0]);
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c) {
+            double xc = c - cx, yc = r - cy, v[3];
+            or_sample(T, W, H, ca * xc - sa * yc + cx + theta[1], sa * xc + ca * yc + cy + theta[2], v);
+            out[r * W + c] = v[0];
+        }
+}
+
+void or_warp_grid(const or_grid_t *g, const double *T, const double *cx, const double *cy, double *out)
+{
+    for (int r = 0; r < g->H0; ++r)
+        for (int c = 0; c < g->W0; ++c) {
+            double ux, uy, v[3];
+            or_grid_eval(g, cx, cy, (double)c, (double)r, &ux, &uy);
+            or_sample(T, g->W0, g->H0, c + ux, r + uy, v);
+            out[r * g->W0 + c] = v[0];
+        }
 }
