@@ -176,7 +176,9 @@ int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int W, int H, i
  * operators A(f_{i-1}, f_i), then B along the DAG of `schedule`.
  *   frames     fp32 [N][H][pitch], host or device (host frames are copied in).
  *   out        N-1 elements phi_{0,1}..phi_{0,N-1} (host or device).
- *   fields_out REG_NONRIGID: [N-1][2][H][W] fp32 (host or device); NULL for rigid.
+ *   fields_out REG_NONRIGID: [N-1][2][H][W] fp32 (host or device), or NULL to skip
+ *              the dense fields (reg_scan_grids then gives the control values).
+ *              NULL for rigid.
  *   per_op     optional host array of (N-1) + (#B operators of the schedule)
  *              stats, leaves first, then the B operators in DAG order
  *              (reg_scan_work() gives the count).
@@ -184,6 +186,34 @@ int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int W, int H, i
 int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch,
              int schedule, int exec, reg_elem_t *out, float *fields_out,
              reg_stats_t *per_op, void *stream);
+
+/* Control values of the N-1 prefixes phi_{0,1}..phi_{0,N-1} of the last
+ * successful REG_NONRIGID reg_scan on ctx: grids_out, device, [N-1][ny][nx]
+ * (x, y) pairs, ny/nx from reg_grid_dims for that scan's W, H.  n_out (host,
+ * optional) receives N-1.  Errors: REG_ESTATE if ctx has no nonrigid scan
+ * result; REG_EINVAL for a host grids_out. */
+int reg_scan_grids(reg_ctx_t *ctx, float *grids_out, int *n_out, void *stream);
+
+/* Registered series and its average [Sec. 2: every frame of the series is
+ * registered to the first one, then the series is averaged].
+ *   out_k(x) = f_k(phi_{0,k}(x)), k = 0..N-1 (phi_{0,0} = identity), bilinear
+ *   with clamp-to-edge, the sampling of the operator; mean(x) = (1/N) sum_k out_k(x),
+ *   summed per chunk of 64 frames with compensation and over chunks in FP64, in
+ *   a fixed order (bitwise reproducible).
+ *   frames   device fp32 [N][H][pitch], N >= 1.
+ *   elems    REG_RIGID: the N-1 prefixes from reg_scan (host or device), element
+ *            k-1 = phi_{0,k}.  Ignored for REG_NONRIGID.
+ *   grids    REG_NONRIGID: device [N-1][ny][nx] (x, y) control values of the
+ *            prefixes, as reg_scan_grids writes them.  Ignored for REG_RIGID.
+ *   out      device [N][H][W] fp32, or NULL.   mean  device [H][W] fp32, or NULL.
+ * Source tiles are staged in shared memory by TMA when frames is 16-byte
+ * aligned, pitch % 4 == 0 and W >= 80, H >= 40; otherwise samples are read from
+ * global memory (same results).  The call returns after its work on `stream`
+ * has completed.  Errors: REG_EINVAL (NULL or host frames/grids, both outputs
+ * NULL, N < 1, W or H < 2), REG_ETIMEOUT (a bounded wait on a TMA load gave up),
+ * REG_ECUDA. */
+int reg_warp(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch,
+             const reg_elem_t *elems, const float *grids, float *out, float *mean, void *stream);
 
 /* Number of B applications the schedule uses for n = N-1 elements (host only,
  * no GPU needed).  Returns -1 for an unknown schedule. */
@@ -298,7 +328,8 @@ typedef struct {
     double  pyramid_ms;        /* device time of the pyramid build, same method */
     int32_t graph_captures;    /* REG_EXEC_GRAPH: 1 if this call captured a new graph, 0 if it
                                   replayed the cached one (always 0 for the other executors) */
-    int32_t reserved;
+    int32_t tma_staged;        /* reg_warp: 1 if the source tiles were staged in shared memory
+                                  by TMA, 0 if sampled from global memory */
 } reg_timing_t;
 
 /* Enable (1) or disable (0) event timing of the kernels launched by later calls. */

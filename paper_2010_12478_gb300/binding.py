@@ -30,7 +30,8 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_scan_work", "reg_scan_dag", "reg_pyramid", "reg_energy", "reg_compose_grid", "reg_grid_dims",
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
-           "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load"]
+           "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load",
+           "reg_scan_grids", "reg_warp"]
 
 
 class RegError(RuntimeError):
@@ -62,7 +63,7 @@ class reg_stats_t(ctypes.Structure):
 class reg_timing_t(ctypes.Structure):
     _fields_ = [("op_launches", ctypes.c_int32), ("pyramid_launches", ctypes.c_int32),
                 ("op_kernel_ms", ctypes.c_double), ("pyramid_ms", ctypes.c_double),
-                ("graph_captures", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph_captures", ctypes.c_int32), ("tma_staged", ctypes.c_int32)]
 
 
 class reg_result_t(ctypes.Structure):
@@ -101,6 +102,8 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(reg_elem_t), ctypes.POINTER(reg_elem_t),
                                            ctypes.POINTER(reg_stats_t), vp]
         L.reg_autotune.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(ip)]
+        L.reg_scan_grids.argtypes = [vp, fp, ctypes.POINTER(ip), vp]
+        L.reg_warp.argtypes = [vp, fp, ip, ip, ip, ip, ctypes.POINTER(reg_elem_t), fp, fp, fp, vp]
         L.reg_autotune_save.argtypes = [vp, ctypes.c_char_p]
         L.reg_autotune_load.argtypes = [vp, ctypes.c_char_p]
         L.reg_ctx_set_timing.argtypes = [vp, ip]
@@ -220,7 +223,8 @@ class Context:
         t = reg_timing_t()
         check(lib().reg_ctx_last_timing(self.h, ctypes.byref(t)), "reg_ctx_last_timing")
         return dict(op_launches=t.op_launches, pyramid_launches=t.pyramid_launches,
-                    op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms, graph_captures=t.graph_captures)
+                    op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms, graph_captures=t.graph_captures,
+                    tma_staged=t.tma_staged)
 
     # ---- operators
     def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,
@@ -250,6 +254,26 @@ class Context:
         st = [stats_dict(s, self.cfg.levels) for s in stats] if stats is not None else None
         return el, st
 
+    def scan_grids(self, out):
+        """Control values [N-1, ny, nx, 2] (device) of the last nonrigid scan's prefixes."""
+        n = ctypes.c_int()
+        check(lib().reg_scan_grids(self.h, _ptr(out), ctypes.byref(n), None), "reg_scan_grids")
+        return n.value
+
+    def warp(self, frames, elems=None, grids=None, out=None, mean=None, stream=None):
+        """Registered series out[k] = f_k o phi_{0,k} and/or its mean (device tensors).
+        elems: rigid prefixes, as returned by scan() (a list of tuples), as an elem_array(),
+        or as a device tensor holding reg_elem_t records; grids: nonrigid control values."""
+        N, H, W = frames.shape
+        if elems is None or isinstance(elems, ctypes.Array):
+            eptr = elems
+        elif hasattr(elems, "data_ptr"):
+            eptr = ctypes.cast(ctypes.c_void_p(elems.data_ptr()), ctypes.POINTER(reg_elem_t))
+        else:
+            eptr = elem_array(elems)
+        check(lib().reg_warp(self.h, _ptr(frames), N, W, H, W, eptr, _ptr(grids), _ptr(out), _ptr(mean),
+                             _stream(stream)), "reg_warp")
+
     # ---- kernel-level steps
     def pyramid(self, frame, levels: int, storage: str, out):
         H, W = frame.shape
@@ -275,6 +299,14 @@ class Context:
 
     def compose_grid(self, q1, q2, W: int, H: int, out):
         check(lib().reg_compose_grid(self.h, _ptr(q1), _ptr(q2), W, H, _ptr(out), None), "reg_compose_grid")
+
+
+def elem_array(elems):
+    """ctypes array of reg_elem_t from (i, k, alpha, gx, gy) tuples (host memory)."""
+    arr = (reg_elem_t * max(1, len(elems)))()
+    for j, e in enumerate(elems):
+        arr[j] = reg_elem_t(int(e[0]), int(e[1]), float(e[2]), float(e[3]), float(e[4]))
+    return arr
 
 
 def grid_dims(W: int, H: int, grid: int = 0, levels: int = 2):

@@ -268,6 +268,9 @@ struct reg_ctx {
     std::vector<cudaEvent_t> op_events;
     bool pool_ready = false;
     // REG_EXEC_GRAPH: the captured plain-path launches and the plan they were captured for
+    // last successful nonrigid reg_scan: prefixes' node indices are in node_ids
+    int last_n = 0, last_gnx = 0, last_gny = 0;
+    DevBuf warp_ws;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;   // graphs are captured here (the caller's stream may be the legacy one)
     uint64_t graph_key = 0;
@@ -871,7 +874,6 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     if (pitch < W) return fail(REG_EINVAL, "pitch %d < W %d", pitch, W);
     if (exec != REG_EXEC_PLAIN && exec != REG_EXEC_LEVEL && exec != REG_EXEC_PERSISTENT && exec != REG_EXEC_GRAPH)
         return fail(REG_EINVAL, "exec %d", exec);
-    if (ctx->cfg.mode == REG_NONRIGID && !fields_out) return fail(REG_EINVAL, "fields_out is NULL for nonrigid");
     std::lock_guard<std::mutex> lock(ctx->mu);
     CU(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -922,10 +924,13 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
         el[i].gy = (float)th[3 * node + 2];
     }
     CHECK(copy_out(out, el.data(), sizeof(reg_elem_t) * n, s));
+    ctx->last_n = 0;
     if (ctx->cfg.mode == REG_NONRIGID) {
-        // dense finest-level fields of the prefixes, written by one kernel
         CHECK(ctx->node_ids.reserve(sizeof(int) * n));
         CU(cudaMemcpyAsync(ctx->node_ids.ptr, plan.out_nodes.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    }
+    if (ctx->cfg.mode == REG_NONRIGID && fields_out) {
+        // dense finest-level fields of the prefixes, written by one kernel
         const size_t fb = sizeof(float) * 2 * (size_t)W * H;
         float *dst = (float *)fields_out;
         const bool direct = is_device_ptr(fields_out);
@@ -943,6 +948,87 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     timing_resolve(ctx);
     for (int e = 0; e < n_ops; ++e)
         if (st[e].status != kDevOk) return fail(REG_EINVAL, "operator %d failed on the device (%d)", e, st[e].status);
+    if (ctx->cfg.mode == REG_NONRIGID) {
+        ctx->last_n = n;
+        ctx->last_gnx = p.gnx;
+        ctx->last_gny = p.gny;
+    }
+    return REG_OK;
+}
+
+// ------------------------------------------------------------------ reg_scan_grids / reg_warp
+extern "C" int reg_scan_grids(reg_ctx_t *ctx, float *grids_out, int *n_out, void *stream)
+{
+    if (!ctx || !grids_out) return fail(REG_EINVAL, "ctx/grids_out is NULL");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ctx->last_n <= 0) return fail(REG_ESTATE, "no nonrigid scan result on this context");
+    CU(cudaSetDevice(ctx->device));
+    if (!is_device_ptr(grids_out)) return fail(REG_EINVAL, "grids_out must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(launch_grid_gather(ctx->node_grid.as<float2>(), ctx->node_ids.as<int>(), ctx->last_n,
+                          ctx->last_gnx * ctx->last_gny, (float2 *)grids_out, s));
+    CU(cudaStreamSynchronize(s));
+    if (n_out) *n_out = ctx->last_n;
+    return REG_OK;
+}
+
+extern "C" int reg_warp(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch,
+                        const reg_elem_t *elems, const float *grids, float *out, float *mean, void *stream)
+{
+    if (!ctx || !frames) return fail(REG_EINVAL, "ctx/frames is NULL");
+    if (!out && !mean) return fail(REG_EINVAL, "out and mean are both NULL");
+    if (N < 1) return fail(REG_EINVAL, "need N >= 1 frames, got %d", N);
+    if (W < 2 || H < 2 || pitch < W) return fail(REG_EINVAL, "need W, H >= 2 and pitch >= W");
+    const bool nonrigid = ctx->cfg.mode == REG_NONRIGID;
+    if (N > 1 && !nonrigid && !elems) return fail(REG_EINVAL, "elems is NULL");
+    if (N > 1 && nonrigid && !grids) return fail(REG_EINVAL, "grids is NULL");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CU(cudaSetDevice(ctx->device));
+    if (!is_device_ptr(frames) || (N > 1 && nonrigid && !is_device_ptr(grids)) || (out && !is_device_ptr(out)) ||
+        (mean && !is_device_ptr(mean)))
+        return fail(REG_EINVAL, "frames, grids, out and mean must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    WarpJob j;
+    memset(&j, 0, sizeof(j));
+    j.frames = frames;
+    j.N = N;
+    j.W = W;
+    j.H = H;
+    j.pitch = pitch;
+    j.mode = ctx->cfg.mode;
+    j.out = out;
+    j.mean = mean;
+    if (nonrigid) {
+        GridDims gd;
+        CHECK(grid_dims(W, H, ctx->cfg.grid, ctx->cfg.levels, gd));
+        j.nx = gd.nx;
+        j.ny = gd.ny;
+        j.s = gd.s;
+        j.grids = (const float2 *)grids;
+    }
+    // workspace: per-frame parameters and chunk partial sums, then the rigid elements and status
+    const size_t wb = warp_workspace_bytes(N, W, H, mean != nullptr);
+    const size_t eb = 256 * (((size_t)std::max(1, N - 1) * sizeof(reg_elem_t) + 255) / 256);
+    CHECK(ctx->warp_ws.reserve(wb + eb + 256));
+    char *ws = (char *)ctx->warp_ws.ptr;
+    j.ws = ws;
+    j.status = (int *)(ws + wb + eb);
+    if (!nonrigid && N > 1) {
+        reg_elem_t *de = (reg_elem_t *)(ws + wb);
+        CU(cudaMemcpyAsync(de, elems, sizeof(reg_elem_t) * (N - 1), cudaMemcpyDefault, s));
+        j.elems = de;
+    }
+    j.timeout_ns = 2LL * 1000 * 1000 * 1000;
+    CU(cudaMemsetAsync(j.status, 0, sizeof(int), s));
+    int used_tma = 0;
+    CU(launch_warp(j, s, &used_tma));
+    int st = 0;
+    CU(cudaMemcpyAsync(&st, j.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (st == kDevWaitTimeout) return fail(REG_ETIMEOUT, "a bounded wait on a TMA load gave up");
+    memset(&ctx->last, 0, sizeof(ctx->last));
+    ctx->last.op_launches = (N > 1 && !nonrigid) + 1 + (mean != nullptr);   // parameter prep, warp, mean
+    ctx->last.tma_staged = used_tma;
     return REG_OK;
 }
 

@@ -43,7 +43,8 @@ static_assert(sizeof(OpStats) == sizeof(reg_stats_t), "stats layout");
 enum DevStatus : int32_t {
     kDevOk = 0,
     kDevBadOp = 1,       // operator descriptor out of range / non-adjacent
-    kDevQueueTimeout = 2 // bounded wait on the ready queue gave up
+    kDevQueueTimeout = 2, // bounded wait on the ready queue gave up
+    kDevWaitTimeout = 3   // bounded wait on a TMA load (mbarrier) gave up
 };
 
 struct Config {
@@ -92,6 +93,25 @@ cudaError_t launch_persistent(const Params &p, int storage, int cluster, int wor
 // Clusters of `cluster` CTAs of the persistent kernel that fit on the device at once
 // (occupancy query), or -1 if the query fails.
 int persistent_resident_clusters(const Params &p, int storage, int cluster);
+
+// Registered series (reg_warp): out_k = f_k o phi_{0,k} and their mean.
+struct WarpJob {
+    const float *frames;       // device [N][H][pitch]
+    int N, W, H, pitch;
+    int mode;
+    const reg_elem_t *elems;   // rigid: N-1 device elements phi_{0,k}, k = 1..N-1
+    const float2 *grids;       // nonrigid: N-1 device control grids [ny][nx]
+    int nx, ny, s;
+    float *out;                // device [N][H][W] or null
+    float *mean;               // device [H][W] or null
+    void *ws;                  // warp_workspace_bytes() of device memory
+    int *status;               // device status word (kDevWaitTimeout on a timed-out load)
+    long long timeout_ns;
+};
+size_t warp_workspace_bytes(int N, int W, int H, bool mean);
+// *used_tma = 1 when the source boxes were staged by TMA (aligned frames, pitch % 4 == 0).
+cudaError_t launch_warp(const WarpJob &j, cudaStream_t s, int *used_tma);
+cudaError_t launch_grid_gather(const float2 *src, const int *nodes, int n, int Nc, float2 *dst, cudaStream_t s);
 cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
                           const float2 *grid_dev, double *out_dev, float2 *grad_dev,
                           cudaStream_t s);
