@@ -38,7 +38,7 @@
 typedef struct {
     int levels;        /* number of pyramid levels L */
     int max_iter;      /* accepted steps allowed per level */
-    int max_rejects;   /* line-search halvings allowed per iteration */
+    int max_rejects;   /* rejected line-search trials allowed per iteration */
     double tol_grad;   /* stop when the metric gradient norm falls below */
     double tol_rel_e;  /* stop when an accepted step lowers E by less than tol_rel_e*|E| */
     double armijo_c;   /* sufficient-decrease constant */
@@ -82,6 +82,20 @@ void or_downsample(const double *src, int W, int H, double *dst)
 static double clampd(double v, double lo, double hi)
 {
     return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* Step-size rule of the line search (Armijo backtracking with safeguarded quadratic
+ * interpolation, Nocedal and Wright, Numerical Optimization, Sec. 3.5).  After a trial at
+ * step tau with energy Et, tq minimises the parabola through E(0) = E, E'(0) = slope and
+ * E(tau) = Et.  A rejected trial retries at tq clamped to [0.1 tau, 0.5 tau]; an accepted one
+ * starts the next line search at tq clamped to [0.5 tau, 4 tau].  Without positive curvature
+ * (den <= 0) the rule falls back to halving / doubling.                                     */
+static double or_next_tau(double E, double slope, double tau, double Et, int accepted)
+{
+    const double den = Et - E - slope * tau;
+    if (!(den > 0.0)) return accepted ? 2.0 * tau : 0.5 * tau;
+    const double tq = -slope * tau * tau / (2.0 * den);
+    return accepted ? fmin(fmax(tq, 0.5 * tau), 4.0 * tau) : fmin(fmax(tq, 0.1 * tau), 0.5 * tau);
 }
 
 void or_sample(const double *T, int W, int H, double px, double py, double out[3])
@@ -220,14 +234,14 @@ static void or_rigid_level(const double *R, const double *T, int W, int H,
             st->evals[lvl] += 1;
             if (Et <= E + cfg->armijo_c * tau * slope) { accepted = 1; break; }
             st->rejects += 1;
-            tau *= 0.5;
+            tau = or_next_tau(E, slope, tau, Et, 0);
         }
         if (!accepted) { stop = OR_STOP_LS; break; }
         th[0] = tt[0]; th[1] = tt[1]; th[2] = tt[2];
         st->iters[lvl] += 1;
         double Eold = E;
+        tau = or_next_tau(E, slope, tau, Et, 1);
         E = Et;
-        tau *= 2.0;
         if (Eold - Et <= cfg->tol_rel_e * fabs(Eold)) { stop = OR_STOP_REL; break; }
         or_rigid_energy(R, T, W, H, th, &E, g);
         st->evals[lvl] += 1;
@@ -412,15 +426,15 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
             st->evals[l] += 1;
             if (Et <= E + cfg->armijo_c * tau * slope) { accepted = 1; break; }
             st->rejects += 1;
-            tau *= 0.5;
+            tau = or_next_tau(E, slope, tau, Et, 0);
         }
         if (!accepted) { stop = OR_STOP_LS; break; }
         memcpy(cx, tx, sizeof(double) * Nc);
         memcpy(cy, ty, sizeof(double) * Nc);
         st->iters[l] += 1;
         double Eold = E;
+        tau = or_next_tau(E, slope, tau, Et, 1);
         E = Et;
-        tau *= 2.0;
         if (Eold - Et <= cfg->tol_rel_e * fabs(Eold)) { stop = OR_STOP_REL; break; }
         or_grid_energy(R, T, W, H, l, g, cx, cy, cfg->lambda, &E, gx, gy);
         st->evals[l] += 1;
