@@ -88,7 +88,7 @@ extern "C" {
 /* why a level stopped (reg_stats_t.stop) */
 #define REG_STOP_GRAD    0   /* metric gradient norm below tol_grad */
 #define REG_STOP_REL     1   /* accepted step lowered E by less than tol_rel_e * |E| */
-#define REG_STOP_LS      2   /* line search exhausted max_rejects halvings */
+#define REG_STOP_LS      2   /* line search exhausted max_rejects rejected trials */
 #define REG_STOP_MAXIT   3   /* max_iter accepted steps */
 
 /* ---- data types --------------------------------------------------------- */
@@ -106,7 +106,7 @@ typedef struct {
     int    mode;          /* REG_RIGID or REG_NONRIGID */
     int    levels;        /* pyramid levels, 1..REG_MAX_LEVELS */
     int    max_iter;      /* accepted gradient-flow steps per level */
-    int    max_rejects;   /* Armijo halvings per step */
+    int    max_rejects;   /* rejected Armijo trials allowed per step */
     double tol_grad;      /* stop: metric norm of the descent direction */
     double tol_rel_e;     /* stop: relative energy decrease of an accepted step */
     double armijo_c;      /* sufficient-decrease constant */

@@ -33,6 +33,7 @@ namespace reg {
 
 constexpr int kWarps = kThreads / 32;
 constexpr int kNM = 16;        // moment slots per reduction
+constexpr int kMaxCluster = 16; // CTAs per operator at most (non-portable cluster size)
 constexpr int kChunk = 32;     // pixels per thread between float-float flushes
 
 // ------------------------------------------------------------------ loads
@@ -86,14 +87,14 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float h2, float l2)
 // it does not occupy registers of every thread.
 struct RigidCtl {
     double th[3], tt[3], d[3];
-    double E, tau, slope, sr, srr, m0, P, cx, cy;
+    double E, tau, slope, sr, srr, m0, P, cx, cy, invP, inv_m0;
     double a, b, rbar, tbar;       // NCC terms at th
     double ta, tb, trbar, ttbar;   // at the trial point tt
     int nrej, iters, evals, stop, rejects;
 };
 
 struct FieldCtl {
-    double E, tau, tau_pend, slope, P, Nc, sr, srr;
+    double E, tau, tau_pend, slope, P, Nc, sr, srr, invP, invNc;
     double a, b, rbar, tbar;      // NCC terms at the current field
     double ta, tb, trbar, ttbar;  // at the trial field
     int degen, tdegen;
@@ -102,7 +103,7 @@ struct FieldCtl {
 
 struct Smem {
     float2 warp[kWarps][kNM];   // per-warp (hi, lo) partials
-    double part[2][kNM];        // this CTA's partials, read by the whole cluster
+    double part[2][kMaxCluster][kNM];   // every CTA's partials, pushed here by each CTA
     double tot[kNM];            // cluster totals
     float pm[16];               // pass parameters broadcast by thread 0
     int action;
@@ -135,6 +136,7 @@ __device__ __forceinline__ void cluster_reduce(float (&hi)[NM], float (&lo)[NM],
         for (int m = 0; m < NM; ++m) sm.warp[w][m] = make_float2(hi[m], lo[m]);
     }
     __syncthreads();
+    const unsigned C = cl.num_blocks(), me = cl.block_rank();
     if (tid < NM) {
         float h = 0.f, l = 0.f;
         for (int k = 0; k < kWarps; ++k) {
@@ -142,15 +144,18 @@ __device__ __forceinline__ void cluster_reduce(float (&hi)[NM], float (&lo)[NM],
             if (MAXLAST && tid == NM - 1) h = fmaxf(h, v.x);
             else ff_add(h, l, v.x, v.y);
         }
-        sm.part[buf][tid] = (double)h + (double)l;
+        // push this CTA's partial into slot `me` of every CTA of the cluster (remote stores do
+        // not wait; the cluster barrier below makes them visible)
+        const double v = (double)h + (double)l;
+        for (unsigned r = 0; r < C; ++r) *cl.map_shared_rank(&sm.part[buf][me][tid], r) = v;
     }
     if (fence) __threadfence();
     cl.sync();
     if (tid < NM) {
+        // every CTA adds the same values in rank order: identical totals everywhere
         double s = 0.0;
-        const unsigned C = cl.num_blocks();
         for (unsigned r = 0; r < C; ++r) {
-            double v = *cl.map_shared_rank(&sm.part[buf][tid], r);
+            const double v = sm.part[buf][r][tid];
             if (MAXLAST && tid == NM - 1) s = fmax(s, v);
             else s = __dadd_rn(s, v);
         }
@@ -173,24 +178,48 @@ struct Ncc {
 };
 
 // NCC = S'_RT / sqrt(S'_RR S'_TT) from shifted sums; dNCC/dTw(x) = a (r - rbar) - b (t - tbar).
-// Explicit round-to-nearest operations keep the result independent of FMA contraction,
-// so identical inputs (t == r) give exactly NCC = 1 and a zero gradient.
-__device__ Ncc ncc_terms(double P, double sr, double st, double srr, double stt, double srt)
+// 1/sqrt(q) for a positive finite q without a double-precision divide or square root (both
+// are long instruction sequences on this GPU): an FP32 seed on the mantissa scaled to [1, 4),
+// then two Newton-Raphson steps y <- y (3 - q y^2) / 2, each squaring the relative error
+// (2e-7 -> 1e-13 -> 1e-26, i.e. to double rounding).
+__device__ __forceinline__ double rsqrt_nr(double q)
+{
+    const int e = ilogb(q) & ~1;   // even exponent: q = m 2^e, m in [1, 4)
+    const double m = ldexp(q, -e);
+    double y = ldexp((double)rsqrtf((float)m), -e / 2);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double t = __dmul_rn(q, __dmul_rn(y, y));
+        y = __dmul_rn(y, __fma_rn(-0.5, t, 1.5));
+    }
+    return y;
+}
+
+// NCC and its gradient coefficients from the shifted sums (invP = 1/P, formed once per level).
+// Explicit round-to-nearest operations keep the result independent of FMA contraction; when
+// S'_rt == S'_rr == S'_tt (T o phi equals R up to the shift: identical inputs) the result is
+// exactly NCC = 1 with a == b, so the gradient vanishes exactly.
+__device__ Ncc ncc_terms(double P, double invP, double sr, double st, double srr, double stt, double srt)
 {
     Ncc o;
-    double Srr = __dsub_rn(srr, __ddiv_rn(__dmul_rn(sr, sr), P));
-    double Stt = __dsub_rn(stt, __ddiv_rn(__dmul_rn(st, st), P));
-    double Srt = __dsub_rn(srt, __ddiv_rn(__dmul_rn(sr, st), P));
-    o.rbar = __ddiv_rn(sr, P);
-    o.tbar = __ddiv_rn(st, P);
+    const double Srr = __dsub_rn(srr, __dmul_rn(__dmul_rn(sr, sr), invP));
+    const double Stt = __dsub_rn(stt, __dmul_rn(__dmul_rn(st, st), invP));
+    const double Srt = __dsub_rn(srt, __dmul_rn(__dmul_rn(sr, st), invP));
+    o.rbar = __dmul_rn(sr, invP);
+    o.tbar = __dmul_rn(st, invP);
     if (Srr < 1e-12 * P || Stt < 1e-12 * P) {
         o.ncc = 0.0; o.a = 0.0; o.b = 0.0; o.degenerate = 1;
         return o;
     }
-    double root = __dsqrt_rn(__dmul_rn(Srr, Stt));
-    o.ncc = __ddiv_rn(Srt, root);
-    o.a = __ddiv_rn(1.0, root);
-    o.b = __ddiv_rn(o.ncc, Stt);
+    const double a = rsqrt_nr(__dmul_rn(Srr, Stt));   // 1 / sqrt(S'_rr S'_tt)
+    o.a = a;
+    if (Srt == Srr && Srr == Stt) {
+        o.ncc = 1.0;
+        o.b = a;
+    } else {
+        o.ncc = __dmul_rn(Srt, a);
+        o.b = __dmul_rn(__dmul_rn(o.ncc, Srr), __dmul_rn(a, a));   // NCC / S'_tt
+    }
     o.degenerate = 0;
     return o;
 }
@@ -461,6 +490,20 @@ __device__ void rigid_grad_params(const RigidCtl &k, float *pm)
     pm[9] = (float)k.tbar;
 }
 
+// Step-size rule of the line search: Armijo backtracking with safeguarded quadratic
+// interpolation (Nocedal and Wright, Numerical Optimization, Sec. 3.5).  tq minimises the
+// parabola through E(0) = E, E'(0) = slope and E(tau) = Et; a rejected trial retries at tq
+// clamped to [0.1 tau, 0.5 tau], an accepted one starts the next search at tq clamped to
+// [0.5 tau, 4 tau]; without positive curvature the rule halves / doubles.
+__device__ __forceinline__ double next_tau(double E, double slope, double tau, double Et, bool accepted)
+{
+    const double den = Et - E - slope * tau;
+    if (!(den > 0.0)) return accepted ? 2.0 * tau : 0.5 * tau;
+    const double r = rsqrt_nr(2.0 * den);   // 1 / (2 den) = r^2, without a divide
+    const double tq = -slope * tau * tau * (r * r);
+    return accepted ? fmin(fmax(tq, 0.5 * tau), 4.0 * tau) : fmin(fmax(tq, 0.1 * tau), 0.5 * tau);
+}
+
 // Thread-0 controller after an ENERGY (level start), GRAD or TRIAL pass.  Returns the next
 // action and writes its parameters.  Same rules as the oracle's level loop.
 __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int action, float *pm)
@@ -468,7 +511,7 @@ __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int
     if (action == kActEnergy) {
         k.sr = tot[3];
         k.srr = tot[4];
-        const Ncc n = ncc_terms(k.P, k.sr, tot[0], k.srr, tot[1], tot[2]);
+        const Ncc n = ncc_terms(k.P, k.invP, k.sr, tot[0], k.srr, tot[1], tot[2]);
         k.E = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
         k.a = n.a; k.b = n.b; k.rbar = n.rbar; k.tbar = n.tbar;
         rigid_grad_params(k, pm);
@@ -476,37 +519,38 @@ __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int
     }
     if (action == kActGrad) {
         double g[3];
-        for (int q = 0; q < 3; ++q) g[q] = tot[q] / k.P;
+        for (int q = 0; q < 3; ++q) g[q] = tot[q] * k.invP;
         k.evals += 1;
         if (k.iters >= cfg.max_iter) { k.stop = REG_STOP_MAXIT; return kActDone; }
-        k.d[0] = -g[0] / k.m0; k.d[1] = -g[1]; k.d[2] = -g[2];
+        k.d[0] = -g[0] * k.inv_m0; k.d[1] = -g[1]; k.d[2] = -g[2];
         k.slope = g[0] * k.d[0] + g[1] * k.d[1] + g[2] * k.d[2];
-        double gn = sqrt(-k.slope);
-        if (!(gn >= cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
-        if (k.tau * gn > cfg.step_cap) k.tau = cfg.step_cap / gn;
+        // |g|_M = sqrt(-slope); the tests compare squares (no square root unless the cap applies)
+        const double gn2 = -k.slope;
+        if (!(gn2 >= cfg.tol_grad * cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
+        if (k.tau * k.tau * gn2 > cfg.step_cap * cfg.step_cap) k.tau = cfg.step_cap / sqrt(gn2);
         k.nrej = 0;
         for (int q = 0; q < 3; ++q) k.tt[q] = k.th[q] + k.tau * k.d[q];
         rigid_params(k.tt, pm);
         return kActTrial;
     }
     // trial
-    const Ncc n = ncc_terms(k.P, k.sr, tot[0], k.srr, tot[1], tot[2]);
+    const Ncc n = ncc_terms(k.P, k.invP, k.sr, tot[0], k.srr, tot[1], tot[2]);
     const double Et = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
     k.evals += 1;
     if (Et <= k.E + cfg.armijo_c * k.tau * k.slope) {
         for (int q = 0; q < 3; ++q) k.th[q] = k.tt[q];
         k.iters += 1;
         const double Eold = k.E;
+        k.tau = next_tau(k.E, k.slope, k.tau, Et, true);
         k.E = Et;
         k.a = n.a; k.b = n.b; k.rbar = n.rbar; k.tbar = n.tbar;
-        k.tau *= 2.0;
         if (Eold - Et <= cfg.tol_rel_e * fabs(Eold)) { k.stop = REG_STOP_REL; return kActDone; }
         rigid_grad_params(k, pm);
         return kActGrad;
     }
     k.rejects += 1;
     k.nrej += 1;
-    k.tau *= 0.5;
+    k.tau = next_tau(k.E, k.slope, k.tau, Et, false);
     if (k.nrej > cfg.max_rejects) { k.stop = REG_STOP_LS; return kActDone; }
     for (int q = 0; q < 3; ++q) k.tt[q] = k.th[q] + k.tau * k.d[q];
     rigid_params(k.tt, pm);
@@ -561,10 +605,12 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
         strip_rows(L.H, rank, C, r0, r1);
         if (tid == 0) {
             k.P = (double)L.W * (double)L.H;
+            k.invP = 1.0 / k.P;
             k.cx = 0.5 * (L.W - 1);
             k.cy = 0.5 * (L.H - 1);
             double rho = 0.25 * (L.W + L.H);
             k.m0 = rho * rho;
+            k.inv_m0 = 1.0 / k.m0;
             k.tau = cfg.tau0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
             rigid_params(k.th, sm.pm);
@@ -890,9 +936,9 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
 
 __device__ double field_energy(FieldCtl &k, const Config &cfg, const double *tot, bool trial)
 {
-    Ncc n = ncc_terms(k.P, k.sr, tot[0], k.srr, tot[1], tot[2]);
+    Ncc n = ncc_terms(k.P, k.invP, k.sr, tot[0], k.srr, tot[1], tot[2]);
     double Ed = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
-    double E = Ed + 0.5 * cfg.lambda * tot[5] / k.P;
+    double E = Ed + 0.5 * cfg.lambda * tot[5] * k.invP;
     if (trial) { k.ta = n.a; k.tb = n.b; k.trbar = n.rbar; k.ttbar = n.tbar; k.tdegen = n.degenerate; }
     else { k.a = n.a; k.b = n.b; k.rbar = n.rbar; k.tbar = n.tbar; k.degen = n.degenerate; }
     return E;
@@ -921,11 +967,11 @@ __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int
     if (action == kActGrad) {
         k.evals += 1;
         if (k.iters >= cfg.max_iter) { k.stop = REG_STOP_MAXIT; return kActDone; }
-        const double ss = tot[0], dmax = sqrt(tot[1]);
-        k.slope = -ss / k.Nc;
-        const double gn = sqrt(ss / k.Nc);
-        if (!(gn >= cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
-        if (k.tau * dmax > cfg.step_cap) k.tau = cfg.step_cap / dmax;
+        // |g| = sqrt(ss / Nc) and the largest control step dmax = sqrt(tot[1]): compared squared
+        const double ss = tot[0], dmax2 = tot[1];
+        k.slope = -ss * k.invNc;
+        if (!(ss * k.invNc >= cfg.tol_grad * cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
+        if (k.tau * k.tau * dmax2 > cfg.step_cap * cfg.step_cap) k.tau = cfg.step_cap / sqrt(dmax2);
         k.nrej = 0;
         pm[0] = (float)k.tau;
         return kActTrial;
@@ -936,17 +982,17 @@ __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int
     if (Et <= k.E + cfg.armijo_c * k.tau * k.slope) {
         k.iters += 1;
         const double Eold = k.E;
+        k.tau_pend = (double)(float)k.tau;
+        k.tau = next_tau(k.E, k.slope, k.tau, Et, true);
         k.E = Et;
         k.a = k.ta; k.b = k.tb; k.rbar = k.trbar; k.tbar = k.ttbar; k.degen = k.tdegen;
-        k.tau_pend = (double)(float)k.tau;
-        k.tau *= 2.0;
         if (Eold - Et <= cfg.tol_rel_e * fabs(Eold)) { k.stop = REG_STOP_REL; return kActDone; }
         field_grad_params(k, cfg, pm);
         return kActGrad;   // c is advanced to ct before the gradient pass
     }
     k.rejects += 1;
     k.nrej += 1;
-    k.tau *= 0.5;
+    k.tau = next_tau(k.E, k.slope, k.tau, Et, false);
     k.tau_pend = 0.0;
     if (k.nrej > cfg.max_rejects) { k.stop = REG_STOP_LS; return kActDone; }
     pm[0] = (float)k.tau;
@@ -1007,6 +1053,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
     if (tid == 0) {
         memset(&k, 0, sizeof(k));
         k.Nc = (double)Nc;
+        k.invNc = 1.0 / k.Nc;
     }
     int stops[kMaxLevels], iters[kMaxLevels], evals[kMaxLevels];
     for (int l = Lc - 1; l >= 0; --l) {
@@ -1020,6 +1067,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
         grid_rows(G, GL, rank, C, cr0, cr1, r0, r1);
         if (tid == 0) {
             k.P = (double)L.W * (double)L.H;
+            k.invP = 1.0 / k.P;
             k.tau = cfg.tau0;
             k.tau_pend = 0.0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
@@ -1206,6 +1254,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
         if (tid == 0) memset(&k, 0, sizeof(k));
         __syncthreads();
         k.P = (double)L.W * L.H;
+        k.invP = 1.0 / k.P;
         k.th[0] = theta[0]; k.th[1] = theta[1]; k.th[2] = theta[2];
         float pm[10];
         rigid_params(k.th, pm);
@@ -1234,7 +1283,9 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
         if (tid == 0) {
             memset(&k, 0, sizeof(k));
             k.P = (double)L.W * L.H;
+            k.invP = 1.0 / k.P;
             k.Nc = Nc;
+            k.invNc = 1.0 / k.Nc;
             k.sr = sm.tot[3]; k.srr = sm.tot[4];
             out[0] = field_energy(k, p.cfg, sm.tot, false);
             field_grad_params(k, p.cfg, sm.pm);

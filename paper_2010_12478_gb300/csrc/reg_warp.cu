@@ -19,6 +19,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "reg_f2.cuh"
 #include "reg_internal.h"
 
 namespace reg {
@@ -222,21 +223,6 @@ __device__ __forceinline__ float sample(const WarpArgs &a, const WarpSmem &sm, i
     // (the identity, whole-pixel shifts, the clamped edge) return pixel values unchanged
     const float top = fmaf(fx, t01, fmaf(-fx, t00, t00)), bot = fmaf(fx, t11, fmaf(-fx, t10, t10));
     return fmaf(fy, bot, fmaf(-fy, top, top));
-}
-
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n sub.rn.f32x2 z, x, y;\n"
-        " mov.b64 {%0, %1}, z;\n}\n"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-
-__device__ __forceinline__ float2 f2(float x)
-{
-    return make_float2(x, x);
 }
 
 // Per-thread pixel columns: c0 = x0 + lane and c1 = c0 + 32, processed as one float2 pair.
