@@ -144,21 +144,22 @@ def algorithmic_bytes(stats, H, W, levels, storage_bytes, mode):
     return total
 
 
-def profile_traffic(kernel_src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
-    p = os.path.join(ROOT, "profiles", "op_kernel_c2_rigid.md")
+def profile_traffic(name: str, src: str, key: str):
+    """A DRAM-traffic figure from a committed ncu summary (profiles/<name>.md), if that summary
+    was taken on the current kernel source (its sha256 prefix); else None."""
+    p = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(p):
         return None
     text = open(p).read()
     m = re.search(r"kernel source sha256: ([0-9a-f]{12})", text)
-    t = re.search(r"dram bytes per launch \(scaled\): ([0-9.e+]+)", text)
-    if not m or not t or m.group(1) != kernel_src_hash:
+    t = re.search(re.escape(key) + r": ([0-9.e+]+)", text)
+    if not m or not t or m.group(1) != kernel_hash(src):
         return None
     return float(t.group(1))
 
 
-def kernel_hash():
-    p = os.path.join(ROOT, "paper_2010_12478_gb300", "csrc", "reg_kernels.cu")
+def kernel_hash(src: str = "reg_kernels.cu"):
+    p = os.path.join(ROOT, "paper_2010_12478_gb300", "csrc", src)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
 
 
@@ -248,7 +249,7 @@ def serving(dev, mode: str, frames_per_stream: int, seed: int = 1410):
 
 
 # ------------------------------------------------------------------ precision
-def precision(frames, mode: str, n_samples: int = 2):
+def precision(frames, mode: str, n_samples: int = 6):
     """Per pyramid storage type: scan throughput on the workload and the maximum displacement
     error of sampled neighbour operators A(f_i, f_{i+1}) against the FP64 oracle."""
     import numpy as np
@@ -288,8 +289,61 @@ def precision(frames, mode: str, n_samples: int = 2):
                 ctx1.pairwise(frames[i].contiguous(), frames[i + 1].contiguous(), field_out=u)
                 errs.append(O.max_px_error(u.cpu().numpy(), O.grid_dense(g, ref[i].phi), H, W, "nonrigid"))
         out[storage] = {"frames_per_s": round(n / dt, 2), "max_px_error_vs_oracle": round(max(errs), 5),
-                        "operators_sampled": len(idx)}
+                        "median_px_error_vs_oracle": round(float(np.median(errs)), 5),
+                        "bar_px": 0.02 if storage == "f32" else 0.1,
+                        "operators_over_bar": [idx[j] for j, e in enumerate(errs)
+                                               if e > (0.02 if storage == "f32" else 0.1)],
+                        "operators_sampled": idx}
+    out["oracle_stop_reasons"] = {i: [int(v) for v in ref[i].stats.stop[:oc.levels]] for i in idx}
     return out
+
+
+# ------------------------------------------------------------------ registered series
+def registered_series(ctx, frames, mode: str, steps: int, warmup: int, peak: float, peak_src: str, world: int):
+    """reg_warp on the workload: out_k = f_k o phi_{0,k} for every frame and the series mean,
+    from the deformations of one scan; device-resident, CUDA events over `steps` calls."""
+    import ctypes
+    import torch
+    from paper_2010_12478_gb300 import binding as B
+    N, H, W = frames.shape
+    els, _ = ctx.scan(frames, schedule="brent_kung", exec="persistent",
+                      fields_out=None, want_stats=False)
+    kw = {}
+    if mode == "rigid":
+        arr = B.elem_array(els)
+        raw = torch.empty(ctypes.sizeof(arr), dtype=torch.uint8)
+        ctypes.memmove(raw.data_ptr(), ctypes.addressof(arr), ctypes.sizeof(arr))
+        kw["elems"] = raw.to(frames.device)
+    else:
+        nx, ny, _ = B.grid_dims(W, H, ctx.cfg.grid, ctx.cfg.levels)
+        g = torch.empty((N - 1, ny, nx, 2), device=frames.device)
+        ctx.scan_grids(g)
+        kw["grids"] = g
+    out = torch.empty_like(frames)
+    mean = torch.empty((H, W), device=frames.device)
+    for _ in range(warmup):
+        ctx.warp(frames, out=out, mean=mean, **kw)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ctx.warp(frames, out=out, mean=mean, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    alg = 8.0 * N * H * W + 4.0 * H * W   # each frame read once, each registered frame written once, the mean
+    achieved = alg / (ms / 1e3) / 1e9
+    tim = ctx.last_timing()
+    return {"value": round(world * N / (ms / 1e3), 1), "unit": "frames/s", "ms_per_call": round(ms, 4),
+            "outputs": "registered frames [N][H][W] and their mean",
+            "tma_staged": bool(tim["tma_staged"]),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "traffic": profile_traffic(f"warp_kernel_{'c2' if N <= 256 else 'c3'}_{mode}", "reg_warp.cu",
+                                                    "dram bytes per call (scaled)"),
+                         "peak_source": peak_src, "kernel": "warp_kernel (+ mean_kernel)",
+                         "algorithmic_bytes_per_call": alg}}
 
 
 # ------------------------------------------------------------------ main
@@ -307,6 +361,7 @@ def main():
     ap.add_argument("--oracle-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main timed region only (for profiler captures)")
+    ap.add_argument("--warp", action="store_true", help="with --quick: also run the registered-series stage")
     ap.add_argument("--serve-frames", type=int, default=96, help="frames per stream in the serving run")
     args = ap.parse_args()
 
@@ -348,7 +403,7 @@ def main():
         fl = torch.empty((N - 1, 2, H, W), device=dev) if mode == "nonrigid" else None
         tuned = {}
         if args.cluster == 0 and not args.quick:
-            for ex in ("plain", "persistent"):
+            for ex in ("plain", "persistent", "graph"):
                 tuned[ex] = c.autotune(frames, exec=ex)   # outside every timed region
         return c, fl, tuned
 
@@ -393,18 +448,27 @@ def main():
     launches = sum(t["op_launches"] for t in tim) / len(tim)
     peak, peak_src = peaks()
     achieved = alg / (kms / 1e3) / 1e9 if kms > 0 else 0.0
-    traffic = profile_traffic(kernel_hash())
+    traffic = profile_traffic(f"op_kernel_{args.workload}_{args.mode}", "reg_kernels.cu",
+                              f"dram bytes per step, {args.exec_} executor (scaled)")
     gpu_launches = int(sum(t["op_launches"] + t["pyramid_launches"] for t in tim))
     ev = np.array([sum(s["evals"]) for s in st_list[0]])
 
     levels = cfg.levels
-    batched = e2e = other = serve = prec = None
+    batched = e2e = other = serve = prec = reg_series = None
+    if args.quick and args.warp:
+        reg_series = registered_series(ctx, frames, args.mode, 1, 1, peak, peak_src, world)
     if not args.quick:
         # ---- batched executor on the same workload
         bms, bst, btim = timed(ctx, fields, frames, "persistent", max(3, args.steps // 2), 2)
         batched = {"exec": "persistent", "value": round(world * (N - 1) / (bms / 1e3), 2), "unit": UNIT,
                    "ms_per_step": round(bms, 3), "cluster": tuned.get("persistent", args.cluster),
                    "op_kernel_ms": round(sum(t["op_kernel_ms"] for t in btim) / len(btim), 3)}
+        # ---- the one-operator-per-launch path captured once as a CUDA graph and replayed
+        gms, _, _ = timed(ctx, fields, frames, "graph", max(3, args.steps // 2), 2)
+        batched["graph"] = {"exec": "graph", "value": round(world * (N - 1) / (gms / 1e3), 2), "unit": UNIT,
+                            "ms_per_step": round(gms, 3), "cluster": tuned.get("graph", args.cluster)}
+        # ---- registered series: every frame resampled onto f_0's grid by its prefix, and the mean
+        reg_series = registered_series(ctx, frames, args.mode, max(3, args.steps), 3, peak, peak_src, world)
         # ---- end to end: pinned host frames through the C ABI, copies inside the timed region
         host = frames.cpu().pin_memory()
         ems, _, _ = timed(ctx, fields, host, args.exec_, max(3, args.steps // 2), 1)
@@ -457,6 +521,7 @@ def main():
                          "kernel": "op_kernel (operator kernel)", "algorithmic_bytes_per_step": alg,
                          "kernel_ms_per_step": round(kms, 3), "launches_per_step": launches},
             "batched": batched,
+            "registered_series": reg_series,
             "other_mode": other,
             "serving": serve,
             "precision": prec,
