@@ -121,6 +121,22 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
+def world_max_ms(ms: float, dist, device) -> float:
+    """The step time of the whole job: the slowest rank's (every rank waits at the barrier)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed (independent replicas, weak
+    scaling) over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -424,11 +440,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = world_max_ms(e0.elapsed_time(e1) / steps, dist, dev)
         return ms, st_list, tim
 
     ctx, fields, tuned = make_ctx(args.mode)
@@ -438,8 +450,8 @@ def main():
         ms, st_list, tim = timed(ctx, fields, frames, args.exec_, args.steps, args.warmup)
     clocks = clk.summary()
     n_ops = len(st_list[0])
-    value = world * (N - 1) / (ms / 1e3)
-    ops_per_s = world * n_ops / (ms / 1e3)
+    value = job_rate(N - 1, world, ms)
+    ops_per_s = job_rate(n_ops, world, ms)
 
     # roofline of the operator kernel
     sb = 4 if cfg.storage == "f32" else 2

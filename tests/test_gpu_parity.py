@@ -280,13 +280,22 @@ def test_invalid_arguments_are_rejected():
 
 # ------------------------------------------------------------------ full size (256 x 512^2), sampled
 def test_c2_full_size_sampled_operators_match_oracle():
-    spec = synth.spec_c2()
+    sampled_rigid_scan_parity(synth.spec_c2(), "level", 0)
+
+
+def test_c3_full_size_sampled_operators_match_oracle():
+    # 4,096 frames with uneven iteration counts (SNR 3-20, 5 % jumps) through the persistent
+    # device queue, in the launch shape the batched form uses
+    sampled_rigid_scan_parity(synth.spec_c3(), "persistent", 16)
+
+
+def sampled_rigid_scan_parity(spec, exec_, cluster):
     ser = synth.make_series(spec, device="cuda")
     frames = ser.frames
-    cfg = B.Config()
+    cfg = B.Config(cluster=cluster)
     ctx = B.Context(cfg)
     n = spec.n_frames - 1
-    els, st = ctx.scan(frames, schedule="brent_kung", exec="level")
+    els, st = ctx.scan(frames, schedule="brent_kung", exec=exec_)
     ops, out = B.scan_dag("brent_kung", n)
     Fh = frames.cpu().numpy()
     oc = ocfg(cfg)
@@ -319,3 +328,35 @@ def test_c2_full_size_sampled_operators_match_oracle():
         prev = O.Elem(0, i + 1, np.array(els[i][2:], dtype=np.float64))
         e = O.op_B(prev, a, {0: P(0), i + 2: P(i + 2)}, oc)
         assert O.max_px_error(np.array(els[i + 1][2:], dtype=np.float64), e.phi, 512, 512, "rigid") <= PX_TOL
+
+
+def test_c2_full_size_nonrigid_operators_match_oracle():
+    # A and B at 512 x 512 through reg_pairwise in the scan's launch shape (16 CTAs), against the
+    # oracle from the same initial deformation.  Operators whose FP64 flow itself ends on the
+    # relative-decrease test (a flat valley: the minimiser is not determined to 0.02 px by the
+    # energy) are held to the energy bar and 0.05 px; the others to 0.02 px.
+    spec = synth.spec_c2()
+    frames = synth.make_series(spec, device="cuda").frames
+    Fh = frames.cpu().numpy()
+    cfg = B.Config(mode="nonrigid", cluster=16)
+    oc = ocfg(cfg)
+    ctx = B.Context(cfg)
+    g = O.grid_for(512, 512)
+    rng = np.random.default_rng(2010)
+    hard = 0
+    for i in rng.choice(spec.n_frames - 2, 3, replace=False):
+        P = {j: O.pyramid(Fh[j], 2) for j in (i, i + 1, i + 2)}
+        a1, a2 = O.op_A(P, i, i + 1, oc), O.op_A(P, i + 1, i + 2, oc)
+        cases = [(i + 1, None, a1)]
+        init = O.compose_grid(g, a1.phi, a2.phi)
+        phi, so = O.register_nonrigid(P[i], P[i + 2], init, oc)
+        cases.append((i + 2, init, O.Elem(i, i + 2, phi, so)))
+        for k, ini, ref in cases:
+            u = torch.empty((2, 512, 512), device="cuda")
+            fin = torch.from_numpy(O.grid_dense(g, ini).astype(np.float32)).cuda() if ini is not None else None
+            _, st = ctx.pairwise(frames[i].contiguous(), frames[k].contiguous(), field_in=fin, field_out=u)
+            err = O.max_px_error(u.cpu().numpy(), ref.phi, 512, 512, "nonrigid")
+            converged = ref.stats.stop[0] == 0
+            hard += not converged
+            assert rel(st["energy"], ref.stats.energy) <= E_TOL, (i, k)
+            assert err <= (PX_TOL if converged else 0.05), (i, k, err, list(ref.stats.stop))
