@@ -849,10 +849,37 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
             const float2 c00 = c[j0], c01 = c[j0 + 1], c10 = c[j0 + G.nx], c11 = c[j0 + G.nx + 1];
             const float2 dtop = make_float2(c01.x - c00.x, c01.y - c00.y);
             const float2 dbot = make_float2(c11.x - c10.x, c11.y - c10.y);
-            const bool pow2 = (w == sl);
             float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (w == sl && sl <= 32) {
+                // Full-width cell whose width divides the warp: every lane keeps one column
+                // (x = x0 + lane mod sl) and walks rows 32/sl apart, so the weight along x and
+                // the x-interpolated control values are fixed per lane; the y weights are summed
+                // and the x weights applied once at the end (the bilinear weight factorises).
+                const int x = x0 + (lane & (sl - 1)), dy = 32 >> lg;
+                const float wx = fminf(fmaf(GL.pl, (float)x, GL.off) * GL.scale_inv, (float)(G.nx - 1)) - (float)cxx;
+                const float tx = fmaf(wx, dtop.x, c00.x), ty = fmaf(wx, dtop.y, c00.y);
+                const float bx = fmaf(wx, dbot.x, c10.x), by = fmaf(wx, dbot.y, c10.y);
+                const float ex = bx - tx, ey = by - ty;
+                float st_x = 0.f, st_y = 0.f, sb_x = 0.f, sb_y = 0.f;
+                for (int y = y0 + (lane >> lg); y < y1; y += dy) {
+                    const float wy = fminf(fmaf(GL.pl, (float)y, GL.off) * GL.scale_inv, (float)(G.ny - 1)) - (float)cyy;
+                    float dtx, dty;
+                    const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, x, y, fmaf(wy, ex, tx), fmaf(wy, ey, ty),
+                                                        dtx, dty);
+                    const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
+                    const float tv = tw - L.cR;
+                    // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
+                    const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
+                    const float gx = F * dtx, gy = F * dty, hy = 1.f - wy;
+                    st_x = fmaf(hy, gx, st_x); st_y = fmaf(hy, gy, st_y);
+                    sb_x = fmaf(wy, gx, sb_x); sb_y = fmaf(wy, gy, sb_y);
+                }
+                const float hx = 1.f - wx;
+                acc[0] = hx * st_x; acc[1] = hx * st_y; acc[2] = wx * st_x; acc[3] = wx * st_y;
+                acc[4] = hx * sb_x; acc[5] = hx * sb_y; acc[6] = wx * sb_x; acc[7] = wx * sb_y;
+            } else
             for (int i = lane; i < npx; i += 32) {
-                const int y = y0 + (pow2 ? (i >> lg) : i / w), x = x0 + (pow2 ? (i & (sl - 1)) : i % w);
+                const int y = y0 + i / w, x = x0 + i % w;
                 const float gxf = fminf(fmaf(GL.pl, (float)x, GL.off) * GL.scale_inv, (float)(G.nx - 1));
                 const float gyf = fminf(fmaf(GL.pl, (float)y, GL.off) * GL.scale_inv, (float)(G.ny - 1));
                 const float wx = gxf - (float)cxx, wy = gyf - (float)cyy;
