@@ -178,15 +178,14 @@ struct Ncc {
 };
 
 // NCC = S'_RT / sqrt(S'_RR S'_TT) from shifted sums; dNCC/dTw(x) = a (r - rbar) - b (t - tbar).
-// 1/sqrt(q) for a positive finite q without a double-precision divide or square root (both
-// are long instruction sequences on this GPU): an FP32 seed on the mantissa scaled to [1, 4),
-// then two Newton-Raphson steps y <- y (3 - q y^2) / 2, each squaring the relative error
-// (2e-7 -> 1e-13 -> 1e-26, i.e. to double rounding).
+// 1/sqrt(q) for a positive normal q without a double-precision divide or square root (both
+// are long dependent instruction sequences on this GPU's narrow FP64 unit): the hardware
+// reciprocal-square-root approximation, then two Newton-Raphson steps y <- y (3 - q y^2) / 2,
+// each squaring the relative error (about 1e-7 -> 1e-14 -> double rounding).
 __device__ __forceinline__ double rsqrt_nr(double q)
 {
-    const int e = ilogb(q) & ~1;   // even exponent: q = m 2^e, m in [1, 4)
-    const double m = ldexp(q, -e);
-    double y = ldexp((double)rsqrtf((float)m), -e / 2);
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
         const double t = __dmul_rn(q, __dmul_rn(y, y));
@@ -471,9 +470,10 @@ enum Action { kActGrad = 0, kActTrial = 1, kActDone = 2, kActEnergy = 3, kActFie
 __device__ void rigid_params(const double *th, float *pm)
 {
     const float a = (float)th[0];
-    const float h = sinf(0.5f * a);
+    float h, ch;
+    sincosf(0.5f * a, &h, &ch);
     pm[0] = -2.f * h * h;            // cos(a) - 1 without cancellation
-    pm[1] = sinf(a);
+    pm[1] = 2.f * h * ch;            // sin(a)
     const double ix = rint(th[1]), iy = rint(th[2]);
     pm[2] = (float)(th[1] - ix);
     pm[3] = (float)(th[2] - iy);
@@ -499,8 +499,8 @@ __device__ __forceinline__ double next_tau(double E, double slope, double tau, d
 {
     const double den = Et - E - slope * tau;
     if (!(den > 0.0)) return accepted ? 2.0 * tau : 0.5 * tau;
-    const double r = rsqrt_nr(2.0 * den);   // 1 / (2 den) = r^2, without a divide
-    const double tq = -slope * tau * tau * (r * r);
+    // a step-size estimate needs no more than FP32 relative precision once den is formed
+    const double tq = (-slope * tau * tau) * (double)__frcp_rn((float)(2.0 * den));
     return accepted ? fmin(fmax(tq, 0.5 * tau), 4.0 * tau) : fmin(fmax(tq, 0.1 * tau), 0.5 * tau);
 }
 
