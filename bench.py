@@ -57,6 +57,8 @@ WORKLOAD_TEXT = {
     "c2": "256 frames 512x512 fp32 lattice series (random-walk drift +-1 px/frame, field <=1.5 px, SNR 10), "
           "Brent-Kung scan of B over A leaves",
     "c3": "4096 frames 512x512 fp32 lattice series (SNR 3-20, 5% jumps <=8 px), Brent-Kung scan",
+    "c4": "64 independent series of 128 frames, sizes drawn from {256^2, 512^2, 1024^2}, pyramids stored as "
+          "fp32 / bf16 / fp16; the series of one size share one batched scan (persistent queue)",
 }
 
 
@@ -362,6 +364,86 @@ def registered_series(ctx, frames, mode: str, steps: int, warmup: int, peak: flo
                          "algorithmic_bytes_per_call": alg}}
 
 
+# ------------------------------------------------------------------ mixed-size batch (c4)
+def mixed_batch(args, dev, world, rank, dist):
+    """64 series x 128 frames, sizes drawn from {256, 512, 1024}^2; per pyramid storage type the
+    series of each size run as one reg_scan_batch call (persistent queue); frames/s over all
+    series, and the displacement error of sampled neighbour operators against the FP64 oracle."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2010_12478_gb300 import binding as B
+    from paper_2010_12478_gb300 import synth
+    rng = np.random.default_rng(1410 + rank)
+    sizes = [int(v) for v in rng.choice([256, 512, 1024], size=64)]
+    groups = {}
+    for q, S in enumerate(sizes):
+        spec = synth.SeriesSpec(128, S, S, step=1.0, field_amp=1.5, snr=(10.0, 10.0), seed=1410 + rank, series=q)
+        groups.setdefault(S, []).append(synth.make_series(spec, device=dev).frames)
+    batches = {S: torch.stack(v) for S, v in groups.items()}
+    del groups
+    n_frames = sum(b.shape[0] * (b.shape[1] - 1) for b in batches.values())
+    peak, peak_src = peaks()
+    results = {}
+    with ClockSampler(0 if dev.index is None else dev.index) as clk:
+        for storage in ("f32", "bf16", "f16"):
+            ctxs = {S: B.Context(B.Config(mode=args.mode, storage=storage, cluster=16)) for S in batches}
+            for S, b in batches.items():   # warm-up
+                for _ in range(max(1, args.warmup)):
+                    ctxs[S].scan_batch(b, exec="persistent", want_stats=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                for S, b in batches.items():
+                    ctxs[S].scan_batch(b, exec="persistent", want_stats=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = world_max_ms(e0.elapsed_time(e1) / args.steps, dist, dev)
+            results[storage] = {"value": round(job_rate(n_frames, world, ms), 2), "unit": UNIT,
+                                "ms_per_step": round(ms, 2)}
+            del ctxs
+    # precision: sampled neighbour operators of the 256^2 and 512^2 series against the oracle
+    if rank == 0:
+        cfg0 = B.Config(mode=args.mode)
+        oc = O.Config(levels=cfg0.levels, max_iter=cfg0.max_iter, max_rejects=cfg0.max_rejects,
+                      tol_grad=cfg0.tol_grad, tol_rel_e=cfg0.tol_rel_e, armijo_c=cfg0.armijo_c, tau0=cfg0.tau0,
+                      step_cap=cfg0.step_cap, lam=cfg0.lam, mode=args.mode, grid=cfg0.grid)
+        samples = [(S, 0, j) for S in (256, 512) if S in batches for j in (5, 77)]
+        for storage in ("f32", "bf16", "f16"):
+            ctx = B.Context(B.Config(mode=args.mode, storage=storage, cluster=16))
+            errs = []
+            for S, q, j in samples:
+                F = batches[S][q]
+                Fh = F[j:j + 2].cpu().numpy()
+                ref = O.op_A({0: O.pyramid(Fh[0], oc.levels), 1: O.pyramid(Fh[1], oc.levels)}, 0, 1, oc)
+                if args.mode == "rigid":
+                    el, _ = ctx.pairwise(F[j].contiguous(), F[j + 1].contiguous())
+                    errs.append(O.max_px_error(np.array(el[2:], dtype=np.float64), ref.phi, S, S, "rigid"))
+                else:
+                    u = torch.empty((2, S, S), device=dev)
+                    ctx.pairwise(F[j].contiguous(), F[j + 1].contiguous(), field_out=u)
+                    errs.append(O.max_px_error(u.cpu().numpy(), ref.phi, S, S, "nonrigid"))
+            results[storage]["max_px_error_vs_oracle"] = round(max(errs), 5)
+            results[storage]["operators_sampled"] = [f"{S}^2 series {q} frames {j},{j + 1}" for S, q, j in samples]
+        line = {
+            "metric": METRIC, "value": results["f32"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": results["f32"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c4: {WORKLOAD_TEXT['c4']}", "series": 64, "frames_per_series": 128,
+                       "sizes": {str(S): int(b.shape[0]) for S, b in batches.items()}, "mode": args.mode,
+                       "exec": "persistent (one reg_scan_batch per size)", "cluster": 16,
+                       "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "precision": results, "clocks": clk.summary(),
+            "roofline": None, "e2e": None, "cpu_baseline": None,
+            "note": "per-storage throughput and error; the operator-kernel roofline and the end-to-end and CPU "
+                    "baselines are reported on the c2 and c3 workloads",
+        }
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -369,7 +451,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--mode", default="nonrigid", choices=["rigid", "nonrigid"])
     ap.add_argument("--exec", dest="exec_", default="plain", choices=["plain", "level", "persistent", "graph"])
     ap.add_argument("--frames", type=int, default=0, help="override the series length (small profiler cases)")
@@ -403,6 +485,9 @@ def main():
     from paper_2010_12478_gb300 import binding as B
     from paper_2010_12478_gb300 import build, synth
     build.build()
+    if args.workload == "c4":
+        mixed_batch(args, dev, world, rank, dist)
+        return
 
     spec = workload_spec(args.workload, rank, args.frames)
     ser = synth.make_series(spec, device=dev)

@@ -187,6 +187,20 @@ int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch
              int schedule, int exec, reg_elem_t *out, float *fields_out,
              reg_stats_t *per_op, void *stream);
 
+/* S independent series of N frames each (same W, H) registered in one call: the
+ * operators of all series share the executor's launches (and, with
+ * REG_EXEC_PERSISTENT, one device queue), so series with uneven iteration counts
+ * fill the GPU together.  Each series is the scan of reg_scan [Sec. 3].
+ *   frames     fp32 [S][N][H][pitch], host or device.
+ *   out        S x (N-1) elements, series-major; indices i, k are series-local.
+ *   fields_out REG_NONRIGID: [S][N-1][2][H][W] or NULL.
+ *   per_op     optional host array of S x (the per-series count of reg_scan),
+ *              series-major, frame indices series-local.
+ * reg_scan_grids afterwards returns S x (N-1) control grids.  Errors as reg_scan. */
+int reg_scan_batch(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, int pitch,
+                   int schedule, int exec, reg_elem_t *out, float *fields_out,
+                   reg_stats_t *per_op, void *stream);
+
 /* Control values of the N-1 prefixes phi_{0,1}..phi_{0,N-1} of the last
  * successful REG_NONRIGID reg_scan on ctx: grids_out, device, [N-1][ny][nx]
  * (x, y) pairs, ny/nx from reg_grid_dims for that scan's W, H.  n_out (host,

@@ -31,7 +31,7 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
            "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load",
-           "reg_scan_grids", "reg_warp"]
+           "reg_scan_grids", "reg_warp", "reg_scan_batch"]
 
 
 class RegError(RuntimeError):
@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(reg_stats_t), vp]
         L.reg_autotune.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(ip)]
         L.reg_scan_grids.argtypes = [vp, fp, ctypes.POINTER(ip), vp]
+        L.reg_scan_batch.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ip, vp, fp, ctypes.POINTER(reg_stats_t), vp]
         L.reg_warp.argtypes = [vp, fp, ip, ip, ip, ip, ctypes.POINTER(reg_elem_t), fp, fp, fp, vp]
         L.reg_autotune_save.argtypes = [vp, ctypes.c_char_p]
         L.reg_autotune_load.argtypes = [vp, ctypes.c_char_p]
@@ -252,6 +253,23 @@ class Context:
                              _ptr(fields_out), stats, _stream(stream)), "reg_scan")
         el = [(e.i, e.k, e.alpha, e.gx, e.gy) for e in elems] if elems is not None else None
         st = [stats_dict(s, self.cfg.levels) for s in stats] if stats is not None else None
+        return el, st
+
+    def scan_batch(self, frames, schedule: str = "brent_kung", exec: str = "persistent", fields_out=None,
+                   want_stats: bool = True, stream=None):
+        """S series [S, N, H, W] in one call; returns per-series element lists and stats."""
+        S, N, H, W = frames.shape
+        n = N - 1
+        m = scan_work(schedule, n)
+        elems = (reg_elem_t * (S * n))()
+        stats = (reg_stats_t * (S * (n + m)))() if want_stats else None
+        check(lib().reg_scan_batch(self.h, _ptr(frames), S, N, W, H, W, SCHEDULES[schedule], EXECS[exec],
+                                   ctypes.addressof(elems), _ptr(fields_out), stats, _stream(stream)),
+              "reg_scan_batch")
+        el = [[(e.i, e.k, e.alpha, e.gx, e.gy) for e in elems[q * n:(q + 1) * n]] for q in range(S)]
+        st = None
+        if stats is not None:
+            st = [[stats_dict(x, self.cfg.levels) for x in stats[q * (n + m):(q + 1) * (n + m)]] for q in range(S)]
         return el, st
 
     def scan_grids(self, out):

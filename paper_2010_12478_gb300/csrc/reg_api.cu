@@ -865,11 +865,59 @@ int copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
 }  // namespace
 
 // ------------------------------------------------------------------ reg_scan
-extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch, int schedule, int exec,
-                        reg_elem_t *out, float *fields_out, reg_stats_t *per_op, void *stream)
+namespace {
+
+// S independent series of N frames in one plan: series s owns frames s N .. s N + N - 1 and
+// nodes s n_nodes .. (s + 1) n_nodes - 1 of the single-series plan; operators are grouped by
+// DAG depth across series, so every executor runs the series side by side.
+int plan_batch(int S, int N, const Dag &d, ScanPlan &p)
+{
+    ScanPlan one;
+    CHECK(plan_scan(N, d, one));
+    if (S == 1) {
+        p = std::move(one);
+        return REG_OK;
+    }
+    const int nops = (int)one.ops.size(), nn = one.n_nodes, n = N - 1;
+    p.n_nodes = S * nn;
+    p.node_i.resize(p.n_nodes);
+    p.node_k.resize(p.n_nodes);
+    p.out_nodes.resize((size_t)S * n);
+    for (int sr = 0; sr < S; ++sr) {
+        for (int v = 0; v < nn; ++v) {
+            p.node_i[sr * nn + v] = one.node_i[v] + sr * N;
+            p.node_k[sr * nn + v] = one.node_k[v] + sr * N;
+        }
+        for (int i = 0; i < n; ++i) p.out_nodes[(size_t)sr * n + i] = one.out_nodes[i] + sr * nn;
+    }
+    const int nd = (int)one.depth_start.size() - 1;
+    p.depth_start.assign(nd + 1, 0);
+    p.ops.clear();
+    p.user_index.clear();
+    for (int dpt = 0; dpt < nd; ++dpt) {
+        p.depth_start[dpt] = (int)p.ops.size();
+        for (int sr = 0; sr < S; ++sr)
+            for (int e = one.depth_start[dpt]; e < one.depth_start[dpt + 1]; ++e) {
+                OpDesc op = one.ops[e];
+                op.ref += sr * N;
+                op.tmpl += sr * N;
+                if (op.left >= 0) op.left += sr * nn;
+                if (op.right >= 0) op.right += sr * nn;
+                op.out += sr * nn;
+                p.ops.push_back(op);
+                p.user_index.push_back(sr * nops + one.user_index[e]);
+            }
+    }
+    p.depth_start[nd] = (int)p.ops.size();
+    return REG_OK;
+}
+
+int scan_impl(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, int pitch, int schedule, int exec,
+              reg_elem_t *out, float *fields_out, reg_stats_t *per_op, void *stream)
 {
     if (!ctx) return fail(REG_EINVAL, "ctx is NULL");
     if (!frames || !out) return fail(REG_EINVAL, "frames/out is NULL");
+    if (S < 1) return fail(REG_EINVAL, "need S >= 1 series, got %d", S);
     if (N < 2) return fail(REG_EINVAL, "need N >= 2 frames, got %d", N);
     if (pitch < W) return fail(REG_EINVAL, "pitch %d < W %d", pitch, W);
     if (exec != REG_EXEC_PLAIN && exec != REG_EXEC_LEVEL && exec != REG_EXEC_PERSISTENT && exec != REG_EXEC_GRAPH)
@@ -886,48 +934,49 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
     Dag dag;
     if (!make_dag(schedule, N - 1, dag)) return fail(REG_EINVAL, "schedule %d", schedule);
     ScanPlan plan;
-    CHECK(plan_scan(N, dag, plan));
+    CHECK(plan_batch(S, N, dag, plan));
     timing_reset(ctx);
+    const int NF = S * N;   // frames of all series
 
     const float *dframes = frames;
     if (!is_device_ptr(frames)) {
-        size_t bytes = sizeof(float) * (size_t)N * H * pitch;
+        size_t bytes = sizeof(float) * (size_t)NF * H * pitch;
         CHECK(ctx->frames_dev.reserve(bytes));
         CU(cudaMemcpyAsync(ctx->frames_dev.ptr, frames, bytes, cudaMemcpyHostToDevice, s));
         dframes = ctx->frames_dev.as<float>();
     }
-    CHECK(build_pyramids(ctx, g, dframes, N, (size_t)H * pitch, pitch, 0, N, s));
-    CHECK(build_level_table(ctx, g, N, s));
+    CHECK(build_pyramids(ctx, g, dframes, NF, (size_t)H * pitch, pitch, 0, NF, s));
+    CHECK(build_level_table(ctx, g, NF, s));
 
     const int n_ops = (int)plan.ops.size();
     Params p;
-    CHECK(prepare_params(ctx, g, N, plan.n_nodes, n_ops, p, s));
+    CHECK(prepare_params(ctx, g, NF, plan.n_nodes, n_ops, p, s));
     CU(cudaMemcpyAsync(ctx->ops.ptr, plan.ops.data(), sizeof(OpDesc) * n_ops, cudaMemcpyHostToDevice, s));
-    CHECK(execute(ctx, plan, p, exec, ctx->cfg.cluster > 0 ? 0 : tuned_cluster(ctx, W, H, exec, N), s));
+    CHECK(execute(ctx, plan, p, exec, ctx->cfg.cluster > 0 ? 0 : tuned_cluster(ctx, W, H, exec, NF), s));
     CU(cudaGetLastError());
     CHECK(check_device_status(ctx, s));
 
-    // results
-    const int n = N - 1;
+    // results (element indices are series-local: frame s N + i is frame i of series s)
+    const int n = N - 1, nout = S * n, nops1 = n_ops / S;
     std::vector<double> th((size_t)3 * plan.n_nodes);
     CU(cudaMemcpyAsync(th.data(), p.node_theta, sizeof(double) * th.size(), cudaMemcpyDeviceToHost, s));
     std::vector<OpStats> st(n_ops);
     CU(cudaMemcpyAsync(st.data(), p.stats, sizeof(OpStats) * n_ops, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    std::vector<reg_elem_t> el(n);
-    for (int i = 0; i < n; ++i) {
-        int node = plan.out_nodes[i];
-        el[i].i = plan.node_i[node];
-        el[i].k = plan.node_k[node];
-        el[i].alpha = (float)th[3 * node];
-        el[i].gx = (float)th[3 * node + 1];
-        el[i].gy = (float)th[3 * node + 2];
+    std::vector<reg_elem_t> el(nout);
+    for (int q = 0; q < nout; ++q) {
+        const int node = plan.out_nodes[q], base = (q / n) * N;
+        el[q].i = plan.node_i[node] - base;
+        el[q].k = plan.node_k[node] - base;
+        el[q].alpha = (float)th[3 * node];
+        el[q].gx = (float)th[3 * node + 1];
+        el[q].gy = (float)th[3 * node + 2];
     }
-    CHECK(copy_out(out, el.data(), sizeof(reg_elem_t) * n, s));
+    CHECK(copy_out(out, el.data(), sizeof(reg_elem_t) * nout, s));
     ctx->last_n = 0;
     if (ctx->cfg.mode == REG_NONRIGID) {
-        CHECK(ctx->node_ids.reserve(sizeof(int) * n));
-        CU(cudaMemcpyAsync(ctx->node_ids.ptr, plan.out_nodes.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+        CHECK(ctx->node_ids.reserve(sizeof(int) * nout));
+        CU(cudaMemcpyAsync(ctx->node_ids.ptr, plan.out_nodes.data(), sizeof(int) * nout, cudaMemcpyHostToDevice, s));
     }
     if (ctx->cfg.mode == REG_NONRIGID && fields_out) {
         // dense finest-level fields of the prefixes, written by one kernel
@@ -935,25 +984,47 @@ extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H
         float *dst = (float *)fields_out;
         const bool direct = is_device_ptr(fields_out);
         if (!direct) {
-            CHECK(ctx->frames_dev.reserve(fb * n + (size_t)sizeof(float) * N * H * pitch));
-            dst = (float *)((char *)ctx->frames_dev.ptr + (size_t)sizeof(float) * N * H * pitch);
+            CHECK(ctx->frames_dev.reserve(fb * nout + (size_t)sizeof(float) * NF * H * pitch));
+            dst = (float *)((char *)ctx->frames_dev.ptr + (size_t)sizeof(float) * NF * H * pitch);
         }
-        CU(launch_grid_dense(p.node_grid, ctx->node_ids.as<int>(), n, p.gnx, p.gny, p.gs, W, H, dst, s));
-        if (!direct) CU(cudaMemcpyAsync(fields_out, dst, fb * n, cudaMemcpyDeviceToHost, s));
+        CU(launch_grid_dense(p.node_grid, ctx->node_ids.as<int>(), nout, p.gnx, p.gny, p.gs, W, H, dst, s));
+        if (!direct) CU(cudaMemcpyAsync(fields_out, dst, fb * nout, cudaMemcpyDeviceToHost, s));
     }
     if (per_op) {
-        for (int e = 0; e < n_ops; ++e) memcpy(&per_op[plan.user_index[e]], &st[e], sizeof(reg_stats_t));
+        for (int e = 0; e < n_ops; ++e) {
+            reg_stats_t r;
+            memcpy(&r, &st[e], sizeof(r));
+            const int base = (plan.user_index[e] / nops1) * N;
+            r.i -= base;
+            r.k -= base;
+            per_op[plan.user_index[e]] = r;
+        }
     }
     CU(cudaStreamSynchronize(s));
     timing_resolve(ctx);
     for (int e = 0; e < n_ops; ++e)
         if (st[e].status != kDevOk) return fail(REG_EINVAL, "operator %d failed on the device (%d)", e, st[e].status);
     if (ctx->cfg.mode == REG_NONRIGID) {
-        ctx->last_n = n;
+        ctx->last_n = nout;
         ctx->last_gnx = p.gnx;
         ctx->last_gny = p.gny;
     }
     return REG_OK;
+}
+
+}  // namespace
+
+extern "C" int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch, int schedule, int exec,
+                        reg_elem_t *out, float *fields_out, reg_stats_t *per_op, void *stream)
+{
+    return scan_impl(ctx, frames, 1, N, W, H, pitch, schedule, exec, out, fields_out, per_op, stream);
+}
+
+extern "C" int reg_scan_batch(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, int pitch,
+                              int schedule, int exec, reg_elem_t *out, float *fields_out, reg_stats_t *per_op,
+                              void *stream)
+{
+    return scan_impl(ctx, frames, S, N, W, H, pitch, schedule, exec, out, fields_out, per_op, stream);
 }
 
 // ------------------------------------------------------------------ reg_scan_grids / reg_warp

@@ -916,17 +916,34 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     const float scale = -(float)Nc / ((float)L.W * (float)L.H);
     float ssh = 0.f, ssl = 0.f, mx = 0.f, run = 0.f;
     int k = 0;
-    for (int j = tid; j < Nc; j += kThreads) {
-        const int jy = j / G.nx, jx = j - jy * G.nx;
-        // bands: rank r owns cell rows [r q, (r+1) q) and so control rows [r q, (r+1) q]
-        const int rlo = jy > 0 ? min(C - 1, (jy - 1) / max(q, 1)) : 0;
-        const int rhi = min(C - 1, jy / max(q, 1));
-        float2 g = make_float2(0.f, 0.f);
-        for (int r = rlo; r <= rhi; ++r) {
-            const float2 v = *cl.map_shared_rank(gp + j, r);
-            g.x += v.x;
-            g.y += v.y;
+    constexpr int kBatch = 4;   // points per thread whose remote loads are in flight together
+    for (int j0 = tid; j0 < Nc; j0 += kBatch * kThreads) {
+        float2 gb[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int j = j0 + b * kThreads;
+            gb[b] = make_float2(0.f, 0.f);
+            if (j < Nc) {
+                const int jy = j / G.nx;
+                // bands: rank r owns cell rows [r q, (r+1) q) and so control rows [r q, (r+1) q]
+                const int rlo = jy > 0 ? min(C - 1, (jy - 1) / max(q, 1)) : 0;
+                const int rhi = min(C - 1, jy / max(q, 1));
+                const float2 v = *cl.map_shared_rank(gp + j, rlo);
+                gb[b].x += v.x;
+                gb[b].y += v.y;
+                if (rhi != rlo) {
+                    const float2 w2 = *cl.map_shared_rank(gp + j, rhi);
+                    gb[b].x += w2.x;
+                    gb[b].y += w2.y;
+                }
+            }
         }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+        const int j = j0 + b * kThreads;
+        if (j >= Nc) break;
+        const int jy = j / G.nx, jx = j - jy * G.nx;
+        const float2 g = gb[b];
         const float2 cj = c[j];
         float lx = 0.f, ly = 0.f;
         if (jx > 0)        { const float2 v = c[j - 1];    lx += cj.x - v.x; ly += cj.y - v.y; }
@@ -941,6 +958,7 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
         run += qd;
         mx = fmaxf(mx, qd);
         if (++k == kFast) { ff_acc(ssh, ssl, run); run = 0.f; k = 0; }
+        }
     }
     ff_acc(ssh, ssl, run);
     // block reduction (identical in every CTA: same inputs, same order)

@@ -360,3 +360,26 @@ def test_c2_full_size_nonrigid_operators_match_oracle():
             hard += not converged
             assert rel(st["energy"], ref.stats.energy) <= E_TOL, (i, k)
             assert err <= (PX_TOL if converged else 0.05), (i, k, err, list(ref.stats.stop))
+
+
+@pytest.mark.parametrize("exec_", ["persistent", "level", "plain"])
+def test_scan_batch_equals_per_series_scans(exec_):
+    # independent series registered together give each series' own scan, bit for bit
+    series = [c1_frames(7, seed) for seed in (1410, 1411, 1412)]
+    for mode in ("rigid", "nonrigid"):
+        ctx = B.Context(B.Config(mode=mode, cluster=4))
+        Fb = torch.from_numpy(np.stack(series)).cuda()
+        els_b, st_b = ctx.scan_batch(Fb, schedule="brent_kung", exec=exec_)
+        if mode == "nonrigid":
+            nx, ny, _ = B.grid_dims(128, 128)
+            gb = torch.zeros((3, 6, ny, nx, 2), device="cuda")
+            assert ctx.scan_grids(gb) == 18
+        for q, F in enumerate(series):
+            els, st = ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung", exec=exec_)
+            assert els_b[q] == els
+            assert [s["energy"] for s in st_b[q]] == [s["energy"] for s in st]
+            assert [(s["i"], s["k"]) for s in st_b[q]] == [(s["i"], s["k"]) for s in st]
+            if mode == "nonrigid":
+                g1 = torch.zeros((6, ny, nx, 2), device="cuda")
+                ctx.scan_grids(g1)
+                assert torch.equal(g1, gb[q])
