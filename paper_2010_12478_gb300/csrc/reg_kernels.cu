@@ -32,7 +32,7 @@ namespace cg = cooperative_groups;
 namespace reg {
 
 constexpr int kWarps = kThreads / 32;
-constexpr int kNM = 16;        // moment slots per reduction
+constexpr int kNM = 8;         // moment slots per reduction (at most 6 are used)
 constexpr int kMaxCluster = 16; // CTAs per operator at most (non-portable cluster size)
 constexpr int kChunk = 32;     // pixels per thread between float-float flushes
 
@@ -120,6 +120,7 @@ template <int NM, bool MAXLAST>
 __device__ __forceinline__ void cluster_reduce(float (&hi)[NM], float (&lo)[NM], Smem &sm,
                                                int &buf, const cg::cluster_group &cl, bool fence)
 {
+    static_assert(NM <= kNM, "reduction slots");
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
@@ -698,6 +699,12 @@ __device__ __forceinline__ float2 grid_eval(const float2 *c, int nx, int ix, int
 
 // Rows and band of control-cell rows owned by a CTA: cell rows [k q, (k+1) q), q = ceil((ny-1)/C);
 // level pixel rows of those cells (the last CTA also takes rows clamped into the last cell row).
+// Partial-gradient buffer of one CTA: the control rows of its band of cell rows, [cr0, cr1].
+__host__ __device__ __forceinline__ int grid_band_elems(int gnx, int gny, int C)
+{
+    return ((gny - 1 + C - 1) / C + 1) * gnx;
+}
+
 __device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int rank, int C, int &cr0, int &cr1,
                                           int &r0, int &r1)
 {
@@ -831,8 +838,8 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     const int Nc = G.nx * G.ny, ncx = G.nx - 1, ncy = G.ny - 1;
     const int sl = G.s >> GL.l;
     const int lg = 31 - __clz(sl);   // sl is a power of two (the spacing is a multiple of 2^l)
-    float *gpf = (float *)gp;
-    for (int j = tid; j < Nc; j += kThreads) gp[j] = make_float2(0.f, 0.f);
+    float *gpf = (float *)gp;   // band-local: control row cr0 + i at gp[i nx .. (i + 1) nx)
+    for (int j = tid; j < (cr1 - cr0 + 1) * G.nx; j += kThreads) gp[j] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int phase = 0; phase < 4; ++phase) {
         const int px = phase & 1, py = phase >> 1;
@@ -904,7 +911,7 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
             if ((lane & 3) == 0) {
                 const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
                 const int corner = vi >> 1;
-                const int jc = j0 + (corner & 1) + (corner >> 1) * G.nx;
+                const int jc = (cyy + (corner >> 1) - cr0) * G.nx + cxx + (corner & 1);
                 gpf[2 * jc + (vi & 1)] += tot8;
             }
         }
@@ -928,11 +935,12 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
                 // bands: rank r owns cell rows [r q, (r+1) q) and so control rows [r q, (r+1) q]
                 const int rlo = jy > 0 ? min(C - 1, (jy - 1) / max(q, 1)) : 0;
                 const int rhi = min(C - 1, jy / max(q, 1));
-                const float2 v = *cl.map_shared_rank(gp + j, rlo);
+                const int jx = j - jy * G.nx;
+                const float2 v = *cl.map_shared_rank(gp + (jy - min(ncy, rlo * q)) * G.nx + jx, rlo);
                 gb[b].x += v.x;
                 gb[b].y += v.y;
                 if (rhi != rlo) {
-                    const float2 w2 = *cl.map_shared_rank(gp + j, rhi);
+                    const float2 w2 = *cl.map_shared_rank(gp + (jy - min(ncy, rhi * q)) * G.nx + jx, rhi);
                     gb[b].x += w2.x;
                     gb[b].y += w2.y;
                 }
@@ -1070,7 +1078,8 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
     const int Lc = cfg.levels;
     const Grid G{p.gnx, p.gny, p.gs};
     const int Nc = G.nx * G.ny;
-    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc, *crow = gbuf + 4 * Nc;
+    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
+    float2 *crow = gp + grid_band_elems(G.nx, G.ny, C);
     int buf = 0;
     // initial control values (finest px), scaled to the coarsest level
     {
@@ -1316,7 +1325,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
     } else {
         const Grid G{p.gnx, p.gny, p.gs};
         const int Nc = G.nx * G.ny;
-        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc, *crow = gbuf + 4 * Nc;
+        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc, *crow = gp + grid_band_elems(G.nx, G.ny, 1);
         for (int j = tid; j < Nc; j += kThreads) c[j] = cgrid[j];
         __syncthreads();
         GridLvl GL;
@@ -1481,9 +1490,13 @@ cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, in
     return cudaErrorInvalidValue;
 }
 
-static size_t grid_smem(const Params &p)
+// Dynamic shared memory of the nonrigid kernels: c, d and the trial c (whole grid), this CTA's
+// band of the partial gradient, one interpolated control row per warp.
+static size_t grid_smem(const Params &p, int cluster)
 {
-    return p.cfg.mode == REG_NONRIGID ? sizeof(float2) * (4 * (size_t)p.gnx * p.gny + (size_t)kWarps * p.gnx) : 0;
+    if (p.cfg.mode != REG_NONRIGID) return 0;
+    return sizeof(float2) * (3 * (size_t)p.gnx * p.gny + (size_t)grid_band_elems(p.gnx, p.gny, cluster) +
+                             (size_t)kWarps * p.gnx);
 }
 
 template <typename K>
@@ -1493,7 +1506,7 @@ static cudaError_t launch_cluster(K kernel, int blocks, int cluster, cudaStream_
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
-    const size_t smem = grid_smem(p);
+    const size_t smem = grid_smem(p, cluster);
     if (smem > 0) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1556,7 +1569,7 @@ static int resident_clusters(K kernel, int cluster, const Params &p)
 {
     if (cluster > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         return -1;
-    const size_t smem = grid_smem(p);
+    const size_t smem = grid_smem(p, cluster);
     if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
     cudaLaunchConfig_t lc = {};
@@ -1599,7 +1612,7 @@ cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
                           double *out_dev, float2 *grad_dev, cudaStream_t s)
 {
     (void)storage;
-    const size_t smem = grid_smem(p);
+    const size_t smem = grid_smem(p, 1);
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(1);
     lc.blockDim = dim3(kThreads);
