@@ -66,7 +66,8 @@ struct __align__(128) WarpSmem {
     int2 org[kStages];
     int fit[kStages];
     float4 rp[kStages];
-    float2 win[kStages][kWinY * kWinX];
+    float2 win[kStages][kWinY * kWinX];  // control points under the tile
+    float2 xint[kStages][kWinY][kTW];   // control rows of the window interpolated along x at each tile column
     int2 wo[kStages];
     int abort;
 };
@@ -108,15 +109,62 @@ __device__ __forceinline__ int cell_of(float gf, int n)
     return min((int)gf, n - 2);
 }
 
+// Control points under the tile (x0, y0): first cell column / row and the point counts.
+struct Window {
+    int cx0, cy0, wx, wy;
+};
+
+__device__ __forceinline__ Window window_of(const WarpArgs &a, int x0, int y0)
+{
+    const int x1 = min(x0 + kTW, a.W) - 1, y1 = min(y0 + kTH, a.H) - 1;
+    Window w;
+    w.cx0 = cell_of(fminf((float)x0 * a.inv_s, (float)(a.nx - 1)), a.nx);
+    w.cy0 = cell_of(fminf((float)y0 * a.inv_s, (float)(a.ny - 1)), a.ny);
+    w.wx = cell_of(fminf((float)x1 * a.inv_s, (float)(a.nx - 1)), a.nx) + 2 - w.cx0;   // <= kWinX for spacing >= 8
+    w.wy = cell_of(fminf((float)y1 * a.inv_s, (float)(a.ny - 1)), a.ny) + 2 - w.cy0;   // <= kWinY
+    return w;
+}
+
+// What the producer needs from global memory for one frame, loaded a frame ahead so that the
+// load latency overlaps the previous frame's work: the rigid parameters, or this lane's share
+// (up to 3 points) of the control window.
+struct Prefetch {
+    float4 q;
+    float2 v[3];
+};
+
+__device__ __forceinline__ Prefetch fetch(const WarpArgs &a, const Window &w, int k)
+{
+    Prefetch f;
+    const int lane = threadIdx.x & 31;
+    if (a.mode == REG_RIGID) {
+        f.q = a.rigid[k];
+        return f;
+    }
+    f.q = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 *g = k > 0 ? a.grids + (size_t)(k - 1) * a.nx * a.ny : nullptr;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int j = lane + 32 * t;
+        f.v[t] = make_float2(0.f, 0.f);
+        if (a.window && g && j < w.wx * w.wy) {
+            const int jy = j / w.wx, jx = j - jy * w.wx;
+            f.v[t] = g[(size_t)(w.cy0 + jy) * a.nx + w.cx0 + jx];
+        }
+    }
+    return f;
+}
+
 // Warp 0: stage the parameters of frame k for the tile (x0, y0) into ring slot st and start
 // the TMA load of its source box.
-__device__ void prepare(const WarpArgs &a, const CUtensorMap *tmap, WarpSmem &sm, int k, int st, int x0, int y0)
+__device__ void prepare(const WarpArgs &a, const CUtensorMap *tmap, WarpSmem &sm, int k, int st, int x0, int y0,
+                        const Window &win, const Prefetch &f)
 {
     const int lane = threadIdx.x & 31;
     const int x1 = min(x0 + kTW, a.W) - 1, y1 = min(y0 + kTH, a.H) - 1;
     float pxlo, pxhi, pylo, pyhi;
     if (a.mode == REG_RIGID) {
-        const float4 q = a.rigid[k];
+        const float4 q = f.q;
         const float cx = 0.5f * (float)(a.W - 1), cy = 0.5f * (float)(a.H - 1);
         pxlo = pylo = 3.0e38f;
         pxhi = pyhi = -3.0e38f;
@@ -133,20 +181,32 @@ __device__ void prepare(const WarpArgs &a, const CUtensorMap *tmap, WarpSmem &sm
     } else {
         float uxlo = 0.f, uxhi = 0.f, uylo = 0.f, uyhi = 0.f;
         if (a.window) {
-            const int cx0 = cell_of(fminf((float)x0 * a.inv_s, (float)(a.nx - 1)), a.nx);
-            const int cx1 = cell_of(fminf((float)x1 * a.inv_s, (float)(a.nx - 1)), a.nx) + 1;
-            const int cy0 = cell_of(fminf((float)y0 * a.inv_s, (float)(a.ny - 1)), a.ny);
-            const int cy1 = cell_of(fminf((float)y1 * a.inv_s, (float)(a.ny - 1)), a.ny) + 1;
-            const int wx = cx1 - cx0 + 1, wy = cy1 - cy0 + 1;   // <= kWinX, kWinY for spacing >= 8
+            const int cx0 = win.cx0, cy0 = win.cy0, wx = win.wx, wy = win.wy;
             uxlo = uylo = 3.0e38f;
             uxhi = uyhi = -3.0e38f;
-            const float2 *g = k > 0 ? a.grids + (size_t)(k - 1) * a.nx * a.ny : nullptr;
-            for (int j = lane; j < wx * wy; j += 32) {
-                const int jy = j / wx, jx = j - jy * wx;
-                const float2 v = g ? g[(size_t)(cy0 + jy) * a.nx + cx0 + jx] : make_float2(0.f, 0.f);
-                sm.win[st][jy * kWinX + jx] = v;
-                uxlo = fminf(uxlo, v.x); uxhi = fmaxf(uxhi, v.x);
-                uylo = fminf(uylo, v.y); uyhi = fmaxf(uyhi, v.y);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int j = lane + 32 * t;
+                if (j < wx * wy) {
+                    const int jy = j / wx, jx = j - jy * wx;
+                    const float2 v = f.v[t];
+                    sm.win[st][jy * kWinX + jx] = v;
+                    uxlo = fminf(uxlo, v.x); uxhi = fmaxf(uxhi, v.x);
+                    uylo = fminf(uylo, v.y); uyhi = fmaxf(uyhi, v.y);
+                }
+            }
+            // each window control row interpolated along x at the tile's columns (a column past
+            // the frame edge uses the last one), so a consumer pixel only interpolates along y
+            __syncwarp();
+#pragma unroll 4
+            for (int j = lane; j < wy * kTW; j += 32) {
+                const int jy = j / kTW, col = j - jy * kTW;
+                const int c = min(x0 + col, a.W - 1);
+                const float gxf = fminf((float)c * a.inv_s, (float)(a.nx - 1));
+                const int ix = cell_of(gxf, a.nx);
+                const float2 *q = sm.win[st] + jy * kWinX + (ix - cx0);
+                const float2 p0 = q[0], p1 = q[1];
+                sm.xint[st][jy][col] = __ffma2_rn(f2(gxf - (float)ix), f2sub(p1, p0), p0);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -228,6 +288,7 @@ __device__ __forceinline__ float sample(const WarpArgs &a, const WarpSmem &sm, i
 // Per-thread pixel columns: c0 = x0 + lane and c1 = c0 + 32, processed as one float2 pair.
 struct Cols {
     int c0, c1;                // clamped to the last column; in0/in1 say which are real
+    int col0, col1;            // the same columns relative to the tile's first one
     bool in0, in1;
     float2 xc;                 // rigid: columns relative to the rotation centre
     int ix0, ix1;              // nonrigid: control cell of each column
@@ -249,14 +310,24 @@ __device__ __forceinline__ void displacement(const WarpArgs &a, const WarpSmem &
         const int iy = cell_of(gyf, a.ny);
         const float2 wy = f2(gyf - (float)iy);
         float2 u[2];
+        if (WINDOW) {
+            // x-interpolated control rows iy, iy + 1 at this lane's two columns
+            const float2 *t = sm.xint[st][iy - sm.wo[st].y], *b = sm.xint[st][iy - sm.wo[st].y + 1];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = h ? cl.col1 : cl.col0;
+                const float2 tv = t[col], bv = b[col];
+                u[h] = __ffma2_rn(wy, f2sub(bv, tv), tv);
+            }
+            vx = make_float2(u[0].x, u[1].x);
+            vy = make_float2(u[0].y, u[1].y);
+            return;
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int ix = h ? cl.ix1 : cl.ix0;
             float2 p00, p01, p10, p11;
-            if (WINDOW) {
-                const float2 *w = sm.win[st] + (iy - sm.wo[st].y) * kWinX + (ix - sm.wo[st].x);
-                p00 = w[0]; p01 = w[1]; p10 = w[kWinX]; p11 = w[kWinX + 1];
-            } else if (k > 0) {
+            if (k > 0) {
                 const float2 *g = a.grids + (size_t)(k - 1) * a.nx * a.ny + (size_t)iy * a.nx + ix;
                 p00 = g[0]; p01 = g[1]; p10 = g[a.nx]; p11 = g[a.nx + 1];
             } else {
@@ -376,8 +447,12 @@ __global__ void __launch_bounds__(kWThreads, 3) warp_kernel(const WarpArgs a, co
     if (warp == kConsumers) {
         // ---- producer: parameters and the TMA load of each frame, up to kStages ahead
         int issued = 0;
+        const Window win = window_of(a, x0, y0);
+        Prefetch cur = fetch(a, win, kb);
         for (int i = 0; i < n; ++i) {
             const int st = i % kStages;
+            Prefetch nxt = cur;
+            if (i + 1 < n) nxt = fetch(a, win, kb + i + 1);   // in flight while this frame is prepared
             if (i >= kStages) {
                 // every lane acquires: lane 0 reuses the box, all lanes rewrite the window
                 const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&sm.empty[st]),
@@ -388,8 +463,9 @@ __global__ void __launch_bounds__(kWThreads, 3) warp_kernel(const WarpArgs a, co
                 }
             }
             if (*abort) break;
-            prepare(a, &tmap, sm, kb + i, st, x0, y0);
+            prepare(a, &tmap, sm, kb + i, st, x0, y0, win, cur);
             issued = i + 1;
+            cur = nxt;
         }
         __syncthreads();
         if (*abort && lane == 0 && a.use_tma) {
@@ -406,6 +482,8 @@ __global__ void __launch_bounds__(kWThreads, 3) warp_kernel(const WarpArgs a, co
     cl.in1 = x0 + lane + 32 < a.W;
     cl.c0 = min(x0 + lane, a.W - 1);
     cl.c1 = min(x0 + lane + 32, a.W - 1);
+    cl.col0 = cl.c0 - x0;
+    cl.col1 = cl.c1 - x0;
     cl.xc = make_float2((float)cl.c0 - 0.5f * (float)(a.W - 1), (float)cl.c1 - 0.5f * (float)(a.W - 1));
     if (MODE == REG_NONRIGID) {
         const float g0 = fminf((float)cl.c0 * a.inv_s, (float)(a.nx - 1));
