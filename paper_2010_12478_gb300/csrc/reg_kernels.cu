@@ -837,7 +837,7 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Nc = G.nx * G.ny, ncx = G.nx - 1, ncy = G.ny - 1;
     const int sl = G.s >> GL.l;
-    const int lg = 31 - __clz(sl);   // sl is a power of two (the spacing is a multiple of 2^l)
+    const int lg = 31 - __clz(sl);   // log2 of sl when sl is a power of two (the fast path below)
     float *gpf = (float *)gp;   // band-local: control row cr0 + i at gp[i nx .. (i + 1) nx)
     for (int j = tid; j < (cr1 - cr0 + 1) * G.nx; j += kThreads) gp[j] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -857,8 +857,8 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
             const float2 dtop = make_float2(c01.x - c00.x, c01.y - c00.y);
             const float2 dbot = make_float2(c11.x - c10.x, c11.y - c10.y);
             float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (w == sl && sl <= 32) {
-                // Full-width cell whose width divides the warp: every lane keeps one column
+            if (w == sl && sl <= 32 && (sl & (sl - 1)) == 0) {
+                // Full-width cell whose width (a power of two) divides the warp: every lane keeps one column
                 // (x = x0 + lane mod sl) and walks rows 32/sl apart, so the weight along x and
                 // the x-interpolated control values are fixed per lane; the y weights are summed
                 // and the x weights applied once at the end (the bilinear weight factorises).
