@@ -252,6 +252,10 @@ extern "C" int reg_scan_dag(int schedule, int n, int32_t *left, int32_t *right, 
 }
 
 // ------------------------------------------------------------------ context
+// Streams of the one-launch-per-operator executor: enough concurrent operators to fill every
+// CTA slot of the GPU (152 SMs x 3-4 CTAs / 16 CTAs per operator = 28-38 operators).
+constexpr int kPoolStreams = 32;
+
 struct reg_ctx {
     reg_config_t cfg;
     int device = 0;
@@ -263,8 +267,8 @@ struct reg_ctx {
     DevBuf means, level_tab, ops, stats, node_theta, node_grid, status, node_ids;
     DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr;
     DevBuf tmp;
-    cudaStream_t pool[16] = {};
-    cudaEvent_t ev_pool_done[16] = {};
+    cudaStream_t pool[kPoolStreams] = {};
+    cudaEvent_t ev_pool_done[kPoolStreams] = {};
     std::vector<cudaEvent_t> op_events;
     bool pool_ready = false;
     // REG_EXEC_GRAPH: the captured plain-path launches and the plan they were captured for
@@ -359,7 +363,7 @@ extern "C" void reg_ctx_destroy(reg_ctx_t *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->pool_ready) {
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < kPoolStreams; ++i) {
             cudaStreamDestroy(ctx->pool[i]);
             cudaEventDestroy(ctx->ev_pool_done[i]);
         }
@@ -603,7 +607,7 @@ int plan_scan(int N, const Dag &d, ScanPlan &p)
 int ensure_pool(reg_ctx *ctx)
 {
     if (ctx->pool_ready) return REG_OK;
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < kPoolStreams; ++i) {
         CU(cudaStreamCreateWithFlags(&ctx->pool[i], cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&ctx->ev_pool_done[i], cudaEventDisableTiming));
     }
@@ -673,7 +677,7 @@ uint64_t fnv1a(const void *data, size_t n, uint64_t h)
     return h;
 }
 
-// One launch per operator on the 16-stream pool, in plan order; an operator waits for the
+// One launch per operator on the stream pool, in plan order; an operator waits for the
 // events of the two operators that produce its inputs.  The pool forks from and joins back
 // into s, so the whole sequence can also be captured from s as one graph.
 int launch_plain(reg_ctx *ctx, const ScanPlan &plan, const Params &p, int C, cudaStream_t s)
@@ -683,9 +687,9 @@ int launch_plain(reg_ctx *ctx, const ScanPlan &plan, const Params &p, int C, cud
     std::vector<int> node_op(p.n_nodes, -1);
     for (int e = 0; e < n_ops; ++e) node_op[plan.ops[e].out] = e;
     CU(cudaEventRecord(ctx->ev_pool_done[0], s));
-    for (int i = 0; i < 16; ++i) CU(cudaStreamWaitEvent(ctx->pool[i], ctx->ev_pool_done[0], 0));
+    for (int i = 0; i < kPoolStreams; ++i) CU(cudaStreamWaitEvent(ctx->pool[i], ctx->ev_pool_done[0], 0));
     for (int e = 0; e < n_ops; ++e) {
-        cudaStream_t ls = ctx->pool[e % 16];
+        cudaStream_t ls = ctx->pool[e % kPoolStreams];
         const OpDesc &op = plan.ops[e];
         if (op.left >= 0) {
             CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.left]], 0));
@@ -696,7 +700,7 @@ int launch_plain(reg_ctx *ctx, const ScanPlan &plan, const Params &p, int C, cud
         CU(launch_ops(q, storage, C, 1, ls));
         CU(cudaEventRecord(ctx->op_events[e], ls));
     }
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < kPoolStreams; ++i) {
         CU(cudaEventRecord(ctx->ev_pool_done[i], ctx->pool[i]));
         CU(cudaStreamWaitEvent(s, ctx->ev_pool_done[i], 0));
     }
