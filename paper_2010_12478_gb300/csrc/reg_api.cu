@@ -254,7 +254,7 @@ extern "C" int reg_scan_dag(int schedule, int n, int32_t *left, int32_t *right, 
 // ------------------------------------------------------------------ context
 // Streams of the one-launch-per-operator executor: enough concurrent operators to fill every
 // CTA slot of the GPU (152 SMs x 3-4 CTAs / 16 CTAs per operator = 28-38 operators).
-constexpr int kPoolStreams = 32;
+constexpr int kPoolStreams = 64;
 
 struct reg_ctx {
     reg_config_t cfg;
