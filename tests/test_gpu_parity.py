@@ -276,6 +276,30 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(B.RegError) as e:
         ctx.scan(F)
     assert e.value.code == B.REG_EINVAL
+    # a series of one frame has nothing to register
+    with pytest.raises(B.RegError) as e:
+        ctx.scan(torch.zeros((1, 32, 32), device="cuda"))
+    assert e.value.code == B.REG_EINVAL
+    with pytest.raises(B.RegError) as e:
+        ctx.scan_batch(torch.zeros((2, 1, 32, 32), device="cuda"))
+    assert e.value.code == B.REG_EINVAL
+
+
+@pytest.mark.parametrize("H,W", [(2048, 2048), (1024, 4096)])
+def test_large_frames_energy_and_gradient_match_oracle(H, W):
+    # the largest control grids (65 points per axis; spacing 32 and 64, the latter with cells
+    # wider than a warp) at one evaluation: energy and control-point gradient
+    R, T = synth.translated_pair(H, W, (1.3, -0.6), noise_snr=10.0, seed=9)
+    g = O.grid_for(W, H)
+    assert (g.nx <= 65 and g.ny <= 65) and B.grid_dims(W, H, 0, 1) == (g.nx, g.ny, g.s)
+    c = np.random.default_rng(6).uniform(-0.5, 0.5, size=(2, g.ny, g.nx)) + np.array([1.2, -0.5])[:, None, None]
+    ctx = ctx_of(mode="nonrigid", lam=2.0)
+    cd = torch.from_numpy(np.ascontiguousarray(c.transpose(1, 2, 0)).astype(np.float32)).cuda()
+    gd = torch.zeros((g.ny, g.nx, 2), device="cuda")
+    Eg = ctx.energy_grid(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda(), cd, gd)
+    Eo, go = O.grid_energy(R, T, 0, g, cd.cpu().numpy().transpose(2, 0, 1).astype(np.float64), 2.0)
+    assert rel(Eg, Eo) <= 1e-6
+    np.testing.assert_allclose(gd.cpu().numpy().transpose(2, 0, 1), go, atol=2e-4 * np.abs(go).max())
 
 
 # ------------------------------------------------------------------ full size (256 x 512^2), sampled
