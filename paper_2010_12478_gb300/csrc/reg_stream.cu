@@ -90,8 +90,10 @@ struct Service {
     std::thread th;
     bool stop = false;
     std::vector<reg_stream *> streams;
+    // lanes [0, kLanes/2): B operators at the highest stream priority (each stream's chain
+    // phi_{0,i-1} -> phi_{0,i} is its critical path); [kLanes/2, kLanes): A operators at the lowest
     cudaStream_t lanes[kLanes] = {};
-    int next_lane = 0;
+    int next_lane_a = 0, next_lane_b = 0;
     int device = 0;
     size_t used_bytes = 0;
 };
@@ -136,8 +138,14 @@ Params stream_params(reg_stream *s)
 // Launch one operator (op index e) on a service lane; results to pinned memory; event after.
 int launch_op(Service *sv, reg_stream *s, int e, const OpDesc &op, cudaEvent_t ev)
 {
-    cudaStream_t ls = sv->lanes[sv->next_lane];
-    sv->next_lane = (sv->next_lane + 1) % kLanes;
+    cudaStream_t ls;
+    if (op.left >= 0) {
+        ls = sv->lanes[sv->next_lane_b];
+        sv->next_lane_b = (sv->next_lane_b + 1) % (kLanes / 2);
+    } else {
+        ls = sv->lanes[kLanes / 2 + sv->next_lane_a];
+        sv->next_lane_a = (sv->next_lane_a + 1) % (kLanes / 2);
+    }
     s->h_ops[e] = op;
     if (cudaMemcpyAsync(s->ops + e, s->h_ops + e, sizeof(OpDesc), cudaMemcpyHostToDevice, ls) != cudaSuccess)
         return REG_ECUDA;
@@ -251,7 +259,13 @@ Service *service_of(reg_ctx_t *ctx, bool create)
     Service *sv = new Service();
     sv->device = host_device(ctx);
     cudaSetDevice(sv->device);
-    for (int i = 0; i < kLanes; ++i) cudaStreamCreateWithFlags(&sv->lanes[i], cudaStreamNonBlocking);
+    int prio_low = 0, prio_high = 0;   // numerically smaller is higher
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
+    for (int i = 0; i < kLanes; ++i)
+        cudaStreamCreateWithPriority(&sv->lanes[i], cudaStreamNonBlocking, i < kLanes / 2 ? prio_high : prio_low);
     sv->th = std::thread(service_loop, sv);
     g_services.push_back({ctx, sv});
     return sv;
