@@ -1217,9 +1217,11 @@ __device__ void run_op(const Params &p, int op_index, Smem &sm, float2 *gbuf, co
     else run_nonrigid<S>(p, op, op_index, sm, gbuf, cl);
 }
 
-// Batched launch: cluster q of the grid runs operator op_base + q.
-template <int MODE, typename S>
-__global__ void __launch_bounds__(kThreads, MODE == REG_RIGID ? 4 : 3) op_kernel(Params p)
+// Batched launch: cluster q of the grid runs operator op_base + q.  MINB: CTAs per SM the
+// register budget is sized for (the nonrigid kernels come in a 3-CTA form without spills and a
+// 4-CTA form with a few spilled registers, faster once the clusters are large).
+template <int MODE, typename S, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) op_kernel(Params p)
 {
     __shared__ Smem sm;
     extern __shared__ float2 gbuf[];   // nonrigid: control grid c, d, ct, gp
@@ -1231,8 +1233,8 @@ __global__ void __launch_bounds__(kThreads, MODE == REG_RIGID ? 4 : 3) op_kernel
 
 // Persistent launch: each cluster claims ready operators from the device queue
 // until all n_ops have been claimed.  Every wait is bounded by queue.timeout_ns.
-template <int MODE, typename S>
-__global__ void __launch_bounds__(kThreads, MODE == REG_RIGID ? 4 : 3) persistent_kernel(Params p)
+template <int MODE, typename S, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
 {
     __shared__ Smem sm;
     extern __shared__ float2 gbuf[];
@@ -1528,18 +1530,25 @@ static cudaError_t launch_cluster(K kernel, int blocks, int cluster, cudaStream_
 
 cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_ops, cudaStream_t s)
 {
+    const bool minb4 = cluster >= 16;   // nonrigid: the 4-CTA form for the largest clusters
     const int blocks = n_launch_ops * cluster;
     if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
-        case REG_F32: return launch_cluster(op_kernel<REG_RIGID, float>, blocks, cluster, s, p);
-        case REG_BF16: return launch_cluster(op_kernel<REG_RIGID, __nv_bfloat16>, blocks, cluster, s, p);
-        case REG_F16: return launch_cluster(op_kernel<REG_RIGID, __half>, blocks, cluster, s, p);
+        case REG_F32: return launch_cluster(op_kernel<REG_RIGID, float, 4>, blocks, cluster, s, p);
+        case REG_BF16: return launch_cluster(op_kernel<REG_RIGID, __nv_bfloat16, 4>, blocks, cluster, s, p);
+        case REG_F16: return launch_cluster(op_kernel<REG_RIGID, __half, 4>, blocks, cluster, s, p);
         }
     } else {
         switch (storage) {
-        case REG_F32: return launch_cluster(op_kernel<REG_NONRIGID, float>, blocks, cluster, s, p);
-        case REG_BF16: return launch_cluster(op_kernel<REG_NONRIGID, __nv_bfloat16>, blocks, cluster, s, p);
-        case REG_F16: return launch_cluster(op_kernel<REG_NONRIGID, __half>, blocks, cluster, s, p);
+        case REG_F32: return launch_cluster(minb4 ? op_kernel<REG_NONRIGID, float, 4>
+                                                : op_kernel<REG_NONRIGID, float, 3>,
+                                          blocks, cluster, s, p);
+        case REG_BF16: return launch_cluster(minb4 ? op_kernel<REG_NONRIGID, __nv_bfloat16, 4>
+                                                : op_kernel<REG_NONRIGID, __nv_bfloat16, 3>,
+                                          blocks, cluster, s, p);
+        case REG_F16: return launch_cluster(minb4 ? op_kernel<REG_NONRIGID, __half, 4>
+                                                : op_kernel<REG_NONRIGID, __half, 3>,
+                                          blocks, cluster, s, p);
         }
     }
     return cudaErrorInvalidValue;
@@ -1547,18 +1556,25 @@ cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_o
 
 cudaError_t launch_persistent(const Params &p, int storage, int cluster, int workers, cudaStream_t s)
 {
+    const bool minb4 = cluster >= 16;   // nonrigid: the 4-CTA form for the largest clusters
     const int blocks = workers * cluster;
     if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
-        case REG_F32: return launch_cluster(persistent_kernel<REG_RIGID, float>, blocks, cluster, s, p);
-        case REG_BF16: return launch_cluster(persistent_kernel<REG_RIGID, __nv_bfloat16>, blocks, cluster, s, p);
-        case REG_F16: return launch_cluster(persistent_kernel<REG_RIGID, __half>, blocks, cluster, s, p);
+        case REG_F32: return launch_cluster(persistent_kernel<REG_RIGID, float, 4>, blocks, cluster, s, p);
+        case REG_BF16: return launch_cluster(persistent_kernel<REG_RIGID, __nv_bfloat16, 4>, blocks, cluster, s, p);
+        case REG_F16: return launch_cluster(persistent_kernel<REG_RIGID, __half, 4>, blocks, cluster, s, p);
         }
     } else {
         switch (storage) {
-        case REG_F32: return launch_cluster(persistent_kernel<REG_NONRIGID, float>, blocks, cluster, s, p);
-        case REG_BF16: return launch_cluster(persistent_kernel<REG_NONRIGID, __nv_bfloat16>, blocks, cluster, s, p);
-        case REG_F16: return launch_cluster(persistent_kernel<REG_NONRIGID, __half>, blocks, cluster, s, p);
+        case REG_F32: return launch_cluster(minb4 ? persistent_kernel<REG_NONRIGID, float, 4>
+                                                : persistent_kernel<REG_NONRIGID, float, 3>,
+                                          blocks, cluster, s, p);
+        case REG_BF16: return launch_cluster(minb4 ? persistent_kernel<REG_NONRIGID, __nv_bfloat16, 4>
+                                                : persistent_kernel<REG_NONRIGID, __nv_bfloat16, 3>,
+                                          blocks, cluster, s, p);
+        case REG_F16: return launch_cluster(minb4 ? persistent_kernel<REG_NONRIGID, __half, 4>
+                                                : persistent_kernel<REG_NONRIGID, __half, 3>,
+                                          blocks, cluster, s, p);
         }
     }
     return cudaErrorInvalidValue;
@@ -1590,18 +1606,25 @@ static int resident_clusters(K kernel, int cluster, const Params &p)
 
 int persistent_resident_clusters(const Params &p, int storage, int cluster)
 {
+    const bool minb4 = cluster >= 16;   // nonrigid: the 4-CTA form for the largest clusters
     int n = -1;
     if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
-        case REG_F32: n = resident_clusters(persistent_kernel<REG_RIGID, float>, cluster, p); break;
-        case REG_BF16: n = resident_clusters(persistent_kernel<REG_RIGID, __nv_bfloat16>, cluster, p); break;
-        case REG_F16: n = resident_clusters(persistent_kernel<REG_RIGID, __half>, cluster, p); break;
+        case REG_F32: n = resident_clusters(persistent_kernel<REG_RIGID, float, 4>, cluster, p); break;
+        case REG_BF16: n = resident_clusters(persistent_kernel<REG_RIGID, __nv_bfloat16, 4>, cluster, p); break;
+        case REG_F16: n = resident_clusters(persistent_kernel<REG_RIGID, __half, 4>, cluster, p); break;
         }
     } else {
         switch (storage) {
-        case REG_F32: n = resident_clusters(persistent_kernel<REG_NONRIGID, float>, cluster, p); break;
-        case REG_BF16: n = resident_clusters(persistent_kernel<REG_NONRIGID, __nv_bfloat16>, cluster, p); break;
-        case REG_F16: n = resident_clusters(persistent_kernel<REG_NONRIGID, __half>, cluster, p); break;
+        case REG_F32: n = resident_clusters(minb4 ? persistent_kernel<REG_NONRIGID, float, 4>
+                                                : persistent_kernel<REG_NONRIGID, float, 3>,
+                                          cluster, p); break;
+        case REG_BF16: n = resident_clusters(minb4 ? persistent_kernel<REG_NONRIGID, __nv_bfloat16, 4>
+                                                : persistent_kernel<REG_NONRIGID, __nv_bfloat16, 3>,
+                                          cluster, p); break;
+        case REG_F16: n = resident_clusters(minb4 ? persistent_kernel<REG_NONRIGID, __half, 4>
+                                                : persistent_kernel<REG_NONRIGID, __half, 3>,
+                                          cluster, p); break;
         }
     }
     if (n < 0) cudaGetLastError();
