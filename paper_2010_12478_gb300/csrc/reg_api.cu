@@ -712,7 +712,6 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
 {
     const int n_ops = (int)plan.ops.size();
     const int storage = ctx->cfg.storage;
-    const bool nonrigid = ctx->cfg.mode == REG_NONRIGID;
     const int n_depth = (int)plan.depth_start.size() - 1;
     if (exec == REG_EXEC_LEVEL) {
         for (int dpt = 0; dpt < n_depth; ++dpt) {

@@ -310,7 +310,7 @@ __device__ __forceinline__ void displacement(const WarpArgs &a, const WarpSmem &
         const int iy = cell_of(gyf, a.ny);
         const float2 wy = f2(gyf - (float)iy);
         float2 u[2];
-        if (WINDOW) {
+        if constexpr (WINDOW) {
             // x-interpolated control rows iy, iy + 1 at this lane's two columns
             const float2 *t = sm.xint[st][iy - sm.wo[st].y], *b = sm.xint[st][iy - sm.wo[st].y + 1];
 #pragma unroll
@@ -319,23 +319,21 @@ __device__ __forceinline__ void displacement(const WarpArgs &a, const WarpSmem &
                 const float2 tv = t[col], bv = b[col];
                 u[h] = __ffma2_rn(wy, f2sub(bv, tv), tv);
             }
-            vx = make_float2(u[0].x, u[1].x);
-            vy = make_float2(u[0].y, u[1].y);
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int ix = h ? cl.ix1 : cl.ix0;
-            float2 p00, p01, p10, p11;
-            if (k > 0) {
-                const float2 *g = a.grids + (size_t)(k - 1) * a.nx * a.ny + (size_t)iy * a.nx + ix;
-                p00 = g[0]; p01 = g[1]; p10 = g[a.nx]; p11 = g[a.nx + 1];
-            } else {
-                p00 = p01 = p10 = p11 = make_float2(0.f, 0.f);
+            for (int h = 0; h < 2; ++h) {
+                const int ix = h ? cl.ix1 : cl.ix0;
+                float2 p00, p01, p10, p11;
+                if (k > 0) {
+                    const float2 *g = a.grids + (size_t)(k - 1) * a.nx * a.ny + (size_t)iy * a.nx + ix;
+                    p00 = g[0]; p01 = g[1]; p10 = g[a.nx]; p11 = g[a.nx + 1];
+                } else {
+                    p00 = p01 = p10 = p11 = make_float2(0.f, 0.f);
+                }
+                const float2 wx = f2(h ? cl.wx.y : cl.wx.x);
+                const float2 top = __ffma2_rn(wx, f2sub(p01, p00), p00), bot = __ffma2_rn(wx, f2sub(p11, p10), p10);
+                u[h] = __ffma2_rn(wy, f2sub(bot, top), top);
             }
-            const float2 wx = f2(h ? cl.wx.y : cl.wx.x);
-            const float2 top = __ffma2_rn(wx, f2sub(p01, p00), p00), bot = __ffma2_rn(wx, f2sub(p11, p10), p10);
-            u[h] = __ffma2_rn(wy, f2sub(bot, top), top);
         }
         vx = make_float2(u[0].x, u[1].x);
         vy = make_float2(u[0].y, u[1].y);
