@@ -92,6 +92,8 @@ def lib():
             L.or_grid_dense.argtypes = [gp, dp, dp, dp, dp]
             L.or_grid_level_dense.argtypes = [gp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
             L.or_warp_rigid.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
+            L.or_step_size.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int]
+            L.or_step_size.restype = ctypes.c_double
             L.or_warp_grid.argtypes = [gp, dp, dp, dp, dp]
             _lib = L
     return _lib
@@ -485,6 +487,11 @@ def scan(frames, cfg: Config, dag: Optional[Dag] = None, leaves: Optional[List[E
     for (l, r) in dag.ops:
         nodes.append(op_B(nodes[l], nodes[r], pyrs, cfg))
     return [nodes[o] for o in dag.out]
+
+
+def step_size(E: float, slope: float, tau: float, Et: float, accepted: bool) -> float:
+    """The line search's next step after a trial at tau with energy Et (see oracle.c)."""
+    return float(lib().or_step_size(E, slope, tau, Et, 1 if accepted else 0))
 
 
 # --------------------------------------------------------------------------

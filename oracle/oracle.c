@@ -98,6 +98,12 @@ static double or_next_tau(double E, double slope, double tau, double Et, int acc
     return accepted ? fmin(fmax(tq, 0.5 * tau), 4.0 * tau) : fmin(fmax(tq, 0.1 * tau), 0.5 * tau);
 }
 
+/* The step rule by itself (for its pins). */
+double or_step_size(double E, double slope, double tau, double Et, int accepted)
+{
+    return or_next_tau(E, slope, tau, Et, accepted);
+}
+
 void or_sample(const double *T, int W, int H, double px, double py, double out[3])
 {
     double qx = clampd(px, 0.0, (double)(W - 1));

@@ -1,0 +1,41 @@
+"""The benchmark's bookkeeping on CPU: algorithmic bytes of the operator kernel (every energy
+evaluation reads the reference and template level once: 2 s P_l bytes), and the hash gate that
+keeps a stale ncu traffic figure out of the JSON line."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_algorithmic_bytes_counts_two_levels_per_evaluation():
+    stats = [{"evals": [10, 4]}, {"evals": [3, 0]}]
+    # 512^2 at level 0 and 256^2 at level 1, fp32 (4 bytes)
+    want = (10 + 3) * 2 * 4 * 512 * 512 + 4 * 2 * 4 * 256 * 256
+    assert bench.algorithmic_bytes(stats, 512, 512, 2, 4, "rigid") == want
+    # odd sizes round the coarser level up, 2-byte storage halves the bytes
+    assert bench.algorithmic_bytes([{"evals": [1, 1]}], 5, 7, 2, 2, "rigid") == 2 * 2 * 35 + 2 * 2 * 12
+
+
+def test_profile_traffic_is_used_only_for_the_profiled_source(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    src = tmp_path / "paper_2010_12478_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "k.cu").write_text("kernel v1")
+    (tmp_path / "profiles").mkdir()
+    h = bench.kernel_hash("k.cu")
+    (tmp_path / "profiles" / "p.md").write_text(f"kernel source sha256: {h}\ndram bytes per call (scaled): 1.5e8\n")
+    assert bench.profile_traffic("p", "k.cu", "dram bytes per call (scaled)") == pytest.approx(1.5e8)
+    (src / "k.cu").write_text("kernel v2")   # the kernel changed since the capture
+    assert bench.profile_traffic("p", "k.cu", "dram bytes per call (scaled)") is None
+    assert bench.profile_traffic("missing", "k.cu", "dram bytes per call (scaled)") is None
+
+
+def test_the_committed_profiles_name_their_command_and_source():
+    for name in os.listdir(os.path.join(ROOT, "profiles")):
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        assert "kernel source sha256:" in text and "ncu " in text and "--clock-control none" in text, name

@@ -372,3 +372,25 @@ def test_parallel_scan_equals_sequential_recursion(dag):
     for i, (s, p) in enumerate(zip(seq, par)):
         assert (s.i, s.k) == (p.i, p.k) == (0, i + 1)
         assert O.max_px_error(s.phi, p.phi, 128, 128, "rigid") <= 0.02
+
+
+# ------------------------------------------------------------------ the line search's step rule
+@pytest.mark.parametrize("E0,s,c", [(0.3, -2.0, 5.0), (1.0, -0.01, 0.4), (0.05, -1e-6, 3e-5)])
+def test_step_rule_lands_on_the_minimiser_of_a_parabola(E0, s, c):
+    # E(t) = E0 + s t + c t^2 has its minimum at t* = -s / (2 c); a trial at tau gives the
+    # parabola exactly, so the rule returns t* clamped to its safeguard interval
+    tstar = -s / (2 * c)
+    for tau in (0.3 * tstar, 0.9 * tstar, 1.7 * tstar, 3.0 * tstar, 12.0 * tstar):
+        Et = E0 + s * tau + c * tau * tau
+        accepted = Et <= E0 + 0.25 * tau * s
+        got = O.step_size(E0, s, tau, Et, accepted)
+        lo, hi = (0.5 * tau, 4.0 * tau) if accepted else (0.1 * tau, 0.5 * tau)
+        # Et - E0 - s tau recovers c tau^2 up to the rounding of the energies (a few ulp of E0)
+        rel = max(1e-12, 8e-16 * E0 / (c * tau * tau))
+        assert got == pytest.approx(min(max(tstar, lo), hi), rel=rel)
+
+
+def test_step_rule_without_curvature_doubles_or_halves():
+    # a trial at or below the tangent line (no positive curvature): plain doubling / halving
+    assert O.step_size(1.0, -1.0, 0.5, 0.4, True) == 1.0
+    assert O.step_size(1.0, -1.0, 0.5, 0.5, False) == 0.25
