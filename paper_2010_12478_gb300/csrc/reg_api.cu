@@ -453,7 +453,10 @@ int grid_dims(int W, int H, int grid, int levels, GridDims &g)
     if (g.nx < 2 || g.ny < 2) return fail(REG_EINVAL, "control grid needs >= 2x2 points");
     if ((sp >> (levels - 1)) < 1 || (sp & ((1 << (levels - 1)) - 1)) != 0)
         return fail(REG_EINVAL, "grid spacing %d must be a multiple of 2^(levels-1)", sp);
-    if ((size_t)g.nx * g.ny * 4 * 8 > 200 * 1024)
+    // dynamic shared memory of a one-CTA operator (the largest band): c, d, ct and the band as
+    // float2, then one float4 control row per warp; the static part stays under 8 KB
+    const size_t nc = (size_t)g.nx * g.ny;
+    if (8 * (4 * nc + 1) + 16 * (size_t)(kThreads / 32) * (g.nx - 1) > 216 * 1024)
         return fail(REG_EINVAL, "control grid %dx%d does not fit shared memory; use a larger spacing", g.nx, g.ny);
     return REG_OK;
 }

@@ -705,6 +705,15 @@ __host__ __device__ __forceinline__ int grid_band_elems(int gnx, int gny, int C)
     return ((gny - 1 + C - 1) / C + 1) * gnx;
 }
 
+// Dynamic shared memory of the nonrigid kernels, in float2 units: c, d, ct (whole grid each),
+// the band of partial gradients, then (16-byte aligned) one row of gnx - 1 float4 per warp:
+// the control values of the warp's pixel row interpolated along y, (u_j, u_{j+1} - u_j).
+__host__ __device__ __forceinline__ int grid_crow_offset(int gnx, int gny, int C)
+{
+    const int o = 3 * gnx * gny + grid_band_elems(gnx, gny, C);
+    return o + (o & 1);
+}
+
 __device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int rank, int C, int &cr0, int &cr1,
                                           int &r0, int &r1)
 {
@@ -721,9 +730,9 @@ __device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int r
 // Energy moments of the field ct: slots 0 St, 1 Stt, 2 Srt, with RSTAT (first pass of a level)
 // 3 Sr, 4 Srr; slot 5 = sum over control edges |dct|^2 (rank 0 only, so the cluster sum counts
 // it once).  Each warp first interpolates the control values of its row along y into crow
-// (nx values), so a pixel only interpolates along x.
+// (u_j and u_{j+1} - u_j for the nx - 1 cells), so a pixel only interpolates along x.
 template <typename S, bool RSTAT>
-__device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *ct, float2 *crow_all,
+__device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *ct, float4 *crow_all,
                                  int r0, int r1, Smem &sm, int &buf, const cg::cluster_group &cl)
 {
     const S *R = (const S *)L.R, *T = (const S *)L.T;
@@ -733,48 +742,72 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
 #pragma unroll
     for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
     const int lane = threadIdx.x & 31;
-    float2 *crow = crow_all + (threadIdx.x >> 5) * G.nx;
+    float4 *crow = crow_all + (threadIdx.x >> 5) * (G.nx - 1);
     const S *Rrow = R;
-    for_rows<4>(
-        L.W, r0, r1,
-        [&](int r) {
-            Rrow = R + (size_t)r * L.Rp;
-            const float gyf = fminf(fmaf(GL.pl, (float)r, GL.off) * GL.scale_inv, (float)(G.ny - 1));
-            const int iy = min((int)gyf, G.ny - 2);
-            const float wy = gyf - (float)iy, hy = 1.f - wy;
-            __syncwarp();
-            for (int j = lane; j < G.nx; j += 32) {
-                const float2 p0 = ct[iy * G.nx + j], p1 = ct[(iy + 1) * G.nx + j];
-                crow[j] = make_float2(fmaf(wy, p1.x, hy * p0.x), fmaf(wy, p1.y, hy * p0.y));
-            }
-            __syncwarp();
-        },
-        [&](int r, int c) {
-            const float gxf = fminf(fmaf(GL.pl, (float)c, GL.off) * GL.scale_inv, (float)(G.nx - 1));
-            const int ix = min((int)gxf, G.nx - 2);
-            const float wx = gxf - (float)ix;
-            const float2 p0 = crow[ix], p1 = crow[ix + 1];
-            const float ux = fmaf(wx, p1.x - p0.x, p0.x), uy = fmaf(wx, p1.y - p0.y, p0.y);
-            float dtx, dty;
-            const float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c, r, ux, uy, dtx, dty);
-            const float rv = ldS<S>(Rrow + c) - L.cR;
-            const float tv = tw - L.cR;
-            a[0] += tv;
-            acc_prod(a[1], e1, tv, tv);
-            acc_prod(a[2], e2, rv, tv);
-            if constexpr (RSTAT) {
-                a[3] += rv;
-                acc_prod(a[4], e4, rv, rv);
-            }
-        },
-        [&]() {
+    auto row = [&](int r) {
+        Rrow = R + (size_t)r * L.Rp;
+        const float gyf = fminf(fmaf(GL.pl, (float)r, GL.off) * GL.scale_inv, (float)(G.ny - 1));
+        const int iy = min((int)gyf, G.ny - 2);
+        const float wy = gyf - (float)iy, hy = 1.f - wy;
+        __syncwarp();
+        for (int j = lane; j < G.nx - 1; j += 32) {
+            const float2 a0 = ct[iy * G.nx + j], a1 = ct[(iy + 1) * G.nx + j];
+            const float2 b0 = ct[iy * G.nx + j + 1], b1 = ct[(iy + 1) * G.nx + j + 1];
+            const float ux0 = fmaf(wy, a1.x, hy * a0.x), uy0 = fmaf(wy, a1.y, hy * a0.y);
+            const float ux1 = fmaf(wy, b1.x, hy * b0.x), uy1 = fmaf(wy, b1.y, hy * b0.y);
+            crow[j] = make_float4(ux0, uy0, ux1 - ux0, uy1 - uy0);
+        }
+        __syncwarp();
+    };
+    auto pixel = [&](int r, int c, float ux, float uy) {
+        float dtx, dty;
+        const float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c, r, ux, uy, dtx, dty);
+        const float rv = ldS<S>(Rrow + c) - L.cR;
+        const float tv = tw - L.cR;
+        a[0] += tv;
+        acc_prod(a[1], e1, tv, tv);
+        acc_prod(a[2], e2, rv, tv);
+        if constexpr (RSTAT) {
+            a[3] += rv;
+            acc_prod(a[4], e4, rv, rv);
+        }
+    };
+    auto flush_fast = [&]() {
 #pragma unroll
-            for (int m = 0; m < (RSTAT ? 5 : 3); ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
-            lo[1] += e1; lo[2] += e2;
-            e1 = 0.f; e2 = 0.f;
-            if constexpr (RSTAT) { lo[4] += e4; e4 = 0.f; }
-        },
-        []() {});
+        for (int m = 0; m < (RSTAT ? 5 : 3); ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
+        lo[1] += e1; lo[2] += e2;
+        e1 = 0.f; e2 = 0.f;
+        if constexpr (RSTAT) { lo[4] += e4; e4 = 0.f; }
+    };
+    // A lane's columns are 32 apart.  When the cell width sl at this level is a power of two
+    // dividing 32, the spacing a power of two and no column reaches the grid's last line, every
+    // column of a lane has the same offset in its cell: the weight along x is fixed per lane and
+    // the cell index is a shift.  Both are exact, so the values equal the general form's.
+    const int sl = G.s >> GL.l;
+    const bool fast = sl >= 1 && sl <= 32 && (sl & (sl - 1)) == 0 && (sl << GL.l) == G.s &&
+                      fmaf(GL.pl, (float)(L.W - 1), GL.off) * GL.scale_inv < (float)(G.nx - 1);
+    if (fast) {
+        const int lgl = 31 - __clz(sl);
+        const float wxl = fmaf(GL.pl, (float)(lane & (sl - 1)), GL.off) * GL.scale_inv;
+        for_rows<4>(
+            L.W, r0, r1, row,
+            [&](int r, int c) {
+                const float4 q = crow[c >> lgl];
+                pixel(r, c, fmaf(wxl, q.z, q.x), fmaf(wxl, q.w, q.y));
+            },
+            flush_fast, []() {});
+    } else {
+        for_rows<4>(
+            L.W, r0, r1, row,
+            [&](int r, int c) {
+                const float gxf = fminf(fmaf(GL.pl, (float)c, GL.off) * GL.scale_inv, (float)(G.nx - 1));
+                const int ix = min((int)gxf, G.nx - 2);
+                const float wx = gxf - (float)ix;
+                const float4 q = crow[ix];
+                pixel(r, c, fmaf(wx, q.z, q.x), fmaf(wx, q.w, q.y));
+            },
+            flush_fast, []() {});
+    }
     if (cl.block_rank() == 0) {
         const int Nc = G.nx * G.ny;
         float e = 0.f;
@@ -837,7 +870,10 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Nc = G.nx * G.ny, ncx = G.nx - 1, ncy = G.ny - 1;
     const int sl = G.s >> GL.l;
-    const int lg = 31 - __clz(sl);   // log2 of sl when sl is a power of two (the fast path below)
+    const int lg = 31 - __clz(max(sl, 1));   // log2 of sl when sl is a power of two (the fast path below)
+    // fast path: cell width a power of two dividing 32, spacing a power of two
+    const bool pow2 = sl >= 1 && sl <= 32 && (sl & (sl - 1)) == 0 && (sl << GL.l) == G.s;
+    const float dwy = (float)(32 >> lg) * GL.pl * GL.scale_inv;   // weight step between a lane's rows
     float *gpf = (float *)gp;   // band-local: control row cr0 + i at gp[i nx .. (i + 1) nx)
     for (int j = tid; j < (cr1 - cr0 + 1) * G.nx; j += kThreads) gp[j] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -857,19 +893,26 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
             const float2 dtop = make_float2(c01.x - c00.x, c01.y - c00.y);
             const float2 dbot = make_float2(c11.x - c10.x, c11.y - c10.y);
             float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (w == sl && sl <= 32 && (sl & (sl - 1)) == 0) {
+            if (w == sl && pow2) {
                 // Full-width cell whose width (a power of two) divides the warp: every lane keeps one column
                 // (x = x0 + lane mod sl) and walks rows 32/sl apart, so the weight along x and
                 // the x-interpolated control values are fixed per lane; the y weights are summed
                 // and the x weights applied once at the end (the bilinear weight factorises).
+                // With a power-of-two spacing the weights are exact dyadic values, so the weight
+                // along y advances by a constant and equals the per-row formula
+                // min(g(y), ny - 1) - cyy, g(y) = (2^l y + off) / s.
                 const int x = x0 + (lane & (sl - 1)), dy = 32 >> lg;
                 const float wx = fminf(fmaf(GL.pl, (float)x, GL.off) * GL.scale_inv, (float)(G.nx - 1)) - (float)cxx;
                 const float tx = fmaf(wx, dtop.x, c00.x), ty = fmaf(wx, dtop.y, c00.y);
                 const float bx = fmaf(wx, dbot.x, c10.x), by = fmaf(wx, dbot.y, c10.y);
                 const float ex = bx - tx, ey = by - ty;
+                const float wmax = (float)(G.ny - 1 - cyy);
+                float wyk = fmaf(GL.pl, (float)(lane >> lg), GL.off) * GL.scale_inv;
                 float st_x = 0.f, st_y = 0.f, sb_x = 0.f, sb_y = 0.f;
+#pragma unroll 4
                 for (int y = y0 + (lane >> lg); y < y1; y += dy) {
-                    const float wy = fminf(fmaf(GL.pl, (float)y, GL.off) * GL.scale_inv, (float)(G.ny - 1)) - (float)cyy;
+                    const float wy = fminf(wyk, wmax);
+                    wyk += dwy;
                     float dtx, dty;
                     const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, x, y, fmaf(wy, ex, tx), fmaf(wy, ey, ty),
                                                         dtx, dty);
@@ -1079,7 +1122,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
     const Grid G{p.gnx, p.gny, p.gs};
     const int Nc = G.nx * G.ny;
     float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
-    float2 *crow = gp + grid_band_elems(G.nx, G.ny, C);
+    float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, C));
     int buf = 0;
     // initial control values (finest px), scaled to the coarsest level
     {
@@ -1224,7 +1267,7 @@ template <int MODE, typename S, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) op_kernel(Params p)
 {
     __shared__ Smem sm;
-    extern __shared__ float2 gbuf[];   // nonrigid: control grid c, d, ct, gp
+    extern __shared__ __align__(16) float2 gbuf[];   // nonrigid: control grid c, d, ct, gp
     cg::cluster_group cl = cg::this_cluster();
     const int q = blockIdx.x / cl.num_blocks();
     run_op<MODE, S>(p, p.op_base + q, sm, gbuf, cl);
@@ -1237,7 +1280,7 @@ template <int MODE, typename S, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
 {
     __shared__ Smem sm;
-    extern __shared__ float2 gbuf[];
+    extern __shared__ __align__(16) float2 gbuf[];
     cg::cluster_group cl = cg::this_cluster();
     const bool leader = cl.block_rank() == 0 && threadIdx.x == 0;
     for (;;) {
@@ -1300,7 +1343,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
                                                           double *out, float2 *grad_c)
 {
     __shared__ Smem sm;
-    extern __shared__ float2 gbuf[];
+    extern __shared__ __align__(16) float2 gbuf[];
     cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x;
     int buf = 0;
@@ -1327,7 +1370,8 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
     } else {
         const Grid G{p.gnx, p.gny, p.gs};
         const int Nc = G.nx * G.ny;
-        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc, *crow = gp + grid_band_elems(G.nx, G.ny, 1);
+        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc;
+        float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, 1));
         for (int j = tid; j < Nc; j += kThreads) c[j] = cgrid[j];
         __syncthreads();
         GridLvl GL;
@@ -1492,13 +1536,12 @@ cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, in
     return cudaErrorInvalidValue;
 }
 
-// Dynamic shared memory of the nonrigid kernels: c, d and the trial c (whole grid), this CTA's
-// band of the partial gradient, one interpolated control row per warp.
+// Dynamic shared memory of the nonrigid kernels (layout at grid_crow_offset).
 static size_t grid_smem(const Params &p, int cluster)
 {
     if (p.cfg.mode != REG_NONRIGID) return 0;
-    return sizeof(float2) * (3 * (size_t)p.gnx * p.gny + (size_t)grid_band_elems(p.gnx, p.gny, cluster) +
-                             (size_t)kWarps * p.gnx);
+    return sizeof(float2) * (size_t)grid_crow_offset(p.gnx, p.gny, cluster) +
+           sizeof(float4) * (size_t)kWarps * (p.gnx - 1);
 }
 
 template <typename K>
