@@ -80,3 +80,31 @@ def test_library_work_counts_match_paper(lib):
     for n in (2, 16, 256, 4096):
         assert B.scan_work("brent_kung", n) == 2 * n - 2 - n.bit_length() + 1
     assert lib.reg_scan_work(99, 10) == -1
+
+
+@pytest.mark.parametrize("W,H,grid", [(512, 512, 0), (1024, 1024, 0), (2048, 1536, 0), (4096, 4096, 0),
+                                      (500, 333, 0), (144, 128, 0), (45, 67, 0), (128, 144, 4),
+                                      (512, 512, 12), (512, 512, 24)])
+def test_control_grid_matches_oracle_geometry(lib, W, H, grid):
+    # the library's control grid (host C++) equals the oracle's independently written rule:
+    # spacing 16 doubled until <= 65 points per axis, points cover the frame
+    g = O.grid_for(W, H, grid)
+    assert B.grid_dims(W, H, grid, 2) == (g.nx, g.ny, g.s)
+    assert (g.nx - 1) * g.s >= W - 1 and (g.ny - 1) * g.s >= H - 1
+    if grid == 0:
+        assert max(g.nx, g.ny) <= 65
+
+
+def test_control_grid_rejections(lib):
+    with pytest.raises(B.RegError) as e:   # spacing must halve exactly at every level
+        B.grid_dims(512, 512, 10, 3)
+    assert e.value.code == B.REG_EINVAL
+    with pytest.raises(B.RegError) as e:
+        B.grid_dims(512, 512, -1, 2)
+    assert e.value.code == B.REG_EINVAL
+    # shared-memory fit of a one-CTA operator: c, d, ct and the band (4 float2 per point) plus
+    # one 16-byte control row per warp; 1,000 x 2 points fit, 1,300 x 2 do not
+    assert B.grid_dims(1999, 3, 2, 2)[:2] == (1000, 2)
+    with pytest.raises(B.RegError) as e:
+        B.grid_dims(2599, 3, 2, 2)
+    assert e.value.code == B.REG_EINVAL and "shared memory" in str(e.value)
