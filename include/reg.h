@@ -93,8 +93,8 @@ extern "C" {
 
 /* ---- data types --------------------------------------------------------- */
 
-/* Scan element: deformation plus indices, 20 bytes [Sec. 5: "20 bytes of
- * deformation data and indices"].  Rigid parameters (alpha in radians, G in
+/* Scan element: deformation plus indices, 20 bytes [Sec. 5: the data a rank
+ * exchanges per element].  Rigid parameters (alpha in radians, G in
  * pixels of the finest level).  For REG_NONRIGID the field lives in a separate
  * buffer and alpha/gx/gy hold the field's mean displacement (alpha = 0). */
 typedef struct {
