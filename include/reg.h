@@ -283,7 +283,10 @@ int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W, int H,
                const double *theta, const float *grid_values, double *energy,
                double *grad, float *grad_values, void *stream);
 
-/* Control grid of a W x H frame for spacing `grid` (0 = auto) and `levels` (host only). */
+/* Control grid of a W x H frame for spacing `grid` (0 = auto) and `levels` (host only).
+ * REG_EINVAL when the spacing is negative or not a multiple of 2^(levels-1), when the grid
+ * has fewer than 2 x 2 points, or when one operator's grid state (4 x 8 B per point plus a
+ * 16-byte control row per warp) would exceed 216 KB of shared memory. */
 int reg_grid_dims(int W, int H, int grid, int levels, int *nx, int *ny, int *spacing);
 
 /* Nonrigid composition at the control points (B's initial guess, Sec. 2.3.2):
