@@ -320,7 +320,9 @@ int reg_stream_close(reg_stream_t *s);
 /* Choose the number of CTAs that cooperate on one operator (the "tile": rows of
  * each pyramid level per CTA) for this frame size, mode, storage type and
  * executor, by timing reg_scan on `frames` with 1, 2, 4, 8 and 16 CTAs per
- * operator (each twice, after one untimed run) and keeping the fastest.  Later
+ * operator (each twice, after one untimed run; nonrigid scans are timed without
+ * dense fields, whose kernel costs the same for every candidate) and keeping the
+ * fastest.  Later
  * reg_scan calls on the context with cfg.cluster == 0 and a matching shape
  * (same W, H, mode, storage, executor and floor(log2 N)) use the choice.
  * Arguments as reg_scan; best (host, optional) receives the choice.  The paper

@@ -1309,29 +1309,27 @@ extern "C" int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, i
     const int saved = ctx->cfg.cluster;
     const int n = N - 1;
     std::vector<reg_elem_t> out(n);
-    const size_t fb = sizeof(float) * 2 * (size_t)W * H * n;
-    void *fields = nullptr;
-    if (ctx->cfg.mode == REG_NONRIGID) {
-        if (cudaMalloc(&fields, fb) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(REG_ENOMEM, "autotune: field buffer");
-        }
-    }
+    // no dense fields while timing: their kernel runs after the scan and costs the same for
+    // every candidate, and for long series the buffer would take gigabytes
+    float *fields = nullptr;
     cudaStream_t s = nullptr;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return fail(REG_ECUDA, "autotune: cudaEventCreate: %s", cudaGetErrorString(e));
+    }
     int best_c = 0, rc = REG_OK;
     float best_ms = 1e30f;
     const int cands[] = {1, 2, 4, 8, 16};
     for (int c : cands) {
         ctx->cfg.cluster = c;
-        rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), (float *)fields, nullptr, s);
+        rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), fields, nullptr, s);
         if (rc != REG_OK) break;   // e.g. a cluster size the device cannot schedule
         float ms_min = 1e30f;
         for (int rep = 0; rep < 2 && rc == REG_OK; ++rep) {
             cudaEventRecord(e0, s);
-            rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), (float *)fields, nullptr, s);
+            rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), fields, nullptr, s);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -1344,7 +1342,6 @@ extern "C" int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, i
     ctx->cfg.cluster = saved;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (fields) cudaFree(fields);
     if (best_c == 0) return rc != REG_OK ? rc : fail(REG_ECUDA, "autotune: no candidate ran");
     ctx->tuned[std::make_tuple(W, H, ctx->cfg.mode, ctx->cfg.storage, exec, log2_floor(N))] = best_c;
     if (best) *best = best_c;
