@@ -241,25 +241,29 @@ int reg_scan_dag(int schedule, int n, int32_t *left, int32_t *right, int32_t *ou
 /* Allocation-free rigid pairwise registration (the paper has no counterpart:
  * this serves callers that may not allocate device memory when they register,
  * e.g. a real-time acquisition loop where cudaMalloc/cudaFree would stall the
- * device, code running under CUDA-graph stream capture, or an application that
- * hands the GPU a fixed memory budget up front).  Same result as reg_pairwise
- * for REG_RIGID, computed without any allocation: pyramids and operator state
- * live in one file-scope device array of about 12.2 MB, sized for frames of at
- * most 1,048,576 pixels (W, H <= 4096), which every GPU that loads libreg keeps
- * until the process exits.
- *   cfg      configuration (host); mode must be REG_RIGID.
+ * device, or an application that hands the GPU a fixed memory budget up front).
+ * Same result as reg_pairwise for REG_RIGID, computed without any allocation:
+ * pyramids and operator state live in one file-scope device array of about
+ * 12.2 MB, sized for frames of at most 1,048,576 pixels (W, H <= 4096), which
+ * every GPU that loads libreg keeps until the process exits.
+ *   cfg      configuration (host); mode must be REG_RIGID; the other fields are
+ *            checked by the rules of reg_ctx_create.
  *   device   CUDA device to run on (made current for the call, then restored).
- *   R, T     device fp32 images, H rows of `pitch` elements; host memory is
- *            rejected (REG_EINVAL) because staging it would need an allocation.
+ *   R, T     fp32 images, H rows of `pitch` elements, in device memory of `device`
+ *            (or managed memory); host memory and memory of another GPU are
+ *            rejected (REG_EINVAL): staging or peer access would need allocations.
  *   init     host, NULL = identity.  out (host) receives phi; stats (host) optional.
- * Errors: REG_EINVAL for a nonrigid config, sizes beyond the limit (with a
- * message naming it), host or NULL pointers; REG_ECUDA for CUDA failures.
+ *   stream   a stream of `device` (REG_EINVAL otherwise), or NULL.
+ * Errors: REG_EINVAL for a nonrigid or otherwise invalid config, sizes beyond the
+ * limit (with a message naming it), host, foreign-device or NULL pointers, a stream
+ * of another device; REG_ECUDA for CUDA failures.
  * The first call for a device resolves the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call shares the one array and overwrites what the
- * previous call left there: calls that overlap on the GPU (other host threads,
- * other streams) race and must be serialised by the caller.  The call returns
- * after its work on `stream` has completed. */
+ * (cudaGetSymbolAddress) with that device current.  The call waits for `stream`
+ * several times (the level means come back to the host between the pyramid and the
+ * operator) and returns after its work has completed, so it must not be made while
+ * `stream` is being captured into a CUDA graph.  Every call shares the one array
+ * and overwrites what the previous call left there: calls that overlap on the GPU
+ * (other host threads, other streams) race and must be serialised by the caller. */
 int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const float *R, const float *T, int W, int H,
                          int pitch, const reg_elem_t *init, reg_elem_t *out, reg_stats_t *stats, void *stream);
 

@@ -229,14 +229,18 @@ class Context:
 
     # ---- operators
     def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,
-                 stream=None):
-        H, W = R.shape[-2], R.shape[-1]
+                 stream=None, W: Optional[int] = None, pitch: Optional[int] = None):
+        """A (init None) or B's minimisation from init.  R, T: [H, W] arrays, or [H, pitch] rows
+        of which the first W columns are the frame (pass W and pitch)."""
+        H = R.shape[-2]
+        W = R.shape[-1] if W is None else W
+        pitch = R.shape[-1] if pitch is None else pitch
         out = reg_elem_t()
         st = reg_stats_t()
         ini = None
         if init is not None:
             ini = reg_elem_t(0, 1, float(init[0]), float(init[1]), float(init[2]))
-        check(lib().reg_pairwise(self.h, _ptr(R), _ptr(T), W, H, W, ctypes.byref(ini) if ini else None,
+        check(lib().reg_pairwise(self.h, _ptr(R), _ptr(T), W, H, pitch, ctypes.byref(ini) if ini else None,
                                  _ptr(field_in), ctypes.byref(out), _ptr(field_out), ctypes.byref(st),
                                  _stream(stream)), "reg_pairwise")
         return (out.i, out.k, out.alpha, out.gx, out.gy), stats_dict(st, self.cfg.levels)
@@ -334,14 +338,18 @@ def grid_dims(W: int, H: int, grid: int = 0, levels: int = 2):
     return nx.value, ny.value, sp.value
 
 
-def pairwise_noalloc(cfg: Config, R, T, init: Optional[Sequence[float]] = None, device: int = 0, stream=None):
-    """reg_pairwise_noalloc: rigid pairwise registration that allocates nothing (device R, T)."""
-    H, W = R.shape[-2], R.shape[-1]
+def pairwise_noalloc(cfg: Config, R, T, init: Optional[Sequence[float]] = None, device: int = 0, stream=None,
+                     W: Optional[int] = None, pitch: Optional[int] = None):
+    """reg_pairwise_noalloc: rigid pairwise registration that allocates nothing (device R, T;
+    [H, pitch] rows of which the first W columns are the frame when W and pitch are given)."""
+    H = R.shape[-2]
+    W = R.shape[-1] if W is None else W
+    pitch = R.shape[-1] if pitch is None else pitch
     c = cfg.c()
     out = reg_elem_t()
     st = reg_stats_t()
     ini = reg_elem_t(0, 1, float(init[0]), float(init[1]), float(init[2])) if init is not None else None
-    check(lib().reg_pairwise_noalloc(ctypes.byref(c), device, _ptr(R), _ptr(T), W, H, W,
+    check(lib().reg_pairwise_noalloc(ctypes.byref(c), device, _ptr(R), _ptr(T), W, H, pitch,
                                      ctypes.byref(ini) if ini else None, ctypes.byref(out), ctypes.byref(st),
                                      _stream(stream)), "reg_pairwise_noalloc")
     return (out.i, out.k, out.alpha, out.gx, out.gy), stats_dict(st, cfg.levels)

@@ -326,6 +326,8 @@ static int validate_cfg(const reg_config_t &c)
     return REG_OK;
 }
 
+int reg::validate_config(const reg_config_t &c) { return validate_cfg(c); }
+
 extern "C" int reg_ctx_create(const reg_config_t *cfg, int device, reg_ctx_t **out)
 {
     if (!out) return fail(REG_EINVAL, "out is NULL");

@@ -3,16 +3,18 @@
 // Some callers cannot allocate device memory at the moment they need a
 // registration: an acquisition loop with a real-time budget (cudaMalloc and
 // cudaFree can synchronise the whole device and stall the detector readout),
-// code that runs while a stream is being captured into a CUDA graph (where
-// allocation calls are not allowed), or a host application that hands the GPU
-// a fixed memory pool up front and forbids later allocations.  This entry point
-// serves them: everything it needs beyond the caller's inputs and outputs lives
-// in one file-scope device array, sized once for frames of up to
-// kMaxPixels pixels, which every GPU that loads the library holds until the
-// process exits.
+// or a host application that hands the GPU a fixed memory pool up front and
+// forbids later allocations.  This entry point serves them: everything it
+// needs beyond the caller's inputs and outputs lives in one file-scope device
+// array, sized once for frames of up to kMaxPixels pixels, which every GPU
+// that loads the library holds until the process exits.  The call waits for
+// its stream several times (the level means come back to the host between
+// the pyramid and the operator), so it is not meant to be recorded into a
+// CUDA graph: a caller must not make it while `stream` is being captured.
 #include <cstring>
 #include <mutex>
 
+#include "reg_host.h"
 #include "reg_internal.h"
 
 namespace {
@@ -49,14 +51,17 @@ int noalloc_fail(int code, const char *msg)
     return code;
 }
 
-bool on_device(const void *p)
+// Device memory of `device` itself, or managed memory.  Memory of another GPU is refused: the
+// pyramid kernels would read it directly, without peer access.
+bool on_device(const void *p, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -66,13 +71,10 @@ extern "C" int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const f
                                     void *stream)
 {
     if (!cfg || !R || !T || !out) return noalloc_fail(REG_EINVAL, "cfg, R, T and out are required");
+    // the configuration rules of reg_ctx_create, so that every config reg_pairwise rejects is rejected here
+    const int vrc = validate_config(*cfg);
+    if (vrc != REG_OK) return vrc;
     if (cfg->mode != REG_RIGID) return noalloc_fail(REG_EINVAL, "the allocation-free entry point is rigid only");
-    if (cfg->levels < 1 || cfg->levels > kMaxLevels) return noalloc_fail(REG_EINVAL, "levels must be 1..8");
-    if (cfg->storage != REG_F32 && cfg->storage != REG_BF16 && cfg->storage != REG_F16)
-        return noalloc_fail(REG_EINVAL, "unknown storage type");
-    if (cfg->cluster != 0 && cfg->cluster != 1 && cfg->cluster != 2 && cfg->cluster != 4 && cfg->cluster != 8 &&
-        cfg->cluster != 16)
-        return noalloc_fail(REG_EINVAL, "cluster must be 0, 1, 2, 4, 8 or 16");
     if (W < 2 || H < 2 || pitch < W) return noalloc_fail(REG_EINVAL, "need W, H >= 2 and pitch >= W");
     if ((long long)W * H > kMaxPixels || W > 4096 || H > 4096)
         return noalloc_fail(REG_EINVAL,
@@ -110,9 +112,17 @@ extern "C" int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const f
     int rc = REG_OK;
     cudaStream_t s = (cudaStream_t)stream;
     do {
-        if (!on_device(R) || !on_device(T)) {
-            rc = noalloc_fail(REG_EINVAL, "R and T must be device memory");
+        if (!on_device(R, device) || !on_device(T, device)) {
+            rc = noalloc_fail(REG_EINVAL, "R and T must be device memory of `device` (or managed memory)");
             break;
+        }
+        if (stream) {
+            int sdev = -1;
+            if (cudaStreamGetDevice(s, &sdev) != cudaSuccess || sdev != device) {
+                cudaGetLastError();
+                rc = noalloc_fail(REG_EINVAL, "stream does not belong to `device`");
+                break;
+            }
         }
         unsigned char *base = nullptr;
         {

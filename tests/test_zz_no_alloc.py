@@ -1,8 +1,9 @@
 """reg_pairwise_noalloc: the allocation-free rigid pairwise registration.
 
 Callers that must not allocate device memory when they register (a real-time
-acquisition loop, code under CUDA-graph capture, a fixed memory pool) use this
-entry point; it keeps its working data in a static device array.  It must give
+acquisition loop whose frame budget a cudaMalloc could break, an application
+that hands the GPU a fixed memory pool up front) use this entry point; it keeps
+its working data in a static device array.  It must give
 the same registration as reg_pairwise, call after call, even though every call
 reuses the array the previous call left behind.  This file is collected last
 so that a run stopping at the first failure has run every other test first.
@@ -63,3 +64,65 @@ def test_noalloc_rejects_oversized_and_nonrigid_requests():
     with pytest.raises(B.RegError) as e:
         B.pairwise_noalloc(B.Config(mode="nonrigid"), small, small)
     assert e.value.code == B.REG_EINVAL
+
+
+@pytest.mark.parametrize("case", ["init", "bf16", "pitched"])
+def test_noalloc_matches_pairwise_with_init_storage_and_pitch(case):
+    # the initial-deformation path, the 2-byte pyramid storage and frames whose rows are
+    # longer than W, each against reg_pairwise with the same arguments, two calls in a row
+    from paper_2010_12478_gb300 import build
+    build.build()
+    H, W = 96, 160
+    cfg = B.Config(storage="bf16" if case == "bf16" else "f32")
+    ctx = B.Context(cfg)
+    R, T = synth.rigid_pair(H, W, 0.005, (2.3, -1.4), noise_snr=10.0, seed=73)
+    init = [0.003, 2.0, -1.0] if case == "init" else None
+    if case == "pitched":
+        pitch = W + 24
+        Rw = torch.zeros((H, pitch), device="cuda")
+        Tw = torch.full((H, pitch), 5.0, device="cuda")   # columns beyond W must never be read
+        Rw[:, :W] = torch.from_numpy(R).cuda()
+        Tw[:, :W] = torch.from_numpy(T).cuda()
+        kw = dict(W=W, pitch=pitch)
+        Rd, Td = Rw, Tw
+    else:
+        kw = {}
+        Rd, Td = torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda()
+    _, ref = ctx.pairwise(Rd, Td, init=init, **kw)
+    torch.cuda.synchronize()
+    if case == "pitched":
+        # the pitched rows give the registration of the W-column frames themselves
+        _, ref2 = ctx.pairwise(torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda())
+        assert ref2["theta"] == ref["theta"]
+    for _ in range(2):
+        _, st = B.pairwise_noalloc(cfg, Rd, Td, init=init, **kw)
+        assert _max_px(np.array(st["theta"]), np.array(ref["theta"]), H, W) <= PX_TOL
+        assert abs(st["energy"] - ref["energy"]) <= E_TOL * abs(ref["energy"])
+
+
+def test_noalloc_calls_leave_device_free_memory_unchanged():
+    # the property the entry point exists for: after a first call (which may load the kernels'
+    # code), further calls take no device memory
+    from paper_2010_12478_gb300 import build
+    build.build()
+    cfg = B.Config()
+    R, T = synth.rigid_pair(128, 128, 0.002, (0.8, 1.1), noise_snr=10.0, seed=74)
+    Rd, Td = torch.from_numpy(R).cuda(), torch.from_numpy(T).cuda()
+    B.pairwise_noalloc(cfg, Rd, Td)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        B.pairwise_noalloc(cfg, Rd, Td)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_rejects_configs_that_reg_pairwise_rejects():
+    from paper_2010_12478_gb300 import build
+    build.build()
+    small = torch.zeros((64, 64), device="cuda")
+    for bad in (dict(max_iter=-1), dict(tau0=0.0), dict(step_cap=-1.0), dict(armijo_c=1.5), dict(lam=-1.0)):
+        with pytest.raises(B.RegError) as e:
+            B.pairwise_noalloc(B.Config(**bad), small, small)
+        assert e.value.code == B.REG_EINVAL
