@@ -75,6 +75,7 @@ def lib():
             dpp = ctypes.POINTER(dp)
             L.or_downsample.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
             L.or_sample.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+            L.or_sample_q.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
             L.or_rigid_energy.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
             L.or_rigid_energy.restype = ctypes.c_int
             L.or_rigid_compose.argtypes = [dp, dp, dp]
@@ -116,8 +117,8 @@ class Config:
     levels: int = 2
     max_iter: int = 500
     max_rejects: int = 30
-    tol_grad: float = 1e-5
-    tol_rel_e: float = 1e-10
+    tol_grad: float = 1e-4
+    tol_rel_e: float = 0.0
     armijo_c: float = 0.25
     tau0: float = 1.0
     step_cap: float = 0.5
@@ -167,6 +168,16 @@ def sample(T, px: float, py: float):
     H, W = T.shape
     out = np.empty(3, dtype=np.float64)
     lib().or_sample(_dp(T), W, H, px, py, _dp(out))
+    return out
+
+
+def sample_q(T, px: float, py: float):
+    """Quadratic B-spline model of T's samples (edge samples replicated) at (px, py):
+    (value, d/dpx, d/dpy).  The image model of the nonrigid energy."""
+    T = _f64(T)
+    H, W = T.shape
+    out = np.empty(3, dtype=np.float64)
+    lib().or_sample_q(_dp(T), W, H, px, py, _dp(out))
     return out
 
 

@@ -25,9 +25,14 @@
  *
  * Conventions (readings where the paper is silent):
  *   pixel (r, c) sits at x = (c, r); centre c0 = ((W-1)/2, (H-1)/2);
- *   bilinear sampling with clamp-to-edge; the derivative is the analytic
- *   derivative of the interpolant in the cell, 0 along a clamped axis;
- *   cell choice x0 = min(floor(px), W-2) so that W >= 2 and H >= 2 suffice.
+ *   rigid map and registered frames: bilinear sampling with clamp-to-edge;
+ *   the derivative is the analytic derivative of the interpolant in the
+ *   cell, 0 along a clamped axis; cell choice x0 = min(floor(px), W-2) so
+ *   that W >= 2 and H >= 2 suffice;
+ *   nonrigid field: both frames are taken through the quadratic B-spline
+ *   model of their samples (samples beyond the border replicate the edge),
+ *   a continuously differentiable image, so that the energy of the local
+ *   control values has a continuous gradient (see or_sample_q).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -119,6 +124,55 @@ void or_sample(const double *T, int W, int H, double px, double py, double out[3
     out[0] = (1.0 - fy) * top + fy * bot;
     out[1] = (px < 0.0 || px > W - 1) ? 0.0 : (1.0 - fy) * (t01 - t00) + fy * (t11 - t10);
     out[2] = (py < 0.0 || py > H - 1) ? 0.0 : bot - top;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quadratic B-spline model of the samples T_k (k on the integer grid):     */
+/*   T(p) = sum_k T_k b(px - kx) b(py - ky),                                  */
+/*   b(t) = 3/4 - t^2 (|t| <= 1/2), (|t| - 3/2)^2 / 2 (1/2 <= |t| <= 3/2), 0 */
+/* with T_k for k outside the frame equal to the nearest edge sample.  The  */
+/* model is continuously differentiable everywhere (b is C1), reproduces    */
+/* affine images, and at a pixel centre equals the separable filter         */
+/* (1/8, 3/4, 1/8) of the samples with derivative the central difference.   */
+/* out[0] = T(p), out[1] = dT/dpx, out[2] = dT/dpy.                         */
+/* ------------------------------------------------------------------------ */
+
+static int clampi(int v, int lo, int hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* The three nonzero weights b(t + 1), b(t), b(t - 1) at offset t in [-1/2, 1/2) from the
+ * nearest sample, and their derivatives. */
+static void bspline2_weights(double t, double w[3], double dw[3])
+{
+    w[0] = 0.5 * (0.5 - t) * (0.5 - t);
+    w[1] = 0.75 - t * t;
+    w[2] = 0.5 * (0.5 + t) * (0.5 + t);
+    dw[0] = -(0.5 - t);
+    dw[1] = -2.0 * t;
+    dw[2] = 0.5 + t;
+}
+
+void or_sample_q(const double *T, int W, int H, double px, double py, double out[3])
+{
+    const int nx = (int)floor(px + 0.5), ny = (int)floor(py + 0.5);   /* nearest sample */
+    double wx[3], dwx[3], wy[3], dwy[3];
+    bspline2_weights(px - nx, wx, dwx);
+    bspline2_weights(py - ny, wy, dwy);
+    double v = 0.0, gx = 0.0, gy = 0.0;
+    for (int j = 0; j < 3; ++j) {
+        const int y = clampi(ny - 1 + j, 0, H - 1);
+        for (int i = 0; i < 3; ++i) {
+            const double t = T[y * W + clampi(nx - 1 + i, 0, W - 1)];
+            v += wx[i] * wy[j] * t;
+            gx += dwx[i] * wy[j] * t;
+            gy += wx[i] * dwy[j] * t;
+        }
+    }
+    out[0] = v;
+    out[1] = gx;
+    out[2] = gy;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -334,7 +388,9 @@ double or_grid_regulariser(const or_grid_t *g, const double *cx, const double *c
 }
 
 /* Energy at level l (images R, T of that level, W x H) for control values c
- * given in pixels of that level; gradient dE/dc (same units) if gx/gy given. */
+ * given in pixels of that level; gradient dE/dc (same units) if gx/gy given.
+ * Both frames are taken through the quadratic B-spline model (or_sample_q):
+ * the reference at its pixel centres, the template at x + u(x).            */
 int or_grid_energy(const double *R, const double *T, int W, int H, int l, const or_grid_t *g,
                    const double *cx, const double *cy, double lambda, double *E, double *gx, double *gy)
 {
@@ -342,6 +398,14 @@ int or_grid_energy(const double *R, const double *T, int W, int H, int l, const 
     const double scale = ldexp(1.0, l), off = 0.5 * (scale - 1.0);
     or_moments_t m = {(double)P, 0, 0, 0, 0, 0};
     double *tw = NULL, *dtx = NULL, *dty = NULL;
+    /* the reference through the same image model, at its pixel centres */
+    double *Rm = (double *)malloc(sizeof(double) * P);
+    for (int r = 0; r < H; ++r)
+        for (int c = 0; c < W; ++c) {
+            double s[3];
+            or_sample_q(R, W, H, (double)c, (double)r, s);
+            Rm[r * W + c] = s[0];
+        }
     if (gx) {
         tw = (double *)malloc(sizeof(double) * P);
         dtx = (double *)malloc(sizeof(double) * P);
@@ -352,8 +416,8 @@ int or_grid_energy(const double *R, const double *T, int W, int H, int l, const 
             int i = r * W + c;
             double ux, uy, s[3];
             or_grid_eval(g, cx, cy, scale * c + off, scale * r + off, &ux, &uy);
-            or_sample(T, W, H, c + ux, r + uy, s);
-            double rv = R[i], tv = s[0];
+            or_sample_q(T, W, H, c + ux, r + uy, s);
+            double rv = Rm[i], tv = s[0];
             m.sR += rv; m.sT += tv; m.sRR += rv * rv; m.sTT += tv * tv; m.sRT += rv * tv;
             if (gx) { tw[i] = tv; dtx[i] = s[1]; dty[i] = s[2]; }
         }
@@ -368,7 +432,7 @@ int or_grid_energy(const double *R, const double *T, int W, int H, int l, const 
                     int i = r * W + c, jx, jy;
                     double wx, wy;
                     or_grid_cell(g, scale * c + off, scale * r + off, &jx, &jy, &wx, &wy);
-                    double f = -(n.a * (R[i] - n.rbar) - n.b * (tw[i] - n.tbar));
+                    double f = -(n.a * (Rm[i] - n.rbar) - n.b * (tw[i] - n.tbar));
                     double ax = f * dtx[i], ay = f * dty[i];
                     int j = jy * g->nx + jx;
                     double w[4] = {(1 - wx) * (1 - wy), wx * (1 - wy), (1 - wx) * wy, wx * wy};
@@ -393,6 +457,7 @@ int or_grid_energy(const double *R, const double *T, int W, int H, int l, const 
         }
         free(tw); free(dtx); free(dty);
     }
+    free(Rm);
     return n.degenerate;
 }
 

@@ -3,7 +3,8 @@
 Each test checks the oracle against something other than itself: values the
 paper prints (tests/golden/scan_work.json), closed forms, invariants, library
 routines (numpy's corrcoef), brute-force search and exactness properties of
-bilinear interpolation.  A dropped term, a wrong sign, a transposed operand or
+the two image models (bilinear interpolation; the quadratic B-spline model of
+the nonrigid energy).  A dropped term, a wrong sign, a transposed operand or
 a wrong index in the oracle fails at least one of them.
 """
 import json
@@ -78,12 +79,86 @@ def test_sample_clamps_to_edge_with_zero_derivative_along_clamped_axis():
 
 
 # ---------------------------------------------------------------- NCC energy
+def smooth_1_8_3_4_1_8(img):
+    """The separable filter (1/8, 3/4, 1/8) with edge samples replicated (numpy, by hand)."""
+    p = np.pad(img, 1, mode="edge")
+    rows = 0.125 * p[:-2, :] + 0.75 * p[1:-1, :] + 0.125 * p[2:, :]
+    return 0.125 * rows[:, :-2] + 0.75 * rows[:, 1:-1] + 0.125 * rows[:, 2:]
+
+
 def test_ncc_energy_equals_corrcoef_at_identity():
     R, T = rand_img(12, 10, 3), rand_img(12, 10, 4)
     E = O.rigid_energy(R, T, [0.0, 0.0, 0.0], grad=False)
     assert E == pytest.approx(1.0 - np.corrcoef(R.ravel(), T.ravel())[0, 1], abs=1e-13)
+    # the nonrigid energy takes both frames through the B-spline model: at the zero field that is
+    # the correlation of the two filtered frames
     g = O.grid_for(10, 12, 4)
-    assert O.grid_energy(R, T, 0, g, np.zeros((2, g.ny, g.nx)), 5.0, grad=False) == pytest.approx(E, abs=1e-13)
+    Eg = O.grid_energy(R, T, 0, g, np.zeros((2, g.ny, g.nx)), 5.0, grad=False)
+    Rf, Tf = smooth_1_8_3_4_1_8(R), smooth_1_8_3_4_1_8(T)
+    assert Eg == pytest.approx(1.0 - np.corrcoef(Rf.ravel(), Tf.ravel())[0, 1], abs=1e-13)
+
+
+# ---------------------------------------------------------------- quadratic B-spline image model
+def test_bspline_model_at_pixel_centres_is_the_filter_and_central_difference():
+    T = rand_img(9, 11, 81)
+    Tf = smooth_1_8_3_4_1_8(T)
+    p = np.pad(T, 1, mode="edge")
+    # d/dx at a centre: central difference along x, filtered (1/8, 3/4, 1/8) along y; and vice versa
+    cx = 0.5 * (p[:, 2:] - p[:, :-2])
+    dx = 0.125 * cx[:-2, :] + 0.75 * cx[1:-1, :] + 0.125 * cx[2:, :]
+    cy = 0.5 * (p[2:, :] - p[:-2, :])
+    dy = 0.125 * cy[:, :-2] + 0.75 * cy[:, 1:-1] + 0.125 * cy[:, 2:]
+    for r in range(9):
+        for c in range(11):
+            v, gx, gy = O.sample_q(T, float(c), float(r))
+            assert v == pytest.approx(Tf[r, c], abs=1e-15)
+            assert gx == pytest.approx(dx[r, c], abs=1e-15) and gy == pytest.approx(dy[r, c], abs=1e-15)
+
+
+def test_bspline_model_reproduces_affine_images():
+    H, W = 12, 15
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    T = 0.3 + 0.7 * x - 0.45 * y
+    rng = np.random.default_rng(82)
+    for px, py in rng.uniform(1.5, [W - 2.5, H - 2.5], size=(20, 2)):
+        v, gx, gy = O.sample_q(T, px, py)
+        assert v == pytest.approx(0.3 + 0.7 * px - 0.45 * py, abs=1e-13)
+        assert gx == pytest.approx(0.7, abs=1e-13) and gy == pytest.approx(-0.45, abs=1e-13)
+    # a constant image stays constant with zero derivative anywhere, inside or outside
+    for px, py in ((-7.3, 2.2), (3.4, 40.0), (5.5, 5.5)):
+        v, gx, gy = O.sample_q(np.full((6, 7), 0.25), px, py)
+        assert v == pytest.approx(0.25, abs=1e-15) and abs(gx) <= 1e-15 and abs(gy) <= 1e-15
+
+
+def test_bspline_model_is_continuously_differentiable():
+    # value and derivatives agree on both sides of a knot (half-integer), where the tap set changes
+    T = rand_img(10, 10, 83)
+    e = 1e-9
+    for px, py in ((3.5, 4.2), (6.1, 2.5), (0.5, 0.5), (-0.5, 7.3), (9.5, 9.5)):
+        for dx, dy in ((e, 0.0), (0.0, e)):
+            a = O.sample_q(T, px - dx, py - dy)
+            b = O.sample_q(T, px + dx, py + dy)
+            np.testing.assert_allclose(a, b, atol=1e-8)
+
+
+def test_bspline_model_replicates_edges_outside_the_frame():
+    T = rand_img(7, 8, 84)
+    # far to the left every tap in x is column 0: the value is that column's y-model, d/dx = 0
+    v, gx, gy = O.sample_q(T, -6.0, 3.0)
+    assert v == pytest.approx(0.125 * T[2, 0] + 0.75 * T[3, 0] + 0.125 * T[4, 0], abs=1e-15)
+    assert gx == 0.0 and gy == pytest.approx(0.5 * (T[4, 0] - T[2, 0]), abs=1e-15)
+    v, gx, gy = O.sample_q(T, 100.0, 100.0)   # beyond the far corner
+    assert v == pytest.approx(T[-1, -1], abs=1e-15) and abs(gx) <= 1e-15 and abs(gy) <= 1e-15
+
+
+def test_bspline_derivative_matches_central_differences():
+    T = rand_img(16, 16, 85)
+    h = 1e-6
+    for px, py in np.random.default_rng(86).uniform(-1.0, 16.0, size=(25, 2)):
+        v, gx, gy = O.sample_q(T, px, py)
+        fx = (O.sample_q(T, px + h, py)[0] - O.sample_q(T, px - h, py)[0]) / (2 * h)
+        fy = (O.sample_q(T, px, py + h)[0] - O.sample_q(T, px, py - h)[0]) / (2 * h)
+        assert gx == pytest.approx(fx, abs=1e-7) and gy == pytest.approx(fy, abs=1e-7)
 
 
 def test_ncc_by_hand_on_2x2():
@@ -216,6 +291,64 @@ def test_nonrigid_recovers_smooth_field():
     # and the field moved away from a pure translation where the truth does
     tf = ser.truth_field(1)
     assert np.abs(tf - tf.mean(axis=(1, 2), keepdims=True)).max() > 0.1
+
+
+def test_nonrigid_flow_stops_on_the_metric_gradient_norm():
+    # the reading of the stop rule: a level ends when |d|_M = sqrt(mean_j |Nc dE/dc_j|^2) falls
+    # below tol_grad; check it on the returned control values with the energy's own gradient
+    ser = synth.make_series(synth.SeriesSpec(2, 96, 96, step=1.5, field_amp=1.0, snr=(10, 10), seed=32))
+    F = ser.frames.numpy()
+    cfg = O.Config(levels=2, mode="nonrigid")
+    c, st = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, cfg)
+    assert st.stop == [0, 0]
+    g = O.grid_for(96, 96)
+    _, gr = O.grid_energy(F[0].astype(np.float64), F[1].astype(np.float64), 0, g, c, cfg.lam)
+    Nc = g.nx * g.ny
+    assert math.sqrt(((Nc * gr) ** 2).sum() / Nc) < cfg.tol_grad
+
+
+@pytest.mark.parametrize("seed", [33, 34])
+def test_nonrigid_result_is_insensitive_to_float32_sized_perturbations(seed):
+    # with a continuously differentiable energy and the gradient stop, the result is the minimiser
+    # to within the stop tolerance: frames perturbed at the float32 rounding level (1e-7 relative)
+    # give the same deformation to a few thousandths of a pixel
+    ser = synth.make_series(synth.SeriesSpec(2, 128, 128, step=1.0, field_amp=1.5, snr=(10, 10), seed=seed))
+    F = ser.frames.numpy().astype(np.float64)
+    cfg = O.Config(levels=2, mode="nonrigid")
+    c0, _ = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, cfg)
+    rng = np.random.default_rng(seed)
+    Fp = F * (1.0 + 1e-7 * rng.standard_normal(F.shape))
+    c1, _ = O.register_nonrigid(O.pyramid(Fp[0], 2), O.pyramid(Fp[1], 2), None, cfg)
+    assert O.max_px_error(c0, c1, 128, 128, "nonrigid") <= 0.005
+
+
+# ---------------------------------------------------------------- three levels
+@pytest.mark.parametrize("seed", range(3))
+def test_three_levels_recover_known_translation_on_a_coarse_lattice(seed):
+    # with a 16-px lattice the coarsest of three levels still resolves the period (4 px)
+    rng = np.random.default_rng(300 + seed)
+    s = rng.uniform(-6.0, 6.0, size=2)
+    R, T = synth.translated_pair(160, 160, s, seed=seed, noise_snr=None if seed % 2 == 0 else 20.0, period=16.0,
+                                 sigma=3.0)
+    th, st = O.register_rigid(O.pyramid(R, 3), O.pyramid(T, 3), np.zeros(3), O.Config(levels=3))
+    assert abs(th[1] - s[0]) <= 0.05 and abs(th[2] - s[1]) <= 0.05, (th, s)
+    ser = synth.make_series(synth.SeriesSpec(2, 128, 128, step=4.0, field_amp=1.0, snr=(10, 10), period=16.0,
+                                             sigma=3.0, field_rate=(0.8, 1.2), seed=310 + seed))
+    F = ser.frames.numpy()
+    c, _ = O.register_nonrigid(O.pyramid(F[0], 3), O.pyramid(F[1], 3), None, O.Config(levels=3, mode="nonrigid"))
+    err = (O.grid_dense(O.grid_for(128, 128), c) - ser.truth_field(1))[:, 16:-16, 16:-16]
+    assert np.sqrt((err ** 2).sum(0).mean()) <= 0.1
+
+
+def test_three_level_flow_lands_on_brute_force_minimiser():
+    R, T = synth.rigid_pair(64, 64, 0.0, (2.63, -1.41), noise_snr=6.0, seed=42, period=16.0, sigma=3.0)
+    cfg = O.Config(levels=3, tol_grad=1e-7)
+    th, _ = O.register_rigid(O.pyramid(R, 3), O.pyramid(T, 3), np.zeros(3), cfg)
+    grid = np.arange(-0.05, 0.05 + 1e-12, 0.005)
+    E = np.array([[O.rigid_energy(R, T, [th[0], th[1] + a, th[2] + b], grad=False) for b in grid] for a in grid])
+    ia, ib = np.unravel_index(E.argmin(), E.shape)
+    assert abs(grid[ia]) <= 0.005 and abs(grid[ib]) <= 0.005
+    assert abs(th[1] - 2.63) <= 0.05 and abs(th[2] + 1.41) <= 0.05
 
 
 # ---------------------------------------------------------------- brute force
