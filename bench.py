@@ -1,18 +1,21 @@
 #!/usr/bin/env python
 """Benchmark: registered frames/s of the registration scan on one GB300.
 
-Workload (default ``c2``): a synthetic 256-frame series of 512x512 fp32 lattice
-frames (random-walk drift U(+-1) px/frame per axis, smooth field <= 1.5 px,
-SNR 10, seed 1410), registered to frame 0 by the Brent-Kung scan of the
-operator B, leaves A(f_{i-1}, f_i); 2-level pyramid; FP32 arithmetic with
-float-float/FP64 reductions and FP64 step control.  One step = pyramid build
-+ all operators + results back on the host, through reg_scan.
+Workload (default ``c3``): a synthetic 4,096-frame series of 512x512 fp32
+lattice frames (random-walk drift U(+-1) px/frame per axis, smooth field
+<= 1.5 px, SNR U(3, 20) per frame, 5 % of frames with jumps of up to 8 px,
+seed 1410), registered to frame 0 by the Brent-Kung scan of the operator B
+over the leaves A(f_{i-1}, f_i); nonrigid control-grid model, 2-level pyramid,
+FP32 arithmetic with float-float/FP64 reductions and FP64 step control.  One
+step = pyramid build + all operators + results on the host, through reg_scan.
 
-``value``: frames/s with the frames resident in HBM, executor ``plain`` (one
-operator per kernel launch, the workload's stated form).  ``batched`` gives
-the same workload through the persistent device-queue executor.  ``e2e``:
-the same call with pinned HOST frames (host->device copy of the series and
-device->host copy of the results inside the timed region).
+``value``: frames/s with the frames resident in HBM, through the persistent
+device-queue executor with autotuned CTAs per operator (the workload's batched
+form).  ``forms`` gives the same workload one operator per launch and as a
+replayed CUDA graph; ``phases`` the A leaves and the B scan timed apart.
+``e2e``: the same call with pinned HOST frames (host->device copy of the
+series and device->host copy of the results, for the nonrigid model every
+prefix's control values, inside the timed region).
 
 Run ``python bench.py --impl reference`` for the FP64 CPU oracle on a
 bounded sample of the same workload.
@@ -56,7 +59,8 @@ WORKLOAD_TEXT = {
     "c1": "16 frames 128x128 fp32 lattice series, sequential-recursion workload size",
     "c2": "256 frames 512x512 fp32 lattice series (random-walk drift +-1 px/frame, field <=1.5 px, SNR 10), "
           "Brent-Kung scan of B over A leaves",
-    "c3": "4096 frames 512x512 fp32 lattice series (SNR 3-20, 5% jumps <=8 px), Brent-Kung scan",
+    "c3": "4096 frames 512x512 fp32 lattice series (random-walk drift +-1 px/frame, field <=1.5 px, SNR 3-20, "
+          "5% jumps <=8 px), Brent-Kung scan of B over A leaves",
     "c4": "64 independent series of 128 frames, sizes drawn from {256^2, 512^2, 1024^2}, pyramids stored as "
           "fp32 / bf16 / fp16; the series of one size share one batched scan (persistent queue)",
 }
@@ -280,7 +284,7 @@ def serving(dev, mode: str, frames_per_stream: int, seed: int = 1410):
         rate = float(rng.uniform(50.0, 400.0))
         spec = synth.SeriesSpec(frames_per_stream, S, S, step=1.0, field_amp=1.5, snr=(10.0, 10.0),
                                 seed=seed + 100 + k)
-        fr = synth.make_series(spec, device=dev).frames.cpu().pin_memory()
+        fr = synth.make_series(spec, device=dev).frames   # device-resident acquisition buffers
         t = np.cumsum(rng.exponential(1.0 / rate, size=frames_per_stream))
         plan.append((S, rate, fr, t))
     ctx = B.Context(B.Config(mode=mode, mem_budget=40 << 30))
@@ -315,8 +319,9 @@ def serving(dev, mode: str, frames_per_stream: int, seed: int = 1410):
                                                 "p99": round(float(np.percentile(lat, 99)), 3),
                                                 "max": round(float(lat.max()), 3)},
             "admission_refusals": refused, "budget_bytes": 40 << 30,
-            "frames_per_stream_note": f"{frames_per_stream} frames per stream (the workload names 2048; shortened "
-                                      f"so the default bench stays within minutes)"}
+            "frames_per_stream": frames_per_stream,
+            "offered_fps": round(sum(rate for (_, rate, _, _) in plan), 1),
+            "frames_source": "device memory (each submit copies the frame into the stream's slot)"}
 
 
 # ------------------------------------------------------------------ precision
@@ -341,11 +346,10 @@ def precision(frames, mode: str, n_samples: int = 6):
     out = {}
     for storage in ("f32", "bf16", "f16"):
         ctx = B.Context(B.Config(mode=mode, storage=storage))
-        fo = torch.empty((n, 2, H, W), device=frames.device) if mode == "nonrigid" else None
-        ctx.scan(frames, schedule="brent_kung", exec="persistent", fields_out=fo)
+        ctx.scan(frames, schedule="brent_kung", exec="persistent")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        els, st = ctx.scan(frames, schedule="brent_kung", exec="persistent", fields_out=fo)
+        els, st = ctx.scan(frames, schedule="brent_kung", exec="persistent")
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         errs = []
@@ -498,22 +502,31 @@ def mixed_batch(args, dev, world, rank, dist):
 
 
 # ------------------------------------------------------------------ main
+def paper_bounds(N: int, P: int, C1: float = 1.0):
+    """The paper's upper bounds on the speedup of the scan registration and of the full
+    registration on P workers (Sec. 5.2): (N-1) / (2N/P - 1 + C1 log2 P) and
+    (2N-1) / (3N/P - 1 + C1 log2 P)."""
+    lg = math.log2(P) if P > 1 else 0.0
+    return {"P": P, "C1": C1, "scan": round((N - 1) / (2.0 * N / P - 1.0 + C1 * lg), 2),
+            "full": round((2 * N - 1) / (3.0 * N / P - 1.0 + C1 * lg), 2)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--mode", default="nonrigid", choices=["rigid", "nonrigid"])
-    ap.add_argument("--exec", dest="exec_", default="plain", choices=["plain", "level", "persistent", "graph"])
+    ap.add_argument("--exec", dest="exec_", default="persistent", choices=["plain", "level", "persistent", "graph"])
     ap.add_argument("--frames", type=int, default=0, help="override the series length (small profiler cases)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per operator; 0 = autotuned")
-    ap.add_argument("--oracle-budget", type=float, default=15.0)
+    ap.add_argument("--oracle-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main timed region only (for profiler captures)")
     ap.add_argument("--warp", action="store_true", help="with --quick: also run the registered-series stage")
-    ap.add_argument("--serve-frames", type=int, default=96, help="frames per stream in the serving run")
+    ap.add_argument("--serve-frames", type=int, default=2048, help="frames per stream in the serving run")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -551,19 +564,18 @@ def main():
         if dist:
             dist.barrier()
 
-    def make_ctx(mode):
+    def make_ctx(mode, tune_execs):
         c = B.Context(B.Config(mode=mode, cluster=args.cluster), device=local)
         c.set_timing(True)
-        fl = torch.empty((N - 1, 2, H, W), device=dev) if mode == "nonrigid" else None
         tuned = {}
         if args.cluster == 0 and not args.quick:
-            for ex in ("plain", "persistent", "graph"):
+            for ex in tune_execs:
                 tuned[ex] = c.autotune(frames, exec=ex)   # outside every timed region
-        return c, fl, tuned
+        return c, tuned
 
-    def timed(ctx, fields, src, exec_, steps, warmup):
+    def timed(ctx, src, exec_, steps, warmup, split=False, grids=None, grids_host=None):
         for _ in range(warmup):
-            ctx.scan(src, schedule="brent_kung", exec=exec_, fields_out=fields)
+            ctx.scan(src, schedule="brent_kung", exec=exec_, split=split)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -572,20 +584,24 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            _, st = ctx.scan(src, schedule="brent_kung", exec=exec_, fields_out=fields)
+            _, st = ctx.scan(src, schedule="brent_kung", exec=exec_, split=split)
             st_list.append(st)
             tim.append(ctx.last_timing())
+            if grids is not None:
+                # the nonrigid result proper: every prefix's control values, back on the host
+                ctx.scan_grids(grids)
+                grids_host.copy_(grids)
         e1.record()
         torch.cuda.synchronize()
         barrier()
         ms = world_max_ms(e0.elapsed_time(e1) / steps, dist, dev)
         return ms, st_list, tim
 
-    ctx, fields, tuned = make_ctx(args.mode)
+    ctx, tuned = make_ctx(args.mode, [args.exec_] + (["plain"] if args.exec_ != "plain" else []))
     cfg = ctx.cfg
     # ---- main timed region (device-resident frames, the workload's stated executor)
     with ClockSampler(local) as clk:
-        ms, st_list, tim = timed(ctx, fields, frames, args.exec_, args.steps, args.warmup)
+        ms, st_list, tim = timed(ctx, frames, args.exec_, args.steps, args.warmup)
     clocks = clk.summary()
     n_ops = len(st_list[0])
     value = job_rate(N - 1, world, ms)
@@ -598,54 +614,97 @@ def main():
     launches = sum(t["op_launches"] for t in tim) / len(tim)
     peak, peak_src = peaks()
     achieved = alg / (kms / 1e3) / 1e9 if kms > 0 else 0.0
-    traffic = profile_traffic(f"op_kernel_{args.workload}_{args.mode}", "reg_kernels.cu",
-                              f"dram bytes per step, {args.exec_} executor (scaled)")
+    kname = "persistent_kernel" if args.exec_ == "persistent" else "op_kernel"
+    traffic = profile_traffic(f"{kname}_{args.workload}_{args.mode}", "reg_kernels.cu",
+                              "dram bytes per step (scaled)")
     gpu_launches = int(sum(t["op_launches"] + t["pyramid_launches"] for t in tim))
     ev = np.array([sum(s["evals"]) for s in st_list[0]])
+    nl = N - 1
+    ev_a, ev_b = ev[:nl], ev[nl:]
 
     levels = cfg.levels
-    batched = e2e = other = serve = prec = reg_series = None
+    forms = phases = e2e = other = serve = prec = reg_series = imbalance = None
     if args.quick and args.warp:
         reg_series = registered_series(ctx, frames, args.mode, 1, 1, peak, peak_src, world)
     if not args.quick:
-        # ---- batched executor on the same workload
-        bms, bst, btim = timed(ctx, fields, frames, "persistent", max(3, args.steps // 2), 2)
-        batched = {"exec": "persistent", "value": round(world * (N - 1) / (bms / 1e3), 2), "unit": UNIT,
-                   "ms_per_step": round(bms, 3), "cluster": tuned.get("persistent", args.cluster),
-                   "op_kernel_ms": round(sum(t["op_kernel_ms"] for t in btim) / len(btim), 3)}
-        # ---- the one-operator-per-launch path captured once as a CUDA graph and replayed
-        gms, _, _ = timed(ctx, fields, frames, "graph", max(3, args.steps // 2), 2)
-        batched["graph"] = {"exec": "graph", "value": round(world * (N - 1) / (gms / 1e3), 2), "unit": UNIT,
-                            "ms_per_step": round(gms, 3), "cluster": tuned.get("graph", args.cluster)}
+        # ---- the other executors on the same workload: one operator per launch, and those launches
+        # captured once as a CUDA graph and replayed (same CTAs per operator as the tuned plain path)
+        forms = {args.exec_: {"value": round(value, 2), "ms_per_step": round(ms, 3),
+                              "cluster": tuned.get(args.exec_, args.cluster)}}
+        for ex in ("plain", "graph", "persistent"):
+            if ex == args.exec_:
+                continue
+            if ex == "graph":
+                gctx = B.Context(B.Config(mode=args.mode, cluster=tuned.get("plain", args.cluster) or 0),
+                                 device=local)
+                gctx.set_timing(True)
+                fms, _, ftim = timed(gctx, frames, ex, max(2, args.steps // 2), 2)
+                del gctx
+            else:
+                fms, _, ftim = timed(ctx, frames, ex, max(2, args.steps // 2), 2)
+            forms[ex] = {"value": round(job_rate(N - 1, world, fms), 2), "ms_per_step": round(fms, 3),
+                         "op_kernel_ms": round(sum(t["op_kernel_ms"] for t in ftim) / len(ftim), 3),
+                         "cluster": tuned.get(ex if ex != "graph" else "plain", args.cluster)}
+        # ---- "full" vs "scan" (Sec. 5.2): the A leaves to completion, then the B operators
+        pms, _, ptim = timed(ctx, frames, args.exec_, 2, 1, split=True)
+        leaf_ms = sum(t["leaf_ms"] for t in ptim) / len(ptim)
+        dag_ms = sum(t["dag_ms"] for t in ptim) / len(ptim)
+        # operator slots: 152 SMs x 3 CTAs per SM / CTAs per operator
+        workers = 152 * 3 // max(1, tuned.get(args.exec_, args.cluster) or 8)
+        phases = {"exec": args.exec_, "leaf_ops": ptim[0]["leaf_ops"], "dag_ops": ptim[0]["dag_ops"],
+                  "leaf_ms": round(leaf_ms, 3), "dag_ms": round(dag_ms, 3),
+                  "scan_frames_per_s": round(job_rate(N - 1, world, dag_ms), 2),
+                  "full_frames_per_s": round(job_rate(N - 1, world, leaf_ms + dag_ms), 2),
+                  "overlapped_full_frames_per_s": round(value, 2),
+                  "evals_per_op": {"A": round(float(ev_a.mean()), 2), "B": round(float(ev_b.mean()), 2)},
+                  "ms_per_op": {"A": round(leaf_ms / max(1, ptim[0]["leaf_ops"]), 5),
+                                "B": round(dag_ms / max(1, ptim[0]["dag_ops"]), 5)},
+                  "paper_bounds_context": paper_bounds(N, max(2, workers)),
+                  "note": "scan = the B operators given the A leaves (the paper's scan registration); full = "
+                          "A then B; overlapped = the main value, where B operators start as soon as their "
+                          "inputs exist; paper_bounds_context evaluates the paper's speedup bounds for P "
+                          "concurrent operator slots (context only)"}
+        # ---- load imbalance of the operators (Sec. 3.2): per-operator work from the evaluation
+        # counts, over segments of the series as the paper's ranks would hold them
+        imbalance = imbalance_metric(ev_a, [64, 256, 1024])
         # ---- registered series: every frame resampled onto f_0's grid by its prefix, and the mean
         reg_series = registered_series(ctx, frames, args.mode, max(3, args.steps), 3, peak, peak_src, world)
-        # ---- end to end: pinned host frames through the C ABI, copies inside the timed region
+        # ---- end to end: pinned host frames through the C ABI, copies inside the timed region, the
+        # prefixes (and for the nonrigid model every prefix's control values) back on the host
         host = frames.cpu().pin_memory()
-        ems, _, _ = timed(ctx, fields, host, args.exec_, max(3, args.steps // 2), 1)
+        grids = grids_host = None
+        gbytes = 0
+        if args.mode == "nonrigid":
+            nx, ny, _ = B.grid_dims(W, H, cfg.grid, cfg.levels)
+            grids = torch.empty((N - 1, ny, nx, 2), device=dev)
+            grids_host = torch.empty((N - 1, ny, nx, 2), pin_memory=True)
+            gbytes = grids.numel() * 4
+        ems, _, _ = timed(ctx, host, args.exec_, max(2, args.steps // 2), 1, grids=grids, grids_host=grids_host)
         n_nodes = (N - 1) + B.scan_work("brent_kung", N - 1)
-        d2h = 4 * N * levels + 16 + 24 * n_nodes + 144 * n_ops + 20 * (N - 1)
-        e2e = {"value": round(world * (N - 1) / (ems / 1e3), 2), "unit": UNIT,
+        d2h = 4 * N * levels + 16 + 24 * n_nodes + 144 * n_ops + 20 * (N - 1) + gbytes
+        e2e = {"value": round(job_rate(N - 1, world, ems), 2), "unit": UNIT,
                "h2d_bytes_per_step": int(N * H * W * 4), "d2h_bytes_per_step": int(d2h)}
+        del grids, grids_host, host
         # ---- the other deformation model on the same workload
         omode = "rigid" if args.mode == "nonrigid" else "nonrigid"
-        octx, ofields, otuned = make_ctx(omode)
-        oms, ost, _ = timed(octx, ofields, frames, args.exec_, max(3, args.steps // 2), 2)
-        obms, _, _ = timed(octx, ofields, frames, "persistent", max(3, args.steps // 2), 2)
+        octx, otuned = make_ctx(omode, [args.exec_])
+        oms, ost, _ = timed(octx, frames, args.exec_, max(2, args.steps // 2), 2)
         oev = np.array([sum(s["evals"]) for s in ost[0]])
-        other = {"mode": omode, "value": round(world * (N - 1) / (oms / 1e3), 2), "unit": UNIT,
-                 "exec": args.exec_, "batched_value": round(world * (N - 1) / (obms / 1e3), 2),
-                 "evals_per_operator": {"mean": round(float(oev.mean()), 2), "max": int(oev.max())},
+        other = {"mode": omode, "value": round(job_rate(N - 1, world, oms), 2), "unit": UNIT,
+                 "exec": args.exec_, "evals_per_operator": {"mean": round(float(oev.mean()), 2),
+                                                            "max": int(oev.max())},
                  "cluster": otuned}
         del octx
         if rank == 0:
             # ---- serving: eight Poisson streams, online registration, p50/p99 latency
-            serve = {m: serving(dev, m, args.serve_frames) for m in (args.mode, omode)}
+            serve = {args.mode: serving(dev, args.mode, args.serve_frames),
+                     omode: serving(dev, omode, min(args.serve_frames, 256))}
             # ---- precision forms: pyramid storage fp32 / bf16 / fp16
             prec = precision(frames, args.mode)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and not args.quick and world == 1:
-        fr = frames.cpu().numpy()
+        fr = frames[:min(N, 1200)].cpu().numpy()   # as many frames as a bounded sample reaches
         ops1, dt1, sample1 = oracle_sample(fr, cfg, args.oracle_budget)
         opsp, dtp, cores, samplep = oracle_sample_parallel(fr, cfg, args.oracle_budget)
         scale = (N - 1) / n_ops
@@ -663,21 +722,25 @@ def main():
             "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "frames": N, "H": H,
                        "W": W, "mode": args.mode, "levels": levels, "schedule": "brent_kung",
                        "exec": args.exec_, "cluster": args.cluster or {"autotuned": tuned},
+                       "image_model": "quadratic B-spline (nonrigid energy), bilinear (rigid energy)",
+                       "stop": f"metric gradient norm < {cfg.tol_grad:g}, at most {cfg.max_iter} steps per level",
                        "l2": "inputs larger than L2 (frames %d MiB > 129 MB L2)" % (N * H * W * 4 >> 20),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "ops_per_s": round(ops_per_s, 2), "operators_per_step": n_ops,
-            "evals_per_operator": {"mean": round(float(ev.mean()), 2), "max": int(ev.max())},
+            "evals_per_operator": {"mean": round(float(ev.mean()), 2), "max": int(ev.max()),
+                                   "A": round(float(ev_a.mean()), 2), "B": round(float(ev_b.mean()), 2)},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback 6.8 TB/s",
-                         "kernel": "op_kernel (operator kernel)", "algorithmic_bytes_per_step": alg,
+                         "kernel": f"{kname} (operator kernel)", "algorithmic_bytes_per_step": alg,
                          "kernel_ms_per_step": round(kms, 3), "launches_per_step": launches,
-                         "caveat": "issue-bound, not DRAM-bound: in the committed ncu captures the two "
-                                   "pyramids of an operator stay in L2 (about 90 % hit rate, DRAM about "
-                                   "0.1 % busy) and the kernel issues on about 55 % of cycles with the ALU "
-                                   "pipe busiest; the algorithmic bytes come from L2 about 150 times over"},
-            "batched": batched,
+                         "caveat": "issue-bound, not DRAM-bound: the two pyramids of an operator stay in L2 "
+                                   "(see the committed ncu summaries); the algorithmic bytes are read from L2 "
+                                   "many times over"},
+            "forms": forms,
+            "phases": phases,
+            "imbalance": imbalance,
             "registered_series": reg_series,
             "other_mode": other,
             "serving": serve,
@@ -692,6 +755,31 @@ def main():
         dist.destroy_process_group()
 
 
+def imbalance_metric(evals, segments):
+    """The load-imbalance measure of Sec. 3.2 on measured work: the series' neighbour operators A
+    cut into S contiguous segments (as ranks would hold them); per segment the work T_s = sum of
+    its operators' energy evaluations; imbalance = (max_s T_s - mean) / mean."""
+    import numpy as np
+    out = {}
+    ev = np.asarray(evals, dtype=np.float64)
+    for S in segments:
+        if S > len(ev):
+            continue
+        T = np.array([seg.sum() for seg in np.array_split(ev, S)])
+        out[str(S)] = round(float((T.max() - T.mean()) / T.mean()), 4)
+    return {"segments": out, "work": "energy evaluations per operator A(f_i, f_i+1)",
+            "per_operator": {"mean": round(float(ev.mean()), 2), "max": int(ev.max()),
+                             "cv": round(float(ev.std() / ev.mean()), 4)}}
+
+
+def render_prefix(spec, n):
+    """Frames 0..n-1 of the series ``spec`` describes (the same parameters as the full series)."""
+    import numpy as np
+    from paper_2010_12478_gb300 import synth
+    phase, shifts, modes, snr = synth._draw_parameters(spec)
+    return np.stack([synth.render_frame(spec, phase, shifts[t], modes, t, float(snr[t])).numpy() for t in range(n)])
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
     if rank != 0:
@@ -700,9 +788,10 @@ def run_reference(args, world, rank):
     from paper_2010_12478_gb300 import binding as B
     from paper_2010_12478_gb300 import synth
     spec = workload_spec(args.workload, 0)
-    ser = synth.make_series(spec, device="cpu")
-    fr = ser.frames.numpy()
-    N = fr.shape[0]
+    N = spec.n_frames
+    # the frames a bounded sample can reach (frame triples from the start of the series), rendered
+    # exactly as in the full series
+    fr = render_prefix(spec, min(N, 1200))
     n_ops = (N - 1) + len(__import__("oracle").dag_brent_kung(N - 1).ops)
     cfg = B.Config(mode=args.mode)
     budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
@@ -720,8 +809,10 @@ def run_reference(args, world, rank):
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * tot_dt / args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "mode": args.mode,
-                       "levels": cfg.levels, "schedule": "brent_kung"},
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "frames": N,
+                       "H": spec.H, "W": spec.W, "mode": args.mode, "levels": cfg.levels, "schedule": "brent_kung",
+                       "image_model": "quadratic B-spline (nonrigid energy), bilinear (rigid energy)",
+                       "stop": f"metric gradient norm < {cfg.tol_grad:g}, at most {cfg.max_iter} steps per level"},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step: {sample} (about {budget:.0f} s); frames/s = operators/s x "
                                        f"{N - 1}/{n_ops}"},

@@ -19,7 +19,10 @@
  *                 a grid of spacing s (finest pixels) at points (jx s, jy s),
  *                 jx < nx = ceil((W-1)/s) + 1; energy 1 - NCC + lambda/(2P) sum over
  *                 control-grid edges |c_a - c_b|^2 (an extension: the paper's
- *                 deformation is rigid).  Control values are stored as (x, y) float
+ *                 deformation is rigid).  Both frames enter this energy through the
+ *                 quadratic B-spline model of their samples (edges replicated), a
+ *                 continuously differentiable image; the rigid energy samples the
+ *                 frames bilinearly.  Control values are stored as (x, y) float
  *                 pairs, row-major [ny][nx]; dense fields as planes [2][H][W].
  *
  * Conventions common to every entry point:
@@ -83,6 +86,12 @@ extern "C" {
                                    launch cost.  The graph is rebuilt when N, the schedule, the
                                    frame geometry or a workspace changes. */
 
+/* OR into `exec` of reg_scan / reg_scan_batch (not with REG_EXEC_GRAPH): every neighbour
+ * operator A runs to completion before the first B, and with timing enabled the two phases are
+ * timed separately (reg_timing_t.leaf_ms, dag_ms).  The paper reports the scan of B alone and
+ * the full registration with the A's before it (Sec. 5.2, its scan and full speedup bounds). */
+#define REG_EXEC_SPLIT_PHASES 0x100
+
 #define REG_MAX_LEVELS 8
 
 /* why a level stopped (reg_stats_t.stop) */
@@ -107,8 +116,9 @@ typedef struct {
     int    levels;        /* pyramid levels, 1..REG_MAX_LEVELS */
     int    max_iter;      /* accepted gradient-flow steps per level */
     int    max_rejects;   /* rejected Armijo trials allowed per step */
-    double tol_grad;      /* stop: metric norm of the descent direction */
-    double tol_rel_e;     /* stop: relative energy decrease of an accepted step */
+    double tol_grad;      /* stop: metric norm of the descent direction (default 1e-4) */
+    double tol_rel_e;     /* stop: relative energy decrease of an accepted step; 0 (default)
+                             stops only on an accepted step that does not lower E at all */
     double armijo_c;      /* sufficient-decrease constant */
     double tau0;          /* first trial step of each level */
     double step_cap;      /* largest step, pixels of the current level */
@@ -146,7 +156,8 @@ typedef struct {
 
 /* ---- configuration and context ----------------------------------------- */
 
-/* Fill *cfg with the defaults (rigid, 2 levels, FP32 storage, auto tiles). */
+/* Fill *cfg with the defaults (rigid, 2 levels, FP32 storage, auto tiles; stop on a metric
+ * gradient norm below 1e-4, at most 500 accepted steps per level). */
 void reg_config_default(reg_config_t *cfg);
 
 /* Create a context on CUDA device `device`.  The context owns its pyramids,
@@ -204,9 +215,19 @@ int reg_scan_batch(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int
 /* Control values of the N-1 prefixes phi_{0,1}..phi_{0,N-1} of the last
  * successful REG_NONRIGID reg_scan on ctx: grids_out, device, [N-1][ny][nx]
  * (x, y) pairs, ny/nx from reg_grid_dims for that scan's W, H.  n_out (host,
- * optional) receives N-1.  Errors: REG_ESTATE if ctx has no nonrigid scan
- * result; REG_EINVAL for a host grids_out. */
+ * optional) receives N-1.  A later reg_pairwise or reg_energy on ctx ends the
+ * availability.  Errors: REG_ESTATE if ctx has no nonrigid scan result;
+ * REG_EINVAL for a host grids_out. */
 int reg_scan_grids(reg_ctx_t *ctx, float *grids_out, int *n_out, void *stream);
+
+/* Control values of chosen operators' results of the last successful REG_NONRIGID reg_scan
+ * or reg_scan_batch on ctx (inspection of the scan's intermediate deformations, e.g. a B
+ * operator's inputs).  ops (host) holds n operator indices in the per_op order of that call:
+ * leaves A(f_j, f_{j+1}) first, then the B operators in DAG order (series-major for a batch).
+ * grids_out: device, [n][ny][nx] (x, y) pairs.  A later reg_pairwise or reg_energy on ctx
+ * reuses the node storage and ends the availability.  Errors: REG_ESTATE without such a
+ * result; REG_EINVAL for an index out of range or a host grids_out. */
+int reg_scan_node_grids(reg_ctx_t *ctx, const int32_t *ops, int n, float *grids_out, void *stream);
 
 /* Registered series and its average [Sec. 2: every frame of the series is
  * registered to the first one, then the series is averaged].
@@ -353,6 +374,9 @@ typedef struct {
                                   replayed the cached one (always 0 for the other executors) */
     int32_t tma_staged;        /* reg_warp: 1 if the source tiles were staged in shared memory
                                   by TMA, 0 if sampled from global memory */
+    int32_t leaf_ops, dag_ops; /* REG_EXEC_SPLIT_PHASES: operators A (DAG depth 0) and B */
+    double  leaf_ms, dag_ms;   /* REG_EXEC_SPLIT_PHASES with timing: device time of the A phase and
+                                  of the B phase (same method as op_kernel_ms) */
 } reg_timing_t;
 
 /* Enable (1) or disable (0) event timing of the kernels launched by later calls. */

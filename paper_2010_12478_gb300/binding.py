@@ -22,6 +22,7 @@ RIGID, NONRIGID = 0, 1
 F32, BF16, F16 = 0, 1, 2
 SCHEDULES = {"sequential": 0, "brent_kung": 1, "dissemination": 2, "ladner_fischer": 3}
 EXECS = {"plain": 0, "level": 1, "persistent": 2, "graph": 3}
+SPLIT_PHASES = 0x100   # OR into an executor: A leaves before the first B, phases timed apart
 STORAGES = {"f32": F32, "bf16": BF16, "f16": F16}
 MAX_LEVELS = 8
 
@@ -31,7 +32,7 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
            "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load",
-           "reg_scan_grids", "reg_warp", "reg_scan_batch"]
+           "reg_scan_grids", "reg_warp", "reg_scan_batch", "reg_scan_node_grids"]
 
 
 class RegError(RuntimeError):
@@ -63,7 +64,9 @@ class reg_stats_t(ctypes.Structure):
 class reg_timing_t(ctypes.Structure):
     _fields_ = [("op_launches", ctypes.c_int32), ("pyramid_launches", ctypes.c_int32),
                 ("op_kernel_ms", ctypes.c_double), ("pyramid_ms", ctypes.c_double),
-                ("graph_captures", ctypes.c_int32), ("tma_staged", ctypes.c_int32)]
+                ("graph_captures", ctypes.c_int32), ("tma_staged", ctypes.c_int32),
+                ("leaf_ops", ctypes.c_int32), ("dag_ops", ctypes.c_int32),
+                ("leaf_ms", ctypes.c_double), ("dag_ms", ctypes.c_double)]
 
 
 class reg_result_t(ctypes.Structure):
@@ -103,6 +106,7 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(reg_stats_t), vp]
         L.reg_autotune.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(ip)]
         L.reg_scan_grids.argtypes = [vp, fp, ctypes.POINTER(ip), vp]
+        L.reg_scan_node_grids.argtypes = [vp, vp, ip, fp, vp]
         L.reg_scan_batch.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ip, vp, fp, ctypes.POINTER(reg_stats_t), vp]
         L.reg_warp.argtypes = [vp, fp, ip, ip, ip, ip, ctypes.POINTER(reg_elem_t), fp, fp, fp, vp]
         L.reg_autotune_save.argtypes = [vp, ctypes.c_char_p]
@@ -145,8 +149,8 @@ class Config:
     levels: int = 2
     max_iter: int = 500
     max_rejects: int = 30
-    tol_grad: float = 1e-5
-    tol_rel_e: float = 1e-10
+    tol_grad: float = 1e-4
+    tol_rel_e: float = 0.0
     armijo_c: float = 0.25
     tau0: float = 1.0
     step_cap: float = 0.5
@@ -225,7 +229,8 @@ class Context:
         check(lib().reg_ctx_last_timing(self.h, ctypes.byref(t)), "reg_ctx_last_timing")
         return dict(op_launches=t.op_launches, pyramid_launches=t.pyramid_launches,
                     op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms, graph_captures=t.graph_captures,
-                    tma_staged=t.tma_staged)
+                    tma_staged=t.tma_staged, leaf_ops=t.leaf_ops, dag_ops=t.dag_ops, leaf_ms=t.leaf_ms,
+                    dag_ms=t.dag_ms)
 
     # ---- operators
     def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,
@@ -246,14 +251,16 @@ class Context:
         return (out.i, out.k, out.alpha, out.gx, out.gy), stats_dict(st, self.cfg.levels)
 
     def scan(self, frames, schedule: str = "brent_kung", exec: str = "level", fields_out=None,
-             out_elems=None, want_stats: bool = True, stream=None):
+             out_elems=None, want_stats: bool = True, stream=None, split: bool = False):
+        """reg_scan; split=True runs every A leaf before the first B and times the phases apart."""
         N, H, W = frames.shape
         n = N - 1
         m = scan_work(schedule, n)
         elems = (reg_elem_t * n)() if out_elems is None else None
         stats = (reg_stats_t * (n + m))() if want_stats else None
         out_ptr = ctypes.addressof(elems) if elems is not None else _ptr(out_elems)
-        check(lib().reg_scan(self.h, _ptr(frames), N, W, H, W, SCHEDULES[schedule], EXECS[exec], out_ptr,
+        ex = EXECS[exec] | (SPLIT_PHASES if split else 0)
+        check(lib().reg_scan(self.h, _ptr(frames), N, W, H, W, SCHEDULES[schedule], ex, out_ptr,
                              _ptr(fields_out), stats, _stream(stream)), "reg_scan")
         el = [(e.i, e.k, e.alpha, e.gx, e.gy) for e in elems] if elems is not None else None
         st = [stats_dict(s, self.cfg.levels) for s in stats] if stats is not None else None
@@ -281,6 +288,12 @@ class Context:
         n = ctypes.c_int()
         check(lib().reg_scan_grids(self.h, _ptr(out), ctypes.byref(n), None), "reg_scan_grids")
         return n.value
+
+    def scan_node_grids(self, ops: Sequence[int], out):
+        """Control values [len(ops), ny, nx, 2] (device) of the given operators' results of the last
+        nonrigid scan (per_op order: leaves first, then B operators in DAG order)."""
+        idx = np.ascontiguousarray(np.asarray(ops, dtype=np.int32))
+        check(lib().reg_scan_node_grids(self.h, idx.ctypes.data, len(idx), _ptr(out), None), "reg_scan_node_grids")
 
     def warp(self, frames, elems=None, grids=None, out=None, mean=None, stream=None):
         """Registered series out[k] = f_k o phi_{0,k} and/or its mean (device tensors).

@@ -263,7 +263,8 @@ struct reg_ctx {
     std::mutex mu;
     // workspaces
     DevBuf frames_dev;      // host-supplied frames staged on the device
-    DevBuf pyr[kMaxLevels]; // pyramid levels of all frames
+    DevBuf pyr[kMaxLevels]; // pyramid levels of all frames (nonrigid: with a replicated border)
+    DevBuf spyr[kMaxLevels]; // nonrigid: the B-spline model of every level at its pixel centres
     DevBuf means, level_tab, ops, stats, node_theta, node_grid, status, node_ids;
     DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr;
     DevBuf tmp;
@@ -274,6 +275,8 @@ struct reg_ctx {
     // REG_EXEC_GRAPH: the captured plain-path launches and the plan they were captured for
     // last successful nonrigid reg_scan: prefixes' node indices are in node_ids
     int last_n = 0, last_gnx = 0, last_gny = 0;
+    std::vector<int> last_op_nodes;   // node produced by each operator, in per_op order
+    DevBuf pick_ids;                  // reg_scan_node_grids: node indices of one request
     DevBuf warp_ws;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture = nullptr;   // graphs are captured here (the caller's stream may be the legacy one)
@@ -286,6 +289,8 @@ struct reg_ctx {
     std::vector<cudaEvent_t> tev;   // timing events, used in pairs
     size_t tev_used = 0;
     std::vector<std::pair<int, int>> op_pairs, pyr_pairs;
+    size_t split_from = 0, split_at = 0;   // REG_EXEC_SPLIT_PHASES: op_pairs [from, at) = A, [at, end) = B
+    bool split = false;
     reg_timing_t last = {};
 };
 
@@ -297,8 +302,8 @@ extern "C" void reg_config_default(reg_config_t *c)
     c->levels = 2;
     c->max_iter = 500;
     c->max_rejects = 30;
-    c->tol_grad = 1e-5;
-    c->tol_rel_e = 1e-10;
+    c->tol_grad = 1e-4;
+    c->tol_rel_e = 0.0;
     c->armijo_c = 0.25;
     c->tau0 = 1.0;
     c->step_cap = 0.5;
@@ -317,6 +322,7 @@ static int validate_cfg(const reg_config_t &c)
     if (c.max_iter < 0 || c.max_rejects < 0) return fail(REG_EINVAL, "negative iteration limits");
     if (!(c.tau0 > 0) || !(c.step_cap > 0) || !(c.armijo_c > 0 && c.armijo_c < 1))
         return fail(REG_EINVAL, "tau0/step_cap/armijo_c out of range");
+    if (!(c.tol_grad >= 0) || !(c.tol_rel_e >= 0)) return fail(REG_EINVAL, "tol_grad/tol_rel_e must be >= 0");
     if (c.storage != REG_F32 && c.storage != REG_BF16 && c.storage != REG_F16)
         return fail(REG_EINVAL, "storage %d", c.storage);
     if (c.cluster != 0 && c.cluster != 1 && c.cluster != 2 && c.cluster != 4 && c.cluster != 8 && c.cluster != 16)
@@ -386,6 +392,8 @@ void timing_reset(reg_ctx *ctx)
     ctx->tev_used = 0;
     ctx->op_pairs.clear();
     ctx->pyr_pairs.clear();
+    ctx->split = false;
+    ctx->split_from = ctx->split_at = 0;
     memset(&ctx->last, 0, sizeof(ctx->last));
 }
 
@@ -416,6 +424,12 @@ void timing_resolve(reg_ctx *ctx)
     };
     ctx->last.op_kernel_ms = sum(ctx->op_pairs);
     ctx->last.pyramid_ms = sum(ctx->pyr_pairs);
+    if (ctx->split) {
+        std::vector<std::pair<int, int>> a(ctx->op_pairs.begin() + ctx->split_from, ctx->op_pairs.begin() + ctx->split_at);
+        std::vector<std::pair<int, int>> b(ctx->op_pairs.begin() + ctx->split_at, ctx->op_pairs.end());
+        ctx->last.leaf_ms = sum(a);
+        ctx->last.dag_ms = sum(b);
+    }
 }
 
 struct Geometry {
@@ -481,25 +495,34 @@ Config dev_config(const reg_config_t &c)
 
 // Build the pyramids of `nf` frames (device fp32, frame f at frames + f*fstride,
 // rows of `pitch`) into ctx->pyr starting at frame slot `first`, and fill the
-// level table rows of those frames.  `total` frames are reserved.
+// level table rows of those frames.  `total` frames are reserved.  The nonrigid
+// model stores every level with a replicated border (its B-spline window) and the
+// model at the pixel centres (its reference role) beside it.
 int build_pyramids(reg_ctx *ctx, const Geometry &g, const float *frames, int nf, size_t fstride, int pitch,
                    int first, int total, cudaStream_t s)
 {
     const int L = g.levels;
     const size_t sb = storage_bytes(ctx->cfg.storage);
-    void *base[kMaxLevels];
-    size_t stride[kMaxLevels];
+    const bool nonrigid = ctx->cfg.mode == REG_NONRIGID;
+    PyrOut o;
+    memset(&o, 0, sizeof(o));
+    o.pad = nonrigid ? kPad : 0;
     for (int l = 0; l < L; ++l) {
-        stride[l] = (size_t)g.W[l] * g.H[l];
-        CHECK(ctx->pyr[l].reserve(stride[l] * sb * total));
-        base[l] = (char *)ctx->pyr[l].ptr + stride[l] * sb * first;
+        o.raw_stride[l] = level_elems(g.W[l], g.H[l], o.pad);
+        CHECK(ctx->pyr[l].reserve(o.raw_stride[l] * sb * total));
+        o.raw[l] = (char *)ctx->pyr[l].ptr + o.raw_stride[l] * sb * first;
+        if (nonrigid) {
+            o.smooth_stride[l] = (size_t)g.W[l] * g.H[l];
+            CHECK(ctx->spyr[l].reserve(o.smooth_stride[l] * sb * total));
+            o.smooth[l] = (char *)ctx->spyr[l].ptr + o.smooth_stride[l] * sb * first;
+        }
     }
     CHECK(ctx->means.reserve(sizeof(float) * (size_t)total * L));
     int e0 = timing_mark(ctx, s);
-    CU(launch_pyramid(frames, nf, fstride, g.W[0], g.H[0], pitch, L, ctx->cfg.storage, base, stride,
+    CU(launch_pyramid(frames, nf, fstride, g.W[0], g.H[0], pitch, L, ctx->cfg.storage, o,
                       ctx->means.as<float>() + (size_t)first * L, s));
     ctx->pyr_pairs.push_back({e0, timing_mark(ctx, s)});
-    ctx->last.pyramid_launches += 2 * L;
+    ctx->last.pyramid_launches += (nonrigid ? 4 : 2) * L;
     return REG_OK;
 }
 
@@ -508,6 +531,7 @@ int build_level_table(reg_ctx *ctx, const Geometry &g, int total, cudaStream_t s
 {
     const int L = g.levels;
     const size_t sb = storage_bytes(ctx->cfg.storage);
+    const int pad = ctx->cfg.mode == REG_NONRIGID ? kPad : 0;
     std::vector<float> means((size_t)total * L);
     CU(cudaMemcpyAsync(means.data(), ctx->means.ptr, sizeof(float) * means.size(), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -515,10 +539,18 @@ int build_level_table(reg_ctx *ctx, const Geometry &g, int total, cudaStream_t s
     for (int f = 0; f < total; ++f)
         for (int l = 0; l < L; ++l) {
             LevelDesc &d = tab[(size_t)f * L + l];
-            d.ptr = (const char *)ctx->pyr[l].ptr + (size_t)g.W[l] * g.H[l] * sb * f;
+            const size_t raw = level_elems(g.W[l], g.H[l], pad);
+            d.ptr = (const char *)ctx->pyr[l].ptr + (raw * f + level_origin(g.W[l], pad)) * sb;
             d.W = g.W[l];
             d.H = g.H[l];
-            d.pitch = g.W[l];
+            d.pitch = level_pitch(g.W[l], pad);
+            if (pad) {
+                d.rptr = (const char *)ctx->spyr[l].ptr + (size_t)g.W[l] * g.H[l] * sb * f;
+                d.rpitch = g.W[l];
+            } else {
+                d.rptr = d.ptr;
+                d.rpitch = d.pitch;
+            }
             d.mean = means[(size_t)f * L + l];
         }
     CHECK(ctx->level_tab.reserve(sizeof(LevelDesc) * tab.size()));
@@ -696,10 +728,9 @@ int launch_plain(reg_ctx *ctx, const ScanPlan &plan, const Params &p, int C, cud
     for (int e = 0; e < n_ops; ++e) {
         cudaStream_t ls = ctx->pool[e % kPoolStreams];
         const OpDesc &op = plan.ops[e];
-        if (op.left >= 0) {
-            CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.left]], 0));
-            CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.right]], 0));
-        }
+        // inputs produced by an earlier launch on s are complete: the pool forked from s after it
+        if (op.left >= 0 && node_op[op.left] >= 0) CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.left]], 0));
+        if (op.left >= 0 && node_op[op.right] >= 0) CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.right]], 0));
         Params q = p;
         q.op_base = e;
         CU(launch_ops(q, storage, C, 1, ls));
@@ -788,27 +819,30 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
     }
     if (exec == REG_EXEC_PERSISTENT) {
         // consumers (CSR by node) and pending counts
-        std::vector<int> pending(n_ops, 0), cstart(p.n_nodes + 1, 0), cons;
+        // an operator waits for the inputs that operators of this launch produce (inputs of an
+        // earlier launch on the same stream are complete)
+        std::vector<int> pending(n_ops, 0), cstart(p.n_nodes + 1, 0), cons, node_made(p.n_nodes, 0);
         std::vector<int> ready;
+        for (int e = 0; e < n_ops; ++e) node_made[plan.ops[e].out] = 1;
         for (int e = 0; e < n_ops; ++e) {
             const OpDesc &op = plan.ops[e];
             if (op.left >= 0) {
-                pending[e] = 2;
-                cstart[op.left + 1]++;
-                cstart[op.right + 1]++;
-            } else {
-                ready.push_back(e);
+                for (int v : {op.left, op.right})
+                    if (node_made[v]) {
+                        pending[e] += 1;
+                        cstart[v + 1]++;
+                    }
             }
+            if (pending[e] == 0) ready.push_back(e);
         }
         for (int v = 0; v < p.n_nodes; ++v) cstart[v + 1] += cstart[v];
         cons.assign(std::max(1, cstart[p.n_nodes]), 0);
         std::vector<int> fillp(cstart.begin(), cstart.end() - 1);
         for (int e = 0; e < n_ops; ++e) {
             const OpDesc &op = plan.ops[e];
-            if (op.left >= 0) {
-                cons[fillp[op.left]++] = e;
-                cons[fillp[op.right]++] = e;
-            }
+            if (op.left >= 0)
+                for (int v : {op.left, op.right})
+                    if (node_made[v]) cons[fillp[v]++] = e;
         }
         // Host-side fault injection for tests: REG_FAULT_INJECT=stuck_op keeps the last operator
         // waiting for an input that never arrives, so the device queue's bounded wait must give
@@ -861,6 +895,47 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
         return REG_OK;
     }
     return fail(REG_EINVAL, "exec %d", exec);
+}
+
+// The operators [b, e) of a plan (whole DAG depths) as a plan of their own, with Params whose
+// descriptors and stats start at operator b.
+void sub_plan(const ScanPlan &plan, const Params &p, int b, int e, ScanPlan &sub, Params &q)
+{
+    sub.ops.assign(plan.ops.begin() + b, plan.ops.begin() + e);
+    sub.user_index.assign(plan.user_index.begin() + b, plan.user_index.begin() + e);
+    sub.depth_start.clear();
+    for (int v : plan.depth_start)
+        if (v >= b && v <= e && (sub.depth_start.empty() || v - b != sub.depth_start.back()))
+            sub.depth_start.push_back(v - b);
+    sub.n_nodes = plan.n_nodes;
+    sub.out_nodes = plan.out_nodes;
+    q = p;
+    q.ops = p.ops + b;
+    q.stats = p.stats + b;
+    q.n_ops = e - b;
+}
+
+// REG_EXEC_SPLIT_PHASES: every A leaf (DAG depth 0) runs to completion before the first B,
+// and the two phases are timed separately (the paper's "full" vs "scan" registration).
+int execute_split(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, cudaStream_t s)
+{
+    const int n_ops = (int)plan.ops.size();
+    const int nl = plan.depth_start.size() > 1 ? plan.depth_start[1] : n_ops;
+    const size_t k0 = ctx->op_pairs.size();
+    ctx->split_at = k0;
+    for (int phase = 0; phase < 2; ++phase) {
+        const int b = phase == 0 ? 0 : nl, e = phase == 0 ? nl : n_ops;
+        if (b == e) continue;
+        ScanPlan sub;
+        Params q;
+        sub_plan(plan, p, b, e, sub, q);
+        CHECK(execute(ctx, sub, q, exec, tuned, s));
+        if (phase == 0) ctx->split_at = ctx->op_pairs.size();
+    }
+    ctx->split_from = k0;
+    ctx->last.leaf_ops = nl;
+    ctx->last.dag_ops = n_ops - nl;
+    return REG_OK;
 }
 
 int copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s)
@@ -928,8 +1003,12 @@ int scan_impl(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, i
     if (S < 1) return fail(REG_EINVAL, "need S >= 1 series, got %d", S);
     if (N < 2) return fail(REG_EINVAL, "need N >= 2 frames, got %d", N);
     if (pitch < W) return fail(REG_EINVAL, "pitch %d < W %d", pitch, W);
+    const bool split = (exec & REG_EXEC_SPLIT_PHASES) != 0;
+    exec &= ~REG_EXEC_SPLIT_PHASES;
     if (exec != REG_EXEC_PLAIN && exec != REG_EXEC_LEVEL && exec != REG_EXEC_PERSISTENT && exec != REG_EXEC_GRAPH)
         return fail(REG_EINVAL, "exec %d", exec);
+    if (split && exec == REG_EXEC_GRAPH)
+        return fail(REG_EINVAL, "REG_EXEC_SPLIT_PHASES is not available with REG_EXEC_GRAPH");
     std::lock_guard<std::mutex> lock(ctx->mu);
     CU(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -960,7 +1039,13 @@ int scan_impl(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, i
     Params p;
     CHECK(prepare_params(ctx, g, NF, plan.n_nodes, n_ops, p, s));
     CU(cudaMemcpyAsync(ctx->ops.ptr, plan.ops.data(), sizeof(OpDesc) * n_ops, cudaMemcpyHostToDevice, s));
-    CHECK(execute(ctx, plan, p, exec, ctx->cfg.cluster > 0 ? 0 : tuned_cluster(ctx, W, H, exec, NF), s));
+    const int tuned = ctx->cfg.cluster > 0 ? 0 : tuned_cluster(ctx, W, H, exec, NF);
+    if (split) {
+        ctx->split = true;
+        CHECK(execute_split(ctx, plan, p, exec, tuned, s));
+    } else {
+        CHECK(execute(ctx, plan, p, exec, tuned, s));
+    }
     CU(cudaGetLastError());
     CHECK(check_device_status(ctx, s));
 
@@ -1016,6 +1101,8 @@ int scan_impl(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, i
         ctx->last_n = nout;
         ctx->last_gnx = p.gnx;
         ctx->last_gny = p.gny;
+        ctx->last_op_nodes.assign(n_ops, 0);
+        for (int e = 0; e < n_ops; ++e) ctx->last_op_nodes[plan.user_index[e]] = plan.ops[e].out;
     }
     return REG_OK;
 }
@@ -1048,6 +1135,28 @@ extern "C" int reg_scan_grids(reg_ctx_t *ctx, float *grids_out, int *n_out, void
                           ctx->last_gnx * ctx->last_gny, (float2 *)grids_out, s));
     CU(cudaStreamSynchronize(s));
     if (n_out) *n_out = ctx->last_n;
+    return REG_OK;
+}
+
+extern "C" int reg_scan_node_grids(reg_ctx_t *ctx, const int32_t *ops, int n, float *grids_out, void *stream)
+{
+    if (!ctx || !ops || !grids_out || n < 1) return fail(REG_EINVAL, "NULL argument or n < 1");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ctx->last_n <= 0) return fail(REG_ESTATE, "no nonrigid scan result on this context");
+    CU(cudaSetDevice(ctx->device));
+    if (!is_device_ptr(grids_out)) return fail(REG_EINVAL, "grids_out must be device memory");
+    std::vector<int> nodes(n);
+    for (int q = 0; q < n; ++q) {
+        if (ops[q] < 0 || ops[q] >= (int)ctx->last_op_nodes.size())
+            return fail(REG_EINVAL, "operator %d not in 0..%zu", ops[q], ctx->last_op_nodes.size() - 1);
+        nodes[q] = ctx->last_op_nodes[ops[q]];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CHECK(ctx->pick_ids.reserve(sizeof(int) * n));
+    CU(cudaMemcpyAsync(ctx->pick_ids.ptr, nodes.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CU(launch_grid_gather(ctx->node_grid.as<float2>(), ctx->pick_ids.as<int>(), n, ctx->last_gnx * ctx->last_gny,
+                          (float2 *)grids_out, s));
+    CU(cudaStreamSynchronize(s));
     return REG_OK;
 }
 
@@ -1127,6 +1236,7 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     Geometry g;
     CHECK(geometry(W, H, ctx->cfg.levels, g));
     timing_reset(ctx);
+    ctx->last_n = 0;   // the node storage of the last scan is reused below
     const size_t fbytes = sizeof(float) * (size_t)H * pitch;
     // staged R and T, then (nonrigid) one dense field for the initial guess or the result
     CHECK(ctx->frames_dev.reserve(2 * fbytes + (nonrigid ? sizeof(float) * 2 * (size_t)W * H : 0)));
@@ -1201,15 +1311,15 @@ extern "C" int reg_pyramid(reg_ctx_t *ctx, const float *frame, int W, int H, int
     std::lock_guard<std::mutex> lock(ctx->mu);
     CU(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    void *base[kMaxLevels];
-    size_t stride[kMaxLevels];
+    PyrOut o;
+    memset(&o, 0, sizeof(o));
     size_t off = 0;
     for (int l = 0; l < levels; ++l) {
-        stride[l] = (size_t)g.W[l] * g.H[l];
-        base[l] = (char *)out + off;
-        off += stride[l] * storage_bytes(storage);
+        o.raw_stride[l] = (size_t)g.W[l] * g.H[l];
+        o.raw[l] = (char *)out + off;
+        off += o.raw_stride[l] * storage_bytes(storage);
     }
-    CU(launch_pyramid(frame, 1, (size_t)H * pitch, W, H, pitch, levels, storage, base, stride, nullptr, s));
+    CU(launch_pyramid(frame, 1, (size_t)H * pitch, W, H, pitch, levels, storage, o, nullptr, s));
     CU(cudaStreamSynchronize(s));
     return REG_OK;
 }
@@ -1227,6 +1337,7 @@ extern "C" int reg_energy(reg_ctx_t *ctx, const float *R, const float *T, int W,
     CU(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     reg_config_t saved = ctx->cfg;
+    ctx->last_n = 0;   // the node storage of the last scan is reused below
     ctx->cfg.levels = 1;
     ctx->cfg.storage = REG_F32;
     Geometry g;

@@ -15,9 +15,30 @@ constexpr int kThreads = 256;          // threads per CTA of the operator kernel
 
 // One pyramid level of one frame, as the operator kernels read it.
 struct LevelDesc {
-    const void *ptr;   // storage-typed pixels, row-major
-    int W, H, pitch;   // pitch in elements
-    float mean;        // level mean (FP32 shift constant of the moment sums)
+    const void *ptr;    // template role: storage-typed samples, row-major, pixel (0, 0)
+    const void *rptr;   // reference role: the same samples (rigid model) or the B-spline model
+                        // at the pixel centres (nonrigid model)
+    int W, H, pitch;    // pitch of ptr, in elements
+    int rpitch;         // pitch of rptr, in elements
+    float mean;         // level mean (FP32 shift constant of the moment sums)
+};
+
+// Pyramid layout.  The nonrigid model samples the quadratic B-spline of a level's samples with
+// edges replicated; storing every level of that model with a border of kPad replicated samples
+// on each side lets a 3x3 tap window at a nearest sample clamped to [-1, W] x [-1, H] read
+// without per-tap clamps and still equal the edge-replicated model everywhere.
+constexpr int kPad = 2;
+inline int level_pitch(int W, int pad) { return W + 2 * pad; }
+inline size_t level_elems(int W, int H, int pad) { return (size_t)(W + 2 * pad) * (H + 2 * pad); }
+inline size_t level_origin(int W, int pad) { return (size_t)pad * (W + 2 * pad) + pad; }
+
+// Where launch_pyramid writes the levels of frame 0 (frame f at + f * stride elements).
+struct PyrOut {
+    void *raw[kMaxLevels];            // start of level l's block (border included)
+    size_t raw_stride[kMaxLevels];
+    void *smooth[kMaxLevels];         // B-spline model at the pixel centres, W_l x H_l, or null
+    size_t smooth_stride[kMaxLevels];
+    int pad;                          // 0, or kPad replicated border samples around each level
 };
 
 // One operator application.  left < 0: A(f_ref, f_tmpl) from the identity (or
@@ -81,11 +102,10 @@ struct Params {
 };
 
 // Host launchers (reg_kernels.cu).
-// Pyramids of N frames: level l of frame f at level_base[l] + f * level_stride[l] (elements,
-// storage-typed); means[f * levels + l] = mean of that level.
+// Pyramids of N frames (frame f at frames + f * fstride, rows of `pitch`) into the layout `out`
+// (storage-typed); means[f * levels + l] = mean of level l of frame f (or null).
 cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, int H, int pitch, int levels,
-                           int storage, void *const *level_base, const size_t *level_stride, float *means,
-                           cudaStream_t s);
+                           int storage, const PyrOut &out, float *means, cudaStream_t s);
 cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_ops,
                        cudaStream_t s);
 cudaError_t launch_persistent(const Params &p, int storage, int cluster, int workers,

@@ -352,6 +352,49 @@ __device__ __forceinline__ float sample_cg(const float *F, int W, int H, int xi,
     return fmaf(fy, bot, (1.f - fy) * top);
 }
 
+// Quadratic B-spline model of the samples of T (storage S) at p = (xi + vx, yi + vy), with the
+// samples beyond the border replicating the edge: the image model of the nonrigid energy,
+// continuously differentiable everywhere.  With n the nearest sample and t = p - n in
+// [-1/2, 1/2) per axis, the three taps n - 1, n, n + 1 carry the weights (1/2 - t)^2 / 2,
+// 3/4 - t^2, (1/2 + t)^2 / 2 and, for the derivative, t - 1/2, -2 t, t + 1/2.  T addresses
+// pixel (0, 0) of a level stored with a replicated border of kPad >= 2 samples (row pitch Tp):
+// n clamped to [-1, W] x [-1, H] keeps the window inside the border and equals the
+// edge-replicated model for any p.
+template <typename S, bool DERIV>
+__device__ __forceinline__ float sample_q(const S *T, int W, int H, int Tp, int xi, int yi, float vx, float vy,
+                                          float &dtx, float &dty)
+{
+    vx = fminf(fmaxf(vx, -1.0e6f), 1.0e6f);   // also maps NaN into range: every access stays in bounds
+    vy = fminf(fmaxf(vy, -1.0e6f), 1.0e6f);
+    const float flx = floorf(vx), fly = floorf(vy);
+    float tx = vx - flx, ty = vy - fly;   // [0, 1), exact
+    int nx = xi + (int)flx, ny = yi + (int)fly;
+    if (tx >= 0.5f) { tx -= 1.f; ++nx; }  // nearest sample, t in [-1/2, 1/2), exact
+    if (ty >= 0.5f) { ty -= 1.f; ++ny; }
+    nx = min(max(nx, -1), W);
+    ny = min(max(ny, -1), H);
+    const S *p0 = T + (ptrdiff_t)(ny - 1) * Tp + nx;
+    const S *p1 = p0 + Tp, *p2 = p1 + Tp;
+    const float ax = 0.5f - tx, bx = 0.5f + tx, ay = 0.5f - ty, by = 0.5f + ty;
+    const float wx0 = 0.5f * ax * ax, wx1 = fmaf(-tx, tx, 0.75f), wx2 = 0.5f * bx * bx;
+    const float wy0 = 0.5f * ay * ay, wy1 = fmaf(-ty, ty, 0.75f), wy2 = 0.5f * by * by;
+    const float t00 = ldS<S>(p0 - 1), t01 = ldS<S>(p0), t02 = ldS<S>(p0 + 1);
+    const float t10 = ldS<S>(p1 - 1), t11 = ldS<S>(p1), t12 = ldS<S>(p1 + 1);
+    const float t20 = ldS<S>(p2 - 1), t21 = ldS<S>(p2), t22 = ldS<S>(p2 + 1);
+    const float a0 = fmaf(wx2, t02, fmaf(wx1, t01, wx0 * t00));
+    const float a1 = fmaf(wx2, t12, fmaf(wx1, t11, wx0 * t10));
+    const float a2 = fmaf(wx2, t22, fmaf(wx1, t21, wx0 * t20));
+    if (DERIV) {
+        const float m2x = -2.f * tx;
+        const float b0 = fmaf(bx, t02, fmaf(m2x, t01, -ax * t00));
+        const float b1 = fmaf(bx, t12, fmaf(m2x, t11, -ax * t10));
+        const float b2 = fmaf(bx, t22, fmaf(m2x, t21, -ax * t20));
+        dtx = fmaf(wy2, b2, fmaf(wy1, b1, wy0 * b0));
+        dty = fmaf(by, a2, fmaf(-2.f * ty, a1, -ay * a0));
+    }
+    return fmaf(wy2, a2, fmaf(wy1, a1, wy0 * a0));
+}
+
 // ================================================================== rigid
 // Energy pass moment slots: 0 St, 1 Stt, 2 Srt (t = T(phi(x)) - cR, r = R(x) - cR), and with
 // RSTAT (first pass of a level) 3 Sr, 4 Srr.
@@ -563,7 +606,7 @@ __device__ __forceinline__ Lvl level_of(const Params &p, int ref, int tmpl, int 
     const LevelDesc &a = p.levels[ref * p.cfg.levels + l];
     const LevelDesc &b = p.levels[tmpl * p.cfg.levels + l];
     Lvl L;
-    L.R = a.ptr; L.T = b.ptr; L.W = a.W; L.H = a.H; L.Rp = a.pitch; L.Tp = b.pitch; L.cR = a.mean;
+    L.R = a.rptr; L.T = b.ptr; L.W = a.W; L.H = a.H; L.Rp = a.rpitch; L.Tp = b.pitch; L.cR = a.mean;
     return L;
 }
 
@@ -761,7 +804,7 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     };
     auto pixel = [&](int r, int c, float ux, float uy) {
         float dtx, dty;
-        const float tw = sample_at<S, false>(T, L.W, L.H, L.Tp, c, r, ux, uy, dtx, dty);
+        const float tw = sample_q<S, false>(T, L.W, L.H, L.Tp, c, r, ux, uy, dtx, dty);
         const float rv = ldS<S>(Rrow + c) - L.cR;
         const float tv = tw - L.cR;
         a[0] += tv;
@@ -914,8 +957,8 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
                     const float wy = fminf(wyk, wmax);
                     wyk += dwy;
                     float dtx, dty;
-                    const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, x, y, fmaf(wy, ex, tx), fmaf(wy, ey, ty),
-                                                        dtx, dty);
+                    const float tw = sample_q<S, true>(T, L.W, L.H, L.Tp, x, y, fmaf(wy, ex, tx), fmaf(wy, ey, ty),
+                                                       dtx, dty);
                     const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
                     const float tv = tw - L.cR;
                     // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
@@ -937,7 +980,7 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
                 const float bx = fmaf(wx, dbot.x, c10.x), by = fmaf(wx, dbot.y, c10.y);
                 const float ux = fmaf(wy, bx - tx, tx), uy = fmaf(wy, by - ty, ty);
                 float dtx, dty;
-                const float tw = sample_at<S, true>(T, L.W, L.H, L.Tp, x, y, ux, uy, dtx, dty);
+                const float tw = sample_q<S, true>(T, L.W, L.H, L.Tp, x, y, ux, uy, dtx, dty);
                 const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
                 const float tv = tw - L.cR;
                 // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
@@ -1403,18 +1446,21 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
 }
 
 // ================================================================== pyramid
-// All kernels take a batch of frames (grid.z or grid.x = frame).
+// All kernels take a batch of frames (grid.z or grid.x = frame).  Level pointers address pixel
+// (0, 0) of frame 0; rows are `pitch` elements apart and frames `stride` elements apart.
 template <typename S>
-__global__ void pyr_level0(const float *frames, size_t fstride, int W, int H, int pitch, S *out, size_t ostride)
+__global__ void pyr_level0(const float *frames, size_t fstride, int W, int H, int pitch, S *out, size_t ostride,
+                           int opitch)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     const size_t f = blockIdx.z;
-    if (c < W && r < H) out[f * ostride + (size_t)r * W + c] = toS<S>(__ldg(frames + f * fstride + (size_t)r * pitch + c));
+    if (c < W && r < H)
+        out[f * ostride + (size_t)r * opitch + c] = toS<S>(__ldg(frames + f * fstride + (size_t)r * pitch + c));
 }
 
 // Level l+1 from level l: 2x2 box average, last odd row/column clamped.
 template <typename S>
-__global__ void pyr_down(const S *src, size_t sstride, int W, int H, S *dst, size_t dstride)
+__global__ void pyr_down(const S *src, size_t sstride, int spitch, int W, int H, S *dst, size_t dstride, int dpitch)
 {
     const int w2 = (W + 1) / 2, h2 = (H + 1) / 2;
     const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
@@ -1422,22 +1468,70 @@ __global__ void pyr_down(const S *src, size_t sstride, int W, int H, S *dst, siz
     src += blockIdx.z * sstride;
     dst += blockIdx.z * dstride;
     int r0 = 2 * r, r1 = min(2 * r + 1, H - 1), c0 = 2 * c, c1 = min(2 * c + 1, W - 1);
-    float v = ((ldS<S>(src + (size_t)r0 * W + c0) + ldS<S>(src + (size_t)r0 * W + c1)) +
-               ldS<S>(src + (size_t)r1 * W + c0)) + ldS<S>(src + (size_t)r1 * W + c1);
-    dst[(size_t)r * w2 + c] = toS<S>(0.25f * v);
+    float v = ((ldS<S>(src + (size_t)r0 * spitch + c0) + ldS<S>(src + (size_t)r0 * spitch + c1)) +
+               ldS<S>(src + (size_t)r1 * spitch + c0)) + ldS<S>(src + (size_t)r1 * spitch + c1);
+    dst[(size_t)r * dpitch + c] = toS<S>(0.25f * v);
+}
+
+// Replicated border of `pad` samples around a W x H level (pitch W + 2 pad): thread t covers
+// one border sample, the top and bottom bands first, then the left and right bands.
+template <typename S>
+__global__ void pyr_border(S *lvl, size_t stride, int W, int H, int pad)
+{
+    const int pitch = W + 2 * pad;
+    const int bands = 2 * pad * pitch, sides = 2 * pad * H;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= bands + sides) return;
+    lvl += blockIdx.z * stride;
+    int r, c;
+    if (t < bands) {
+        const int q = t / pitch;                      // 0 .. 2 pad - 1
+        r = q < pad ? q - pad : H + (q - pad);        // -pad .. -1, then H .. H + pad - 1
+        c = t - q * pitch - pad;                      // -pad .. W + pad - 1
+    } else {
+        const int u = t - bands, q = u / H;           // 0 .. 2 pad - 1
+        r = u - q * H;
+        c = q < pad ? q - pad : W + (q - pad);
+    }
+    const int rs = min(max(r, 0), H - 1), cs = min(max(c, 0), W - 1);
+    lvl[(ptrdiff_t)r * pitch + c] = lvl[(size_t)rs * pitch + cs];
+}
+
+// The quadratic B-spline model at the pixel centres: the separable filter (1/8, 3/4, 1/8) of a
+// bordered level (its replicated border supplies the outer taps), with the operations of
+// sample_q at a zero offset, so that a frame registered to itself matches bit for bit.  Written
+// as a plain W x H level.
+template <typename S>
+__global__ void pyr_smooth(const S *src, size_t sstride, int spitch, int W, int H, S *dst, size_t dstride)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (c >= W || r >= H) return;
+    const S *p = src + blockIdx.z * sstride + (size_t)r * spitch + c;
+    float row[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const S *q = p + (ptrdiff_t)(k - 1) * spitch;
+        row[k] = fmaf(0.125f, ldS<S>(q + 1), fmaf(0.75f, ldS<S>(q), 0.125f * ldS<S>(q - 1)));
+    }
+    dst[blockIdx.z * dstride + (size_t)r * W + c] = toS<S>(fmaf(0.125f, row[2], fmaf(0.75f, row[1], 0.125f * row[0])));
 }
 
 // Mean of one level of each frame (one CTA per frame), deterministic float-float sum.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) level_mean(const S *img, size_t stride, int n, float *mean, int mstride)
+__global__ void __launch_bounds__(kThreads) level_mean(const S *img, size_t stride, int W, int H, int pitch,
+                                                       float *mean, int mstride)
 {
     __shared__ float2 ws[kWarps];
     img += blockIdx.x * stride;
+    const int n = W * H;
     float hi = 0.f, lo = 0.f;
     for (int base = 0; base < n; base += kThreads * kChunk) {
         float a = 0.f;
         const int e = min(n, base + kThreads * kChunk);
-        for (int i = base + threadIdx.x; i < e; i += kThreads) a += ldS<S>(img + i);
+        for (int i = base + threadIdx.x; i < e; i += kThreads) {
+            const int r = i / W;
+            a += ldS<S>(img + (size_t)r * pitch + (i - r * W));
+        }
         ff_acc(hi, lo, a);
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -1502,36 +1596,57 @@ __global__ void grid_from_dense_kernel(const float *u, int W, int H, Grid G, flo
 // ================================================================== host launchers
 template <typename S>
 static cudaError_t pyramid_t(const float *frames, int N, size_t fstride, int W, int H, int pitch, int levels,
-                             void *const *level_base, const size_t *level_stride, float *means, cudaStream_t s)
+                             const PyrOut &o, float *means, cudaStream_t s)
 {
-    pyr_level0<S><<<dim3((W + 127) / 128, H, N), 128, 0, s>>>(frames, fstride, W, H, pitch,
-                                                              (S *)level_base[0], level_stride[0]);
+    S *lv[kMaxLevels];
     int w = W, h = H;
+    for (int l = 0; l < levels; ++l) {
+        lv[l] = (S *)o.raw[l] + level_origin(w, o.pad);
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    pyr_level0<S><<<dim3((W + 127) / 128, H, N), 128, 0, s>>>(frames, fstride, W, H, pitch, lv[0], o.raw_stride[0],
+                                                              level_pitch(W, o.pad));
+    w = W; h = H;
     for (int l = 0; l + 1 < levels; ++l) {
         int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
-        pyr_down<S><<<dim3((w2 + 127) / 128, h2, N), 128, 0, s>>>((const S *)level_base[l], level_stride[l], w, h,
-                                                                  (S *)level_base[l + 1], level_stride[l + 1]);
+        pyr_down<S><<<dim3((w2 + 127) / 128, h2, N), 128, 0, s>>>(lv[l], o.raw_stride[l], level_pitch(w, o.pad), w, h,
+                                                                  lv[l + 1], o.raw_stride[l + 1],
+                                                                  level_pitch(w2, o.pad));
         w = w2; h = h2;
     }
-    if (means) {
-        w = W; h = H;
-        for (int l = 0; l < levels; ++l) {
-            level_mean<S><<<N, kThreads, 0, s>>>((const S *)level_base[l], level_stride[l], w * h, means + l, levels);
-            w = (w + 1) / 2; h = (h + 1) / 2;
+    w = W; h = H;
+    for (int l = 0; l < levels; ++l) {
+        if (o.pad > 0) {
+            const int nb = 2 * o.pad * level_pitch(w, o.pad) + 2 * o.pad * h;
+            pyr_border<S><<<dim3((nb + 127) / 128, 1, N), 128, 0, s>>>(lv[l], o.raw_stride[l], w, h, o.pad);
+            if (o.smooth[l])
+                pyr_smooth<S><<<dim3((w + 127) / 128, h, N), 128, 0, s>>>(lv[l], o.raw_stride[l], level_pitch(w, o.pad),
+                                                                          w, h, (S *)o.smooth[l], o.smooth_stride[l]);
         }
+        if (means)
+            level_mean<S><<<N, kThreads, 0, s>>>(lv[l], o.raw_stride[l], w, h, level_pitch(w, o.pad), means + l,
+                                                 levels);
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, int H, int pitch, int levels,
-                           int storage, void *const *level_base, const size_t *level_stride, float *means,
-                           cudaStream_t s)
+                           int storage, const PyrOut &out, float *means, cudaStream_t s)
 {
+    if (out.pad != 0) {
+        // the smoothed levels read the 3x3 window of a bordered level
+        if (out.pad < 1) return cudaErrorInvalidValue;
+    } else {
+        for (int l = 0; l < levels; ++l)
+            if (out.smooth[l]) return cudaErrorInvalidValue;
+    }
     switch (storage) {
-    case REG_F32: return pyramid_t<float>(frames, N, fstride, W, H, pitch, levels, level_base, level_stride, means, s);
-    case REG_BF16:
-        return pyramid_t<__nv_bfloat16>(frames, N, fstride, W, H, pitch, levels, level_base, level_stride, means, s);
-    case REG_F16: return pyramid_t<__half>(frames, N, fstride, W, H, pitch, levels, level_base, level_stride, means, s);
+    case REG_F32: return pyramid_t<float>(frames, N, fstride, W, H, pitch, levels, out, means, s);
+    case REG_BF16: return pyramid_t<__nv_bfloat16>(frames, N, fstride, W, H, pitch, levels, out, means, s);
+    case REG_F16: return pyramid_t<__half>(frames, N, fstride, W, H, pitch, levels, out, means, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -152,16 +152,20 @@ extern "C" int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const f
         if (e == cudaSuccess) e = cudaMemsetAsync(theta, 0, 6 * sizeof(double), s);
         // pyramids of R and T, then their level means back to the host for the level table
         void *lr[kMaxLevels], *lt[kMaxLevels];
-        size_t stride[kMaxLevels];
+        PyrOut orr, ot;
+        memset(&orr, 0, sizeof(orr));
+        memset(&ot, 0, sizeof(ot));
         for (int l = 0; l < cfg->levels; ++l) {
             lr[l] = base + kOffR + off_l[l];
             lt[l] = base + kOffT + off_l[l];
-            stride[l] = (size_t)Wl[l] * Hl[l];
+            orr.raw[l] = lr[l];
+            ot.raw[l] = lt[l];
+            orr.raw_stride[l] = ot.raw_stride[l] = (size_t)Wl[l] * Hl[l];
         }
         if (e == cudaSuccess)
-            e = launch_pyramid(R, 1, (size_t)H * pitch, W, H, pitch, cfg->levels, cfg->storage, lr, stride, means, s);
+            e = launch_pyramid(R, 1, (size_t)H * pitch, W, H, pitch, cfg->levels, cfg->storage, orr, means, s);
         if (e == cudaSuccess)
-            e = launch_pyramid(T, 1, (size_t)H * pitch, W, H, pitch, cfg->levels, cfg->storage, lt, stride,
+            e = launch_pyramid(T, 1, (size_t)H * pitch, W, H, pitch, cfg->levels, cfg->storage, ot,
                                means + cfg->levels, s);
         float hmeans[2 * kMaxLevels];
         if (e == cudaSuccess)
@@ -177,9 +181,11 @@ extern "C" int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const f
             for (int l = 0; l < cfg->levels; ++l) {
                 LevelDesc &d = htab[f * cfg->levels + l];
                 d.ptr = f == 0 ? lr[l] : lt[l];
+                d.rptr = d.ptr;
                 d.W = Wl[l];
                 d.H = Hl[l];
                 d.pitch = Wl[l];
+                d.rpitch = Wl[l];
                 d.mean = hmeans[f * cfg->levels + l];
             }
         OpDesc hop{0, 1, -1, -1, 0, init ? 1 : -1};

@@ -56,8 +56,10 @@ struct reg_stream {
     int gnx = 0, gny = 0, gs = 0;
     size_t bytes = 0;
     // device memory (owned)
-    void *pyr[kMaxLevels] = {};
+    void *pyr[kMaxLevels] = {};        // levels of every slot (nonrigid: with a replicated border)
+    void *spyr[kMaxLevels] = {};       // nonrigid: the B-spline model at the pixel centres
     size_t lvl_elems[kMaxLevels] = {};
+    int pad = 0;
     int Wl[kMaxLevels] = {}, Hl[kMaxLevels] = {};
     float *stage = nullptr;      // one fp32 frame being copied in
     float *means = nullptr;      // level means of the frame being staged
@@ -273,8 +275,10 @@ Service *service_of(reg_ctx_t *ctx, bool create)
 
 void free_stream(reg_stream *s)
 {
-    for (int l = 0; l < kMaxLevels; ++l)
+    for (int l = 0; l < kMaxLevels; ++l) {
         if (s->pyr[l]) cudaFree(s->pyr[l]);
+        if (s->spyr[l]) cudaFree(s->spyr[l]);
+    }
     void *dev[] = {s->stage, s->means, s->table, s->ops, s->stats, s->theta, s->grid, s->status};
     for (void *p : dev)
         if (p) cudaFree(p);
@@ -340,8 +344,10 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
         if (rc != REG_OK) return rc;
     }
     const size_t sb = c.storage == REG_F32 ? 4 : 2;
+    const int pad = c.mode == REG_NONRIGID ? kPad : 0;
     size_t pyr_bytes = 0;
-    for (int l = 0; l < c.levels; ++l) pyr_bytes += (size_t)Wl[l] * Hl[l] * sb;
+    for (int l = 0; l < c.levels; ++l)
+        pyr_bytes += (level_elems(Wl[l], Hl[l], pad) + (pad ? (size_t)Wl[l] * Hl[l] : 0)) * sb;
     const int nops = 2 * (kSlots + 1);
     const size_t bytes = pyr_bytes * (kSlots + 1) + sizeof(float) * (size_t)W * H + sizeof(LevelDesc) * (kSlots + 1) * c.levels +
                          (sizeof(OpDesc) + sizeof(OpStats) + 3 * sizeof(double)) * nops +
@@ -367,11 +373,13 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
     s->gs = gs;
     s->bytes = bytes;
     bool ok = true;
+    s->pad = pad;
     for (int l = 0; l < c.levels && ok; ++l) {
         s->Wl[l] = Wl[l];
         s->Hl[l] = Hl[l];
-        s->lvl_elems[l] = (size_t)Wl[l] * Hl[l];
+        s->lvl_elems[l] = level_elems(Wl[l], Hl[l], pad);
         ok = cudaMalloc(&s->pyr[l], s->lvl_elems[l] * sb * (kSlots + 1)) == cudaSuccess;
+        if (ok && pad) ok = cudaMalloc(&s->spyr[l], (size_t)Wl[l] * Hl[l] * sb * (kSlots + 1)) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&s->stage, sizeof(float) * (size_t)W * H) == cudaSuccess;
     ok = ok && cudaMalloc(&s->means, sizeof(float) * kMaxLevels) == cudaSuccess;
@@ -428,25 +436,32 @@ extern "C" int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t f
     // copy the frame in and build its pyramid (the caller's buffer is free on return)
     const size_t fb = sizeof(float) * (size_t)s->W * s->H;
     const size_t sb = s->storage == REG_F32 ? 4 : 2;
-    void *lv[kMaxLevels];
-    size_t stride[kMaxLevels];
+    PyrOut o;
+    memset(&o, 0, sizeof(o));
+    o.pad = s->pad;
     for (int l = 0; l < s->L; ++l) {
-        lv[l] = (char *)s->pyr[l] + s->lvl_elems[l] * sb * slot;
-        stride[l] = s->lvl_elems[l];
+        o.raw[l] = (char *)s->pyr[l] + s->lvl_elems[l] * sb * slot;
+        o.raw_stride[l] = s->lvl_elems[l];
+        if (s->pad) {
+            o.smooth_stride[l] = (size_t)s->Wl[l] * s->Hl[l];
+            o.smooth[l] = (char *)s->spyr[l] + o.smooth_stride[l] * sb * slot;
+        }
     }
     float hmeans[kMaxLevels];
     cudaError_t e = cudaMemcpyAsync(s->stage, frame, fb, cudaMemcpyDefault, s->copy);
     if (e == cudaSuccess)
-        e = launch_pyramid(s->stage, 1, (size_t)s->W * s->H, s->W, s->H, s->W, s->L, s->storage, lv, stride, s->means,
+        e = launch_pyramid(s->stage, 1, (size_t)s->W * s->H, s->W, s->H, s->W, s->L, s->storage, o, s->means,
                            s->copy);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hmeans, s->means, sizeof(float) * s->L, cudaMemcpyDeviceToHost, s->copy);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
     LevelDesc tab[kMaxLevels];
     for (int l = 0; l < s->L; ++l) {
-        tab[l].ptr = lv[l];
+        tab[l].ptr = (char *)o.raw[l] + level_origin(s->Wl[l], s->pad) * sb;
         tab[l].W = s->Wl[l];
         tab[l].H = s->Hl[l];
-        tab[l].pitch = s->Wl[l];
+        tab[l].pitch = level_pitch(s->Wl[l], s->pad);
+        tab[l].rptr = s->pad ? o.smooth[l] : tab[l].ptr;
+        tab[l].rpitch = s->pad ? s->Wl[l] : tab[l].pitch;
         tab[l].mean = hmeans[l];
     }
     if (e == cudaSuccess)

@@ -39,3 +39,22 @@ def test_the_committed_profiles_name_their_command_and_source():
     for name in os.listdir(os.path.join(ROOT, "profiles")):
         text = open(os.path.join(ROOT, "profiles", name)).read()
         assert "kernel source sha256:" in text and "ncu " in text and "--clock-control none" in text, name
+
+
+def test_imbalance_metric_by_hand():
+    # 8 operators with work 1..8 in 2 segments: T = (10, 26), mean 18, imbalance (26 - 18) / 18
+    m = bench.imbalance_metric(list(range(1, 9)), [2, 4, 16])
+    assert m["segments"]["2"] == pytest.approx(8 / 18, abs=1e-4)
+    # 4 segments: T = (3, 7, 11, 15), mean 9
+    assert m["segments"]["4"] == pytest.approx(6 / 9, abs=1e-4)
+    assert "16" not in m["segments"]            # more segments than operators
+    assert bench.imbalance_metric([5] * 12, [3])["segments"]["3"] == 0.0   # equal work: balanced
+
+
+def test_paper_bounds_formulas():
+    # scan: (N-1) / (2N/P - 1 + C1 log2 P); full: (2N-1) / (3N/P - 1 + C1 log2 P)
+    b = bench.paper_bounds(4096, 1024, 1.0)
+    assert b["scan"] == pytest.approx(4095 / (8 - 1 + 10), abs=0.01)
+    assert b["full"] == pytest.approx(8191 / (12 - 1 + 10), abs=0.01)
+    one = bench.paper_bounds(16, 1, 1.0)      # one worker: no speedup on either
+    assert one["scan"] == pytest.approx(15 / 31, abs=0.01) and one["full"] == pytest.approx(31 / 47, abs=0.01)

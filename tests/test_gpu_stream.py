@@ -114,10 +114,13 @@ def test_stream_admission_by_memory_budget_and_poll_timeout():
 
 
 def test_stream_submit_refuses_while_every_slot_is_in_flight():
-    F = series(60, 512, 512, 83)
+    # 2048^2 frames submitted from device memory: a submit takes well under a millisecond while one
+    # B operator of the chain takes tens of milliseconds, so the slots fill up
+    spec = synth.SeriesSpec(60, 2048, 2048, step=1.5, field_amp=0.8, snr=(10, 10), seed=83)
+    F = synth.make_series(spec, device="cuda").frames
     ctx = B.Context(B.Config(mode="nonrigid"))
-    st = B.Stream(ctx, 512, 512)
-    codes = [st.submit(np.ascontiguousarray(f), t) for t, f in enumerate(F)]
+    st = B.Stream(ctx, 2048, 2048)
+    codes = [st.submit(F[t], t) for t in range(F.shape[0])]
     # 24 frame slots; 60 frames arrive far faster than the chain of B operators completes
     assert B.REG_EBUDGET in codes
     assert codes[:25] == [B.REG_OK] * 25

@@ -38,10 +38,13 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(B.reg_elem_t) == 20          # 20-byte scan element (Sec. 5)
     assert ctypes.sizeof(B.reg_stats_t) == 144
-    assert ctypes.sizeof(B.reg_timing_t) == 32
+    assert ctypes.sizeof(B.reg_timing_t) == 56
     cfg = B.reg_config_t()
     lib.reg_config_default(ctypes.byref(cfg))
     assert cfg.levels == 2 and cfg.mode == B.RIGID and cfg.storage == B.F32
+    # the stop rule of the oracle's configuration: metric gradient norm 1e-4, no relative-decrease test
+    assert cfg.tol_grad == O.Config().tol_grad == B.Config().tol_grad == 1e-4
+    assert cfg.tol_rel_e == O.Config().tol_rel_e == B.Config().tol_rel_e == 0.0
 
 
 def test_errors_without_gpu_are_reported_not_crashing(lib):
