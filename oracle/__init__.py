@@ -95,6 +95,8 @@ def lib():
             L.or_warp_rigid.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
             L.or_step_size.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int]
             L.or_step_size.restype = ctypes.c_double
+            L.or_bb_first_step.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_double]
+            L.or_bb_first_step.restype = ctypes.c_double
             L.or_warp_grid.argtypes = [gp, dp, dp, dp, dp]
             _lib = L
     return _lib
@@ -503,6 +505,13 @@ def scan(frames, cfg: Config, dag: Optional[Dag] = None, leaves: Optional[List[E
 def step_size(E: float, slope: float, tau: float, Et: float, accepted: bool) -> float:
     """The line search's next step after a trial at tau with energy Et (see oracle.c)."""
     return float(lib().or_step_size(E, slope, tau, Et, 1 if accepted else 0))
+
+
+def bb_first_step(tau_q: float, tau_acc: float, d_prev, d, m0: float = 1.0) -> float:
+    """First trial of a line search after an accepted step of length tau_acc along d_prev, with the
+    new direction d: the Barzilai-Borwein step in the metric diag(m0, 1, ...), else tau_q."""
+    a, b = _f64(np.ravel(d_prev)), _f64(np.ravel(d))
+    return float(lib().or_bb_first_step(tau_q, tau_acc, _dp(a), _dp(b), a.size, m0))
 
 
 # --------------------------------------------------------------------------

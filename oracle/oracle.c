@@ -109,6 +109,29 @@ double or_step_size(double E, double slope, double tau, double Et, int accepted)
     return or_next_tau(E, slope, tau, Et, accepted);
 }
 
+/* First trial step of a line search after an accepted step (Barzilai and Borwein, "Two-point step
+ * size gradient methods", IMA J. Numer. Anal. 8, 1988, their second step): with the previous
+ * step s = tau_acc d_prev and the change of the descent direction y = d_prev - d (directions in the
+ * metric M, d = -M^-1 grad E), tau = <s, y>_M / <y, y>_M.  M weighs component 0 by m0 (rigid,
+ * m0 = rho^2) and every component by 1 otherwise (pass m0 = 1).  Without positive curvature along
+ * y (<s, y> <= 0 or <y, y> = 0) the step of the quadratic rule, tau_q, stays.                 */
+static double or_bb_step(double tau_q, double tau_acc, const double *dprev, const double *d, int n, double m0)
+{
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double w = k == 0 ? m0 : 1.0, y = dprev[k] - d[k];
+        num += w * dprev[k] * y;
+        den += w * y * y;
+    }
+    return (num > 0.0 && den > 0.0) ? tau_acc * num / den : tau_q;
+}
+
+/* The first-trial rule by itself (for its pins). */
+double or_bb_first_step(double tau_q, double tau_acc, const double *dprev, const double *d, int n, double m0)
+{
+    return or_bb_step(tau_q, tau_acc, dprev, d, n, m0);
+}
+
 void or_sample(const double *T, int W, int H, double px, double py, double out[3])
 {
     double qx = clampd(px, 0.0, (double)(W - 1));
@@ -279,12 +302,15 @@ static void or_rigid_level(const double *R, const double *T, int W, int H,
     or_rigid_energy(R, T, W, H, th, &E, g);
     st->evals[lvl] += 1;
     double tau = cfg->tau0;
+    double dprev[3] = {0.0, 0.0, 0.0}, tau_acc = 0.0;
+    int have_prev = 0;
     int stop = OR_STOP_MAXIT;
     for (int it = 0; it < cfg->max_iter; ++it) {
         double d[3] = {-g[0] / m0, -g[1], -g[2]};
         double slope = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
         double gn = sqrt(-slope);
         if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
+        if (have_prev) tau = or_bb_step(tau, tau_acc, dprev, d, 3, m0);
         if (tau * gn > cfg->step_cap) tau = cfg->step_cap / gn;
         int accepted = 0;
         double tt[3], Et = 0.0;
@@ -299,6 +325,9 @@ static void or_rigid_level(const double *R, const double *T, int W, int H,
         if (!accepted) { stop = OR_STOP_LS; break; }
         th[0] = tt[0]; th[1] = tt[1]; th[2] = tt[2];
         st->iters[lvl] += 1;
+        tau_acc = tau;
+        dprev[0] = d[0]; dprev[1] = d[1]; dprev[2] = d[2];
+        have_prev = 1;
         double Eold = E;
         tau = or_next_tau(E, slope, tau, Et, 1);
         E = Et;
@@ -471,7 +500,10 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
     double *gx = (double *)malloc(sizeof(double) * Nc), *gy = (double *)malloc(sizeof(double) * Nc);
     double *dx = (double *)malloc(sizeof(double) * Nc), *dy = (double *)malloc(sizeof(double) * Nc);
     double *tx = (double *)malloc(sizeof(double) * Nc), *ty = (double *)malloc(sizeof(double) * Nc);
-    double E, Et = 0.0;
+    /* previous direction, both components in one array (x plane then y plane) */
+    double *dp = (double *)malloc(sizeof(double) * 2 * Nc), *dc = (double *)malloc(sizeof(double) * 2 * Nc);
+    double E, Et = 0.0, tau_acc = 0.0;
+    int have_prev = 0;
     or_grid_energy(R, T, W, H, l, g, cx, cy, cfg->lambda, &E, gx, gy);
     st->evals[l] += 1;
     double tau = cfg->tau0;
@@ -489,6 +521,9 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
         double slope = -ss / (double)Nc;
         double gn = sqrt(ss / (double)Nc);
         if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
+        for (int j = 0; j < Nc; ++j) { dc[2 * j] = dx[j]; dc[2 * j + 1] = dy[j]; }
+        /* the metric is the mean over control points: a common factor, 1 suffices here */
+        if (have_prev) tau = or_bb_step(tau, tau_acc, dp, dc, 2 * Nc, 1.0);
         if (tau * dmax > cfg->step_cap) tau = cfg->step_cap / dmax;
         int accepted = 0;
         for (int rej = 0; rej <= cfg->max_rejects; ++rej) {
@@ -503,6 +538,9 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
         memcpy(cx, tx, sizeof(double) * Nc);
         memcpy(cy, ty, sizeof(double) * Nc);
         st->iters[l] += 1;
+        tau_acc = tau;
+        memcpy(dp, dc, sizeof(double) * 2 * Nc);
+        have_prev = 1;
         double Eold = E;
         tau = or_next_tau(E, slope, tau, Et, 1);
         E = Et;
@@ -512,7 +550,7 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
     }
     st->stop[l] = stop;
     if (l == 0) st->energy = E;
-    free(gx); free(gy); free(dx); free(dy); free(tx); free(ty);
+    free(gx); free(gy); free(dx); free(dy); free(tx); free(ty); free(dp); free(dc);
 }
 
 /* Multilevel nonrigid registration on the control grid.  init (finest-level

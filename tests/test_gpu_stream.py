@@ -54,27 +54,41 @@ def test_stream_equals_sequential_scan_and_oracle(mode):
     cfg = B.Config(mode=mode, cluster=4)
     ctx = B.Context(cfg)
     st = B.Stream(ctx, 128, 128)
+    ring = None
+    if mode == "nonrigid":
+        nx, ny, _ = B.grid_dims(128, 128)
+        ring = torch.full((16, ny, nx, 2), 9.0, device="cuda")
+        st.set_grids(ring)
     res = run_stream(st, F, list(range(100, 112)))
     st.close()
     assert [r["frame_id"] for r in res] == list(range(100, 112))
     assert res[0]["elem"][2:] == (0.0, 0.0, 0.0)
-    fo = torch.zeros((11, 2, 128, 128), device="cuda") if mode == "nonrigid" else None
-    els, _ = ctx.scan(torch.from_numpy(F).cuda(), schedule="sequential", exec="plain", fields_out=fo)
+    els, _ = ctx.scan(torch.from_numpy(F).cuda(), schedule="sequential", exec="plain")
     for i in range(1, 12):
         assert res[i]["elem"] == els[i - 1], (i, res[i], els[i - 1])
         assert res[i]["status"] == 0 and res[i]["done_us"] >= res[i]["submit_us"]
+    oc = O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
+                  tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
+                  lam=cfg.lam, mode=cfg.mode)
+    ref = O.scan(F, oc, O.dag_sequential(11))
     if mode == "rigid":
-        oc = O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
-                      tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
-                      lam=cfg.lam, mode=cfg.mode)
-        ref = O.scan(F, oc, O.dag_sequential(11))
         for i, o in enumerate(ref):
             assert O.max_px_error(np.array(res[i + 1]["elem"][2:], np.float64), o.phi, 128, 128, "rigid") <= 0.02
+    else:
+        # every frame's control values: the sequential scan's bit for bit, the oracle's within the bar
+        sg = torch.zeros((11, ny, nx, 2), device="cuda")
+        ctx.scan_grids(sg)
+        assert not ring[0].any()                          # f_0: the identity
+        assert torch.equal(ring[1:12], sg)
+        got = ring[1:12].cpu().numpy().astype(np.float64)
+        for i, o in enumerate(ref):
+            assert O.max_px_error(np.transpose(got[i], (2, 0, 1)), o.phi, 128, 128, "nonrigid") <= 0.02, i
 
 
-def test_stream_results_are_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
+def test_stream_results_are_the_same_alone_and_in_the_mix(mode):
     F = series(10, 160, 144, 82)
-    cfg = B.Config(cluster=4)
+    cfg = B.Config(mode=mode, cluster=4)
     ctx = B.Context(cfg)
     st = B.Stream(ctx, 144, 160)
     alone = run_stream(st, F, list(range(10)))
@@ -101,6 +115,26 @@ def test_stream_results_are_the_same_alone_and_in_the_mix():
     assert all(len(mixed[k]) == 14 for k in range(3))
 
 
+def test_stream_grids_rejections():
+    ctx = B.Context(B.Config())
+    st = B.Stream(ctx, 64, 64)
+    with pytest.raises(B.RegError) as e:
+        st.set_grids(torch.zeros((4, 5, 5, 2), device="cuda"))   # rigid stream: no control grids
+    assert e.value.code == B.REG_EINVAL
+    st.close()
+    ctx = B.Context(B.Config(mode="nonrigid"))
+    st = B.Stream(ctx, 64, 64)
+    nx, ny, _ = B.grid_dims(64, 64)
+    with pytest.raises(B.RegError) as e:
+        st.set_grids(torch.zeros((4, ny, nx, 2)))               # host memory
+    assert e.value.code == B.REG_EINVAL
+    run_stream(st, series(2, 64, 64, 84), [0, 1])
+    with pytest.raises(B.RegError) as e:
+        st.set_grids(torch.zeros((4, ny, nx, 2), device="cuda"))   # after the first submit
+    assert e.value.code == B.REG_ESTATE
+    st.close()
+
+
 def test_stream_admission_by_memory_budget_and_poll_timeout():
     ctx = B.Context(B.Config(mem_budget=64 << 20))
     st = B.Stream(ctx, 128, 128)            # fits
@@ -114,11 +148,12 @@ def test_stream_admission_by_memory_budget_and_poll_timeout():
 
 
 def test_stream_submit_refuses_while_every_slot_is_in_flight():
-    # 2048^2 frames submitted from device memory: a submit takes well under a millisecond while one
-    # B operator of the chain takes tens of milliseconds, so the slots fill up
+    # 2048^2 frames submitted from device memory, and operators that run until their line search
+    # gives up (no gradient stop): a submit takes about a millisecond while one operator of the
+    # chain takes far longer, so the slots fill up
     spec = synth.SeriesSpec(60, 2048, 2048, step=1.5, field_amp=0.8, snr=(10, 10), seed=83)
     F = synth.make_series(spec, device="cuda").frames
-    ctx = B.Context(B.Config(mode="nonrigid"))
+    ctx = B.Context(B.Config(mode="nonrigid", tol_grad=0.0))
     st = B.Stream(ctx, 2048, 2048)
     codes = [st.submit(F[t], t) for t in range(F.shape[0])]
     # 24 frame slots; 60 frames arrive far faster than the chain of B operators completes

@@ -527,3 +527,33 @@ def test_step_rule_without_curvature_doubles_or_halves():
     # a trial at or below the tangent line (no positive curvature): plain doubling / halving
     assert O.step_size(1.0, -1.0, 0.5, 0.4, True) == 1.0
     assert O.step_size(1.0, -1.0, 0.5, 0.5, False) == 0.25
+
+
+# ------------------------------------------------------------------ the first trial step
+def test_bb_first_step_is_the_exact_step_on_a_round_quadratic():
+    # E = a/2 |x|^2 in the plain metric: d = -a x; after a step of tau_acc along d_prev the
+    # Barzilai-Borwein step is 1/a, the exact minimiser along any direction
+    a = 3.7
+    x0 = np.array([0.4, -1.2, 0.9, 2.0])
+    tau_acc = 0.11
+    dp = -a * x0
+    x1 = x0 + tau_acc * dp
+    assert O.bb_first_step(0.5, tau_acc, dp, -a * x1) == pytest.approx(1.0 / a, rel=1e-14)
+
+
+def test_bb_first_step_in_the_rigid_metric():
+    # E = 1/2 sum h_k t_k^2 with h = c (m0, 1, 1): in the metric diag(m0, 1, 1) the direction is
+    # d = -c t and the exact step 1/c
+    c, m0 = 0.8, 40.0
+    h = c * np.array([m0, 1.0, 1.0])
+    t0 = np.array([0.01, 1.5, -0.7])
+    dp = -(h * t0) / np.array([m0, 1.0, 1.0])
+    t1 = t0 + 0.3 * dp
+    d = -(h * t1) / np.array([m0, 1.0, 1.0])
+    assert O.bb_first_step(0.5, 0.3, dp, d, m0) == pytest.approx(1.0 / c, rel=1e-13)
+
+
+def test_bb_first_step_falls_back_without_curvature():
+    dp = np.array([1.0, -2.0])
+    assert O.bb_first_step(0.25, 0.1, dp, dp) == 0.25           # no change of direction
+    assert O.bb_first_step(0.25, 0.1, dp, 2.0 * dp) == 0.25     # negative curvature along the step
