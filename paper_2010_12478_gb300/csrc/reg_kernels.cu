@@ -86,20 +86,31 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float h2, float l2)
 // Step-controller state (FP64), used by thread 0 of each CTA only: kept in shared memory so
 // it does not occupy registers of every thread.
 struct RigidCtl {
-    double th[3], tt[3], d[3];
+    double th[3], tt[3], d[3], dp[3];   // dp: the direction of the last accepted step
     double E, tau, slope, sr, srr, m0, P, cx, cy, invP, inv_m0;
+    double tau_acc;                // length of the last accepted step (along dp)
     double a, b, rbar, tbar;       // NCC terms at th
     double ta, tb, trbar, ttbar;   // at the trial point tt
-    int nrej, iters, evals, stop, rejects;
+    int nrej, iters, evals, stop, rejects, have_prev;
 };
 
 struct FieldCtl {
-    double E, tau, tau_pend, slope, P, Nc, sr, srr, invP, invNc;
+    double E, tau, tau_pend, tau_acc, slope, P, Nc, sr, srr, invP, invNc;
     double a, b, rbar, tbar;      // NCC terms at the current field
     double ta, tb, trbar, ttbar;  // at the trial field
     int degen, tdegen;
-    int nrej, iters, evals, stop, rejects;
+    int nrej, iters, evals, stop, rejects, have_prev;
 };
+
+// First trial of a line search after an accepted step (Barzilai and Borwein, "Two-point step size
+// gradient methods", 1988, their second step): tau = tau_acc <d_prev, d_prev - d> / |d_prev - d|^2
+// in the flow's metric, given num = <d_prev, d_prev - d> and den = |d_prev - d|^2; without positive
+// curvature the quadratic rule's tau_q stays.  The ratio needs no more than FP32 relative precision.
+__device__ __forceinline__ double bb_tau(double tau_q, double tau_acc, double num, double den)
+{
+    if (!(num > 0.0 && den > 0.0)) return tau_q;
+    return tau_acc * num * (double)__frcp_rn((float)den);
+}
 
 struct Smem {
     float2 warp[kWarps][kNM];   // per-warp (hi, lo) partials
@@ -571,6 +582,15 @@ __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int
         // |g|_M = sqrt(-slope); the tests compare squares (no square root unless the cap applies)
         const double gn2 = -k.slope;
         if (!(gn2 >= cfg.tol_grad * cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
+        if (k.have_prev) {
+            double num = 0.0, den = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                const double w = q == 0 ? k.m0 : 1.0, y = k.dp[q] - k.d[q];
+                num += w * k.dp[q] * y;
+                den += w * y * y;
+            }
+            k.tau = bb_tau(k.tau, k.tau_acc, num, den);
+        }
         if (k.tau * k.tau * gn2 > cfg.step_cap * cfg.step_cap) k.tau = cfg.step_cap / sqrt(gn2);
         k.nrej = 0;
         for (int q = 0; q < 3; ++q) k.tt[q] = k.th[q] + k.tau * k.d[q];
@@ -582,7 +602,9 @@ __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int
     const double Et = n.degenerate ? 1.0 : __dsub_rn(1.0, n.ncc);
     k.evals += 1;
     if (Et <= k.E + cfg.armijo_c * k.tau * k.slope) {
-        for (int q = 0; q < 3; ++q) k.th[q] = k.tt[q];
+        for (int q = 0; q < 3; ++q) { k.th[q] = k.tt[q]; k.dp[q] = k.d[q]; }
+        k.tau_acc = k.tau;
+        k.have_prev = 1;
         k.iters += 1;
         const double Eold = k.E;
         k.tau = next_tau(k.E, k.slope, k.tau, Et, true);
@@ -656,6 +678,7 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
             k.m0 = rho * rho;
             k.inv_m0 = 1.0 / k.m0;
             k.tau = cfg.tau0;
+            k.have_prev = 0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
             rigid_params(k.th, sm.pm);
             sm.action = kActEnergy;
@@ -902,8 +925,9 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int l
 // corner, so each corner is updated by one warp at a time, in a fixed order); then every CTA
 // assembles the whole gradient from the (at most two) CTAs whose band holds each control row,
 // and forms d = -(Nc/P) [sum F grad T w + lambda sum_nbrs (c_j - c_k)], F = P dE/dTw.
-// pm: aP, bP, rbar, tbar, lambda.  Returns sum |d|^2 (float-float, in sm.tot[0]) and max |d|^2
-// (sm.tot[1]); identical in every CTA.
+// pm: aP, bP, rbar, tbar, lambda.  Returns sum |d|^2 (float-float, in sm.tot[0]), max |d|^2
+// (sm.tot[1]), and with the direction d held before the call, <d_old, d_old - d> (sm.tot[2]) and
+// |d_old - d|^2 (sm.tot[3]); identical in every CTA.
 template <typename S>
 __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *c, float2 *d,
                                float2 *gp, const float *pm, int cr0, int cr1, Smem &sm, const cg::cluster_group &cl)
@@ -1008,6 +1032,8 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     const int q = (ncy + C - 1) / C;
     const float scale = -(float)Nc / ((float)L.W * (float)L.H);
     float ssh = 0.f, ssl = 0.f, mx = 0.f, run = 0.f;
+    // <d_prev, d_prev - d> and |d_prev - d|^2 for the first trial step (d still holds d_prev)
+    float nmh = 0.f, nml = 0.f, dnh = 0.f, dnl = 0.f, nrun = 0.f, drun = 0.f;
     int k = 0;
     constexpr int kBatch = 4;   // points per thread whose remote loads are in flight together
     for (int j0 = tid; j0 < Nc; j0 += kBatch * kThreads) {
@@ -1047,27 +1073,50 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
         float2 dj;
         dj.x = scale * fmaf(lam, lx, g.x);
         dj.y = scale * fmaf(lam, ly, g.y);
+        const float2 dold = d[j];
         d[j] = dj;
         const float qd = fmaf(dj.x, dj.x, dj.y * dj.y);
+        const float yx = dold.x - dj.x, yy = dold.y - dj.y;
         run += qd;
+        nrun = fmaf(dold.x, yx, fmaf(dold.y, yy, nrun));
+        drun = fmaf(yx, yx, fmaf(yy, yy, drun));
         mx = fmaxf(mx, qd);
-        if (++k == kFast) { ff_acc(ssh, ssl, run); run = 0.f; k = 0; }
+        if (++k == kFast) {
+            ff_acc(ssh, ssl, run); run = 0.f;
+            ff_acc(nmh, nml, nrun); nrun = 0.f;
+            ff_acc(dnh, dnl, drun); drun = 0.f;
+            k = 0;
+        }
         }
     }
     ff_acc(ssh, ssl, run);
+    ff_acc(nmh, nml, nrun);
+    ff_acc(dnh, dnl, drun);
     // block reduction (identical in every CTA: same inputs, same order)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         float h2 = __shfl_xor_sync(0xffffffffu, ssh, off), l2 = __shfl_xor_sync(0xffffffffu, ssl, off);
         ff_add(ssh, ssl, h2, l2);
+        h2 = __shfl_xor_sync(0xffffffffu, nmh, off); l2 = __shfl_xor_sync(0xffffffffu, nml, off);
+        ff_add(nmh, nml, h2, l2);
+        h2 = __shfl_xor_sync(0xffffffffu, dnh, off); l2 = __shfl_xor_sync(0xffffffffu, dnl, off);
+        ff_add(dnh, dnl, h2, l2);
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     }
-    if (lane == 0) { sm.warp[warp][0] = make_float2(ssh, ssl); sm.warp[warp][1] = make_float2(mx, 0.f); }
+    if (lane == 0) {
+        sm.warp[warp][0] = make_float2(ssh, ssl);
+        sm.warp[warp][1] = make_float2(mx, 0.f);
+        sm.warp[warp][2] = make_float2(nmh, nml);
+        sm.warp[warp][3] = make_float2(dnh, dnl);
+    }
     __syncthreads();
-    if (tid == 0) {
-        float h = 0.f, l = 0.f, m = 0.f;
-        for (int w2 = 0; w2 < kWarps; ++w2) { ff_add(h, l, sm.warp[w2][0].x, sm.warp[w2][0].y); m = fmaxf(m, sm.warp[w2][1].x); }
-        sm.tot[0] = (double)h + (double)l;
+    if (tid < 4 && tid != 1) {
+        float h = 0.f, l = 0.f;
+        for (int w2 = 0; w2 < kWarps; ++w2) ff_add(h, l, sm.warp[w2][tid].x, sm.warp[w2][tid].y);
+        sm.tot[tid] = (double)h + (double)l;
+    } else if (tid == 1) {
+        float m = 0.f;
+        for (int w2 = 0; w2 < kWarps; ++w2) m = fmaxf(m, sm.warp[w2][1].x);
         sm.tot[1] = (double)m;
     }
     __syncthreads();
@@ -1110,6 +1159,8 @@ __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int
         const double ss = tot[0], dmax2 = tot[1];
         k.slope = -ss * k.invNc;
         if (!(ss * k.invNc >= cfg.tol_grad * cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
+        // the metric (mean over control points) is a common factor of tot[2] and tot[3]
+        if (k.have_prev) k.tau = bb_tau(k.tau, k.tau_acc, tot[2], tot[3]);
         if (k.tau * k.tau * dmax2 > cfg.step_cap * cfg.step_cap) k.tau = cfg.step_cap / sqrt(dmax2);
         k.nrej = 0;
         pm[0] = (float)k.tau;
@@ -1122,6 +1173,8 @@ __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int
         k.iters += 1;
         const double Eold = k.E;
         k.tau_pend = (double)(float)k.tau;
+        k.tau_acc = k.tau_pend;   // the step applied: c + (float)tau d
+        k.have_prev = 1;
         k.tau = next_tau(k.E, k.slope, k.tau, Et, true);
         k.E = Et;
         k.a = k.ta; k.b = k.tb; k.rbar = k.trbar; k.tbar = k.ttbar; k.degen = k.tdegen;
@@ -1210,6 +1263,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
             k.invP = 1.0 / k.P;
             k.tau = cfg.tau0;
             k.tau_pend = 0.0;
+            k.have_prev = 0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
             sm.action = kActEnergy;
         }
