@@ -51,7 +51,7 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_rejects", ctypes.c_int),
                 ("tol_grad", ctypes.c_double), ("tol_rel_e", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double),
-                ("step_cap", ctypes.c_double), ("lambda_", ctypes.c_double)]
+                ("step_cap", ctypes.c_double), ("lambda_", ctypes.c_double), ("metric", ctypes.c_int)]
 
 
 class _Grid(ctypes.Structure):
@@ -90,6 +90,8 @@ def lib():
             L.or_grid_register.argtypes = [dpp, dpp, ipp, ipp, ctypes.POINTER(_Cfg), gp, dp, dp, dp, dp,
                                            ctypes.POINTER(_Stats)]
             L.or_grid_compose.argtypes = [gp, dp, dp, dp, dp, dp, dp]
+            L.or_grid_metric.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, gp, dp, dp, ctypes.c_double,
+                                         dp, dp]
             L.or_grid_dense.argtypes = [gp, dp, dp, dp, dp]
             L.or_grid_level_dense.argtypes = [gp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
             L.or_warp_rigid.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp]
@@ -119,7 +121,7 @@ class Config:
     levels: int = 2
     max_iter: int = 500
     max_rejects: int = 30
-    tol_grad: float = 1e-4
+    tol_grad: float = 3e-5
     tol_rel_e: float = 0.0
     armijo_c: float = 0.25
     tau0: float = 1.0
@@ -127,10 +129,11 @@ class Config:
     lam: float = 2.0
     grid: int = 0                 # control-grid spacing of the nonrigid field (finest px), 0 = auto
     mode: str = "rigid"           # "rigid" (the paper's map, Sec. 2.3.1) or "nonrigid" (extension)
+    metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control points
 
     def c(self) -> _Cfg:
         return _Cfg(self.levels, self.max_iter, self.max_rejects, self.tol_grad, self.tol_rel_e,
-                    self.armijo_c, self.tau0, self.step_cap, self.lam)
+                    self.armijo_c, self.tau0, self.step_cap, self.lam, self.metric)
 
 
 @dataclasses.dataclass
@@ -229,6 +232,18 @@ def grid_energy(R, T, level: int, g: Grid, c, lam: float, grad: bool = True):
         return float(E[0]), np.stack([gx, gy])
     lib().or_grid_energy(_dp(R), _dp(T), W, H, level, ctypes.byref(gc), _dp(cx), _dp(cy), lam, _dp(E), None, None)
     return float(E[0])
+
+
+def grid_metric(T, level: int, g: Grid, c, lam: float) -> np.ndarray:
+    """The nonrigid flow's scalar product [2, ny, nx] (Gauss-Newton diagonal, normalised) for the
+    level-``level`` template T at control values c (pixels of that level)."""
+    T = _f64(T)
+    H, W = T.shape
+    cx, cy = _f64(c[0]), _f64(c[1])
+    mx = np.zeros((g.ny, g.nx)); my = np.zeros((g.ny, g.nx))
+    gc = g.c()
+    lib().or_grid_metric(_dp(T), W, H, level, ctypes.byref(gc), _dp(cx), _dp(cy), lam, _dp(mx), _dp(my))
+    return np.stack([mx, my])
 
 
 def grid_regulariser(g: Grid, c, lam: float, P: float) -> float:

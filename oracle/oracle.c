@@ -50,6 +50,7 @@ typedef struct {
     double tau0;       /* first trial step of each level */
     double step_cap;   /* largest step, in pixels of the current level */
     double lambda;     /* regulariser weight (nonrigid only) */
+    int metric;        /* nonrigid flow's scalar product: 0 mean over control points, 1 Gauss-Newton diagonal */
 } or_cfg_t;
 
 typedef struct {
@@ -115,21 +116,25 @@ double or_step_size(double E, double slope, double tau, double Et, int accepted)
  * metric M, d = -M^-1 grad E), tau = <s, y>_M / <y, y>_M.  M weighs component 0 by m0 (rigid,
  * m0 = rho^2) and every component by 1 otherwise (pass m0 = 1).  Without positive curvature along
  * y (<s, y> <= 0 or <y, y> = 0) the step of the quadratic rule, tau_q, stays.                 */
-static double or_bb_step(double tau_q, double tau_acc, const double *dprev, const double *d, int n, double m0)
+static double or_bb_step(double tau_q, double tau_acc, const double *dprev, const double *d, const double *w, int n)
 {
     double num = 0.0, den = 0.0;
     for (int k = 0; k < n; ++k) {
-        const double w = k == 0 ? m0 : 1.0, y = dprev[k] - d[k];
-        num += w * dprev[k] * y;
-        den += w * y * y;
+        const double wk = w ? w[k] : 1.0, y = dprev[k] - d[k];
+        num += wk * dprev[k] * y;
+        den += wk * y * y;
     }
     return (num > 0.0 && den > 0.0) ? tau_acc * num / den : tau_q;
 }
 
-/* The first-trial rule by itself (for its pins). */
+/* The first-trial rule by itself (for its pins), metric diag(m0, 1, 1, ...). */
 double or_bb_first_step(double tau_q, double tau_acc, const double *dprev, const double *d, int n, double m0)
 {
-    return or_bb_step(tau_q, tau_acc, dprev, d, n, m0);
+    double *w = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (int k = 0; k < n; ++k) w[k] = k == 0 ? m0 : 1.0;
+    const double t = or_bb_step(tau_q, tau_acc, dprev, d, w, n);
+    free(w);
+    return t;
 }
 
 void or_sample(const double *T, int W, int H, double px, double py, double out[3])
@@ -310,7 +315,10 @@ static void or_rigid_level(const double *R, const double *T, int W, int H,
         double slope = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
         double gn = sqrt(-slope);
         if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
-        if (have_prev) tau = or_bb_step(tau, tau_acc, dprev, d, 3, m0);
+        if (have_prev) {
+            const double w[3] = {m0, 1.0, 1.0};
+            tau = or_bb_step(tau, tau_acc, dprev, d, w, 3);
+        }
         if (tau * gn > cfg->step_cap) tau = cfg->step_cap / gn;
         int accepted = 0;
         double tt[3], Et = 0.0;
@@ -490,9 +498,63 @@ int or_grid_energy(const double *R, const double *T, int W, int H, int l, const 
     return n.degenerate;
 }
 
+/* Scalar product of the nonrigid flow (cfg->metric = 1): per control point and axis the
+ * Gauss-Newton curvature of the data term plus the regulariser's,
+ *   m_j^x = sum_x w_j(x)^2 (dT/dpx)^2 / (P var T) + lambda n_j / P   (likewise for y),
+ * with w_j the bilinear weight of control point j at pixel x, dT the derivative of the image
+ * model at x + u(x) for the level's initial control values, var T the variance of those samples
+ * and n_j the number of grid neighbours of j; normalised by the mean of all 2 Nc values and
+ * floored at 1e-3 of it.  <u, v> = (1/Nc) sum_j (m_j^x u_j^x v_j^x + m_j^y u_j^y v_j^y): a fixed
+ * scalar product per level in which every control point's step is scaled by its own curvature
+ * (control points outside the overlap of the two frames are held by the regulariser alone).   */
+void or_grid_metric(const double *T, int W, int H, int l, const or_grid_t *g, const double *cx,
+                    const double *cy, double lambda, double *mx, double *my)
+{
+    const int P = W * H, Nc = g->nx * g->ny;
+    const double scale = ldexp(1.0, l), off = 0.5 * (scale - 1.0);
+    double st = 0.0, stt = 0.0;
+    for (int j = 0; j < Nc; ++j) { mx[j] = 0.0; my[j] = 0.0; }
+    for (int r = 0; r < H; ++r) {
+        for (int c = 0; c < W; ++c) {
+            int jx, jy;
+            double ux, uy, wx, wy, s[3];
+            or_grid_eval(g, cx, cy, scale * c + off, scale * r + off, &ux, &uy);
+            or_sample_q(T, W, H, c + ux, r + uy, s);
+            st += s[0];
+            stt += s[0] * s[0];
+            or_grid_cell(g, scale * c + off, scale * r + off, &jx, &jy, &wx, &wy);
+            const int j = jy * g->nx + jx;
+            const double w[4] = {(1 - wx) * (1 - wy), wx * (1 - wy), (1 - wx) * wy, wx * wy};
+            const int idx[4] = {j, j + 1, j + g->nx, j + g->nx + 1};
+            for (int q = 0; q < 4; ++q) {
+                mx[idx[q]] += w[q] * w[q] * s[1] * s[1];
+                my[idx[q]] += w[q] * w[q] * s[2] * s[2];
+            }
+        }
+    }
+    const double var = stt / P - (st / P) * (st / P);
+    const double dk = var > 0.0 ? 1.0 / (P * var) : 0.0;
+    double mean = 0.0;
+    for (int jy = 0; jy < g->ny; ++jy)
+        for (int jx = 0; jx < g->nx; ++jx) {
+            const int j = jy * g->nx + jx;
+            const int nb = (jx > 0) + (jx + 1 < g->nx) + (jy > 0) + (jy + 1 < g->ny);
+            mx[j] = mx[j] * dk + lambda * nb / P;
+            my[j] = my[j] * dk + lambda * nb / P;
+            mean += mx[j] + my[j];
+        }
+    mean /= 2.0 * Nc;
+    for (int j = 0; j < Nc; ++j) {
+        if (!(mean > 0.0)) { mx[j] = 1.0; my[j] = 1.0; continue; }
+        mx[j] = fmax(mx[j] / mean, 1e-3);
+        my[j] = fmax(my[j] / mean, 1e-3);
+    }
+}
+
 /* One level of gradient flow for the control values (pixels of level l).
- * Metric: the mean over control points, <v, w> = (1/Nc) sum v.w, so the
- * descent direction is d = -Nc dE/dc and tau |d_j| is a move in pixels.    */
+ * Metric: cfg->metric 1, the Gauss-Newton diagonal of or_grid_metric; 0, the
+ * mean over control points, <v, w> = (1/Nc) sum v.w.  The descent direction is
+ * d = -M^-1 dE/dc and tau |d_j| is a move in pixels.                       */
 static void or_grid_level(const double *R, const double *T, int W, int H, int l, const or_grid_t *g,
                           const or_cfg_t *cfg, double *cx, double *cy, or_stats_t *st)
 {
@@ -502,19 +564,29 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
     double *tx = (double *)malloc(sizeof(double) * Nc), *ty = (double *)malloc(sizeof(double) * Nc);
     /* previous direction, both components in one array (x plane then y plane) */
     double *dp = (double *)malloc(sizeof(double) * 2 * Nc), *dc = (double *)malloc(sizeof(double) * 2 * Nc);
+    /* the level's scalar product, per control point and axis (interleaved like dc) */
+    double *mx = (double *)malloc(sizeof(double) * Nc), *my = (double *)malloc(sizeof(double) * Nc);
+    double *mw = (double *)malloc(sizeof(double) * 2 * Nc);
     double E, Et = 0.0, tau_acc = 0.0;
     int have_prev = 0;
+    if (cfg->metric == 1) {
+        or_grid_metric(T, W, H, l, g, cx, cy, cfg->lambda, mx, my);
+    } else {
+        for (int j = 0; j < Nc; ++j) { mx[j] = 1.0; my[j] = 1.0; }
+    }
+    for (int j = 0; j < Nc; ++j) { mw[2 * j] = mx[j]; mw[2 * j + 1] = my[j]; }
     or_grid_energy(R, T, W, H, l, g, cx, cy, cfg->lambda, &E, gx, gy);
     st->evals[l] += 1;
     double tau = cfg->tau0;
     int stop = OR_STOP_MAXIT;
     for (int it = 0; it < cfg->max_iter; ++it) {
+        /* d = -M^-1 grad E; ss = Nc |d|_M^2 = sum_j (m^x dx^2 + m^y dy^2); dmax = max_j |d_j| in px */
         double ss = 0.0, dmax = 0.0;
         for (int j = 0; j < Nc; ++j) {
-            dx[j] = -(double)Nc * gx[j];
-            dy[j] = -(double)Nc * gy[j];
+            dx[j] = -(double)Nc * gx[j] / mx[j];
+            dy[j] = -(double)Nc * gy[j] / my[j];
             double q = dx[j] * dx[j] + dy[j] * dy[j];
-            ss += q;
+            ss += mx[j] * dx[j] * dx[j] + my[j] * dy[j] * dy[j];
             if (q > dmax) dmax = q;
         }
         dmax = sqrt(dmax);
@@ -522,8 +594,8 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
         double gn = sqrt(ss / (double)Nc);
         if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
         for (int j = 0; j < Nc; ++j) { dc[2 * j] = dx[j]; dc[2 * j + 1] = dy[j]; }
-        /* the metric is the mean over control points: a common factor, 1 suffices here */
-        if (have_prev) tau = or_bb_step(tau, tau_acc, dp, dc, 2 * Nc, 1.0);
+        /* the metric's common factor 1/Nc cancels in the ratio */
+        if (have_prev) tau = or_bb_step(tau, tau_acc, dp, dc, mw, 2 * Nc);
         if (tau * dmax > cfg->step_cap) tau = cfg->step_cap / dmax;
         int accepted = 0;
         for (int rej = 0; rej <= cfg->max_rejects; ++rej) {
@@ -550,7 +622,7 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
     }
     st->stop[l] = stop;
     if (l == 0) st->energy = E;
-    free(gx); free(gy); free(dx); free(dy); free(tx); free(ty); free(dp); free(dc);
+    free(gx); free(gy); free(dx); free(dy); free(tx); free(ty); free(dp); free(dc); free(mx); free(my); free(mw);
 }
 
 /* Multilevel nonrigid registration on the control grid.  init (finest-level

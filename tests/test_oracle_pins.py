@@ -557,3 +557,51 @@ def test_bb_first_step_falls_back_without_curvature():
     dp = np.array([1.0, -2.0])
     assert O.bb_first_step(0.25, 0.1, dp, dp) == 0.25           # no change of direction
     assert O.bb_first_step(0.25, 0.1, dp, 2.0 * dp) == 0.25     # negative curvature along the step
+
+
+# ------------------------------------------------------------------ the nonrigid flow's scalar product
+def test_metric_on_an_affine_image_is_the_closed_form():
+    # T = 0.2 + b x + c y: the model's derivative is (b, c) wherever its window stays inside the frame,
+    # so for a control point whose support does too, sum_x w_j(x)^2 dT^2 = b^2 S^2 (resp. c^2 S^2),
+    # S = sum over one axis of the tent weight squared = 1 + 2 sum_{t=1}^{s-1} (1 - t/s)^2
+    H, W, sp_ = 49, 65, 8
+    b, c = 0.03, -0.05
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    T = 0.2 + b * x + c * y
+    g = O.grid_for(W, H, sp_)
+    lam = 1.5
+    m = O.grid_metric(T, 0, g, np.zeros((2, g.ny, g.nx)), lam)
+    P = W * H
+    var = smooth_1_8_3_4_1_8(T).var()    # variance of the model's samples at the zero field
+    S = 1.0 + 2.0 * sum((1.0 - t / sp_) ** 2 for t in range(1, sp_))
+    # unnormalised values of the whole grid, then the normalisation by the mean of all 2 Nc values
+    nb = np.zeros((g.ny, g.nx))
+    nb[:, 1:] += 1; nb[:, :-1] += 1; nb[1:, :] += 1; nb[:-1, :] += 1
+    interior = (slice(2, g.ny - 2), slice(2, g.nx - 2))       # supports [8 (j-1), 8 (j+1)] 2 px or more inside
+    raw_x = b * b * S * S / (P * var) + lam * 4 / P
+    raw_y = c * c * S * S / (P * var) + lam * 4 / P
+    ratio = (m[0][interior] / raw_x).ravel().tolist() + (m[1][interior] / raw_y).ravel().tolist()
+    np.testing.assert_allclose(ratio, ratio[0], rtol=1e-10)   # one normalisation constant for all
+    assert m[0][interior] == pytest.approx(raw_x * ratio[0], rel=1e-12)
+
+
+def test_metric_of_a_constant_image_is_the_regulariser_alone():
+    g = O.grid_for(40, 30, 8)
+    m = O.grid_metric(np.full((30, 40), 0.4), 0, g, np.zeros((2, g.ny, g.nx)), 2.0)
+    nb = np.zeros((g.ny, g.nx))
+    nb[:, 1:] += 1; nb[:, :-1] += 1; nb[1:, :] += 1; nb[:-1, :] += 1
+    np.testing.assert_allclose(m[0], nb / nb.mean(), rtol=1e-13)
+    np.testing.assert_allclose(m[1], nb / nb.mean(), rtol=1e-13)
+
+
+def test_the_metric_changes_the_path_not_the_minimiser():
+    # the stationary point of the energy does not depend on the scalar product of the flow
+    ser = synth.make_series(synth.SeriesSpec(2, 96, 96, step=1.5, field_amp=1.0, snr=(10, 10), seed=35))
+    F = ser.frames.numpy()
+    out = []
+    for metric in (0, 1):
+        cfg = O.Config(levels=2, mode="nonrigid", metric=metric, tol_grad=1e-7, max_iter=4000)
+        c, st = O.register_nonrigid(O.pyramid(F[0], 2), O.pyramid(F[1], 2), None, cfg)
+        assert st.stop == [0, 0]
+        out.append(c)
+    assert O.max_px_error(out[0], out[1], 96, 96, "nonrigid") <= 1e-4
