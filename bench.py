@@ -193,7 +193,8 @@ def oracle_sample(frames_np, cfg_bind, budget_s: float):
     import oracle as O
     oc = O.Config(levels=cfg_bind.levels, max_iter=cfg_bind.max_iter, max_rejects=cfg_bind.max_rejects,
                   tol_grad=cfg_bind.tol_grad, tol_rel_e=cfg_bind.tol_rel_e, armijo_c=cfg_bind.armijo_c,
-                  tau0=cfg_bind.tau0, step_cap=cfg_bind.step_cap, lam=cfg_bind.lam, mode=cfg_bind.mode)
+                  tau0=cfg_bind.tau0, step_cap=cfg_bind.step_cap, lam=cfg_bind.lam, mode=cfg_bind.mode,
+                metric=cfg_bind.metric)
     t0 = time.perf_counter()
     pyr = {}
     ops = 0
@@ -237,7 +238,8 @@ def oracle_sample_parallel(frames_np, cfg_bind, budget_s: float, workers: int = 
     workers = workers or os.cpu_count() or 1
     cfgd = dict(levels=cfg_bind.levels, max_iter=cfg_bind.max_iter, max_rejects=cfg_bind.max_rejects,
                 tol_grad=cfg_bind.tol_grad, tol_rel_e=cfg_bind.tol_rel_e, armijo_c=cfg_bind.armijo_c,
-                tau0=cfg_bind.tau0, step_cap=cfg_bind.step_cap, lam=cfg_bind.lam, mode=cfg_bind.mode)
+                tau0=cfg_bind.tau0, step_cap=cfg_bind.step_cap, lam=cfg_bind.lam, mode=cfg_bind.mode,
+                metric=cfg_bind.metric)
     N = frames_np.shape[0]
     tasks = [(frames_np[3 * q:3 * q + 3].copy(), cfgd) for q in range(max(1, (N - 1) // 3))]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
@@ -340,7 +342,7 @@ def precision(frames, mode: str, n_samples: int = 6):
     cfg0 = B.Config(mode=mode)
     oc = O.Config(levels=cfg0.levels, max_iter=cfg0.max_iter, max_rejects=cfg0.max_rejects, tol_grad=cfg0.tol_grad,
                   tol_rel_e=cfg0.tol_rel_e, armijo_c=cfg0.armijo_c, tau0=cfg0.tau0, step_cap=cfg0.step_cap,
-                  lam=cfg0.lam, mode=mode, grid=cfg0.grid)
+                  lam=cfg0.lam, mode=mode, grid=cfg0.grid, metric=cfg0.metric)
     for i in idx:
         ref[i] = O.op_A({i: O.pyramid(Fh[i], oc.levels), i + 1: O.pyramid(Fh[i + 1], oc.levels)}, i, i + 1, oc)
     out = {}
@@ -466,7 +468,8 @@ def mixed_batch(args, dev, world, rank, dist):
         cfg0 = B.Config(mode=args.mode)
         oc = O.Config(levels=cfg0.levels, max_iter=cfg0.max_iter, max_rejects=cfg0.max_rejects,
                       tol_grad=cfg0.tol_grad, tol_rel_e=cfg0.tol_rel_e, armijo_c=cfg0.armijo_c, tau0=cfg0.tau0,
-                      step_cap=cfg0.step_cap, lam=cfg0.lam, mode=args.mode, grid=cfg0.grid)
+                      step_cap=cfg0.step_cap, lam=cfg0.lam, mode=args.mode, grid=cfg0.grid,
+                      metric=cfg0.metric)
         samples = [(S, 0, j) for S in (256, 512) if S in batches for j in (5, 77)]
         for storage in ("f32", "bf16", "f16"):
             ctx = B.Context(B.Config(mode=args.mode, storage=storage, cluster=16))

@@ -116,7 +116,7 @@ typedef struct {
     int    levels;        /* pyramid levels, 1..REG_MAX_LEVELS */
     int    max_iter;      /* accepted gradient-flow steps per level */
     int    max_rejects;   /* rejected Armijo trials allowed per step */
-    double tol_grad;      /* stop: metric norm of the descent direction (default 1e-4) */
+    double tol_grad;      /* stop: metric norm of the descent direction (default 3e-5) */
     double tol_rel_e;     /* stop: relative energy decrease of an accepted step; 0 (default)
                              stops only on an accepted step that does not lower E at all */
     double armijo_c;      /* sufficient-decrease constant */
@@ -129,7 +129,18 @@ typedef struct {
     size_t mem_budget;    /* stream service: device bytes it may hold; 0 = unlimited */
     int    grid;          /* REG_NONRIGID control-grid spacing in finest pixels; 0 = auto (16,
                              doubled until at most 65 points per axis); a multiple of 2^(levels-1) */
+    int    metric;        /* REG_NONRIGID scalar product of the gradient flow: REG_METRIC_GAUSS_NEWTON
+                             (default) or REG_METRIC_MEAN */
 } reg_config_t;
+
+/* Scalar product of the nonrigid gradient flow [Sec. 2.3.1 takes the flow with respect to a
+ * scalar product it does not fix].  REG_METRIC_MEAN: the mean over control points.
+ * REG_METRIC_GAUSS_NEWTON: per level, each control point and axis weighted by the Gauss-Newton
+ * curvature of the data term at the level's initial deformation, sum_x w_j(x)^2 (dT/dp)^2 /
+ * (P var T), plus the regulariser's lambda n_j / P (n_j neighbours), normalised by the mean and
+ * floored at 1e-3 of it: each control point's step is scaled by its own curvature. */
+#define REG_METRIC_MEAN         0
+#define REG_METRIC_GAUSS_NEWTON 1
 
 typedef struct {
     int32_t i, k;                      /* the element this operator produced */
@@ -157,7 +168,8 @@ typedef struct {
 /* ---- configuration and context ----------------------------------------- */
 
 /* Fill *cfg with the defaults (rigid, 2 levels, FP32 storage, auto tiles; stop on a metric
- * gradient norm below 1e-4, at most 500 accepted steps per level). */
+ * gradient norm below 3e-5, at most 500 accepted steps per level; Gauss-Newton scalar product
+ * for the nonrigid flow). */
 void reg_config_default(reg_config_t *cfg);
 
 /* Create a context on CUDA device `device`.  The context owns its pyramids,
@@ -331,6 +343,16 @@ int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out);
 /* Submit one frame (host or device, [H][W] fp32; copied before return).
  * REG_EBUDGET: no slot or memory free right now; retry after polling. */
 int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t frame_id);
+
+/* REG_NONRIGID streams: the control values of every result, not only its mean displacement.
+ * ring: caller-owned device memory of `capacity` grids [capacity][ny][nx] (x, y) pairs (ny, nx
+ * from reg_grid_dims for the stream's W, H and the context's configuration).  The control values
+ * of phi_{0,i} are in ring[i % capacity] by the time frame i's result is reported by
+ * reg_stream_poll (elem.k = i; f_0 gets the identity), and stay there until the result of frame
+ * i + capacity is computed: capacity must cover the frames in flight plus those not yet
+ * consumed.  Call before the first submit.  Errors: REG_EINVAL for a rigid stream, a host ring
+ * or capacity < 1; REG_ESTATE after the first submit. */
+int reg_stream_grids(reg_stream_t *s, float *ring, int capacity);
 
 /* Collect up to `max` finished results in submission order; waits up to
  * timeout_us for at least one (0 = do not wait).  *n_out = number written.

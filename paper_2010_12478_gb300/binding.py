@@ -32,7 +32,7 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
            "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load",
-           "reg_scan_grids", "reg_warp", "reg_scan_batch", "reg_scan_node_grids"]
+           "reg_scan_grids", "reg_warp", "reg_scan_batch", "reg_scan_node_grids", "reg_stream_grids"]
 
 
 class RegError(RuntimeError):
@@ -51,7 +51,8 @@ class reg_config_t(ctypes.Structure):
                 ("max_rejects", ctypes.c_int), ("tol_grad", ctypes.c_double), ("tol_rel_e", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double), ("step_cap", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("storage", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("grid", ctypes.c_int)]
+                ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("grid", ctypes.c_int),
+                ("metric", ctypes.c_int)]
 
 
 class reg_stats_t(ctypes.Structure):
@@ -101,6 +102,7 @@ def lib() -> ctypes.CDLL:
         L.reg_stream_submit.argtypes = [vp, fp, ctypes.c_uint64]
         L.reg_stream_poll.argtypes = [vp, ctypes.POINTER(reg_result_t), ip, ctypes.POINTER(ctypes.c_int), ip]
         L.reg_stream_close.argtypes = [vp]
+        L.reg_stream_grids.argtypes = [vp, fp, ip]
         L.reg_pairwise_noalloc.argtypes = [ctypes.POINTER(reg_config_t), ip, fp, fp, ip, ip, ip,
                                            ctypes.POINTER(reg_elem_t), ctypes.POINTER(reg_elem_t),
                                            ctypes.POINTER(reg_stats_t), vp]
@@ -149,7 +151,7 @@ class Config:
     levels: int = 2
     max_iter: int = 500
     max_rejects: int = 30
-    tol_grad: float = 1e-4
+    tol_grad: float = 3e-5
     tol_rel_e: float = 0.0
     armijo_c: float = 0.25
     tau0: float = 1.0
@@ -160,12 +162,13 @@ class Config:
     workers: int = 0
     mem_budget: int = 0
     grid: int = 0
+    metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control points
 
     def c(self) -> reg_config_t:
         return reg_config_t(RIGID if self.mode == "rigid" else NONRIGID, self.levels, self.max_iter,
                             self.max_rejects, self.tol_grad, self.tol_rel_e, self.armijo_c, self.tau0,
                             self.step_cap, self.lam, STORAGES[self.storage], self.cluster, self.workers,
-                            self.mem_budget, self.grid)
+                            self.mem_budget, self.grid, self.metric)
 
 
 def stats_dict(s: reg_stats_t, levels: int) -> dict:
@@ -376,6 +379,11 @@ class Stream:
         h = ctypes.c_void_p()
         check(lib().reg_stream_open(ctx.h, W, H, ctypes.byref(h)), "reg_stream_open")
         self.h = h
+
+    def set_grids(self, ring):
+        """Nonrigid streams: write each result's control values into ring[i % len(ring)] (device
+        tensor [capacity, ny, nx, 2]); call before the first submit."""
+        check(lib().reg_stream_grids(self.h, _ptr(ring), ring.shape[0]), "reg_stream_grids")
 
     def submit(self, frame, frame_id: int) -> int:
         return lib().reg_stream_submit(self.h, _ptr(frame), frame_id)

@@ -302,8 +302,9 @@ extern "C" void reg_config_default(reg_config_t *c)
     c->levels = 2;
     c->max_iter = 500;
     c->max_rejects = 30;
-    c->tol_grad = 1e-4;
+    c->tol_grad = 3e-5;
     c->tol_rel_e = 0.0;
+    c->metric = REG_METRIC_GAUSS_NEWTON;
     c->armijo_c = 0.25;
     c->tau0 = 1.0;
     c->step_cap = 0.5;
@@ -329,6 +330,7 @@ static int validate_cfg(const reg_config_t &c)
         return fail(REG_EINVAL, "cluster %d not in {0,1,2,4,8,16}", c.cluster);
     if (c.lambda < 0) return fail(REG_EINVAL, "lambda < 0");
     if (c.grid < 0) return fail(REG_EINVAL, "grid < 0");
+    if (c.metric != REG_METRIC_MEAN && c.metric != REG_METRIC_GAUSS_NEWTON) return fail(REG_EINVAL, "metric %d", c.metric);
     return REG_OK;
 }
 
@@ -469,10 +471,10 @@ int grid_dims(int W, int H, int grid, int levels, GridDims &g)
     if (g.nx < 2 || g.ny < 2) return fail(REG_EINVAL, "control grid needs >= 2x2 points");
     if ((sp >> (levels - 1)) < 1 || (sp & ((1 << (levels - 1)) - 1)) != 0)
         return fail(REG_EINVAL, "grid spacing %d must be a multiple of 2^(levels-1)", sp);
-    // dynamic shared memory of a one-CTA operator (the largest band): c, d, ct and the band as
-    // float2, then one float4 control row per warp; the static part stays under 8 KB
+    // dynamic shared memory of a one-CTA operator (the largest band): c, d, ct, the scalar product
+    // and the band as float2, then one float4 control row per warp; the static part stays under 8 KB
     const size_t nc = (size_t)g.nx * g.ny;
-    if (8 * (4 * nc + 1) + 16 * (size_t)(kThreads / 32) * (g.nx - 1) > 216 * 1024)
+    if (8 * (5 * nc + 1) + 16 * (size_t)(kThreads / 32) * (g.nx - 1) > 216 * 1024)
         return fail(REG_EINVAL, "control grid %dx%d does not fit shared memory; use a larger spacing", g.nx, g.ny);
     return REG_OK;
 }
@@ -490,6 +492,7 @@ Config dev_config(const reg_config_t &c)
     d.tau0 = c.tau0;
     d.step_cap = c.step_cap;
     d.lambda = c.lambda;
+    d.metric = c.metric;
     return d;
 }
 

@@ -71,6 +71,7 @@ enum DevStatus : int32_t {
 struct Config {
     int mode, levels, max_iter, max_rejects;
     double tol_grad, tol_rel_e, armijo_c, tau0, step_cap, lambda;
+    int metric;   // nonrigid scalar product: REG_METRIC_MEAN or REG_METRIC_GAUSS_NEWTON
 };
 
 // Ready-queue state of the persistent executor (device memory).
@@ -106,6 +107,8 @@ struct Params {
 // (storage-typed); means[f * levels + l] = mean of level l of frame f (or null).
 cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, int H, int pitch, int levels,
                            int storage, const PyrOut &out, float *means, cudaStream_t s);
+// tab[l].mean = means[l] for l < L (a slot's level table rows after its pyramid build).
+cudaError_t launch_set_level_means(LevelDesc *tab, const float *means, int L, cudaStream_t s);
 cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_ops,
                        cudaStream_t s);
 cudaError_t launch_persistent(const Params &p, int storage, int cluster, int workers,

@@ -519,7 +519,7 @@ __device__ void eval_rigid_grad(const Lvl &L, int r0, int r1, const float *pm, S
     cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
 }
 
-enum Action { kActGrad = 0, kActTrial = 1, kActDone = 2, kActEnergy = 3, kActField = 4 };
+enum Action { kActGrad = 0, kActTrial = 1, kActDone = 2, kActEnergy = 3, kActField = 4, kActMetric = 5 };
 
 
 __device__ void rigid_params(const double *th, float *pm)
@@ -771,12 +771,13 @@ __host__ __device__ __forceinline__ int grid_band_elems(int gnx, int gny, int C)
     return ((gny - 1 + C - 1) / C + 1) * gnx;
 }
 
-// Dynamic shared memory of the nonrigid kernels, in float2 units: c, d, ct (whole grid each),
-// the band of partial gradients, then (16-byte aligned) one row of gnx - 1 float4 per warp:
-// the control values of the warp's pixel row interpolated along y, (u_j, u_{j+1} - u_j).
+// Dynamic shared memory of the nonrigid kernels, in float2 units: c, d, ct, mt (whole grid each;
+// mt the flow's scalar product per control point and axis), the band of partial gradients, then
+// (16-byte aligned) one row of gnx - 1 float4 per warp: the control values of the warp's pixel row
+// interpolated along y, (u_j, u_{j+1} - u_j).
 __host__ __device__ __forceinline__ int grid_crow_offset(int gnx, int gny, int C)
 {
-    const int o = 3 * gnx * gny + grid_band_elems(gnx, gny, C);
+    const int o = 4 * gnx * gny + grid_band_elems(gnx, gny, C);
     return o + (o & 1);
 }
 
@@ -925,12 +926,19 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int l
 // corner, so each corner is updated by one warp at a time, in a fixed order); then every CTA
 // assembles the whole gradient from the (at most two) CTAs whose band holds each control row,
 // and forms d = -(Nc/P) [sum F grad T w + lambda sum_nbrs (c_j - c_k)], F = P dE/dTw.
-// pm: aP, bP, rbar, tbar, lambda.  Returns sum |d|^2 (float-float, in sm.tot[0]), max |d|^2
-// (sm.tot[1]), and with the direction d held before the call, <d_old, d_old - d> (sm.tot[2]) and
-// |d_old - d|^2 (sm.tot[3]); identical in every CTA.
-template <typename S>
+// d = -M^-1 grad E with the scalar product mt.  pm: aP, bP, rbar, tbar, lambda.  Returns
+// sum_j m_j |d_j|^2 (float-float, in sm.tot[0]), max |d_j|^2 (sm.tot[1]), and with the direction
+// d held before the call, <d_old, d_old - d>_M (sm.tot[2]) and |d_old - d|_M^2 (sm.tot[3]);
+// identical in every CTA.
+//
+// METRIC: instead of the gradient, the flow's scalar product at c (the level's initial control
+// values): per control point and axis m = dk sum_x w_j(x)^2 (dT/dp)^2 + rk n_j (pm[0] = dk =
+// 1/(P var T), pm[1] = rk = lambda/P, n_j the neighbours of j), normalised by the mean of all
+// 2 Nc values and floored at 1e-3 of it, written to mt.
+template <typename S, bool METRIC>
 __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *c, float2 *d,
-                               float2 *gp, const float *pm, int cr0, int cr1, Smem &sm, const cg::cluster_group &cl)
+                               float2 *mt, float2 *gp, const float *pm, int cr0, int cr1, Smem &sm,
+                               const cg::cluster_group &cl)
 {
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     const float aP = pm[0], bP = pm[1], rb = pm[2], tb = pm[3], lam = pm[4];
@@ -983,17 +991,26 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
                     float dtx, dty;
                     const float tw = sample_q<S, true>(T, L.W, L.H, L.Tp, x, y, fmaf(wy, ex, tx), fmaf(wy, ey, ty),
                                                        dtx, dty);
-                    const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
-                    const float tv = tw - L.cR;
-                    // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
-                    const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
-                    const float gx = F * dtx, gy = F * dty, hy = 1.f - wy;
-                    st_x = fmaf(hy, gx, st_x); st_y = fmaf(hy, gy, st_y);
-                    sb_x = fmaf(wy, gx, sb_x); sb_y = fmaf(wy, gy, sb_y);
+                    const float hy = 1.f - wy;
+                    if constexpr (METRIC) {
+                        // squared weights: w^2 = hx^2 hy^2 factorises like w
+                        (void)tw;
+                        const float gx = dtx * dtx, gy = dty * dty, hy2 = hy * hy, wy2 = wy * wy;
+                        st_x = fmaf(hy2, gx, st_x); st_y = fmaf(hy2, gy, st_y);
+                        sb_x = fmaf(wy2, gx, sb_x); sb_y = fmaf(wy2, gy, sb_y);
+                    } else {
+                        const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
+                        const float tv = tw - L.cR;
+                        // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
+                        const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
+                        const float gx = F * dtx, gy = F * dty;
+                        st_x = fmaf(hy, gx, st_x); st_y = fmaf(hy, gy, st_y);
+                        sb_x = fmaf(wy, gx, sb_x); sb_y = fmaf(wy, gy, sb_y);
+                    }
                 }
-                const float hx = 1.f - wx;
-                acc[0] = hx * st_x; acc[1] = hx * st_y; acc[2] = wx * st_x; acc[3] = wx * st_y;
-                acc[4] = hx * sb_x; acc[5] = hx * sb_y; acc[6] = wx * sb_x; acc[7] = wx * sb_y;
+                const float hx = METRIC ? (1.f - wx) * (1.f - wx) : 1.f - wx, vx = METRIC ? wx * wx : wx;
+                acc[0] = hx * st_x; acc[1] = hx * st_y; acc[2] = vx * st_x; acc[3] = vx * st_y;
+                acc[4] = hx * sb_x; acc[5] = hx * sb_y; acc[6] = vx * sb_x; acc[7] = vx * sb_y;
             } else
             for (int i = lane; i < npx; i += 32) {
                 const int y = y0 + i / w, x = x0 + i % w;
@@ -1005,13 +1022,22 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
                 const float ux = fmaf(wy, bx - tx, tx), uy = fmaf(wy, by - ty, ty);
                 float dtx, dty;
                 const float tw = sample_q<S, true>(T, L.W, L.H, L.Tp, x, y, ux, uy, dtx, dty);
-                const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
-                const float tv = tw - L.cR;
-                // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
-                const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
-                const float gx = F * dtx, gy = F * dty;
+                float gx, gy;
+                if constexpr (METRIC) {
+                    (void)tw;
+                    gx = dtx * dtx;
+                    gy = dty * dty;
+                } else {
+                    const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
+                    const float tv = tw - L.cR;
+                    // F = P dE/dTw = -(aP (r - rbar) - bP (t - tbar)), no contraction
+                    const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
+                    gx = F * dtx;
+                    gy = F * dty;
+                }
                 const float hx = 1.f - wx, hy = 1.f - wy;
-                const float w00 = hx * hy, w01 = wx * hy, w10 = hx * wy, w11 = wx * wy;
+                float w00 = hx * hy, w01 = wx * hy, w10 = hx * wy, w11 = wx * wy;
+                if constexpr (METRIC) { w00 *= w00; w01 *= w01; w10 *= w10; w11 *= w11; }
                 acc[0] = fmaf(w00, gx, acc[0]); acc[1] = fmaf(w00, gy, acc[1]);
                 acc[2] = fmaf(w01, gx, acc[2]); acc[3] = fmaf(w01, gy, acc[3]);
                 acc[4] = fmaf(w10, gx, acc[4]); acc[5] = fmaf(w10, gy, acc[5]);
@@ -1031,6 +1057,51 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     const int C = cl.num_blocks();
     const int q = (ncy + C - 1) / C;
     const float scale = -(float)Nc / ((float)L.W * (float)L.H);
+    if constexpr (METRIC) {
+        // m_j = dk sum w^2 dT^2 + rk n_j per axis, then its mean over all 2 Nc values
+        const float dk = pm[0], rk = pm[1];
+        float mh = 0.f, ml = 0.f, mrun = 0.f;
+        int kk = 0;
+        for (int j = tid; j < Nc; j += kThreads) {
+            const int jy = j / G.nx, jx = j - jy * G.nx;
+            const int rlo = jy > 0 ? min(C - 1, (jy - 1) / max(q, 1)) : 0;
+            const int rhi = min(C - 1, jy / max(q, 1));
+            float2 h = *cl.map_shared_rank(gp + (jy - min(ncy, rlo * q)) * G.nx + jx, rlo);
+            if (rhi != rlo) {
+                const float2 h2 = *cl.map_shared_rank(gp + (jy - min(ncy, rhi * q)) * G.nx + jx, rhi);
+                h.x += h2.x;
+                h.y += h2.y;
+            }
+            const float nb = (float)((jx > 0) + (jx + 1 < G.nx) + (jy > 0) + (jy + 1 < G.ny));
+            const float2 m = make_float2(fmaf(dk, h.x, rk * nb), fmaf(dk, h.y, rk * nb));
+            mt[j] = m;
+            mrun += m.x + m.y;
+            if (++kk == kFast) { ff_acc(mh, ml, mrun); mrun = 0.f; kk = 0; }
+        }
+        ff_acc(mh, ml, mrun);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, mh, off), l2 = __shfl_xor_sync(0xffffffffu, ml, off);
+            ff_add(mh, ml, h2, l2);
+        }
+        if (lane == 0) sm.warp[warp][0] = make_float2(mh, ml);
+        __syncthreads();
+        if (tid == 0) {
+            float h = 0.f, l = 0.f;
+            for (int w2 = 0; w2 < kWarps; ++w2) ff_add(h, l, sm.warp[w2][0].x, sm.warp[w2][0].y);
+            sm.tot[0] = ((double)h + (double)l) / (2.0 * Nc);
+        }
+        __syncthreads();
+        const double mean = sm.tot[0];
+        const float inv = mean > 0.0 ? (float)(1.0 / mean) : 0.f;
+        for (int j = tid; j < Nc; j += kThreads) {
+            const float2 m = mt[j];
+            mt[j] = mean > 0.0 ? make_float2(fmaxf(m.x * inv, 1e-3f), fmaxf(m.y * inv, 1e-3f)) : make_float2(1.f, 1.f);
+        }
+        // no CTA may overwrite its band (next gradient pass) while a peer still reads it
+        cl.sync();
+        return;
+    }
     float ssh = 0.f, ssl = 0.f, mx = 0.f, run = 0.f;
     // <d_prev, d_prev - d> and |d_prev - d|^2 for the first trial step (d still holds d_prev)
     float nmh = 0.f, nml = 0.f, dnh = 0.f, dnl = 0.f, nrun = 0.f, drun = 0.f;
@@ -1070,16 +1141,18 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
         if (jx + 1 < G.nx) { const float2 v = c[j + 1];    lx += cj.x - v.x; ly += cj.y - v.y; }
         if (jy > 0)        { const float2 v = c[j - G.nx]; lx += cj.x - v.x; ly += cj.y - v.y; }
         if (jy + 1 < G.ny) { const float2 v = c[j + G.nx]; lx += cj.x - v.x; ly += cj.y - v.y; }
+        // d = -M^-1 grad E with the level's scalar product M (per axis)
+        const float2 mj = mt[j];
         float2 dj;
-        dj.x = scale * fmaf(lam, lx, g.x);
-        dj.y = scale * fmaf(lam, ly, g.y);
+        dj.x = scale * fmaf(lam, lx, g.x) / mj.x;
+        dj.y = scale * fmaf(lam, ly, g.y) / mj.y;
         const float2 dold = d[j];
         d[j] = dj;
         const float qd = fmaf(dj.x, dj.x, dj.y * dj.y);
         const float yx = dold.x - dj.x, yy = dold.y - dj.y;
-        run += qd;
-        nrun = fmaf(dold.x, yx, fmaf(dold.y, yy, nrun));
-        drun = fmaf(yx, yx, fmaf(yy, yy, drun));
+        run = fmaf(mj.x * dj.x, dj.x, fmaf(mj.y * dj.y, dj.y, run));
+        nrun = fmaf(mj.x * dold.x, yx, fmaf(mj.y * dold.y, yy, nrun));
+        drun = fmaf(mj.x * yx, yx, fmaf(mj.y * yy, yy, drun));
         mx = fmaxf(mx, qd);
         if (++k == kFast) {
             ff_acc(ssh, ssl, run); run = 0.f;
@@ -1149,6 +1222,17 @@ __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int
     if (action == kActEnergy) {
         k.sr = tot[3]; k.srr = tot[4];
         k.E = field_energy(k, cfg, tot, false);
+        if (cfg.metric == 1) {
+            // the level's scalar product at its initial control values: 1/(P var T) and lambda/P
+            const double vt = (tot[1] - tot[0] * tot[0] * k.invP) * k.invP;
+            pm[0] = vt > 0.0 ? (float)(k.invP / vt) : 0.f;
+            pm[1] = (float)(cfg.lambda * k.invP);
+            return kActMetric;
+        }
+        field_grad_params(k, cfg, pm);
+        return kActGrad;
+    }
+    if (action == kActMetric) {
         field_grad_params(k, cfg, pm);
         return kActGrad;
     }
@@ -1217,7 +1301,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
     const int Lc = cfg.levels;
     const Grid G{p.gnx, p.gny, p.gs};
     const int Nc = G.nx * G.ny;
-    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
+    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *mt = gbuf + 3 * Nc, *gp = gbuf + 4 * Nc;
     float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, C));
     int buf = 0;
     // initial control values (finest px), scaled to the coarsest level
@@ -1258,6 +1342,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
         GL.scale_inv = 1.f / (float)G.s;
         int cr0, cr1, r0, r1;
         grid_rows(G, GL, rank, C, cr0, cr1, r0, r1);
+        for (int j = tid; j < Nc; j += kThreads) mt[j] = make_float2(1.f, 1.f);
         if (tid == 0) {
             k.P = (double)L.W * (double)L.H;
             k.invP = 1.0 / k.P;
@@ -1283,8 +1368,10 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
                 }
                 __syncthreads();
                 grid_energy_pass<S, false>(L, G, GL, ct, crow, r0, r1, sm, buf, cl);
+            } else if (act == kActMetric) {
+                grid_grad_pass<S, true>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
             } else {
-                grid_grad_pass<S>(L, G, GL, c, d, gp, pm, cr0, cr1, sm, cl);
+                grid_grad_pass<S, false>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
             }
             if (tid == 0) {
                 const int next = field_step(k, cfg, sm.tot, act, sm.pm);
@@ -1467,9 +1554,9 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
     } else {
         const Grid G{p.gnx, p.gny, p.gs};
         const int Nc = G.nx * G.ny;
-        float2 *c = gbuf, *d = gbuf + Nc, *gp = gbuf + 3 * Nc;
+        float2 *c = gbuf, *d = gbuf + Nc, *mt = gbuf + 3 * Nc, *gp = gbuf + 4 * Nc;
         float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, 1));
-        for (int j = tid; j < Nc; j += kThreads) c[j] = cgrid[j];
+        for (int j = tid; j < Nc; j += kThreads) { c[j] = cgrid[j]; mt[j] = make_float2(1.f, 1.f); }
         __syncthreads();
         GridLvl GL;
         GL.W = L.W; GL.H = L.H; GL.l = 0; GL.pl = 1.f; GL.off = 0.f; GL.scale_inv = 1.f / (float)G.s;
@@ -1491,8 +1578,8 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
         if (grad_c) {
             float pm[5];
             for (int q = 0; q < 5; ++q) pm[q] = sm.pm[q];
-            grid_grad_pass<S>(L, G, GL, c, d, gp, pm, cr0, cr1, sm, cl);
-            // d = -Nc dE/dc
+            grid_grad_pass<S, false>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
+            // d = -Nc dE/dc (unit scalar product)
             const float s = -1.f / (float)Nc;
             for (int j = tid; j < Nc; j += kThreads) grad_c[j] = make_float2(s * d[j].x, s * d[j].y);
         }
@@ -1599,6 +1686,19 @@ __global__ void __launch_bounds__(kThreads) level_mean(const S *img, size_t stri
         for (int k = 0; k < kWarps; ++k) ff_add(h, l, ws[k].x, ws[k].y);
         mean[(size_t)blockIdx.x * mstride] = (float)(((double)h + (double)l) / (double)n);
     }
+}
+
+// The level means of a freshly built pyramid into its rows of a level table.
+__global__ void set_level_means_kernel(LevelDesc *tab, const float *means, int L)
+{
+    const int l = threadIdx.x;
+    if (l < L) tab[l].mean = means[l];
+}
+
+cudaError_t launch_set_level_means(LevelDesc *tab, const float *means, int L, cudaStream_t s)
+{
+    set_level_means_kernel<<<1, 32, 0, s>>>(tab, means, L);
+    return cudaGetLastError();
 }
 
 // Composition of two control grids at the control points (standalone entry point).

@@ -211,6 +211,7 @@ extern "C" int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const f
         p.cfg.tau0 = cfg->tau0;
         p.cfg.step_cap = cfg->step_cap;
         p.cfg.lambda = cfg->lambda;
+        p.cfg.metric = cfg->metric;
         p.levels = tab;
         p.n_frames = 2;
         p.ops = op;

@@ -61,19 +61,25 @@ struct reg_stream {
     size_t lvl_elems[kMaxLevels] = {};
     int pad = 0;
     int Wl[kMaxLevels] = {}, Hl[kMaxLevels] = {};
-    float *stage = nullptr;      // one fp32 frame being copied in
+    float *stage[2] = {};        // fp32 frames being copied in (two, used in turn)
+    cudaEvent_t stage_free[2] = {};   // the pyramid build that read stage[b] is done
+    int next_stage = 0;
     float *means = nullptr;      // level means of the frame being staged
     LevelDesc *table = nullptr;  // [kSlots + 1][L]; slot 0 holds f_0
     OpDesc *ops = nullptr;       // [2 (kSlots + 1)]: A of slot s at 2s, B at 2s + 1
     OpStats *stats = nullptr;
     double *theta = nullptr;     // nodes, one per op
     float2 *grid = nullptr;
+    float2 *ring = nullptr;      // caller's ring of prefix control grids (reg_stream_grids), or null
+    int ring_cap = 0;
     int *status = nullptr;
     // pinned host mirrors
     OpDesc *h_ops = nullptr;
     double *h_theta = nullptr;
     OpStats *h_stats = nullptr;
-    cudaStream_t copy = nullptr;
+    cudaStream_t copy = nullptr;     // input copies
+    cudaStream_t build = nullptr;    // pyramid builds (after their copy)
+    cudaEvent_t copied = nullptr;    // the last submitted frame has been read
     // host state (guarded by the service mutex)
     Slot slots[kSlots + 1];
     long long submitted = 0;     // frames submitted, f_0 included
@@ -122,6 +128,7 @@ Params stream_params(reg_stream *s)
     p.cfg.tau0 = c.tau0;
     p.cfg.step_cap = c.step_cap;
     p.cfg.lambda = c.lambda;
+    p.cfg.metric = c.metric;
     p.levels = s->table;
     p.n_frames = kSlots + 1;
     p.ops = s->ops;
@@ -138,7 +145,8 @@ Params stream_params(reg_stream *s)
 }
 
 // Launch one operator (op index e) on a service lane; results to pinned memory; event after.
-int launch_op(Service *sv, reg_stream *s, int e, const OpDesc &op, cudaEvent_t ev)
+// prefix >= 0: the operator produces phi_{0,prefix}, whose control values go to the caller's ring.
+int launch_op(Service *sv, reg_stream *s, int e, const OpDesc &op, cudaEvent_t ev, long long prefix)
 {
     cudaStream_t ls;
     if (op.left >= 0) {
@@ -160,6 +168,12 @@ int launch_op(Service *sv, reg_stream *s, int e, const OpDesc &op, cudaEvent_t e
         return REG_ECUDA;
     if (cudaMemcpyAsync(s->h_stats + e, s->stats + e, sizeof(OpStats), cudaMemcpyDeviceToHost, ls) != cudaSuccess)
         return REG_ECUDA;
+    if (prefix >= 0 && s->ring) {
+        const size_t nc = (size_t)s->gnx * s->gny;
+        if (cudaMemcpyAsync(s->ring + (size_t)(prefix % s->ring_cap) * nc, s->grid + (size_t)e * nc,
+                            sizeof(float2) * nc, cudaMemcpyDeviceToDevice, ls) != cudaSuccess)
+            return REG_ECUDA;
+    }
     if (cudaEventRecord(ev, ls) != cudaSuccess) return REG_ECUDA;
     return REG_OK;
 }
@@ -210,7 +224,7 @@ void advance(Service *sv, reg_stream *s)
         // A(f_{i-1}, f_i)
         if (!sl->a_launched && done(sl->ready) && prev_frame_ready && (i == 1 || done(prev->ready))) {
             OpDesc op{i == 1 ? 0 : slot_of(i - 1), si, -1, -1, a_op, -1};
-            if (launch_op(sv, s, a_op, op, sl->a_ev) != REG_OK) { s->error = REG_ECUDA; return; }
+            if (launch_op(sv, s, a_op, op, sl->a_ev, i == 1 ? 1 : -1) != REG_OK) { s->error = REG_ECUDA; return; }
             sl->a_launched = true;
         }
         if (sl->a_launched && !sl->a_done && done(sl->a_ev)) sl->a_done = true;
@@ -223,7 +237,7 @@ void advance(Service *sv, reg_stream *s)
         if (!sl->b_launched && sl->a_done && prev_result) {
             const int left = (i - 1 == 1) ? 2 * slot_of(i - 1) : 2 * slot_of(i - 1) + 1;
             OpDesc op{0, si, left, a_op, b_op, -1};
-            if (launch_op(sv, s, b_op, op, sl->b_ev) != REG_OK) { s->error = REG_ECUDA; return; }
+            if (launch_op(sv, s, b_op, op, sl->b_ev, i) != REG_OK) { s->error = REG_ECUDA; return; }
             sl->b_launched = true;
         }
         if (sl->b_launched && !sl->b_done && done(sl->b_ev)) {
@@ -279,7 +293,7 @@ void free_stream(reg_stream *s)
         if (s->pyr[l]) cudaFree(s->pyr[l]);
         if (s->spyr[l]) cudaFree(s->spyr[l]);
     }
-    void *dev[] = {s->stage, s->means, s->table, s->ops, s->stats, s->theta, s->grid, s->status};
+    void *dev[] = {s->stage[0], s->stage[1], s->means, s->table, s->ops, s->stats, s->theta, s->grid, s->status};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (s->h_ops) cudaFreeHost(s->h_ops);
@@ -292,6 +306,10 @@ void free_stream(reg_stream *s)
     }
     if (s->f0_ready) cudaEventDestroy(s->f0_ready);
     if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->build) cudaStreamDestroy(s->build);
+    if (s->copied) cudaEventDestroy(s->copied);
+    for (int b = 0; b < 2; ++b)
+        if (s->stage_free[b]) cudaEventDestroy(s->stage_free[b]);
     delete s;
 }
 
@@ -349,7 +367,7 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
     for (int l = 0; l < c.levels; ++l)
         pyr_bytes += (level_elems(Wl[l], Hl[l], pad) + (pad ? (size_t)Wl[l] * Hl[l] : 0)) * sb;
     const int nops = 2 * (kSlots + 1);
-    const size_t bytes = pyr_bytes * (kSlots + 1) + sizeof(float) * (size_t)W * H + sizeof(LevelDesc) * (kSlots + 1) * c.levels +
+    const size_t bytes = pyr_bytes * (kSlots + 1) + 2 * sizeof(float) * (size_t)W * H + sizeof(LevelDesc) * (kSlots + 1) * c.levels +
                          (sizeof(OpDesc) + sizeof(OpStats) + 3 * sizeof(double)) * nops +
                          sizeof(float2) * (size_t)gnx * gny * nops + 4096;
     Service *sv = service_of(ctx, true);
@@ -381,7 +399,7 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
         ok = cudaMalloc(&s->pyr[l], s->lvl_elems[l] * sb * (kSlots + 1)) == cudaSuccess;
         if (ok && pad) ok = cudaMalloc(&s->spyr[l], (size_t)Wl[l] * Hl[l] * sb * (kSlots + 1)) == cudaSuccess;
     }
-    ok = ok && cudaMalloc(&s->stage, sizeof(float) * (size_t)W * H) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b) ok = cudaMalloc(&s->stage[b], sizeof(float) * (size_t)W * H) == cudaSuccess;
     ok = ok && cudaMalloc(&s->means, sizeof(float) * kMaxLevels) == cudaSuccess;
     ok = ok && cudaMalloc(&s->table, sizeof(LevelDesc) * (kSlots + 1) * c.levels) == cudaSuccess;
     ok = ok && cudaMalloc(&s->ops, sizeof(OpDesc) * nops) == cudaSuccess;
@@ -393,6 +411,11 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
     ok = ok && cudaMallocHost(&s->h_theta, sizeof(double) * 3 * nops) == cudaSuccess;
     ok = ok && cudaMallocHost(&s->h_stats, sizeof(OpStats) * nops) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&s->build, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&s->copied, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaEventCreateWithFlags(&s->stage_free[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventRecord(s->stage_free[b], s->build) == cudaSuccess;
     for (int k = 0; k <= kSlots && ok; ++k) {
         ok = cudaEventCreateWithFlags(&s->slots[k].ready, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->slots[k].a_ev, cudaEventDisableTiming) == cudaSuccess &&
@@ -401,6 +424,23 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
     ok = ok && cudaEventCreateWithFlags(&s->f0_ready, cudaEventDisableTiming) == cudaSuccess;
     if (ok) ok = cudaMemset(s->status, 0, sizeof(int) * 4) == cudaSuccess &&
                  cudaMemset(s->stats, 0, sizeof(OpStats) * nops) == cudaSuccess;
+    if (ok) {
+        // the level table of every slot: fixed pointers and sizes; each submit writes the means
+        const size_t sbs = c.storage == REG_F32 ? 4 : 2;
+        std::vector<LevelDesc> tab((size_t)(kSlots + 1) * c.levels);
+        for (int k = 0; k <= kSlots; ++k)
+            for (int l = 0; l < c.levels; ++l) {
+                LevelDesc &d = tab[(size_t)k * c.levels + l];
+                memset(&d, 0, sizeof(d));
+                d.ptr = (char *)s->pyr[l] + (s->lvl_elems[l] * k + level_origin(Wl[l], pad)) * sbs;
+                d.W = Wl[l];
+                d.H = Hl[l];
+                d.pitch = level_pitch(Wl[l], pad);
+                d.rptr = pad ? (char *)s->spyr[l] + (size_t)Wl[l] * Hl[l] * sbs * k : d.ptr;
+                d.rpitch = pad ? Wl[l] : d.pitch;
+            }
+        ok = cudaMemcpy(s->table, tab.data(), sizeof(LevelDesc) * tab.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     if (!ok) {
         cudaGetLastError();
         free_stream(s);
@@ -447,29 +487,25 @@ extern "C" int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t f
             o.smooth[l] = (char *)s->spyr[l] + o.smooth_stride[l] * sb * slot;
         }
     }
-    float hmeans[kMaxLevels];
-    cudaError_t e = cudaMemcpyAsync(s->stage, frame, fb, cudaMemcpyDefault, s->copy);
+    // the copy reads the caller's frame into one of two staging buffers (once the build that last
+    // read that buffer is done); the pyramid is built on its own stream after the copy, and only
+    // the copy is waited for here
+    const int b = s->next_stage;
+    s->next_stage ^= 1;
+    cudaError_t e = cudaStreamWaitEvent(s->copy, s->stage_free[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->stage[b], frame, fb, cudaMemcpyDefault, s->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(s->copied, s->copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->build, s->copied, 0);
     if (e == cudaSuccess)
-        e = launch_pyramid(s->stage, 1, (size_t)s->W * s->H, s->W, s->H, s->W, s->L, s->storage, o, s->means,
-                           s->copy);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hmeans, s->means, sizeof(float) * s->L, cudaMemcpyDeviceToHost, s->copy);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
-    LevelDesc tab[kMaxLevels];
-    for (int l = 0; l < s->L; ++l) {
-        tab[l].ptr = (char *)o.raw[l] + level_origin(s->Wl[l], s->pad) * sb;
-        tab[l].W = s->Wl[l];
-        tab[l].H = s->Hl[l];
-        tab[l].pitch = level_pitch(s->Wl[l], s->pad);
-        tab[l].rptr = s->pad ? o.smooth[l] : tab[l].ptr;
-        tab[l].rpitch = s->pad ? s->Wl[l] : tab[l].pitch;
-        tab[l].mean = hmeans[l];
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->table + (size_t)slot * s->L, tab, sizeof(LevelDesc) * s->L, cudaMemcpyHostToDevice,
-                            s->copy);
+        e = launch_pyramid(s->stage[b], 1, (size_t)s->W * s->H, s->W, s->H, s->W, s->L, s->storage, o, s->means,
+                           s->build);
+    if (e == cudaSuccess) e = launch_set_level_means(s->table + (size_t)slot * s->L, s->means, s->L, s->build);
+    if (e == cudaSuccess && index == 0 && s->ring)   // phi_{0,0} is the identity
+        e = cudaMemsetAsync(s->ring, 0, sizeof(float2) * (size_t)s->gnx * s->gny, s->build);
     cudaEvent_t ready = index == 0 ? s->f0_ready : s->slots[slot].ready;
-    if (e == cudaSuccess) e = cudaEventRecord(ready, s->copy);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(s->stage_free[b], s->build);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, s->build);
+    if (e == cudaSuccess) e = cudaEventSynchronize(s->copied);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return host_fail(REG_ECUDA, "staging the frame failed: %s", cudaGetErrorString(e));
@@ -495,6 +531,25 @@ extern "C" int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t f
         }
     }
     sv->cv.notify_all();
+    return REG_OK;
+}
+
+extern "C" int reg_stream_grids(reg_stream_t *s, float *ring, int capacity)
+{
+    if (!s || !ring || capacity < 1) return host_fail(REG_EINVAL, "NULL ring or capacity < 1");
+    if (s->mode != REG_NONRIGID) return host_fail(REG_EINVAL, "control grids exist for REG_NONRIGID streams only");
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ring) != cudaSuccess ||
+        !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return host_fail(REG_EINVAL, "the ring must be device memory");
+    }
+    Service *sv = service_of(s->ctx, false);
+    if (!sv) return host_fail(REG_ESTATE, "stream service is not running");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (s->submitted > 0) return host_fail(REG_ESTATE, "set the ring before the first submit");
+    s->ring = (float2 *)ring;
+    s->ring_cap = capacity;
     return REG_OK;
 }
 
@@ -540,6 +595,8 @@ extern "C" int reg_stream_close(reg_stream_t *s)
     }
     cudaSetDevice(host_device(s->ctx));
     for (int i = 0; i < kLanes; ++i) cudaStreamSynchronize(sv->lanes[i]);
+    cudaStreamSynchronize(s->copy);
+    cudaStreamSynchronize(s->build);
     free_stream(s);
     return rc == REG_OK ? REG_OK : host_fail(rc, "stream close timed out waiting for its frames");
 }

@@ -33,7 +33,7 @@ def ctx_of(**kw):
 def ocfg(cfg: B.Config) -> O.Config:
     return O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
                     tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
-                    lam=cfg.lam, mode=cfg.mode, grid=cfg.grid)
+                    lam=cfg.lam, mode=cfg.mode, grid=cfg.grid, metric=cfg.metric)
 
 
 def rel(a, b):
@@ -590,3 +590,44 @@ def test_node_grids_end_with_a_pairwise_call():
     with pytest.raises(B.RegError) as e:
         ctx.scan_node_grids([0], g)
     assert e.value.code == B.REG_ESTATE
+
+
+def test_c3_full_size_nonrigid_sampled_operators_match_oracle():
+    # the 4,096-frame nonrigid scan through the persistent device queue; the B operators with the
+    # largest drift between their frames (prefixes f_0 -> f_k far down the series, where part of f_0
+    # has no counterpart in f_k) and random ones, against the oracle fed the GPU's exact inputs
+    spec = synth.spec_c3()
+    ser = synth.make_series(spec, device="cuda")
+    frames = ser.frames
+    cfg = B.Config(mode="nonrigid", cluster=4)
+    oc = ocfg(cfg)
+    ctx = B.Context(cfg)
+    n = spec.n_frames - 1
+    els, st = ctx.scan(frames, schedule="brent_kung", exec="persistent")
+    ops, _ = B.scan_dag("brent_kung", n)
+    ik = np.array([(s["i"], s["k"]) for s in st])
+    drift = np.sqrt(((ser.shifts[ik[:, 1]] - ser.shifts[ik[:, 0]]) ** 2).sum(1))
+    rng = np.random.default_rng(3)
+    bops = [int(np.argmax(np.where(np.arange(len(st)) >= n, drift, -1.0)))]
+    bops += [int(v) for v in rng.choice(np.arange(n, len(st)), 2, replace=False)]
+    leaves = [int(v) for v in rng.choice(n, 2, replace=False)]
+    want = leaves + bops + [v for j in bops for v in ops[j - n]]
+    nx, ny, _ = B.grid_dims(512, 512)
+    gd = torch.zeros((len(want), ny, nx, 2), device="cuda")
+    ctx.scan_node_grids(want, gd)
+    grid_of = {w: np.transpose(gd[q].cpu().numpy().astype(np.float64), (2, 0, 1)) for q, w in enumerate(want)}
+
+    def P(i):
+        return O.pyramid(frames[i].cpu().numpy(), cfg.levels)
+
+    for j in leaves:
+        e = O.op_A({j: P(j), j + 1: P(j + 1)}, j, j + 1, oc)
+        assert O.max_px_error(grid_of[j], e.phi, 512, 512, "nonrigid") <= PX_TOL, j
+        assert rel(st[j]["energy"], e.stats.energy) <= E_TOL, j
+    for j in bops:
+        l, r = ops[j - n]
+        el = O.Elem(int(ik[l][0]), int(ik[l][1]), grid_of[l])
+        er = O.Elem(int(ik[r][0]), int(ik[r][1]), grid_of[r])
+        e = O.op_B(el, er, {el.i: P(el.i), er.k: P(er.k)}, oc)
+        assert O.max_px_error(grid_of[j], e.phi, 512, 512, "nonrigid") <= PX_TOL, (j, tuple(ik[j]), drift[j])
+        assert rel(st[j]["energy"], e.stats.energy) <= E_TOL, j

@@ -42,9 +42,11 @@ def test_struct_layouts_match_header(lib):
     cfg = B.reg_config_t()
     lib.reg_config_default(ctypes.byref(cfg))
     assert cfg.levels == 2 and cfg.mode == B.RIGID and cfg.storage == B.F32
-    # the stop rule of the oracle's configuration: metric gradient norm 1e-4, no relative-decrease test
-    assert cfg.tol_grad == O.Config().tol_grad == B.Config().tol_grad == 1e-4
+    # the stop rule and scalar product of the oracle's configuration: metric gradient norm 3e-5, no
+    # relative-decrease test, the Gauss-Newton scalar product for the nonrigid flow
+    assert cfg.tol_grad == O.Config().tol_grad == B.Config().tol_grad == 3e-5
     assert cfg.tol_rel_e == O.Config().tol_rel_e == B.Config().tol_rel_e == 0.0
+    assert cfg.metric == O.Config().metric == B.Config().metric == 1
 
 
 def test_errors_without_gpu_are_reported_not_crashing(lib):
