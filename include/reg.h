@@ -77,6 +77,12 @@ extern "C" {
 #define REG_SCHED_BRENT_KUNG    1   /* work-efficient tree scan                        [Table 1] */
 #define REG_SCHED_DISSEMINATION 2   /* recursive doubling, depth log2 N                [Table 1, Fig. 2] */
 #define REG_SCHED_LADNER_FISCHER 3  /* Ladner-Fischer P_0                              [Table 1] */
+/* online scan with a look-back of k leaves: window products of the last k leaves by doubling,
+ * prefix p_j = p_{j-k} (.) (x_{j-k+1} .. x_j), so k chains of prefixes advance side by side
+ * (p_j = p_{j-1} (.) x_j for j < k); the streaming service's schedule, see reg_stream_set_lookback */
+#define REG_SCHED_LOOKBACK_2    17
+#define REG_SCHED_LOOKBACK_4    18
+#define REG_SCHED_LOOKBACK_8    19
 
 #define REG_EXEC_PLAIN      0   /* one operator per kernel launch, DAG order on a stream pool */
 #define REG_EXEC_LEVEL      1   /* one launch per DAG depth, all its operators batched */

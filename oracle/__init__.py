@@ -75,7 +75,8 @@ def lib():
             dpp = ctypes.POINTER(dp)
             L.or_downsample.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
             L.or_sample.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
-            L.or_sample_q.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+            L.or_sample_q.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, dp]
             L.or_rigid_energy.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp]
             L.or_rigid_energy.restype = ctypes.c_int
             L.or_rigid_compose.argtypes = [dp, dp, dp]
@@ -176,13 +177,13 @@ def sample(T, px: float, py: float):
     return out
 
 
-def sample_q(T, px: float, py: float):
-    """Quadratic B-spline model of T's samples (edge samples replicated) at (px, py):
-    (value, d/dpx, d/dpy).  The image model of the nonrigid energy."""
+def sample_q(T, px: float, py: float, outside: Optional[float] = None):
+    """Quadratic B-spline model of T's samples at (px, py), samples beyond the frame equal to
+    ``outside`` (default: T's mean, as in the nonrigid energy): (value, d/dpx, d/dpy)."""
     T = _f64(T)
     H, W = T.shape
     out = np.empty(3, dtype=np.float64)
-    lib().or_sample_q(_dp(T), W, H, px, py, _dp(out))
+    lib().or_sample_q(_dp(T), W, H, float(T.mean()) if outside is None else float(outside), px, py, _dp(out))
     return out
 
 
@@ -496,8 +497,36 @@ def dag_blelloch(n: int) -> Dag:
     return Dag("blelloch", n, b.ops, cur, exclusive=True)
 
 
+def dag_lookback(n: int, k: int) -> Dag:
+    """The online scan of an acquisition stream with a look-back of k leaves (k a power of two).
+    As leaf j arrives, window nodes w_m(j) = x_{j-2^m+1} (.) ... (.) x_j are formed by doubling,
+    w_m(j) = w_{m-1}(j - 2^(m-1)) (.) w_{m-1}(j) for j >= 2^m - 1, m = 1..log2 k, and the prefix
+    p_j = p_{j-1} (.) x_j for 0 < j < k, p_j = p_{j-k} (.) w_{log2 k}(j) for j >= k.  The chain of
+    prefixes then advances k leaves per operator (k chains side by side); k = 1 is the
+    sequential recursion (Sec. 3)."""
+    if k < 1 or k & (k - 1):
+        raise ValueError("k must be a power of two")
+    b = _Builder(n)
+    m = k.bit_length() - 1
+    w = [list(range(n))] + [[None] * n for _ in range(m)]
+    p = [None] * n
+    for j in range(n):
+        for lev in range(1, m + 1):
+            if j >= (1 << lev) - 1:
+                w[lev][j] = b.op(w[lev - 1][j - (1 << (lev - 1))], w[lev - 1][j])
+        if j == 0:
+            p[0] = 0
+        elif j < k:
+            p[j] = b.op(p[j - 1], j)
+        else:
+            p[j] = b.op(p[j - k], w[m][j])
+    return Dag(f"lookback{k}", n, b.ops, p)
+
+
 DAGS = {"sequential": dag_sequential, "brent_kung": dag_brent_kung,
-        "dissemination": dag_dissemination, "ladner_fischer": dag_ladner_fischer}
+        "dissemination": dag_dissemination, "ladner_fischer": dag_ladner_fischer,
+        "lookback2": lambda n: dag_lookback(n, 2), "lookback4": lambda n: dag_lookback(n, 4),
+        "lookback8": lambda n: dag_lookback(n, 8)}
 
 
 def scan(frames, cfg: Config, dag: Optional[Dag] = None, leaves: Optional[List[Elem]] = None,

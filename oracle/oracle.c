@@ -30,7 +30,7 @@
  *   cell, 0 along a clamped axis; cell choice x0 = min(floor(px), W-2) so
  *   that W >= 2 and H >= 2 suffice;
  *   nonrigid field: both frames are taken through the quadratic B-spline
- *   model of their samples (samples beyond the border replicate the edge),
+ *   model of their samples, extended beyond the border by the frame's mean,
  *   a continuously differentiable image, so that the energy of the local
  *   control values has a continuous gradient (see or_sample_q).
  */
@@ -158,17 +158,14 @@ void or_sample(const double *T, int W, int H, double px, double py, double out[3
 /* Quadratic B-spline model of the samples T_k (k on the integer grid):     */
 /*   T(p) = sum_k T_k b(px - kx) b(py - ky),                                  */
 /*   b(t) = 3/4 - t^2 (|t| <= 1/2), (|t| - 3/2)^2 / 2 (1/2 <= |t| <= 3/2), 0 */
-/* with T_k for k outside the frame equal to the nearest edge sample.  The  */
-/* model is continuously differentiable everywhere (b is C1), reproduces    */
-/* affine images, and at a pixel centre equals the separable filter         */
-/* (1/8, 3/4, 1/8) of the samples with derivative the central difference.   */
+/* with T_k = `outside` for k outside the frame (the energy passes the      */
+/* frame's mean: beyond its border a frame carries no information, and its  */
+/* centred value there is 0).  The model is continuously differentiable     */
+/* everywhere (b is C1), reproduces affine images away from the border, and */
+/* at a pixel centre equals the separable filter (1/8, 3/4, 1/8) of the     */
+/* samples with derivative the central difference.                         */
 /* out[0] = T(p), out[1] = dT/dpx, out[2] = dT/dpy.                         */
 /* ------------------------------------------------------------------------ */
-
-static int clampi(int v, int lo, int hi)
-{
-    return v < lo ? lo : (v > hi ? hi : v);
-}
 
 /* The three nonzero weights b(t + 1), b(t), b(t - 1) at offset t in [-1/2, 1/2) from the
  * nearest sample, and their derivatives. */
@@ -182,7 +179,7 @@ static void bspline2_weights(double t, double w[3], double dw[3])
     dw[2] = 0.5 + t;
 }
 
-void or_sample_q(const double *T, int W, int H, double px, double py, double out[3])
+void or_sample_q(const double *T, int W, int H, double outside, double px, double py, double out[3])
 {
     const int nx = (int)floor(px + 0.5), ny = (int)floor(py + 0.5);   /* nearest sample */
     double wx[3], dwx[3], wy[3], dwy[3];
@@ -190,9 +187,10 @@ void or_sample_q(const double *T, int W, int H, double px, double py, double out
     bspline2_weights(py - ny, wy, dwy);
     double v = 0.0, gx = 0.0, gy = 0.0;
     for (int j = 0; j < 3; ++j) {
-        const int y = clampi(ny - 1 + j, 0, H - 1);
+        const int y = ny - 1 + j;
         for (int i = 0; i < 3; ++i) {
-            const double t = T[y * W + clampi(nx - 1 + i, 0, W - 1)];
+            const int x = nx - 1 + i;
+            const double t = (x < 0 || x >= W || y < 0 || y >= H) ? outside : T[y * W + x];
             v += wx[i] * wy[j] * t;
             gx += dwx[i] * wy[j] * t;
             gy += wx[i] * dwy[j] * t;
@@ -424,10 +422,18 @@ double or_grid_regulariser(const or_grid_t *g, const double *cx, const double *c
     return 0.5 * lambda * s / P;
 }
 
+static double or_mean(const double *A, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += A[i];
+    return s / n;
+}
+
 /* Energy at level l (images R, T of that level, W x H) for control values c
  * given in pixels of that level; gradient dE/dc (same units) if gx/gy given.
- * Both frames are taken through the quadratic B-spline model (or_sample_q):
- * the reference at its pixel centres, the template at x + u(x).            */
+ * Both frames are taken through the quadratic B-spline model (or_sample_q),
+ * each extended by its own mean: the reference at its pixel centres, the
+ * template at x + u(x).                                                     */
 int or_grid_energy(const double *R, const double *T, int W, int H, int l, const or_grid_t *g,
                    const double *cx, const double *cy, double lambda, double *E, double *gx, double *gy)
 {
@@ -437,10 +443,11 @@ int or_grid_energy(const double *R, const double *T, int W, int H, int l, const 
     double *tw = NULL, *dtx = NULL, *dty = NULL;
     /* the reference through the same image model, at its pixel centres */
     double *Rm = (double *)malloc(sizeof(double) * P);
+    const double mR = or_mean(R, P), mT = or_mean(T, P);
     for (int r = 0; r < H; ++r)
         for (int c = 0; c < W; ++c) {
             double s[3];
-            or_sample_q(R, W, H, (double)c, (double)r, s);
+            or_sample_q(R, W, H, mR, (double)c, (double)r, s);
             Rm[r * W + c] = s[0];
         }
     if (gx) {
@@ -453,7 +460,7 @@ int or_grid_energy(const double *R, const double *T, int W, int H, int l, const 
             int i = r * W + c;
             double ux, uy, s[3];
             or_grid_eval(g, cx, cy, scale * c + off, scale * r + off, &ux, &uy);
-            or_sample_q(T, W, H, c + ux, r + uy, s);
+            or_sample_q(T, W, H, mT, c + ux, r + uy, s);
             double rv = Rm[i], tv = s[0];
             m.sR += rv; m.sT += tv; m.sRR += rv * rv; m.sTT += tv * tv; m.sRT += rv * tv;
             if (gx) { tw[i] = tv; dtx[i] = s[1]; dty[i] = s[2]; }
@@ -513,13 +520,14 @@ void or_grid_metric(const double *T, int W, int H, int l, const or_grid_t *g, co
     const int P = W * H, Nc = g->nx * g->ny;
     const double scale = ldexp(1.0, l), off = 0.5 * (scale - 1.0);
     double st = 0.0, stt = 0.0;
+    const double mT = or_mean(T, P);
     for (int j = 0; j < Nc; ++j) { mx[j] = 0.0; my[j] = 0.0; }
     for (int r = 0; r < H; ++r) {
         for (int c = 0; c < W; ++c) {
             int jx, jy;
             double ux, uy, wx, wy, s[3];
             or_grid_eval(g, cx, cy, scale * c + off, scale * r + off, &ux, &uy);
-            or_sample_q(T, W, H, c + ux, r + uy, s);
+            or_sample_q(T, W, H, mT, c + ux, r + uy, s);
             st += s[0];
             stt += s[0] * s[0];
             or_grid_cell(g, scale * c + off, scale * r + off, &jx, &jy, &wx, &wy);

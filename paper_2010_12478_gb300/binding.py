@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libreg.so")
 REG_OK, REG_EINVAL, REG_ENOMEM, REG_EBUDGET, REG_ETIMEOUT, REG_ECUDA, REG_ESTATE = 0, -1, -2, -3, -4, -5, -6
 RIGID, NONRIGID = 0, 1
 F32, BF16, F16 = 0, 1, 2
-SCHEDULES = {"sequential": 0, "brent_kung": 1, "dissemination": 2, "ladner_fischer": 3}
+SCHEDULES = {"sequential": 0, "brent_kung": 1, "dissemination": 2, "ladner_fischer": 3,
+             "lookback2": 17, "lookback4": 18, "lookback8": 19}
 EXECS = {"plain": 0, "level": 1, "persistent": 2, "graph": 3}
 SPLIT_PHASES = 0x100   # OR into an executor: A leaves before the first B, phases timed apart
 STORAGES = {"f32": F32, "bf16": BF16, "f16": F16}

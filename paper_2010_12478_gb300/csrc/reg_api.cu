@@ -216,9 +216,35 @@ Dag dag_ladner_fischer(int n)
     return b.d;
 }
 
+// Online scan with a look-back of k leaves (k a power of two): as leaf j arrives, window nodes
+// w_m(j) = w_{m-1}(j - 2^(m-1)) (.) w_{m-1}(j) for j >= 2^m - 1, m = 1..log2 k, then the prefix
+// p_j = p_{j-1} (.) x_j for 0 < j < k and p_j = p_{j-k} (.) w_{log2 k}(j) for j >= k: k chains of
+// prefixes advance side by side (the streaming service's schedule; k = 1 is the sequential one).
+Dag dag_lookback(int n, int k)
+{
+    DagBuilder b(n);
+    int m = 0;
+    while ((1 << m) < k) ++m;
+    std::vector<std::vector<int>> w(m + 1, std::vector<int>(n, -1));
+    for (int j = 0; j < n; ++j) w[0][j] = j;
+    std::vector<int> p(n, -1);
+    for (int j = 0; j < n; ++j) {
+        for (int lev = 1; lev <= m; ++lev)
+            if (j >= (1 << lev) - 1) w[lev][j] = b.op(w[lev - 1][j - (1 << (lev - 1))], w[lev - 1][j]);
+        if (j == 0) p[0] = 0;
+        else if (j < k) p[j] = b.op(p[j - 1], j);
+        else p[j] = b.op(p[j - k], w[m][j]);
+    }
+    b.d.out = p;
+    return b.d;
+}
+
 bool make_dag(int schedule, int n, Dag &d)
 {
     switch (schedule) {
+    case REG_SCHED_LOOKBACK_2: d = dag_lookback(n, 2); return true;
+    case REG_SCHED_LOOKBACK_4: d = dag_lookback(n, 4); return true;
+    case REG_SCHED_LOOKBACK_8: d = dag_lookback(n, 8); return true;
     case REG_SCHED_SEQ: d = dag_seq(n); return true;
     case REG_SCHED_BRENT_KUNG: d = dag_brent_kung(n); return true;
     case REG_SCHED_DISSEMINATION: d = dag_dissemination(n); return true;

@@ -64,7 +64,8 @@ def test_errors_without_gpu_are_reported_not_crashing(lib):
     assert b"levels" in lib.reg_last_error_message()
 
 
-@pytest.mark.parametrize("name", ["sequential", "brent_kung", "dissemination", "ladner_fischer"])
+@pytest.mark.parametrize("name", ["sequential", "brent_kung", "dissemination", "ladner_fischer", "lookback2",
+                                  "lookback4", "lookback8"])
 def test_library_dag_equals_oracle_dag(lib, name):
     for n in list(range(1, 40)) + [255, 256, 1000, 4095]:
         ops, out = B.scan_dag(name, n)

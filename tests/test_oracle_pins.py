@@ -79,9 +79,10 @@ def test_sample_clamps_to_edge_with_zero_derivative_along_clamped_axis():
 
 
 # ---------------------------------------------------------------- NCC energy
-def smooth_1_8_3_4_1_8(img):
-    """The separable filter (1/8, 3/4, 1/8) with edge samples replicated (numpy, by hand)."""
-    p = np.pad(img, 1, mode="edge")
+def smooth_1_8_3_4_1_8(img, outside=None):
+    """The separable filter (1/8, 3/4, 1/8), samples beyond the frame equal to ``outside`` (default
+    the frame's mean) (numpy, by hand)."""
+    p = np.pad(img, 1, mode="constant", constant_values=img.mean() if outside is None else outside)
     rows = 0.125 * p[:-2, :] + 0.75 * p[1:-1, :] + 0.125 * p[2:, :]
     return 0.125 * rows[:, :-2] + 0.75 * rows[:, 1:-1] + 0.125 * rows[:, 2:]
 
@@ -101,8 +102,8 @@ def test_ncc_energy_equals_corrcoef_at_identity():
 # ---------------------------------------------------------------- quadratic B-spline image model
 def test_bspline_model_at_pixel_centres_is_the_filter_and_central_difference():
     T = rand_img(9, 11, 81)
-    Tf = smooth_1_8_3_4_1_8(T)
-    p = np.pad(T, 1, mode="edge")
+    Tf = smooth_1_8_3_4_1_8(T, outside=0.37)
+    p = np.pad(T, 1, mode="constant", constant_values=0.37)
     # d/dx at a centre: central difference along x, filtered (1/8, 3/4, 1/8) along y; and vice versa
     cx = 0.5 * (p[:, 2:] - p[:, :-2])
     dx = 0.125 * cx[:-2, :] + 0.75 * cx[1:-1, :] + 0.125 * cx[2:, :]
@@ -110,7 +111,7 @@ def test_bspline_model_at_pixel_centres_is_the_filter_and_central_difference():
     dy = 0.125 * cy[:, :-2] + 0.75 * cy[:, 1:-1] + 0.125 * cy[:, 2:]
     for r in range(9):
         for c in range(11):
-            v, gx, gy = O.sample_q(T, float(c), float(r))
+            v, gx, gy = O.sample_q(T, float(c), float(r), outside=0.37)
             assert v == pytest.approx(Tf[r, c], abs=1e-15)
             assert gx == pytest.approx(dx[r, c], abs=1e-15) and gy == pytest.approx(dy[r, c], abs=1e-15)
 
@@ -141,14 +142,19 @@ def test_bspline_model_is_continuously_differentiable():
             np.testing.assert_allclose(a, b, atol=1e-8)
 
 
-def test_bspline_model_replicates_edges_outside_the_frame():
+def test_bspline_model_takes_the_outside_value_beyond_the_frame():
     T = rand_img(7, 8, 84)
-    # far to the left every tap in x is column 0: the value is that column's y-model, d/dx = 0
-    v, gx, gy = O.sample_q(T, -6.0, 3.0)
-    assert v == pytest.approx(0.125 * T[2, 0] + 0.75 * T[3, 0] + 0.125 * T[4, 0], abs=1e-15)
-    assert gx == 0.0 and gy == pytest.approx(0.5 * (T[4, 0] - T[2, 0]), abs=1e-15)
-    v, gx, gy = O.sample_q(T, 100.0, 100.0)   # beyond the far corner
-    assert v == pytest.approx(T[-1, -1], abs=1e-15) and abs(gx) <= 1e-15 and abs(gy) <= 1e-15
+    out = 0.42
+    # far outside every tap is the outside value: the model is that constant, with zero derivative
+    for px, py in ((-6.0, 3.0), (100.0, 100.0), (3.2, -4.0)):
+        v, gx, gy = O.sample_q(T, px, py, outside=out)
+        assert v == pytest.approx(out, abs=1e-15) and abs(gx) <= 1e-15 and abs(gy) <= 1e-15
+    # at x = -1 (a pixel centre outside) the x taps are -2, -1 (outside) and 0 (column 0), weights
+    # 1/8, 3/4, 1/8; at y = 3 the y taps are rows 2, 3, 4 with the same weights
+    v, gx, gy = O.sample_q(T, -1.0, 3.0, outside=out)
+    col = 0.125 * T[2, 0] + 0.75 * T[3, 0] + 0.125 * T[4, 0]
+    assert v == pytest.approx(0.875 * out + 0.125 * col, abs=1e-15)
+    assert gx == pytest.approx(0.5 * (col - out), abs=1e-15)
 
 
 def test_bspline_derivative_matches_central_differences():
@@ -492,7 +498,7 @@ def test_operator_B_rejects_non_adjacent_elements():
         O.op_B(e1, e2, None, O.Config())
 
 
-@pytest.mark.parametrize("dag", ["brent_kung", "dissemination", "ladner_fischer"])
+@pytest.mark.parametrize("dag", ["brent_kung", "dissemination", "ladner_fischer", "lookback2", "lookback4"])
 def test_parallel_scan_equals_sequential_recursion(dag):
     spec = synth.spec_c1()
     spec.n_frames = 9
@@ -605,3 +611,23 @@ def test_the_metric_changes_the_path_not_the_minimiser():
         assert st.stop == [0, 0]
         out.append(c)
     assert O.max_px_error(out[0], out[1], 96, 96, "nonrigid") <= 1e-4
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_lookback_dag_prefixes_work_and_chain_depth(k):
+    # every output is the inclusive prefix; the chain of prefixes advances k leaves per operator, so
+    # the depth is about n/k + 2 log2 k; work: n - 1 prefixes plus sum_m (n - 2^m + 1) windows
+    n = 37
+    d = O.dag_lookback(n, k)
+    sym = [frozenset([j]) for j in range(n)]
+    span = [(j, j) for j in range(n)]
+    for (l, r) in d.ops:
+        assert span[l][1] + 1 == span[r][0]            # B needs adjacent elements
+        span.append((span[l][0], span[r][1]))
+    for i, o in enumerate(d.out):
+        assert span[o] == (0, i)
+    m = k.bit_length() - 1
+    assert d.work() == (n - 1) + sum(n - (1 << lev) + 1 for lev in range(1, m + 1))
+    if k == 1:
+        assert d.ops == O.dag_sequential(n).ops
+    assert d.depth() <= (n - 1) // k + 2 * m + k
