@@ -291,6 +291,11 @@ def serving(dev, mode: str, frames_per_stream: int, seed: int = 1410):
         plan.append((S, rate, fr, t))
     ctx = B.Context(B.Config(mode=mode, mem_budget=40 << 30))
     streams = [B.Stream(ctx, S, S) for (S, _, _, _) in plan]
+    # look-back of each stream's online scan: larger frames make one B slower than the frame interval,
+    # so their prefixes advance in k chains side by side
+    lookback = {256: 1, 512: 2, 1024: 4}
+    for (S, _, _, _), st in zip(plan, streams):
+        st.set_lookback(lookback[S])
     events = sorted((t[j], k, j) for k, (_, _, _, t) in enumerate(plan) for j in range(len(t)))
     results = [[] for _ in plan]
     refused = 0
@@ -315,7 +320,8 @@ def serving(dev, mode: str, frames_per_stream: int, seed: int = 1410):
         st.close()
     lat = np.array([r["done_us"] - r["submit_us"] for rs in results for r in rs]) / 1e3
     n = len(lat)
-    return {"streams": [{"size": S, "rate_fps": round(rate, 1), "frames": len(t)} for (S, rate, _, t) in plan],
+    return {"streams": [{"size": S, "rate_fps": round(rate, 1), "frames": len(t), "lookback": lookback[S]}
+                        for (S, rate, _, t) in plan],
             "mode": mode, "frames": n, "wall_s": round(t1 - t0, 3), "value": round(n / (t1 - t0), 2),
             "unit": "frames/s", "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                                                 "p99": round(float(np.percentile(lat, 99)), 3),

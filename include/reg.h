@@ -20,7 +20,7 @@
  *                 jx < nx = ceil((W-1)/s) + 1; energy 1 - NCC + lambda/(2P) sum over
  *                 control-grid edges |c_a - c_b|^2 (an extension: the paper's
  *                 deformation is rigid).  Both frames enter this energy through the
- *                 quadratic B-spline model of their samples (edges replicated), a
+ *                 quadratic B-spline model of their samples (extended by the mean), a
  *                 continuously differentiable image; the rigid energy samples the
  *                 frames bilinearly.  Control values are stored as (x, y) float
  *                 pairs, row-major [ny][nx]; dense fields as planes [2][H][W].
@@ -349,6 +349,15 @@ int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out);
 /* Submit one frame (host or device, [H][W] fp32; copied before return).
  * REG_EBUDGET: no slot or memory free right now; retry after polling. */
 int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t frame_id);
+
+/* The online scan of the stream (call before the first submit): with a look-back of k leaves
+ * (k in {1, 2, 4, 8}; default 1, the sequential recursion phi_{0,i} = B(phi_{0,i-1}, A_i)), frame
+ * i also brings the window operators of REG_SCHED_LOOKBACK_k and its prefix is
+ * phi_{0,i} = B(phi_{0,i-k}, phi_{i-k,i}), so k chains of prefixes advance side by side: a stream
+ * whose single B takes longer than its frame interval keeps up with about k times the rate, at
+ * 1 + log2 k extra B operators per frame.  The results equal reg_scan with that schedule.
+ * Errors: REG_EINVAL for another k; REG_ESTATE after the first submit. */
+int reg_stream_set_lookback(reg_stream_t *s, int k);
 
 /* REG_NONRIGID streams: the control values of every result, not only its mean displacement.
  * ring: caller-owned device memory of `capacity` grids [capacity][ny][nx] (x, y) pairs (ny, nx

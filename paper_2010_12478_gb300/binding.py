@@ -33,7 +33,8 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_stream_open", "reg_stream_submit", "reg_stream_poll", "reg_stream_close",
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
            "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load",
-           "reg_scan_grids", "reg_warp", "reg_scan_batch", "reg_scan_node_grids", "reg_stream_grids"]
+           "reg_scan_grids", "reg_warp", "reg_scan_batch", "reg_scan_node_grids", "reg_stream_grids",
+           "reg_stream_set_lookback"]
 
 
 class RegError(RuntimeError):
@@ -104,6 +105,7 @@ def lib() -> ctypes.CDLL:
         L.reg_stream_poll.argtypes = [vp, ctypes.POINTER(reg_result_t), ip, ctypes.POINTER(ctypes.c_int), ip]
         L.reg_stream_close.argtypes = [vp]
         L.reg_stream_grids.argtypes = [vp, fp, ip]
+        L.reg_stream_set_lookback.argtypes = [vp, ip]
         L.reg_pairwise_noalloc.argtypes = [ctypes.POINTER(reg_config_t), ip, fp, fp, ip, ip, ip,
                                            ctypes.POINTER(reg_elem_t), ctypes.POINTER(reg_elem_t),
                                            ctypes.POINTER(reg_stats_t), vp]
@@ -380,6 +382,10 @@ class Stream:
         h = ctypes.c_void_p()
         check(lib().reg_stream_open(ctx.h, W, H, ctypes.byref(h)), "reg_stream_open")
         self.h = h
+
+    def set_lookback(self, k: int):
+        """Online scan with a look-back of k leaves (1, 2, 4 or 8); call before the first submit."""
+        check(lib().reg_stream_set_lookback(self.h, k), "reg_stream_set_lookback")
 
     def set_grids(self, ring):
         """Nonrigid streams: write each result's control values into ring[i % len(ring)] (device

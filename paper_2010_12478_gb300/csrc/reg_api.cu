@@ -289,7 +289,7 @@ struct reg_ctx {
     std::mutex mu;
     // workspaces
     DevBuf frames_dev;      // host-supplied frames staged on the device
-    DevBuf pyr[kMaxLevels]; // pyramid levels of all frames (nonrigid: with a replicated border)
+    DevBuf pyr[kMaxLevels]; // pyramid levels of all frames (nonrigid: with a border holding the mean)
     DevBuf spyr[kMaxLevels]; // nonrigid: the B-spline model of every level at its pixel centres
     DevBuf means, level_tab, ops, stats, node_theta, node_grid, status, node_ids;
     DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr;
@@ -525,7 +525,7 @@ Config dev_config(const reg_config_t &c)
 // Build the pyramids of `nf` frames (device fp32, frame f at frames + f*fstride,
 // rows of `pitch`) into ctx->pyr starting at frame slot `first`, and fill the
 // level table rows of those frames.  `total` frames are reserved.  The nonrigid
-// model stores every level with a replicated border (its B-spline window) and the
+// model stores every level with a border holding its mean (its B-spline window) and the
 // model at the pixel centres (its reference role) beside it.
 int build_pyramids(reg_ctx *ctx, const Geometry &g, const float *frames, int nf, size_t fstride, int pitch,
                    int first, int total, cudaStream_t s)

@@ -23,11 +23,11 @@ struct LevelDesc {
     float mean;         // level mean (FP32 shift constant of the moment sums)
 };
 
-// Pyramid layout.  The nonrigid model samples the quadratic B-spline of a level's samples with
-// edges replicated; storing every level of that model with a border of kPad replicated samples
-// on each side lets a 3x3 tap window at a nearest sample clamped to [-1, W] x [-1, H] read
-// without per-tap clamps and still equal the edge-replicated model everywhere.
-constexpr int kPad = 2;
+// Pyramid layout.  The nonrigid model samples the quadratic B-spline of a level's samples
+// extended by the level's mean; storing every level of that model with a border of kPad samples
+// holding the mean lets a 3x3 tap window at a nearest sample clamped to [-2, W + 1] x [-2, H + 1]
+// read without per-tap clamps and still equal the mean-extended model everywhere.
+constexpr int kPad = 3;
 inline int level_pitch(int W, int pad) { return W + 2 * pad; }
 inline size_t level_elems(int W, int H, int pad) { return (size_t)(W + 2 * pad) * (H + 2 * pad); }
 inline size_t level_origin(int W, int pad) { return (size_t)pad * (W + 2 * pad) + pad; }
@@ -38,7 +38,7 @@ struct PyrOut {
     size_t raw_stride[kMaxLevels];
     void *smooth[kMaxLevels];         // B-spline model at the pixel centres, W_l x H_l, or null
     size_t smooth_stride[kMaxLevels];
-    int pad;                          // 0, or kPad replicated border samples around each level
+    int pad;                          // 0, or kPad border samples (the level's mean) around each level
 };
 
 // One operator application.  left < 0: A(f_ref, f_tmpl) from the identity (or

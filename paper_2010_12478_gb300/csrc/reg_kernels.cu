@@ -364,13 +364,13 @@ __device__ __forceinline__ float sample_cg(const float *F, int W, int H, int xi,
 }
 
 // Quadratic B-spline model of the samples of T (storage S) at p = (xi + vx, yi + vy), with the
-// samples beyond the border replicating the edge: the image model of the nonrigid energy,
+// samples beyond the border equal to the level's mean: the image model of the nonrigid energy,
 // continuously differentiable everywhere.  With n the nearest sample and t = p - n in
 // [-1/2, 1/2) per axis, the three taps n - 1, n, n + 1 carry the weights (1/2 - t)^2 / 2,
 // 3/4 - t^2, (1/2 + t)^2 / 2 and, for the derivative, t - 1/2, -2 t, t + 1/2.  T addresses
-// pixel (0, 0) of a level stored with a replicated border of kPad >= 2 samples (row pitch Tp):
-// n clamped to [-1, W] x [-1, H] keeps the window inside the border and equals the
-// edge-replicated model for any p.
+// pixel (0, 0) of a level stored with a border of kPad >= 3 samples holding its mean (row pitch
+// Tp): n clamped to [-2, W + 1] x [-2, H + 1] keeps the window inside the border, and a window
+// clamped there lies wholly in the border, as the true one does: the mean-extended model for any p.
 template <typename S, bool DERIV>
 __device__ __forceinline__ float sample_q(const S *T, int W, int H, int Tp, int xi, int yi, float vx, float vy,
                                           float &dtx, float &dty)
@@ -382,8 +382,8 @@ __device__ __forceinline__ float sample_q(const S *T, int W, int H, int Tp, int 
     int nx = xi + (int)flx, ny = yi + (int)fly;
     if (tx >= 0.5f) { tx -= 1.f; ++nx; }  // nearest sample, t in [-1/2, 1/2), exact
     if (ty >= 0.5f) { ty -= 1.f; ++ny; }
-    nx = min(max(nx, -1), W);
-    ny = min(max(ny, -1), H);
+    nx = min(max(nx, -2), W + 1);
+    ny = min(max(ny, -2), H + 1);
     const S *p0 = T + (ptrdiff_t)(ny - 1) * Tp + nx;
     const S *p1 = p0 + Tp, *p2 = p1 + Tp;
     const float ax = 0.5f - tx, bx = 0.5f + tx, ay = 0.5f - ty, by = 0.5f + ty;
@@ -1614,10 +1614,11 @@ __global__ void pyr_down(const S *src, size_t sstride, int spitch, int W, int H,
     dst[(size_t)r * dpitch + c] = toS<S>(0.25f * v);
 }
 
-// Replicated border of `pad` samples around a W x H level (pitch W + 2 pad): thread t covers
-// one border sample, the top and bottom bands first, then the left and right bands.
+// Border of `pad` samples around a W x H level (pitch W + 2 pad) holding the level's mean (frame
+// f's at mean[f * mstride]): beyond its border a frame is taken to be its mean.  Thread t covers one
+// border sample, the top and bottom bands first, then the left and right bands.
 template <typename S>
-__global__ void pyr_border(S *lvl, size_t stride, int W, int H, int pad)
+__global__ void pyr_border(S *lvl, size_t stride, int W, int H, int pad, const float *mean, int mstride)
 {
     const int pitch = W + 2 * pad;
     const int bands = 2 * pad * pitch, sides = 2 * pad * H;
@@ -1634,12 +1635,11 @@ __global__ void pyr_border(S *lvl, size_t stride, int W, int H, int pad)
         r = u - q * H;
         c = q < pad ? q - pad : W + (q - pad);
     }
-    const int rs = min(max(r, 0), H - 1), cs = min(max(c, 0), W - 1);
-    lvl[(ptrdiff_t)r * pitch + c] = lvl[(size_t)rs * pitch + cs];
+    lvl[(ptrdiff_t)r * pitch + c] = toS<S>(mean[(size_t)blockIdx.z * mstride]);
 }
 
 // The quadratic B-spline model at the pixel centres: the separable filter (1/8, 3/4, 1/8) of a
-// bordered level (its replicated border supplies the outer taps), with the operations of
+// bordered level (its border, the level's mean, supplies the outer taps), with the operations of
 // sample_q at a zero offset, so that a frame registered to itself matches bit for bit.  Written
 // as a plain W x H level.
 template <typename S>
@@ -1771,16 +1771,17 @@ static cudaError_t pyramid_t(const float *frames, int N, size_t fstride, int W, 
     }
     w = W; h = H;
     for (int l = 0; l < levels; ++l) {
+        if (means)
+            level_mean<S><<<N, kThreads, 0, s>>>(lv[l], o.raw_stride[l], w, h, level_pitch(w, o.pad), means + l,
+                                                 levels);
         if (o.pad > 0) {
             const int nb = 2 * o.pad * level_pitch(w, o.pad) + 2 * o.pad * h;
-            pyr_border<S><<<dim3((nb + 127) / 128, 1, N), 128, 0, s>>>(lv[l], o.raw_stride[l], w, h, o.pad);
+            pyr_border<S><<<dim3((nb + 127) / 128, 1, N), 128, 0, s>>>(lv[l], o.raw_stride[l], w, h, o.pad,
+                                                                       means + l, levels);
             if (o.smooth[l])
                 pyr_smooth<S><<<dim3((w + 127) / 128, h, N), 128, 0, s>>>(lv[l], o.raw_stride[l], level_pitch(w, o.pad),
                                                                           w, h, (S *)o.smooth[l], o.smooth_stride[l]);
         }
-        if (means)
-            level_mean<S><<<N, kThreads, 0, s>>>(lv[l], o.raw_stride[l], w, h, level_pitch(w, o.pad), means + l,
-                                                 levels);
         w = (w + 1) / 2;
         h = (h + 1) / 2;
     }
@@ -1791,8 +1792,8 @@ cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, in
                            int storage, const PyrOut &out, float *means, cudaStream_t s)
 {
     if (out.pad != 0) {
-        // the smoothed levels read the 3x3 window of a bordered level
-        if (out.pad < 1) return cudaErrorInvalidValue;
+        // the smoothed levels read the 3x3 window of a bordered level; the border holds the mean
+        if (out.pad < 1 || !means) return cudaErrorInvalidValue;
     } else {
         for (int l = 0; l < levels; ++l)
             if (out.smooth[l]) return cudaErrorInvalidValue;

@@ -30,7 +30,11 @@ namespace {
 constexpr int kLanes = 32;          // CUDA streams the service launches operators on
 constexpr int kSlots = 24;          // frame slots per stream (frames in flight)
 constexpr int kClusterA = 4;    // CTAs per neighbour operator A (fixed: results do not depend on load)
-constexpr int kClusterB = 16;   // CTAs per B: the chain phi_{0,i-1} -> phi_{0,i} is each stream's critical path
+constexpr int kClusterB = 16;   // CTAs per B: the chain of prefixes is each stream's critical path
+// Operators of one frame slot: A at 0, the look-back windows at 1..log2 k, the prefix at kOpP.
+constexpr int kMaxLookbackLog = 3;              // look-back k <= 8
+constexpr int kOpsPerSlot = kMaxLookbackLog + 2;
+constexpr int kOpP = kOpsPerSlot - 1;
 
 double now_us()
 {
@@ -43,8 +47,8 @@ struct Slot {
     uint64_t frame_id = 0;
     double submit_us = 0.0;
     cudaEvent_t ready = nullptr; // pyramid built
-    cudaEvent_t a_ev = nullptr, b_ev = nullptr;
-    bool a_launched = false, a_done = false, b_launched = false, b_done = false;
+    cudaEvent_t ev[kOpsPerSlot] = {};
+    bool launched[kOpsPerSlot] = {}, fin[kOpsPerSlot] = {};
     bool emitted = false;
 };
 
@@ -54,9 +58,10 @@ struct reg_stream {
     reg_ctx_t *ctx = nullptr;
     int W = 0, H = 0, L = 0, storage = REG_F32, mode = REG_RIGID;
     int gnx = 0, gny = 0, gs = 0;
+    int lookback = 1, nlev = 0;  // look-back k of the online scan and log2 k
     size_t bytes = 0;
     // device memory (owned)
-    void *pyr[kMaxLevels] = {};        // levels of every slot (nonrigid: with a replicated border)
+    void *pyr[kMaxLevels] = {};        // levels of every slot (nonrigid: with a border holding the mean)
     void *spyr[kMaxLevels] = {};       // nonrigid: the B-spline model at the pixel centres
     size_t lvl_elems[kMaxLevels] = {};
     int pad = 0;
@@ -132,13 +137,13 @@ Params stream_params(reg_stream *s)
     p.levels = s->table;
     p.n_frames = kSlots + 1;
     p.ops = s->ops;
-    p.n_ops = 2 * (kSlots + 1);
+    p.n_ops = kOpsPerSlot * (kSlots + 1);
     p.node_theta = s->theta;
     p.node_grid = s->grid;
     p.gnx = s->gnx;
     p.gny = s->gny;
     p.gs = s->gs;
-    p.n_nodes = 2 * (kSlots + 1);
+    p.n_nodes = kOpsPerSlot * (kSlots + 1);
     p.stats = s->stats;
     p.status = s->status;
     return p;
@@ -207,51 +212,86 @@ void emit(reg_stream *s, Slot &sl, int node, bool identity)
 
 // One pass of the service over a stream: launch ready operators, note completions,
 // emit results in order, free slots.  Called with the service mutex held.
+//
+// The online scan with a look-back of k leaves (REG_SCHED_LOOKBACK_k; k = 1 is the sequential
+// recursion of Sec. 3): frame i (leaf j = i - 1) brings A_i = A(f_{i-1}, f_i), window operators
+// W_m(i) = B(W_{m-1}(i - 2^(m-1)), W_{m-1}(i)) registering f_{i-2^m} to f_i for i >= 2^m
+// (W_0 = A), and its prefix P(i) = phi_{0,i}: A_1 for i = 1, B(P(i-1), A_i) for i <= k, else
+// B(P(i-k), W_log2k(i)).  k chains of prefixes advance side by side.
 void advance(Service *sv, reg_stream *s)
 {
     if (s->error != REG_OK) return;
     // frames in index order
     std::vector<Slot *> order;
-    for (int k = 1; k <= kSlots; ++k)
-        if (s->slots[k].used) order.push_back(&s->slots[k]);
+    for (int q = 1; q <= kSlots; ++q)
+        if (s->slots[q].used) order.push_back(&s->slots[q]);
     std::sort(order.begin(), order.end(), [](const Slot *a, const Slot *b) { return a->index < b->index; });
+    const int k = s->lookback, m = s->nlev;
+    auto frame = [&](long long f) -> Slot * {   // the live slot of frame f >= 1, or null
+        Slot *q = &s->slots[slot_of(f)];
+        return (q->used && q->index == f) ? q : nullptr;
+    };
+    auto op_of = [&](long long f, int o) { return kOpsPerSlot * slot_of(f) + o; };
+    auto frame_slot = [&](long long f) { return f == 0 ? 0 : slot_of(f); };   // pyramid slot of f_f
+    // node of P(f) and whether it is complete
+    auto prefix_node = [&](long long f) { return f == 1 ? op_of(1, 0) : op_of(f, kOpP); };
+    auto prefix_done = [&](long long f) {
+        Slot *q = frame(f);
+        return q && (f == 1 ? q->fin[0] : q->fin[kOpP]);
+    };
     for (Slot *sl : order) {
         const long long i = sl->index;
         const int si = slot_of(i);
-        const int a_op = 2 * si, b_op = 2 * si + 1;
-        Slot *prev = i > 1 ? &s->slots[slot_of(i - 1)] : nullptr;
-        const bool prev_frame_ready = i == 1 ? done(s->f0_ready) : (prev->used && prev->index == i - 1);
+        Slot *prev = i > 1 ? frame(i - 1) : nullptr;
+        const bool prev_frame_ready = i == 1 ? done(s->f0_ready) : (prev != nullptr);
         // A(f_{i-1}, f_i)
-        if (!sl->a_launched && done(sl->ready) && prev_frame_ready && (i == 1 || done(prev->ready))) {
-            OpDesc op{i == 1 ? 0 : slot_of(i - 1), si, -1, -1, a_op, -1};
-            if (launch_op(sv, s, a_op, op, sl->a_ev, i == 1 ? 1 : -1) != REG_OK) { s->error = REG_ECUDA; return; }
-            sl->a_launched = true;
+        if (!sl->launched[0] && done(sl->ready) && prev_frame_ready && (i == 1 || done(prev->ready))) {
+            OpDesc op{frame_slot(i - 1), si, -1, -1, op_of(i, 0), -1};
+            if (launch_op(sv, s, op_of(i, 0), op, sl->ev[0], i == 1 ? 1 : -1) != REG_OK) { s->error = REG_ECUDA; return; }
+            sl->launched[0] = true;
         }
-        if (sl->a_launched && !sl->a_done && done(sl->a_ev)) sl->a_done = true;
-        if (i == 1) {
-            if (sl->a_done && !sl->emitted) emit(s, *sl, a_op, false);
-            continue;
+        for (int o = 0; o < kOpsPerSlot; ++o)
+            if (sl->launched[o] && !sl->fin[o] && done(sl->ev[o])) sl->fin[o] = true;
+        // windows W_lev(i), lev = 1..m, for i >= 2^lev
+        for (int lev = 1; lev <= m; ++lev) {
+            if (sl->launched[lev] || i < (1LL << lev)) continue;
+            const long long h = 1LL << (lev - 1);
+            Slot *lf = frame(i - h);
+            if (!lf || !lf->fin[lev - 1] || !sl->fin[lev - 1]) continue;
+            OpDesc op{frame_slot(i - (1LL << lev)), si, op_of(i - h, lev - 1), op_of(i, lev - 1), op_of(i, lev), -1};
+            if (launch_op(sv, s, op_of(i, lev), op, sl->ev[lev], -1) != REG_OK) { s->error = REG_ECUDA; return; }
+            sl->launched[lev] = true;
         }
-        // B(phi_{0,i-1}, phi_{i-1,i}), registering f_i onto f_0
-        const bool prev_result = prev->emitted;
-        if (!sl->b_launched && sl->a_done && prev_result) {
-            const int left = (i - 1 == 1) ? 2 * slot_of(i - 1) : 2 * slot_of(i - 1) + 1;
-            OpDesc op{0, si, left, a_op, b_op, -1};
-            if (launch_op(sv, s, b_op, op, sl->b_ev, i) != REG_OK) { s->error = REG_ECUDA; return; }
-            sl->b_launched = true;
+        // the prefix P(i), registering f_i onto f_0
+        if (i > 1 && !sl->launched[kOpP]) {
+            const long long back = i <= k ? i - 1 : i - k;
+            const int win = i <= k ? 0 : m;
+            if (prefix_done(back) && sl->fin[win]) {
+                OpDesc op{0, si, prefix_node(back), op_of(i, win), op_of(i, kOpP), -1};
+                if (launch_op(sv, s, op_of(i, kOpP), op, sl->ev[kOpP], i) != REG_OK) { s->error = REG_ECUDA; return; }
+                sl->launched[kOpP] = true;
+            }
         }
-        if (sl->b_launched && !sl->b_done && done(sl->b_ev)) {
-            sl->b_done = true;
-            emit(s, *sl, b_op, false);
-        }
+        // results in submission order
+        const bool mine = i == 1 ? sl->fin[0] : sl->fin[kOpP];
+        if (mine && !sl->emitted && (i == 1 || (prev && prev->emitted)))
+            emit(s, *sl, i == 1 ? op_of(1, 0) : op_of(i, kOpP), false);
     }
-    // free slot i-1 once A_i and B_i (which read f_{i-1} and phi_{0,i-1}) are done
+    // a frame is done when every operator it brings has completed
+    auto frame_done = [&](long long f) {
+        Slot *q = frame(f);
+        if (!q || !q->fin[0]) return false;
+        for (int lev = 1; lev <= m; ++lev)
+            if (f >= (1LL << lev) && !q->fin[lev]) return false;
+        return f == 1 || q->fin[kOpP];
+    };
+    // free frame i's slot once frames i+1 .. i+k, the only ones that read its pyramid or nodes, are done
     for (Slot *sl : order) {
         if (!sl->used || !sl->emitted) continue;
         const long long i = sl->index;
-        Slot &next = s->slots[slot_of(i + 1)];
-        const bool next_done = next.used && next.index == i + 1 && next.a_done && (next.b_done || i + 1 == 1);
-        if (next_done) sl->used = false;
+        bool free_it = true;
+        for (long long f = i + 1; f <= i + k && free_it; ++f) free_it = frame_done(f);
+        if (free_it) sl->used = false;
     }
 }
 
@@ -301,8 +341,8 @@ void free_stream(reg_stream *s)
     if (s->h_stats) cudaFreeHost(s->h_stats);
     for (int k = 0; k <= kSlots; ++k) {
         if (s->slots[k].ready) cudaEventDestroy(s->slots[k].ready);
-        if (s->slots[k].a_ev) cudaEventDestroy(s->slots[k].a_ev);
-        if (s->slots[k].b_ev) cudaEventDestroy(s->slots[k].b_ev);
+        for (int o = 0; o < kOpsPerSlot; ++o)
+            if (s->slots[k].ev[o]) cudaEventDestroy(s->slots[k].ev[o]);
     }
     if (s->f0_ready) cudaEventDestroy(s->f0_ready);
     if (s->copy) cudaStreamDestroy(s->copy);
@@ -366,7 +406,7 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
     size_t pyr_bytes = 0;
     for (int l = 0; l < c.levels; ++l)
         pyr_bytes += (level_elems(Wl[l], Hl[l], pad) + (pad ? (size_t)Wl[l] * Hl[l] : 0)) * sb;
-    const int nops = 2 * (kSlots + 1);
+    const int nops = kOpsPerSlot * (kSlots + 1);
     const size_t bytes = pyr_bytes * (kSlots + 1) + 2 * sizeof(float) * (size_t)W * H + sizeof(LevelDesc) * (kSlots + 1) * c.levels +
                          (sizeof(OpDesc) + sizeof(OpStats) + 3 * sizeof(double)) * nops +
                          sizeof(float2) * (size_t)gnx * gny * nops + 4096;
@@ -417,9 +457,9 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
         ok = cudaEventCreateWithFlags(&s->stage_free[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventRecord(s->stage_free[b], s->build) == cudaSuccess;
     for (int k = 0; k <= kSlots && ok; ++k) {
-        ok = cudaEventCreateWithFlags(&s->slots[k].ready, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&s->slots[k].a_ev, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&s->slots[k].b_ev, cudaEventDisableTiming) == cudaSuccess;
+        ok = cudaEventCreateWithFlags(&s->slots[k].ready, cudaEventDisableTiming) == cudaSuccess;
+        for (int o = 0; o < kOpsPerSlot && ok; ++o)
+            ok = cudaEventCreateWithFlags(&s->slots[k].ev[o], cudaEventDisableTiming) == cudaSuccess;
     }
     ok = ok && cudaEventCreateWithFlags(&s->f0_ready, cudaEventDisableTiming) == cudaSuccess;
     if (ok) ok = cudaMemset(s->status, 0, sizeof(int) * 4) == cudaSuccess &&
@@ -527,10 +567,24 @@ extern "C" int reg_stream_submit(reg_stream_t *s, const float *frame, uint64_t f
             sl.index = index;
             sl.frame_id = frame_id;
             sl.submit_us = t_submit;
-            sl.a_launched = sl.a_done = sl.b_launched = sl.b_done = sl.emitted = false;
+            for (int o = 0; o < kOpsPerSlot; ++o) sl.launched[o] = sl.fin[o] = false;
+            sl.emitted = false;
         }
     }
     sv->cv.notify_all();
+    return REG_OK;
+}
+
+extern "C" int reg_stream_set_lookback(reg_stream_t *s, int k)
+{
+    if (!s) return host_fail(REG_EINVAL, "NULL stream");
+    if (k != 1 && k != 2 && k != 4 && k != 8) return host_fail(REG_EINVAL, "look-back %d not in {1, 2, 4, 8}", k);
+    Service *sv = service_of(s->ctx, false);
+    if (!sv) return host_fail(REG_ESTATE, "stream service is not running");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (s->submitted > 0) return host_fail(REG_ESTATE, "set the look-back before the first submit");
+    s->lookback = k;
+    s->nlev = k == 1 ? 0 : (k == 2 ? 1 : (k == 4 ? 2 : 3));
     return REG_OK;
 }
 

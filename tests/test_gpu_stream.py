@@ -160,3 +160,46 @@ def test_stream_submit_refuses_while_every_slot_is_in_flight():
     assert B.REG_EBUDGET in codes
     assert codes[:25] == [B.REG_OK] * 25
     st.close()
+
+
+@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
+def test_stream_lookback_equals_the_lookback_scan_and_oracle(k, mode):
+    F = series(13, 96, 112, 85)
+    cfg = B.Config(mode=mode, cluster=4)
+    ctx = B.Context(cfg)
+    st = B.Stream(ctx, 112, 96)
+    st.set_lookback(k)
+    ring = None
+    if mode == "nonrigid":
+        nx, ny, _ = B.grid_dims(112, 96)
+        ring = torch.zeros((16, ny, nx, 2), device="cuda")
+        st.set_grids(ring)
+    res = run_stream(st, F, list(range(13)))
+    st.close()
+    assert [r["frame_id"] for r in res] == list(range(13))
+    els, _ = ctx.scan(torch.from_numpy(F).cuda(), schedule=f"lookback{k}", exec="plain")
+    assert [r["elem"] for r in res[1:]] == els
+    oc = O.Config(levels=cfg.levels, mode=mode, metric=cfg.metric)
+    ref = O.scan(F, oc, O.dag_lookback(12, k))
+    if mode == "nonrigid":
+        sg = torch.zeros((12, ny, nx, 2), device="cuda")
+        ctx.scan_grids(sg)
+        assert torch.equal(ring[1:13], sg)
+        got = ring[1:13].cpu().numpy().astype(np.float64)
+    for i, o in enumerate(ref):
+        phi = np.transpose(got[i], (2, 0, 1)) if mode == "nonrigid" else np.array(res[i + 1]["elem"][2:], np.float64)
+        assert O.max_px_error(phi, o.phi, 96, 112, mode) <= 0.02, (k, i)
+
+
+def test_stream_lookback_rejections():
+    ctx = B.Context(B.Config())
+    st = B.Stream(ctx, 64, 64)
+    with pytest.raises(B.RegError) as e:
+        st.set_lookback(3)
+    assert e.value.code == B.REG_EINVAL
+    run_stream(st, series(2, 64, 64, 86), [0, 1])
+    with pytest.raises(B.RegError) as e:
+        st.set_lookback(2)
+    assert e.value.code == B.REG_ESTATE
+    st.close()
