@@ -477,24 +477,32 @@ def dag_ladner_fischer(n: int, k: int = 0) -> Dag:
 
 
 def dag_blelloch(n: int) -> Dag:
-    """Exclusive tree scan (up-sweep, then down-sweep from the identity, node -1).
-    Counted with its identity applications: work 2(n-1), depth 2 log2 n (Table 1)."""
+    """Exclusive tree scan (up-sweep, then down-sweep from the identity, node -1), on the series
+    padded with identity elements to a power of two P: an application with a padded operand is
+    x (.) e = x and is not made, nor one whose result only feeds padded positions.  Counted with
+    its identity applications: work 2(n-1), depth 2 log2 P (Table 1)."""
     b = _Builder(n)
-    cur = list(range(n))
+    P = 1
+    while P < n:
+        P *= 2
+    cur = list(range(n)) + [-1] * (P - n)
     d = 1
-    while d < n:
-        for i in range(2 * d - 1, n, 2 * d):
-            cur[i] = b.op(cur[i - d], cur[i])
+    while d < P:
+        for i in range(2 * d - 1, P, 2 * d):
+            # padding is a suffix: a padded left operand has a padded right one
+            cur[i] = cur[i - d] if cur[i] == -1 else b.op(cur[i - d], cur[i])
         d *= 2
-    cur[n - 1] = -1
-    d //= 2
+    if n > 0:
+        cur[P - 1] = -1
+    d = P // 2
     while d >= 1:
-        for i in range(2 * d - 1, n, 2 * d):
-            left = cur[i - d]
-            cur[i - d] = cur[i]
-            cur[i] = b.op(cur[i], left)
+        for i in range(2 * d - 1, P, 2 * d):
+            left, parent = cur[i - d], cur[i]
+            cur[i - d] = parent
+            # positions i-d+1 .. i take this value: all padding when i-d+1 >= n
+            cur[i] = b.op(parent, left) if left != -1 and i - d + 1 < n else parent
         d //= 2
-    return Dag("blelloch", n, b.ops, cur, exclusive=True)
+    return Dag("blelloch", n, b.ops, cur[:n], exclusive=True)
 
 
 def dag_lookback(n: int, k: int) -> Dag:

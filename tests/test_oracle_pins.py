@@ -441,13 +441,15 @@ def test_dag_computes_inclusive_prefixes(name):
 
 def test_blelloch_is_exclusive_and_one_shift_from_inclusive():
     # Sec. 1: an exclusive result becomes inclusive by one shift plus one operator application
-    for n in (1, 2, 4, 8, 32):
+    for n in range(1, 70):
         d = O.dag_blelloch(n)
         vals = _concat_check(d)
         excl = ["" if o < 0 else vals[o] for o in d.out]
         for i in range(n):
             assert excl[i] == "".join(f"{j}," for j in range(i))
             assert excl[i] + f"{i}," == "".join(f"{j}," for j in range(i + 1))
+        # Table 1's work 2 (n - 1), identity applications included, also off the powers of two
+        assert d.work() == 2 * max(0, n - 1), n
 
 
 def test_dag_work_and_depth_match_table1_and_fig2():
