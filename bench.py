@@ -579,8 +579,12 @@ def main():
         tuned = {}
         if args.cluster == 0 and not args.quick:
             for ex in tune_execs:
-                tuned[ex] = c.autotune(frames, exec=ex)   # outside every timed region
+                c.autotune(frames, exec=ex)   # outside every timed region
+                tuned[ex] = c.tuned_shape(tuple(frames.shape), ex)
         return c, tuned
+
+    def tuned_cluster(tuned, ex):
+        return (tuned.get(ex) or {}).get("cluster", args.cluster)
 
     def timed(ctx, src, exec_, steps, warmup, split=False, grids=None, grids_host=None):
         for _ in range(warmup):
@@ -632,19 +636,21 @@ def main():
     ev_a, ev_b = ev[:nl], ev[nl:]
 
     levels = cfg.levels
-    forms = phases = e2e = other = serve = prec = reg_series = imbalance = None
+    forms = phases = e2e = other = serve = prec = reg_series = imbalance = mock = None
     if args.quick and args.warp:
         reg_series = registered_series(ctx, frames, args.mode, 1, 1, peak, peak_src, world)
     if not args.quick:
         # ---- the other executors on the same workload: one operator per launch, and those launches
         # captured once as a CUDA graph and replayed (same CTAs per operator as the tuned plain path)
         forms = {args.exec_: {"value": round(value, 2), "ms_per_step": round(ms, 3),
-                              "cluster": tuned.get(args.exec_, args.cluster)}}
+                              "cluster": tuned_cluster(tuned, args.exec_)}}
         for ex in ("plain", "graph", "persistent"):
             if ex == args.exec_:
                 continue
             if ex == "graph":
-                gctx = B.Context(B.Config(mode=args.mode, cluster=tuned.get("plain", args.cluster) or 0),
+                sh = tuned.get("plain") or {}
+                gctx = B.Context(B.Config(mode=args.mode, cluster=sh.get("cluster", args.cluster) or 0,
+                                          unroll=sh.get("unroll", 0), ctas_per_sm=sh.get("ctas_per_sm", 0)),
                                  device=local)
                 gctx.set_timing(True)
                 fms, _, ftim = timed(gctx, frames, ex, max(2, args.steps // 2), 2)
@@ -653,13 +659,13 @@ def main():
                 fms, _, ftim = timed(ctx, frames, ex, max(2, args.steps // 2), 2)
             forms[ex] = {"value": round(job_rate(N - 1, world, fms), 2), "ms_per_step": round(fms, 3),
                          "op_kernel_ms": round(sum(t["op_kernel_ms"] for t in ftim) / len(ftim), 3),
-                         "cluster": tuned.get(ex if ex != "graph" else "plain", args.cluster)}
+                         "cluster": tuned_cluster(tuned, ex if ex != "graph" else "plain")}
         # ---- "full" vs "scan" (Sec. 5.2): the A leaves to completion, then the B operators
         pms, _, ptim = timed(ctx, frames, args.exec_, 2, 1, split=True)
         leaf_ms = sum(t["leaf_ms"] for t in ptim) / len(ptim)
         dag_ms = sum(t["dag_ms"] for t in ptim) / len(ptim)
         # operator slots: 152 SMs x 3 CTAs per SM / CTAs per operator
-        workers = 152 * 3 // max(1, tuned.get(args.exec_, args.cluster) or 8)
+        workers = 152 * 3 // max(1, tuned_cluster(tuned, args.exec_) or 8)
         phases = {"exec": args.exec_, "leaf_ops": ptim[0]["leaf_ops"], "dag_ops": ptim[0]["dag_ops"],
                   "leaf_ms": round(leaf_ms, 3), "dag_ms": round(dag_ms, 3),
                   "scan_frames_per_s": round(job_rate(N - 1, world, dag_ms), 2),
@@ -710,6 +716,8 @@ def main():
                      omode: serving(dev, omode, min(args.serve_frames, 256))}
             # ---- precision forms: pyramid storage fp32 / bf16 / fp16
             prec = precision(frames, args.mode)
+            # ---- the paper's mock operator on the device queue and the per-depth executor
+            mock = mock_study(dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and not args.quick and world == 1:
@@ -731,6 +739,7 @@ def main():
             "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}", "frames": N, "H": H,
                        "W": W, "mode": args.mode, "levels": levels, "schedule": "brent_kung",
                        "exec": args.exec_, "cluster": args.cluster or {"autotuned": tuned},
+                       "launch_shape": {k: tim[0][k] for k in ("cluster", "unroll", "ctas_per_sm")},
                        "image_model": "quadratic B-spline (nonrigid energy), bilinear (rigid energy)",
                        "stop": f"metric gradient norm < {cfg.tol_grad:g}, at most {cfg.max_iter} steps per level",
                        "l2": "inputs larger than L2 (frames %d MiB > 129 MB L2)" % (N * H * W * 4 >> 20),
@@ -750,6 +759,7 @@ def main():
             "forms": forms,
             "phases": phases,
             "imbalance": imbalance,
+            "mock_operator": mock,
             "registered_series": reg_series,
             "other_mode": other,
             "serving": serve,
@@ -762,6 +772,31 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def mock_study(dev, n: int = 98304, t_us: float = 20.0, seed: int = 1410):
+    """The paper's mock operator (Sec. 5.1) on the device executors: n elements, operators of a
+    fixed duration t or of exponentially distributed durations with mean t (Mersenne Twister
+    seeded 1410); per scan DAG and executor the device time of the scan.  The per-depth
+    executor waits for the slowest operator of every depth; the persistent device queue starts an
+    operator as soon as its inputs exist (the GPU's counterpart of the paper's work stealing)."""
+    import numpy as np
+    from paper_2010_12478_gb300 import binding as B
+    ctx = B.Context(B.Config(), device=dev.index or 0)
+    vals = np.arange(n, dtype=np.float64) % 7
+    out = {"elements": n, "mean_op_us": t_us, "seed": seed, "scans": {}}
+    for sched in ("brent_kung", "dissemination", "ladner_fischer", "blelloch"):
+        m = B.scan_work(sched, n)
+        dyn = np.random.RandomState(seed).exponential(t_us, size=m).clip(0.0, 1.0e5).astype(np.float32)
+        row = {"operators": m}
+        for kind, us in (("static", np.full(m, t_us, np.float32)), ("dynamic", dyn)):
+            for ex in ("level", "persistent"):
+                ctx.mock_scan(vals, us, schedule=sched, exec=ex)     # warm-up
+                _, ms = ctx.mock_scan(vals, us, schedule=sched, exec=ex)
+                row[f"{kind}_{ex}_ms"] = round(ms, 3)
+        row["dynamic_queue_speedup"] = round(row["dynamic_level_ms"] / row["dynamic_persistent_ms"], 3)
+        out["scans"][sched] = row
+    return out
 
 
 def imbalance_metric(evals, segments):

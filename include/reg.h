@@ -77,6 +77,7 @@ extern "C" {
 #define REG_SCHED_BRENT_KUNG    1   /* work-efficient tree scan                        [Table 1] */
 #define REG_SCHED_DISSEMINATION 2   /* recursive doubling, depth log2 N                [Table 1, Fig. 2] */
 #define REG_SCHED_LADNER_FISCHER 3  /* Ladner-Fischer P_0                              [Table 1] */
+#define REG_SCHED_BLELLOCH      4   /* exclusive tree scan with the identity      [Table 1]; mock only */
 /* online scan with a look-back of k leaves: window products of the last k leaves by doubling,
  * prefix p_j = p_{j-k} (.) (x_{j-k+1} .. x_j), so k chains of prefixes advance side by side
  * (p_j = p_{j-1} (.) x_j for j < k); the streaming service's schedule, see reg_stream_set_lookback */
@@ -137,6 +138,11 @@ typedef struct {
                              doubled until at most 65 points per axis); a multiple of 2^(levels-1) */
     int    metric;        /* REG_NONRIGID scalar product of the gradient flow: REG_METRIC_GAUSS_NEWTON
                              (default) or REG_METRIC_MEAN */
+    int    unroll;        /* REG_NONRIGID energy passes: pixels in flight per lane (2 or 4); 0 = auto
+                             (the autotuned value, else 4) */
+    int    ctas_per_sm;   /* REG_NONRIGID operator kernels: register budget sized for 3 or 4 CTAs
+                             per SM (80 or 64 registers a thread); 0 = auto (the autotuned value,
+                             else 4 for 16-CTA operators and 3 below) */
 } reg_config_t;
 
 /* Scalar product of the nonrigid gradient flow [Sec. 2.3.1 takes the flow with respect to a
@@ -268,6 +274,22 @@ int reg_scan_node_grids(reg_ctx_t *ctx, const int32_t *ops, int n, float *grids_
 int reg_warp(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch,
              const reg_elem_t *elems, const float *grids, float *out, float *mean, void *stream);
 
+/* Mock operator on the device executors [Sec. 5.1: an artificial operator of fixed or
+ * exponentially distributed running time, to study the scan algorithms and the balance of their
+ * load apart from the registration].  Element j holds values[j]; an operator of the schedule's
+ * DAG adds its two inputs after spinning for its duration on the device clock, on one CTA.
+ *   values     host, n doubles.
+ *   op_us      host, one duration per operator of the DAG in DAG order (reg_scan_dag), in
+ *              microseconds, each in [0, 1e5]; the caller draws them (fixed, or exponential
+ *              with mean t for the paper's dynamic configuration).
+ *   exec       REG_EXEC_PLAIN, REG_EXEC_LEVEL or REG_EXEC_PERSISTENT.
+ *   prefix     host, n doubles: the inclusive prefix sums; for REG_SCHED_BLELLOCH the exclusive
+ *              ones (prefix[0] = 0, the identity).
+ *   elapsed_ms host, optional: device time of the operator phase (CUDA events).
+ * Errors: REG_EINVAL (n < 1, a duration out of range, unknown schedule or executor). */
+int reg_mock_scan(reg_ctx_t *ctx, int n, int schedule, int exec, const double *values, const float *op_us,
+                  double *prefix, double *elapsed_ms);
+
 /* Number of B applications the schedule uses for n = N-1 elements (host only,
  * no GPU needed).  Returns -1 for an unknown schedule. */
 int reg_scan_work(int schedule, int n);
@@ -379,18 +401,27 @@ int reg_stream_close(reg_stream_t *s);
 
 /* ---- autotuner ----------------------------------------------------------- */
 
-/* Choose the number of CTAs that cooperate on one operator (the "tile": rows of
- * each pyramid level per CTA) for this frame size, mode, storage type and
- * executor, by timing reg_scan on `frames` with 1, 2, 4, 8 and 16 CTAs per
- * operator (each twice, after one untimed run; nonrigid scans are timed without
- * dense fields, whose kernel costs the same for every candidate) and keeping the
- * fastest.  Later
- * reg_scan calls on the context with cfg.cluster == 0 and a matching shape
- * (same W, H, mode, storage, executor and floor(log2 N)) use the choice.
- * Arguments as reg_scan; best (host, optional) receives the choice.  The paper
- * has no counterpart (its operator runs on one CPU core). */
+/* Choose the launch shape of the operator kernels (the "tile") for this frame size, mode,
+ * storage type and executor, by timing reg_scan on `frames` (each candidate twice, after one
+ * untimed run; nonrigid scans are timed without dense fields, whose kernel costs the same for
+ * every candidate) and keeping the fastest:
+ *   1. CTAs per operator (rows of each pyramid level per CTA): 1, 2, 4, 8 and 16, for
+ *      REG_NONRIGID each with either register form (3 or 4 CTAs per SM);
+ *   2. REG_NONRIGID, at the chosen pair: pixels per lane of the energy passes (4, then 2).
+ * Fields of cfg that are set (cluster, unroll, ctas_per_sm > 0) are not tuned.  Later reg_scan
+ * calls on the context with a matching shape (same W, H, mode, storage, executor and
+ * floor(log2 N)) use the choice for every field the config leaves at 0.  Arguments as reg_scan;
+ * best (host, optional) receives the CTAs per operator.  A candidate the device cannot schedule
+ * ends the search with the choices so far.  The paper has no counterpart (its operator runs on
+ * one CPU core). */
 int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch,
                  int schedule, int exec, int *best);
+
+/* The autotuned shape for (N, W, H, exec) at the context's mode and storage (host outputs,
+ * each optional): CTAs per operator, energy-pass pixels per lane (0 for REG_RIGID) and the
+ * register form.  REG_EINVAL if there is none. */
+int reg_autotune_get(reg_ctx_t *ctx, int N, int W, int H, int exec, int *cluster, int *unroll,
+                     int *ctas_per_sm);
 
 /* Write / read the context's autotuned choices as JSON lines (host files). */
 int reg_autotune_save(reg_ctx_t *ctx, const char *path);
@@ -414,6 +445,10 @@ typedef struct {
     int32_t leaf_ops, dag_ops; /* REG_EXEC_SPLIT_PHASES: operators A (DAG depth 0) and B */
     double  leaf_ms, dag_ms;   /* REG_EXEC_SPLIT_PHASES with timing: device time of the A phase and
                                   of the B phase (same method as op_kernel_ms) */
+    int32_t cluster;           /* launch shape of the last operator launch: CTAs per operator, */
+    int32_t unroll;            /* energy-pass pixels per lane (0 for REG_RIGID), */
+    int32_t ctas_per_sm;       /* and the register form (CTAs per SM it is sized for) */
+    int32_t reserved;
 } reg_timing_t;
 
 /* Enable (1) or disable (0) event timing of the kernels launched by later calls. */

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libreg.so")
 REG_OK, REG_EINVAL, REG_ENOMEM, REG_EBUDGET, REG_ETIMEOUT, REG_ECUDA, REG_ESTATE = 0, -1, -2, -3, -4, -5, -6
 RIGID, NONRIGID = 0, 1
 F32, BF16, F16 = 0, 1, 2
-SCHEDULES = {"sequential": 0, "brent_kung": 1, "dissemination": 2, "ladner_fischer": 3,
+SCHEDULES = {"sequential": 0, "brent_kung": 1, "dissemination": 2, "ladner_fischer": 3, "blelloch": 4,
              "lookback2": 17, "lookback4": 18, "lookback8": 19}
 EXECS = {"plain": 0, "level": 1, "persistent": 2, "graph": 3}
 SPLIT_PHASES = 0x100   # OR into an executor: A leaves before the first B, phases timed apart
@@ -34,7 +34,7 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_ctx_set_timing", "reg_ctx_last_timing", "reg_strerror", "reg_last_error_message",
            "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load",
            "reg_scan_grids", "reg_warp", "reg_scan_batch", "reg_scan_node_grids", "reg_stream_grids",
-           "reg_stream_set_lookback"]
+           "reg_stream_set_lookback", "reg_mock_scan", "reg_autotune_get"]
 
 
 class RegError(RuntimeError):
@@ -54,7 +54,7 @@ class reg_config_t(ctypes.Structure):
                 ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double), ("step_cap", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("storage", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("grid", ctypes.c_int),
-                ("metric", ctypes.c_int)]
+                ("metric", ctypes.c_int), ("unroll", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
 
 
 class reg_stats_t(ctypes.Structure):
@@ -69,7 +69,8 @@ class reg_timing_t(ctypes.Structure):
                 ("op_kernel_ms", ctypes.c_double), ("pyramid_ms", ctypes.c_double),
                 ("graph_captures", ctypes.c_int32), ("tma_staged", ctypes.c_int32),
                 ("leaf_ops", ctypes.c_int32), ("dag_ops", ctypes.c_int32),
-                ("leaf_ms", ctypes.c_double), ("dag_ms", ctypes.c_double)]
+                ("leaf_ms", ctypes.c_double), ("dag_ms", ctypes.c_double), ("cluster", ctypes.c_int32),
+                ("unroll", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class reg_result_t(ctypes.Structure):
@@ -106,10 +107,12 @@ def lib() -> ctypes.CDLL:
         L.reg_stream_close.argtypes = [vp]
         L.reg_stream_grids.argtypes = [vp, fp, ip]
         L.reg_stream_set_lookback.argtypes = [vp, ip]
+        L.reg_mock_scan.argtypes = [vp, ip, ip, ip, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
         L.reg_pairwise_noalloc.argtypes = [ctypes.POINTER(reg_config_t), ip, fp, fp, ip, ip, ip,
                                            ctypes.POINTER(reg_elem_t), ctypes.POINTER(reg_elem_t),
                                            ctypes.POINTER(reg_stats_t), vp]
         L.reg_autotune.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(ip)]
+        L.reg_autotune_get.argtypes = [vp, ip, ip, ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
         L.reg_scan_grids.argtypes = [vp, fp, ctypes.POINTER(ip), vp]
         L.reg_scan_node_grids.argtypes = [vp, vp, ip, fp, vp]
         L.reg_scan_batch.argtypes = [vp, fp, ip, ip, ip, ip, ip, ip, ip, vp, fp, ctypes.POINTER(reg_stats_t), vp]
@@ -166,12 +169,14 @@ class Config:
     mem_budget: int = 0
     grid: int = 0
     metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control points
+    unroll: int = 0               # nonrigid energy passes: pixels per lane (2, 4); 0 = tuned or 4
+    ctas_per_sm: int = 0          # nonrigid register form (3, 4); 0 = tuned or by CTAs per operator
 
     def c(self) -> reg_config_t:
         return reg_config_t(RIGID if self.mode == "rigid" else NONRIGID, self.levels, self.max_iter,
                             self.max_rejects, self.tol_grad, self.tol_rel_e, self.armijo_c, self.tau0,
                             self.step_cap, self.lam, STORAGES[self.storage], self.cluster, self.workers,
-                            self.mem_budget, self.grid, self.metric)
+                            self.mem_budget, self.grid, self.metric, self.unroll, self.ctas_per_sm)
 
 
 def stats_dict(s: reg_stats_t, levels: int) -> dict:
@@ -221,6 +226,15 @@ class Context:
                                  ctypes.byref(best)), "reg_autotune")
         return best.value
 
+    def tuned_shape(self, frames_shape, exec: str = "persistent") -> Optional[dict]:
+        """The autotuned launch shape for frames of shape (N, H, W) and an executor, or None."""
+        N, H, W = frames_shape
+        c, u, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        if lib().reg_autotune_get(self.h, N, W, H, EXECS[exec], ctypes.byref(c), ctypes.byref(u),
+                                  ctypes.byref(m)) != 0:
+            return None
+        return dict(cluster=c.value, unroll=u.value, ctas_per_sm=m.value)
+
     def autotune_save(self, path: str):
         check(lib().reg_autotune_save(self.h, path.encode()), "reg_autotune_save")
 
@@ -236,7 +250,7 @@ class Context:
         return dict(op_launches=t.op_launches, pyramid_launches=t.pyramid_launches,
                     op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms, graph_captures=t.graph_captures,
                     tma_staged=t.tma_staged, leaf_ops=t.leaf_ops, dag_ops=t.dag_ops, leaf_ms=t.leaf_ms,
-                    dag_ms=t.dag_ms)
+                    dag_ms=t.dag_ms, cluster=t.cluster, unroll=t.unroll, ctas_per_sm=t.ctas_per_sm)
 
     # ---- operators
     def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,
@@ -294,6 +308,17 @@ class Context:
         n = ctypes.c_int()
         check(lib().reg_scan_grids(self.h, _ptr(out), ctypes.byref(n), None), "reg_scan_grids")
         return n.value
+
+    def mock_scan(self, values, op_us, schedule: str = "brent_kung", exec: str = "persistent"):
+        """reg_mock_scan: the schedule's DAG of the mock operator (sum after a spin of op_us[j]
+        microseconds); returns (prefix sums, device milliseconds)."""
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+        us = np.ascontiguousarray(np.asarray(op_us, dtype=np.float32))
+        out = np.zeros(len(v), dtype=np.float64)
+        ms = ctypes.c_double()
+        check(lib().reg_mock_scan(self.h, len(v), SCHEDULES[schedule], EXECS[exec], v.ctypes.data, us.ctypes.data,
+                                  out.ctypes.data, ctypes.byref(ms)), "reg_mock_scan")
+        return out, ms.value
 
     def scan_node_grids(self, ops: Sequence[int], out):
         """Control values [len(ops), ny, nx, 2] (device) of the given operators' results of the last

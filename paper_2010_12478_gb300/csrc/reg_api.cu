@@ -239,9 +239,40 @@ Dag dag_lookback(int n, int k)
     return b.d;
 }
 
+// Blelloch: the reduction tree, then the root set to the identity (node -1) and a down-sweep that
+// hands every left child its parent's value and every right child the parent's value combined
+// with the left child's sum: an exclusive scan, out[i] = x_0 (.) ... (.) x_{i-1}.  The tree spans
+// the next power of two P >= n with identity elements past n; an application with such an operand
+// (x (.) e = x) is not made, nor one whose value only reaches positions >= n.  Table 1 counts the
+// identity applications of the down-sweep: work 2 (n - 1).
+Dag dag_blelloch(int n)
+{
+    DagBuilder b(n);
+    int P = 1;
+    while (P < n) P *= 2;
+    std::vector<int> cur(P, -1);
+    for (int i = 0; i < n; ++i) cur[i] = i;
+    int d = 1;
+    for (; d < P; d *= 2)
+        for (int i = 2 * d - 1; i < P; i += 2 * d)
+            if (cur[i] != -1) cur[i] = b.op(cur[i - d], cur[i]);
+            else cur[i] = cur[i - d];   // padding is a suffix: the left operand alone
+    if (n > 0) cur[P - 1] = -1;
+    for (d = P / 2; d >= 1; d /= 2)
+        for (int i = 2 * d - 1; i < P; i += 2 * d) {
+            const int left = cur[i - d], parent = cur[i];
+            cur[i - d] = parent;
+            cur[i] = (left != -1 && i - d + 1 < n) ? b.op(parent, left) : parent;
+        }
+    cur.resize(n);
+    b.d.out = cur;
+    return b.d;
+}
+
 bool make_dag(int schedule, int n, Dag &d)
 {
     switch (schedule) {
+    case REG_SCHED_BLELLOCH: d = dag_blelloch(n); return true;
     case REG_SCHED_LOOKBACK_2: d = dag_lookback(n, 2); return true;
     case REG_SCHED_LOOKBACK_4: d = dag_lookback(n, 4); return true;
     case REG_SCHED_LOOKBACK_8: d = dag_lookback(n, 8); return true;
@@ -308,8 +339,8 @@ struct reg_ctx {
     cudaStream_t capture = nullptr;   // graphs are captured here (the caller's stream may be the legacy one)
     uint64_t graph_key = 0;
     int graph_captures = 0;
-    // autotuned CTAs per operator, keyed by (W, H, mode, storage, exec, floor(log2 N))
-    std::map<std::tuple<int, int, int, int, int, int>, int> tuned;
+    // autotuned launch shapes, keyed by (W, H, mode, storage, exec, floor(log2 N))
+    std::map<std::tuple<int, int, int, int, int, int>, TileShape> tuned;
     // measurement
     bool timing = false;
     std::vector<cudaEvent_t> tev;   // timing events, used in pairs
@@ -357,6 +388,9 @@ static int validate_cfg(const reg_config_t &c)
     if (c.lambda < 0) return fail(REG_EINVAL, "lambda < 0");
     if (c.grid < 0) return fail(REG_EINVAL, "grid < 0");
     if (c.metric != REG_METRIC_MEAN && c.metric != REG_METRIC_GAUSS_NEWTON) return fail(REG_EINVAL, "metric %d", c.metric);
+    if (c.unroll != 0 && c.unroll != 2 && c.unroll != 4) return fail(REG_EINVAL, "unroll %d not in {0,2,4}", c.unroll);
+    if (c.ctas_per_sm != 0 && c.ctas_per_sm != 3 && c.ctas_per_sm != 4)
+        return fail(REG_EINVAL, "ctas_per_sm %d not in {0,3,4}", c.ctas_per_sm);
     return REG_OK;
 }
 
@@ -595,11 +629,25 @@ int log2_floor(int v)
     return l;
 }
 
-// CTAs per operator chosen by reg_autotune for this shape and executor, or 0.
-int tuned_cluster(const reg_ctx *ctx, int W, int H, int exec, int N)
+// Launch shape chosen by reg_autotune for this frame size and executor (zeros if none), with
+// every field the config fixes taken from the config.
+TileShape tuned_shape(const reg_ctx *ctx, int W, int H, int exec, int N)
 {
+    TileShape t;
     auto it = ctx->tuned.find(std::make_tuple(W, H, ctx->cfg.mode, ctx->cfg.storage, exec, log2_floor(N)));
-    return it == ctx->tuned.end() ? 0 : it->second;
+    if (it != ctx->tuned.end()) t = it->second;
+    if (ctx->cfg.cluster > 0) t.cluster = ctx->cfg.cluster;
+    if (ctx->cfg.unroll > 0) t.unroll = ctx->cfg.unroll;
+    if (ctx->cfg.ctas_per_sm > 0) t.minb = ctx->cfg.ctas_per_sm;
+    return t;
+}
+
+// Record the shape of an operator launch in the context's accounting.
+void note_shape(reg_ctx *ctx, const Params &p, int C)
+{
+    ctx->last.cluster = C;
+    ctx->last.unroll = p.cfg.mode == REG_NONRIGID ? (p.unroll == 2 ? 2 : 4) : 0;
+    ctx->last.ctas_per_sm = p.cfg.mode == REG_NONRIGID ? (p.minb > 0 ? p.minb : (C >= 16 ? 4 : 3)) : 4;
 }
 
 int pow2_floor(int v)
@@ -759,7 +807,7 @@ int launch_plain(reg_ctx *ctx, const ScanPlan &plan, const Params &p, int C, cud
         const OpDesc &op = plan.ops[e];
         // inputs produced by an earlier launch on s are complete: the pool forked from s after it
         if (op.left >= 0 && node_op[op.left] >= 0) CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.left]], 0));
-        if (op.left >= 0 && node_op[op.right] >= 0) CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.right]], 0));
+        if (op.right >= 0 && node_op[op.right] >= 0) CU(cudaStreamWaitEvent(ls, ctx->op_events[node_op[op.right]], 0));
         Params q = p;
         q.op_base = e;
         CU(launch_ops(q, storage, C, 1, ls));
@@ -773,15 +821,18 @@ int launch_plain(reg_ctx *ctx, const ScanPlan &plan, const Params &p, int C, cud
 }
 
 // Execute the planned operators.
-int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, cudaStream_t s)
+int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, const TileShape &tuned, cudaStream_t s)
 {
     const int n_ops = (int)plan.ops.size();
     const int storage = ctx->cfg.storage;
     const int n_depth = (int)plan.depth_start.size() - 1;
+    p.unroll = tuned.unroll;
+    p.minb = tuned.minb;
     if (exec == REG_EXEC_LEVEL) {
         for (int dpt = 0; dpt < n_depth; ++dpt) {
             int b = plan.depth_start[dpt], e = plan.depth_start[dpt + 1];
-            int C = tuned > 0 ? tuned : auto_cluster(ctx, e - b);
+            int C = tuned.cluster > 0 ? tuned.cluster : auto_cluster(ctx, e - b);
+            note_shape(ctx, p, C);
             int chunk = std::max(1, e - b);
             for (int q = b; q < e; q += chunk) {
                 p.op_base = q;
@@ -796,7 +847,8 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
     if (exec == REG_EXEC_PLAIN) {
         CHECK(ensure_pool(ctx));
         CHECK(ensure_op_events(ctx, n_ops));
-        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
+        const int C = tuned.cluster > 0 ? tuned.cluster : 8;
+        note_shape(ctx, p, C);
         const int t0 = timing_mark(ctx, s);
         CHECK(launch_plain(ctx, plan, p, C, s));
         ctx->op_pairs.push_back({t0, timing_mark(ctx, s)});
@@ -806,7 +858,8 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
     if (exec == REG_EXEC_GRAPH) {
         CHECK(ensure_pool(ctx));
         CHECK(ensure_op_events(ctx, n_ops));
-        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
+        const int C = tuned.cluster > 0 ? tuned.cluster : 8;
+        note_shape(ctx, p, C);
         // The graph bakes in the kernel arguments (workspace pointers, config) and the
         // dependency edges; the descriptors themselves are read from device memory when it runs.
         p.op_base = 0;
@@ -855,13 +908,11 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
         for (int e = 0; e < n_ops; ++e) node_made[plan.ops[e].out] = 1;
         for (int e = 0; e < n_ops; ++e) {
             const OpDesc &op = plan.ops[e];
-            if (op.left >= 0) {
-                for (int v : {op.left, op.right})
-                    if (node_made[v]) {
-                        pending[e] += 1;
-                        cstart[v + 1]++;
-                    }
-            }
+            for (int v : {op.left, op.right})
+                if (v >= 0 && node_made[v]) {
+                    pending[e] += 1;
+                    cstart[v + 1]++;
+                }
             if (pending[e] == 0) ready.push_back(e);
         }
         for (int v = 0; v < p.n_nodes; ++v) cstart[v + 1] += cstart[v];
@@ -869,9 +920,8 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
         std::vector<int> fillp(cstart.begin(), cstart.end() - 1);
         for (int e = 0; e < n_ops; ++e) {
             const OpDesc &op = plan.ops[e];
-            if (op.left >= 0)
-                for (int v : {op.left, op.right})
-                    if (node_made[v]) cons[fillp[v]++] = e;
+            for (int v : {op.left, op.right})
+                if (v >= 0 && node_made[v]) cons[fillp[v]++] = e;
         }
         // Host-side fault injection for tests: REG_FAULT_INJECT=stuck_op keeps the last operator
         // waiting for an input that never arrives, so the device queue's bounded wait must give
@@ -908,7 +958,8 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, 
             long long ms = atoll(t);
             if (ms > 0) p.queue.timeout_ns = ms * 1000 * 1000;
         }
-        const int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : (tuned > 0 ? tuned : 8);
+        const int C = tuned.cluster > 0 ? tuned.cluster : 8;
+        note_shape(ctx, p, C);
         int workers = ctx->cfg.workers;
         if (workers <= 0) {
             // one worker per cluster slot the device holds at once; extra workers would only wait
@@ -946,7 +997,7 @@ void sub_plan(const ScanPlan &plan, const Params &p, int b, int e, ScanPlan &sub
 
 // REG_EXEC_SPLIT_PHASES: every A leaf (DAG depth 0) runs to completion before the first B,
 // and the two phases are timed separately (the paper's "full" vs "scan" registration).
-int execute_split(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, int tuned, cudaStream_t s)
+int execute_split(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, const TileShape &tuned, cudaStream_t s)
 {
     const int n_ops = (int)plan.ops.size();
     const int nl = plan.depth_start.size() > 1 ? plan.depth_start[1] : n_ops;
@@ -1048,6 +1099,8 @@ int scan_impl(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, i
         CHECK(grid_dims(W, H, ctx->cfg.grid, ctx->cfg.levels, gd));
     }
     Dag dag;
+    if (schedule == REG_SCHED_BLELLOCH)
+        return fail(REG_EINVAL, "the Blelloch scan is exclusive: available to reg_mock_scan, not to registration");
     if (!make_dag(schedule, N - 1, dag)) return fail(REG_EINVAL, "schedule %d", schedule);
     ScanPlan plan;
     CHECK(plan_batch(S, N, dag, plan));
@@ -1068,7 +1121,7 @@ int scan_impl(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, i
     Params p;
     CHECK(prepare_params(ctx, g, NF, plan.n_nodes, n_ops, p, s));
     CU(cudaMemcpyAsync(ctx->ops.ptr, plan.ops.data(), sizeof(OpDesc) * n_ops, cudaMemcpyHostToDevice, s));
-    const int tuned = ctx->cfg.cluster > 0 ? 0 : tuned_cluster(ctx, W, H, exec, NF);
+    const TileShape tuned = tuned_shape(ctx, W, H, exec, NF);
     if (split) {
         ctx->split = true;
         CHECK(execute_split(ctx, plan, p, exec, tuned, s));
@@ -1149,6 +1202,95 @@ extern "C" int reg_scan_batch(reg_ctx_t *ctx, const float *frames, int S, int N,
                               void *stream)
 {
     return scan_impl(ctx, frames, S, N, W, H, pitch, schedule, exec, out, fields_out, per_op, stream);
+}
+
+// ------------------------------------------------------------------ mock operator
+extern "C" int reg_mock_scan(reg_ctx_t *ctx, int n, int schedule, int exec, const double *values, const float *op_us,
+                             double *prefix, double *elapsed_ms)
+{
+    if (!ctx || !values || !op_us || !prefix) return fail(REG_EINVAL, "NULL argument");
+    if (n < 1) return fail(REG_EINVAL, "need n >= 1 elements");
+    if (exec != REG_EXEC_PLAIN && exec != REG_EXEC_LEVEL && exec != REG_EXEC_PERSISTENT)
+        return fail(REG_EINVAL, "exec %d (plain, level or persistent)", exec);
+    Dag dag;
+    if (!make_dag(schedule, n, dag)) return fail(REG_EINVAL, "schedule %d", schedule);
+    const int m = (int)dag.left.size();
+    for (int j = 0; j < m; ++j)
+        if (!(op_us[j] >= 0.f && op_us[j] <= 1.0e5f)) return fail(REG_EINVAL, "duration of operator %d not in [0, 1e5] us", j);
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    CU(cudaSetDevice(ctx->device));
+    timing_reset(ctx);
+    // plan: the DAG's operators by depth (the identity, node -1, has depth 0)
+    ScanPlan plan;
+    plan.n_nodes = n + m;
+    std::vector<int> depth(plan.n_nodes, 0), op_depth(m);
+    std::vector<OpDesc> user(m);
+    for (int j = 0; j < m; ++j) {
+        const int l = dag.left[j], r = dag.right[j], o = n + j;
+        depth[o] = 1 + std::max(l >= 0 ? depth[l] : 0, depth[r]);
+        op_depth[j] = depth[o] - 1;
+        user[j] = OpDesc{0, 0, l, r, o, -1};
+    }
+    int maxd = 0;
+    for (int v : op_depth) maxd = std::max(maxd, v);
+    plan.depth_start.assign(maxd + 2, 0);
+    for (int v : op_depth) plan.depth_start[v + 1]++;
+    for (int q = 0; q <= maxd; ++q) plan.depth_start[q + 1] += plan.depth_start[q];
+    std::vector<int> fill(plan.depth_start.begin(), plan.depth_start.end() - 1);
+    plan.ops.resize(m);
+    plan.user_index.resize(m);
+    for (int j = 0; j < m; ++j) {
+        const int e = fill[op_depth[j]]++;
+        plan.ops[e] = user[j];
+        plan.user_index[e] = j;
+    }
+    plan.out_nodes = dag.out;
+    std::vector<float> us(std::max(1, m));
+    for (int e = 0; e < m; ++e) us[e] = op_us[plan.user_index[e]];
+    // device state: descriptors, durations, node values (component 0 of node_theta)
+    cudaStream_t s = nullptr;
+    Params p;
+    memset(&p, 0, sizeof(p));
+    p.cfg.mode = kModeMock;
+    p.n_ops = m;
+    p.n_nodes = plan.n_nodes;
+    CHECK(ctx->ops.reserve(sizeof(OpDesc) * std::max(1, m)));
+    CHECK(ctx->stats.reserve(sizeof(OpStats) * std::max(1, m)));
+    CHECK(ctx->node_theta.reserve(sizeof(double) * 3 * plan.n_nodes));
+    CHECK(ctx->tmp.reserve(sizeof(float) * us.size()));
+    CHECK(ctx->status.reserve(sizeof(int) * 4));
+    ctx->last_n = 0;   // the node storage of the last scan is reused here
+    p.ops = ctx->ops.as<OpDesc>();
+    p.stats = ctx->stats.as<OpStats>();
+    p.node_theta = ctx->node_theta.as<double>();
+    p.mock_us = ctx->tmp.as<float>();
+    p.status = ctx->status.as<int>();
+    std::vector<double> th((size_t)3 * plan.n_nodes, 0.0);
+    for (int j = 0; j < n; ++j) th[3 * j] = values[j];
+    CU(cudaMemcpyAsync(p.node_theta, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, s));
+    if (m > 0) {
+        CU(cudaMemcpyAsync(ctx->ops.ptr, plan.ops.data(), sizeof(OpDesc) * m, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync((void *)p.mock_us, us.data(), sizeof(float) * m, cudaMemcpyHostToDevice, s));
+    }
+    CU(cudaMemsetAsync(p.status, 0, sizeof(int) * 4, s));
+    const bool timing = ctx->timing;
+    ctx->timing = true;
+    TileShape one;
+    one.cluster = 1;   // one CTA per mock operator
+    int rc = REG_OK;
+    if (m > 0) rc = execute(ctx, plan, p, exec, one, s);
+    if (rc == REG_OK && cudaGetLastError() != cudaSuccess) rc = fail(REG_ECUDA, "mock operator launch failed");
+    if (rc == REG_OK) rc = check_device_status(ctx, s);
+    if (rc == REG_OK && cudaMemcpyAsync(th.data(), p.node_theta, sizeof(double) * th.size(), cudaMemcpyDeviceToHost,
+                                        s) != cudaSuccess)
+        rc = fail(REG_ECUDA, "mock scan: copy of the node values");
+    if (rc == REG_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(REG_ECUDA, "mock scan: synchronize");
+    if (rc == REG_OK) timing_resolve(ctx);   // the events are read while timing is still on
+    ctx->timing = timing;
+    CHECK(rc);
+    for (int i = 0; i < n; ++i) prefix[i] = dag.out[i] >= 0 ? th[3 * dag.out[i]] : 0.0;
+    if (elapsed_ms) *elapsed_ms = ctx->last.op_kernel_ms;
+    return REG_OK;
 }
 
 // ------------------------------------------------------------------ reg_scan_grids / reg_warp
@@ -1296,6 +1438,9 @@ extern "C" int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int 
     }
     int C = ctx->cfg.cluster > 0 ? ctx->cfg.cluster : 8;
     p.op_base = 0;
+    p.unroll = ctx->cfg.unroll;
+    p.minb = ctx->cfg.ctas_per_sm;
+    note_shape(ctx, p, C);
     int e0 = timing_mark(ctx, s);
     CU(launch_ops(p, ctx->cfg.storage, C, 1, s));
     ctx->op_pairs.push_back({e0, timing_mark(ctx, s)});
@@ -1448,7 +1593,7 @@ extern "C" int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, i
 {
     if (!ctx || !frames) return fail(REG_EINVAL, "NULL argument");
     if (N < 2) return fail(REG_EINVAL, "need N >= 2 frames");
-    const int saved = ctx->cfg.cluster;
+    const reg_config_t saved = ctx->cfg;
     const int n = N - 1;
     std::vector<reg_elem_t> out(n);
     // no dense fields while timing: their kernel runs after the scan and costs the same for
@@ -1461,14 +1606,10 @@ extern "C" int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, i
         if (e0) cudaEventDestroy(e0);
         return fail(REG_ECUDA, "autotune: cudaEventCreate: %s", cudaGetErrorString(e));
     }
-    int best_c = 0, rc = REG_OK;
-    float best_ms = 1e30f;
-    const int cands[] = {1, 2, 4, 8, 16};
-    for (int c : cands) {
-        ctx->cfg.cluster = c;
-        rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), fields, nullptr, s);
-        if (rc != REG_OK) break;   // e.g. a cluster size the device cannot schedule
-        float ms_min = 1e30f;
+    // time one candidate (the config's fields as set): best of two runs after an untimed one
+    auto trial = [&](float &ms_min) {
+        ms_min = 1e30f;
+        int rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), fields, nullptr, s);
         for (int rep = 0; rep < 2 && rc == REG_OK; ++rep) {
             cudaEventRecord(e0, s);
             rc = reg_scan(ctx, frames, N, W, H, pitch, schedule, exec, out.data(), fields, nullptr, s);
@@ -1478,15 +1619,68 @@ extern "C" int reg_autotune(reg_ctx_t *ctx, const float *frames, int N, int W, i
             cudaEventElapsedTime(&ms, e0, e1);
             ms_min = std::min(ms_min, ms);
         }
-        if (rc != REG_OK) break;
-        if (ms_min < best_ms) { best_ms = ms_min; best_c = c; }
+        return rc;
+    };
+    // the tuned entry is cleared first, so a candidate's unset fields take the built-in rule
+    const auto key = std::make_tuple(W, H, saved.mode, saved.storage, exec, log2_floor(N));
+    ctx->tuned.erase(key);
+    TileShape bestT;
+    int rc = REG_OK;
+    float best_ms = 1e30f;
+    // 1. CTAs per operator (nonrigid: with either register form), at the default pixels per lane
+    const bool nonrigid = saved.mode == REG_NONRIGID;
+    const int clusters[] = {1, 2, 4, 8, 16};
+    for (int c : clusters) {
+        if (saved.cluster > 0 && c != saved.cluster) continue;
+        bool stop = false;
+        for (int mb : {3, 4}) {
+            if (!nonrigid && mb == 4) continue;
+            if (nonrigid && saved.ctas_per_sm > 0 && mb != saved.ctas_per_sm) continue;
+            ctx->cfg.cluster = c;
+            if (nonrigid) ctx->cfg.ctas_per_sm = mb;
+            float ms;
+            rc = trial(ms);
+            if (rc != REG_OK) { stop = true; break; }   // e.g. a cluster size the device cannot schedule
+            if (ms < best_ms) {
+                best_ms = ms;
+                bestT.cluster = c;
+                bestT.minb = nonrigid ? mb : 0;
+            }
+        }
+        if (stop) break;
     }
-    ctx->cfg.cluster = saved;
+    // 2. nonrigid: the other pixels per lane at that shape
+    if (bestT.cluster > 0 && nonrigid) {
+        ctx->cfg.cluster = bestT.cluster;
+        ctx->cfg.ctas_per_sm = bestT.minb;
+        bestT.unroll = saved.unroll > 0 ? saved.unroll : 4;
+        if (saved.unroll == 0) {
+            ctx->cfg.unroll = 2;
+            float ms;
+            if (trial(ms) == REG_OK && ms < best_ms) {
+                best_ms = ms;
+                bestT.unroll = 2;
+            }
+        }
+    }
+    ctx->cfg = saved;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best_c == 0) return rc != REG_OK ? rc : fail(REG_ECUDA, "autotune: no candidate ran");
-    ctx->tuned[std::make_tuple(W, H, ctx->cfg.mode, ctx->cfg.storage, exec, log2_floor(N))] = best_c;
-    if (best) *best = best_c;
+    if (bestT.cluster == 0) return rc != REG_OK ? rc : fail(REG_ECUDA, "autotune: no candidate ran");
+    ctx->tuned[key] = bestT;
+    if (best) *best = bestT.cluster;
+    return REG_OK;
+}
+
+extern "C" int reg_autotune_get(reg_ctx_t *ctx, int N, int W, int H, int exec, int *cluster, int *unroll,
+                                int *ctas_per_sm)
+{
+    if (!ctx) return fail(REG_EINVAL, "ctx is NULL");
+    auto it = ctx->tuned.find(std::make_tuple(W, H, ctx->cfg.mode, ctx->cfg.storage, exec, log2_floor(N)));
+    if (it == ctx->tuned.end()) return fail(REG_EINVAL, "no autotuned shape for %dx%d, %d frames, exec %d", W, H, N, exec);
+    if (cluster) *cluster = it->second.cluster;
+    if (unroll) *unroll = it->second.unroll;
+    if (ctas_per_sm) *ctas_per_sm = it->second.minb;
     return REG_OK;
 }
 
@@ -1499,7 +1693,8 @@ extern "C" int reg_autotune_save(reg_ctx_t *ctx, const char *path)
         int W, H, mode, storage, exec, lg;
         std::tie(W, H, mode, storage, exec, lg) = kv.first;
         fprintf(f, "{\"W\": %d, \"H\": %d, \"mode\": %d, \"storage\": %d, \"exec\": %d, \"log2_frames\": %d, "
-                   "\"cluster\": %d}\n", W, H, mode, storage, exec, lg, kv.second);
+                   "\"cluster\": %d, \"unroll\": %d, \"ctas_per_sm\": %d}\n", W, H, mode, storage, exec, lg,
+                kv.second.cluster, kv.second.unroll, kv.second.minb);
     }
     fclose(f);
     return REG_OK;
@@ -1513,11 +1708,18 @@ extern "C" int reg_autotune_load(reg_ctx_t *ctx, const char *path)
     char line[512];
     int loaded = 0;
     while (fgets(line, sizeof(line), f)) {
-        int W, H, mode, storage, exec, lg, c;
-        if (sscanf(line, "{\"W\": %d, \"H\": %d, \"mode\": %d, \"storage\": %d, \"exec\": %d, \"log2_frames\": %d, "
-                         "\"cluster\": %d}", &W, &H, &mode, &storage, &exec, &lg, &c) == 7 &&
-            (c == 1 || c == 2 || c == 4 || c == 8 || c == 16)) {
-            ctx->tuned[std::make_tuple(W, H, mode, storage, exec, lg)] = c;
+        int W, H, mode, storage, exec, lg, c, u = 0, m = 0;
+        // lines written before the energy-pass shape was tuned end after "cluster"
+        const int got = sscanf(line, "{\"W\": %d, \"H\": %d, \"mode\": %d, \"storage\": %d, \"exec\": %d, "
+                                     "\"log2_frames\": %d, \"cluster\": %d, \"unroll\": %d, \"ctas_per_sm\": %d}",
+                               &W, &H, &mode, &storage, &exec, &lg, &c, &u, &m);
+        if ((got == 7 || got == 9) && (c == 1 || c == 2 || c == 4 || c == 8 || c == 16) &&
+            (u == 0 || u == 2 || u == 4) && (m == 0 || m == 3 || m == 4)) {
+            TileShape t;
+            t.cluster = c;
+            t.unroll = u;
+            t.minb = m;
+            ctx->tuned[std::make_tuple(W, H, mode, storage, exec, lg)] = t;
             ++loaded;
         }
     }

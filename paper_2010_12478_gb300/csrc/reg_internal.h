@@ -68,6 +68,9 @@ enum DevStatus : int32_t {
     kDevWaitTimeout = 3   // bounded wait on a TMA load (mbarrier) gave up
 };
 
+// Operator model of a launch beyond REG_RIGID / REG_NONRIGID: the mock operator of reg_mock_scan.
+constexpr int kModeMock = 2;
+
 struct Config {
     int mode, levels, max_iter, max_rejects;
     double tol_grad, tol_rel_e, armijo_c, tau0, step_cap, lambda;
@@ -95,11 +98,21 @@ struct Params {
     int op_base;               // first op of this launch (batched launches)
     double *node_theta;        // [n_nodes][3]: rigid (alpha, Gx, Gy); nonrigid (0, mean c_x, mean c_y)
     float2 *node_grid;         // nonrigid: [n_nodes][gny * gnx] control values (finest px)
+    const float *mock_us;      // mock operator (kModeMock): duration of each operator, microseconds
+    int unroll;                // nonrigid energy passes: pixels in flight per lane (2 or 4; 0 = 4)
+    int minb;                  // nonrigid register form: CTAs per SM (3 or 4; 0 = 4 at 16 CTAs per
+                               // operator, else 3)
     int gnx, gny, gs;          // nonrigid control grid: points per axis and spacing (finest px)
     int n_nodes;
     OpStats *stats;            // [n_ops]
     int *status;               // kernel status word (first device error)
     Queue queue;               // persistent executor only
+};
+
+// Launch shape of the operator kernels (0 = not chosen): CTAs per operator, energy-pass pixels
+// per lane, and register form (CTAs per SM the kernel's register budget is sized for).
+struct TileShape {
+    int cluster = 0, unroll = 0, minb = 0;
 };
 
 // Host launchers (reg_kernels.cu).

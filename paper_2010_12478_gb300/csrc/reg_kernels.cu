@@ -798,7 +798,7 @@ __device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int r
 // 3 Sr, 4 Srr; slot 5 = sum over control edges |dct|^2 (rank 0 only, so the cluster sum counts
 // it once).  Each warp first interpolates the control values of its row along y into crow
 // (u_j and u_{j+1} - u_j for the nx - 1 cells), so a pixel only interpolates along x.
-template <typename S, bool RSTAT>
+template <typename S, bool RSTAT, int U>
 __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *ct, float4 *crow_all,
                                  int r0, int r1, Smem &sm, int &buf, const cg::cluster_group &cl)
 {
@@ -856,7 +856,7 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     if (fast) {
         const int lgl = 31 - __clz(sl);
         const float wxl = fmaf(GL.pl, (float)(lane & (sl - 1)), GL.off) * GL.scale_inv;
-        for_rows<4>(
+        for_rows<U>(
             L.W, r0, r1, row,
             [&](int r, int c) {
                 const float4 q = crow[c >> lgl];
@@ -864,7 +864,7 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
             },
             flush_fast, []() {});
     } else {
-        for_rows<4>(
+        for_rows<U>(
             L.W, r0, r1, row,
             [&](int r, int c) {
                 const float gxf = fminf(fmaf(GL.pl, (float)c, GL.off) * GL.scale_inv, (float)(G.nx - 1));
@@ -1291,7 +1291,7 @@ __device__ __forceinline__ float2 grid_eval_global(const float2 *q, const Grid &
     return u;
 }
 
-template <typename S>
+template <typename S, int U>
 __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Smem &sm, float2 *gbuf,
                              const cg::cluster_group &cl)
 {
@@ -1360,14 +1360,14 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
 #pragma unroll
             for (int q = 0; q < 5; ++q) pm[q] = sm.pm[q];
             if (act == kActEnergy) {
-                grid_energy_pass<S, true>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
+                grid_energy_pass<S, true, U>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
             } else if (act == kActTrial) {
                 for (int j = tid; j < Nc; j += kThreads) {
                     const float2 a = c[j], b = d[j];
                     ct[j] = make_float2(fmaf(pm[0], b.x, a.x), fmaf(pm[0], b.y, a.y));
                 }
                 __syncthreads();
-                grid_energy_pass<S, false>(L, G, GL, ct, crow, r0, r1, sm, buf, cl);
+                grid_energy_pass<S, false, U>(L, G, GL, ct, crow, r0, r1, sm, buf, cl);
             } else if (act == kActMetric) {
                 grid_grad_pass<S, true>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
             } else {
@@ -1419,8 +1419,37 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
 }
 
 // ================================================================== kernels
+// Mock operator (Sec. 5.1): the two input values are added after a spin of the operator's given
+// duration on %globaltimer (at most 100 ms, and a bounded number of sleeps), as the paper's
+// artificial operator of fixed or exponentially distributed running time.  left < 0 is the
+// identity (0), which the exclusive Blelloch scan feeds in.
+__device__ void run_mock(const Params &p, const OpDesc &op, int op_index, const cg::cluster_group &cl)
+{
+    if (threadIdx.x != 0 || cl.block_rank() != 0) return;
+    const double a = op.left >= 0 ? __ldcg(p.node_theta + 3 * op.left) : 0.0;
+    const double b = __ldcg(p.node_theta + 3 * op.right);
+    const long long dur = (long long)(fminf(fmaxf(p.mock_us[op_index], 0.f), 1.0e5f) * 1000.0f);
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int it = 0; it < (1 << 24); ++it) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if ((long long)(t - t0) >= dur) break;
+        __nanosleep(100);
+    }
+    __stcg(p.node_theta + 3 * op.out, a + b);
+    OpStats &st = p.stats[op_index];
+    st.i = op.ref;
+    st.k = op.tmpl;
+    st.status = kDevOk;
+    st.energy = a + b;
+}
+
 __device__ bool op_valid(const Params &p, const OpDesc &op)
 {
+    if (p.cfg.mode == kModeMock) {
+        auto ok = [&](int n) { return n >= 0 && n < p.n_nodes; };
+        return ok(op.out) && ok(op.right) && (op.left < 0 || ok(op.left));
+    }
     auto node_ok = [&](int n) { return n >= 0 && n < p.n_nodes; };
     if (op.ref < 0 || op.ref >= p.n_frames || op.tmpl < 0 || op.tmpl >= p.n_frames) return false;
     if (!node_ok(op.out)) return false;
@@ -1429,7 +1458,7 @@ __device__ bool op_valid(const Params &p, const OpDesc &op)
     return true;
 }
 
-template <int MODE, typename S>
+template <int MODE, typename S, int U>
 __device__ void run_op(const Params &p, int op_index, Smem &sm, float2 *gbuf, const cg::cluster_group &cl)
 {
     const OpDesc op = p.ops[op_index];
@@ -1441,26 +1470,28 @@ __device__ void run_op(const Params &p, int op_index, Smem &sm, float2 *gbuf, co
         return;
     }
     if constexpr (MODE == REG_RIGID) run_rigid<S>(p, op, op_index, sm, cl);
-    else run_nonrigid<S>(p, op, op_index, sm, gbuf, cl);
+    else if constexpr (MODE == kModeMock) run_mock(p, op, op_index, cl);
+    else run_nonrigid<S, U>(p, op, op_index, sm, gbuf, cl);
 }
 
 // Batched launch: cluster q of the grid runs operator op_base + q.  MINB: CTAs per SM the
 // register budget is sized for (the nonrigid kernels come in a 3-CTA form without spills and a
-// 4-CTA form with a few spilled registers, faster once the clusters are large).
-template <int MODE, typename S, int MINB>
+// 4-CTA form with a few spilled registers, faster once the clusters are large).  U: pixels in
+// flight per lane in the nonrigid energy passes (2 or 4, the tile shape reg_autotune chooses).
+template <int MODE, typename S, int MINB, int U = 4>
 __global__ void __launch_bounds__(kThreads, MINB) op_kernel(Params p)
 {
     __shared__ Smem sm;
     extern __shared__ __align__(16) float2 gbuf[];   // nonrigid: control grid c, d, ct, gp
     cg::cluster_group cl = cg::this_cluster();
     const int q = blockIdx.x / cl.num_blocks();
-    run_op<MODE, S>(p, p.op_base + q, sm, gbuf, cl);
+    run_op<MODE, S, U>(p, p.op_base + q, sm, gbuf, cl);
     cl.sync();   // no CTA leaves while a peer may still read its shared memory
 }
 
 // Persistent launch: each cluster claims ready operators from the device queue
 // until all n_ops have been claimed.  Every wait is bounded by queue.timeout_ns.
-template <int MODE, typename S, int MINB>
+template <int MODE, typename S, int MINB, int U = 4>
 __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
 {
     __shared__ Smem sm;
@@ -1488,7 +1519,7 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
                         break;
                     }
                     __nanosleep(ns);
-                    if (ns < 4096) ns *= 2;
+                    if (ns < 1024) ns *= 2;
                 }
                 (void)t0;
                 __threadfence();
@@ -1499,21 +1530,34 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
         const int op = *cl.map_shared_rank(&sm.idata[1], 0);
         cl.sync();
         if (op < 0) break;
-        run_op<MODE, S>(p, op, sm, gbuf, cl);
+        run_op<MODE, S, U>(p, op, sm, gbuf, cl);
         cl.sync();
-        if (leader) {
-            // publish the produced node and release its consumers
-            __threadfence();
+        if (cl.block_rank() == 0) {
+            // publish the produced node and release its consumers, spread over the CTA's threads (a
+            // node of a Ladner-Fischer scan has up to n/2 consumers); each warp claims the queue
+            // slots of the consumers it made ready with one atomic on the tail
+            __threadfence();   // the cluster's writes of the node, seen through cl.sync, go first
             const int node = p.ops[op].out;
-            for (int e = p.queue.cons_start[node]; e < p.queue.cons_start[node + 1]; ++e) {
-                int c = p.queue.consumers[e];
-                if (atomicSub(p.queue.pending + c, 1) == 1) {
-                    int t = atomicAdd(p.queue.tail, 1);
-                    __threadfence();
-                    atomicExch(p.queue.slots + t, c);
+            const int cb = p.queue.cons_start[node], ce = p.queue.cons_start[node + 1];
+            const int lane = threadIdx.x & 31;
+            for (int base = cb; base < ce; base += kThreads) {
+                const int e = base + threadIdx.x;
+                int c = -1;
+                bool ready = false;
+                if (e < ce) {
+                    c = p.queue.consumers[e];
+                    ready = atomicSub(p.queue.pending + c, 1) == 1;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ready);
+                if (m) {
+                    const int first = __ffs(m) - 1;
+                    int t0 = 0;
+                    if (lane == first) t0 = atomicAdd(p.queue.tail, __popc(m));
+                    t0 = __shfl_sync(0xffffffffu, t0, first);
+                    if (ready) atomicExch(p.queue.slots + t0 + __popc(m & ((1u << lane) - 1)), c);
                 }
             }
-            atomicAdd(p.queue.done, 1);
+            if (threadIdx.x == 0) atomicAdd(p.queue.done, 1);
         }
     }
     cl.sync();
@@ -1562,7 +1606,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
         GL.W = L.W; GL.H = L.H; GL.l = 0; GL.pl = 1.f; GL.off = 0.f; GL.scale_inv = 1.f / (float)G.s;
         int cr0, cr1, r0, r1;
         grid_rows(G, GL, 0, 1, cr0, cr1, r0, r1);
-        grid_energy_pass<S, true>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
+        grid_energy_pass<S, true, 4>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
         FieldCtl &k = sm.fctl;
         if (tid == 0) {
             memset(&k, 0, sizeof(k));
@@ -1841,10 +1885,36 @@ static cudaError_t launch_cluster(K kernel, int blocks, int cluster, cudaStream_
     return cudaLaunchKernelEx(&lc, kernel, p);
 }
 
+typedef void (*OpKernelFn)(Params);
+
+// The nonrigid kernel for a storage type, launch form, register form and energy-pass unroll.
+template <typename S>
+static OpKernelFn nonrigid_fn(bool persistent, bool minb4, int unroll)
+{
+    const bool u2 = unroll == 2;
+    if (persistent) {
+        if (minb4) return u2 ? persistent_kernel<REG_NONRIGID, S, 4, 2> : persistent_kernel<REG_NONRIGID, S, 4, 4>;
+        return u2 ? persistent_kernel<REG_NONRIGID, S, 3, 2> : persistent_kernel<REG_NONRIGID, S, 3, 4>;
+    }
+    if (minb4) return u2 ? op_kernel<REG_NONRIGID, S, 4, 2> : op_kernel<REG_NONRIGID, S, 4, 4>;
+    return u2 ? op_kernel<REG_NONRIGID, S, 3, 2> : op_kernel<REG_NONRIGID, S, 3, 4>;
+}
+
+static OpKernelFn nonrigid_kernel(int storage, bool persistent, bool minb4, int unroll)
+{
+    switch (storage) {
+    case REG_F32: return nonrigid_fn<float>(persistent, minb4, unroll);
+    case REG_BF16: return nonrigid_fn<__nv_bfloat16>(persistent, minb4, unroll);
+    case REG_F16: return nonrigid_fn<__half>(persistent, minb4, unroll);
+    }
+    return nullptr;
+}
+
 cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_ops, cudaStream_t s)
 {
-    const bool minb4 = cluster >= 16;   // nonrigid: the 4-CTA form for the largest clusters
+    const bool minb4 = p.minb > 0 ? p.minb == 4 : cluster >= 16;   // nonrigid register form
     const int blocks = n_launch_ops * cluster;
+    if (p.cfg.mode == kModeMock) return launch_cluster(op_kernel<kModeMock, float, 4>, blocks, cluster, s, p);
     if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
         case REG_F32: return launch_cluster(op_kernel<REG_RIGID, float, 4>, blocks, cluster, s, p);
@@ -1852,25 +1922,17 @@ cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_o
         case REG_F16: return launch_cluster(op_kernel<REG_RIGID, __half, 4>, blocks, cluster, s, p);
         }
     } else {
-        switch (storage) {
-        case REG_F32: return launch_cluster(minb4 ? op_kernel<REG_NONRIGID, float, 4>
-                                                : op_kernel<REG_NONRIGID, float, 3>,
-                                          blocks, cluster, s, p);
-        case REG_BF16: return launch_cluster(minb4 ? op_kernel<REG_NONRIGID, __nv_bfloat16, 4>
-                                                : op_kernel<REG_NONRIGID, __nv_bfloat16, 3>,
-                                          blocks, cluster, s, p);
-        case REG_F16: return launch_cluster(minb4 ? op_kernel<REG_NONRIGID, __half, 4>
-                                                : op_kernel<REG_NONRIGID, __half, 3>,
-                                          blocks, cluster, s, p);
-        }
+        OpKernelFn k = nonrigid_kernel(storage, false, minb4, p.unroll);
+        if (k) return launch_cluster(k, blocks, cluster, s, p);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_persistent(const Params &p, int storage, int cluster, int workers, cudaStream_t s)
 {
-    const bool minb4 = cluster >= 16;   // nonrigid: the 4-CTA form for the largest clusters
+    const bool minb4 = p.minb > 0 ? p.minb == 4 : cluster >= 16;   // nonrigid register form
     const int blocks = workers * cluster;
+    if (p.cfg.mode == kModeMock) return launch_cluster(persistent_kernel<kModeMock, float, 4>, blocks, cluster, s, p);
     if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
         case REG_F32: return launch_cluster(persistent_kernel<REG_RIGID, float, 4>, blocks, cluster, s, p);
@@ -1878,17 +1940,8 @@ cudaError_t launch_persistent(const Params &p, int storage, int cluster, int wor
         case REG_F16: return launch_cluster(persistent_kernel<REG_RIGID, __half, 4>, blocks, cluster, s, p);
         }
     } else {
-        switch (storage) {
-        case REG_F32: return launch_cluster(minb4 ? persistent_kernel<REG_NONRIGID, float, 4>
-                                                : persistent_kernel<REG_NONRIGID, float, 3>,
-                                          blocks, cluster, s, p);
-        case REG_BF16: return launch_cluster(minb4 ? persistent_kernel<REG_NONRIGID, __nv_bfloat16, 4>
-                                                : persistent_kernel<REG_NONRIGID, __nv_bfloat16, 3>,
-                                          blocks, cluster, s, p);
-        case REG_F16: return launch_cluster(minb4 ? persistent_kernel<REG_NONRIGID, __half, 4>
-                                                : persistent_kernel<REG_NONRIGID, __half, 3>,
-                                          blocks, cluster, s, p);
-        }
+        OpKernelFn k = nonrigid_kernel(storage, true, minb4, p.unroll);
+        if (k) return launch_cluster(k, blocks, cluster, s, p);
     }
     return cudaErrorInvalidValue;
 }
@@ -1919,26 +1972,19 @@ static int resident_clusters(K kernel, int cluster, const Params &p)
 
 int persistent_resident_clusters(const Params &p, int storage, int cluster)
 {
-    const bool minb4 = cluster >= 16;   // nonrigid: the 4-CTA form for the largest clusters
+    const bool minb4 = p.minb > 0 ? p.minb == 4 : cluster >= 16;   // nonrigid register form
     int n = -1;
-    if (p.cfg.mode == REG_RIGID) {
+    if (p.cfg.mode == kModeMock) {
+        n = resident_clusters(persistent_kernel<kModeMock, float, 4>, cluster, p);
+    } else if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
         case REG_F32: n = resident_clusters(persistent_kernel<REG_RIGID, float, 4>, cluster, p); break;
         case REG_BF16: n = resident_clusters(persistent_kernel<REG_RIGID, __nv_bfloat16, 4>, cluster, p); break;
         case REG_F16: n = resident_clusters(persistent_kernel<REG_RIGID, __half, 4>, cluster, p); break;
         }
     } else {
-        switch (storage) {
-        case REG_F32: n = resident_clusters(minb4 ? persistent_kernel<REG_NONRIGID, float, 4>
-                                                : persistent_kernel<REG_NONRIGID, float, 3>,
-                                          cluster, p); break;
-        case REG_BF16: n = resident_clusters(minb4 ? persistent_kernel<REG_NONRIGID, __nv_bfloat16, 4>
-                                                : persistent_kernel<REG_NONRIGID, __nv_bfloat16, 3>,
-                                          cluster, p); break;
-        case REG_F16: n = resident_clusters(minb4 ? persistent_kernel<REG_NONRIGID, __half, 4>
-                                                : persistent_kernel<REG_NONRIGID, __half, 3>,
-                                          cluster, p); break;
-        }
+        OpKernelFn k = nonrigid_kernel(storage, true, minb4, p.unroll);
+        if (k) n = resident_clusters(k, cluster, p);
     }
     if (n < 0) cudaGetLastError();
     return n;

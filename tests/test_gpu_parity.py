@@ -247,6 +247,25 @@ def test_scan_nonrigid_c1_matches_oracle(exec_):
         assert err <= PX_TOL, (i, err)
 
 
+@pytest.mark.parametrize("unroll,ctas_per_sm", [(2, 3), (4, 4), (2, 4)])
+def test_scan_nonrigid_c1_tile_shapes_match_oracle(unroll, ctas_per_sm):
+    """Every register form and energy-pass unroll the autotuner may choose, against the oracle."""
+    F = c1_frames(6)
+    cfg = B.Config(mode="nonrigid", cluster=4, unroll=unroll, ctas_per_sm=ctas_per_sm)
+    ctx = B.Context(cfg)
+    ctx.set_timing(True)
+    n = len(F) - 1
+    fo = torch.zeros((n, 2, 128, 128), device="cuda")
+    ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung", exec="persistent", fields_out=fo)
+    t = ctx.last_timing()
+    assert (t["cluster"], t["unroll"], t["ctas_per_sm"]) == (4, unroll, ctas_per_sm)
+    ref = oracle_scan(F, cfg, "brent_kung")
+    got = fo.cpu().numpy()
+    for i, o in enumerate(ref):
+        err = O.max_px_error(got[i], o.phi, 128, 128, "nonrigid")
+        assert err <= PX_TOL, (i, err)
+
+
 def test_scan_two_frames():
     F = c1_frames(2)
     ctx = B.Context(B.Config())

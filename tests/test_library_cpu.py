@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(B.reg_elem_t) == 20          # 20-byte scan element (Sec. 5)
     assert ctypes.sizeof(B.reg_stats_t) == 144
-    assert ctypes.sizeof(B.reg_timing_t) == 56
+    assert ctypes.sizeof(B.reg_timing_t) == 72
     cfg = B.reg_config_t()
     lib.reg_config_default(ctypes.byref(cfg))
     assert cfg.levels == 2 and cfg.mode == B.RIGID and cfg.storage == B.F32
@@ -47,6 +47,8 @@ def test_struct_layouts_match_header(lib):
     assert cfg.tol_grad == O.Config().tol_grad == B.Config().tol_grad == 3e-5
     assert cfg.tol_rel_e == O.Config().tol_rel_e == B.Config().tol_rel_e == 0.0
     assert cfg.metric == O.Config().metric == B.Config().metric == 1
+    # the launch shape is left to the autotuner unless set
+    assert cfg.unroll == 0 and cfg.ctas_per_sm == 0 and B.Config().c().unroll == 0
 
 
 def test_errors_without_gpu_are_reported_not_crashing(lib):
@@ -62,14 +64,20 @@ def test_errors_without_gpu_are_reported_not_crashing(lib):
     bad.levels = 9
     assert lib.reg_ctx_create(ctypes.byref(bad), 0, ctypes.byref(h)) == B.REG_EINVAL
     assert b"levels" in lib.reg_last_error_message()
+    for field, value in (("unroll", 3), ("ctas_per_sm", 2)):
+        bad = B.reg_config_t()
+        lib.reg_config_default(ctypes.byref(bad))
+        setattr(bad, field, value)
+        assert lib.reg_ctx_create(ctypes.byref(bad), 0, ctypes.byref(h)) == B.REG_EINVAL
+        assert field.encode() in lib.reg_last_error_message()
 
 
 @pytest.mark.parametrize("name", ["sequential", "brent_kung", "dissemination", "ladner_fischer", "lookback2",
-                                  "lookback4", "lookback8"])
+                                  "lookback4", "lookback8", "blelloch"])
 def test_library_dag_equals_oracle_dag(lib, name):
     for n in list(range(1, 40)) + [255, 256, 1000, 4095]:
         ops, out = B.scan_dag(name, n)
-        ref = O.DAGS[name](n)
+        ref = O.dag_blelloch(n) if name == "blelloch" else O.DAGS[name](n)
         assert ops == [tuple(o) for o in ref.ops], (name, n)
         assert out == ref.out, (name, n)
 
