@@ -323,7 +323,7 @@ struct reg_ctx {
     DevBuf pyr[kMaxLevels]; // pyramid levels of all frames (nonrigid: with a border holding the mean)
     DevBuf spyr[kMaxLevels]; // nonrigid: the B-spline model of every level at its pixel centres
     DevBuf means, level_tab, ops, stats, node_theta, node_grid, status, node_ids;
-    DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr;
+    DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr, q_class;
     DevBuf tmp;
     cudaStream_t pool[kPoolStreams] = {};
     cudaEvent_t ev_pool_done[kPoolStreams] = {};
@@ -932,23 +932,55 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, const TileS
             if (pending[last] == 0) ready.erase(std::remove(ready.begin(), ready.end(), last), ready.end());
             pending[last] += 1;
         }
+        // priority classes: bottom level with the cost of an operator estimated from its span (the
+        // frames it registers across; evaluations grow with the drift to undo), ranked into
+        // kQueueClasses equal groups.  Consumers come after their producers in the plan.
+        std::vector<double> blev(n_ops);
+        for (int e = n_ops - 1; e >= 0; --e) {
+            const OpDesc &op = plan.ops[e];
+            double tail = 0.0;
+            for (int q = cstart[op.out]; q < cstart[op.out + 1]; ++q) tail = std::max(tail, blev[cons[q]]);
+            blev[e] = 1.0 + std::abs(op.tmpl - op.ref) / 64.0 + tail;
+        }
+        std::vector<int> order(n_ops), op_class(n_ops), class_cnt(kQueueClasses, 0);
+        for (int e = 0; e < n_ops; ++e) order[e] = e;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blev[a] > blev[b]; });
+        for (int r = 0; r < n_ops; ++r) {
+            const int c = (int)((long long)r * kQueueClasses / std::max(1, n_ops));
+            op_class[order[r]] = c;
+            class_cnt[c] += 1;
+        }
+        std::vector<int> class_off(kQueueClasses, 0), class_tail(kQueueClasses, 0);
+        for (int c = 1; c < kQueueClasses; ++c) class_off[c] = class_off[c - 1] + class_cnt[c - 1];
         std::vector<int> slots(n_ops, -1);
-        for (size_t i = 0; i < ready.size(); ++i) slots[i] = ready[i];
+        for (int e : ready) {
+            const int c = op_class[e];
+            slots[class_off[c] + class_tail[c]++] = e;
+        }
+        std::vector<int> cls_buf(op_class);
+        cls_buf.insert(cls_buf.end(), class_off.begin(), class_off.end());
         CHECK(ctx->q_slots.reserve(sizeof(int) * std::max(1, n_ops)));
         CHECK(ctx->q_pending.reserve(sizeof(int) * std::max(1, n_ops)));
         CHECK(ctx->q_cons.reserve(sizeof(int) * cons.size()));
         CHECK(ctx->q_cons_start.reserve(sizeof(int) * cstart.size()));
-        CHECK(ctx->q_ctr.reserve(sizeof(int) * 4));
+        CHECK(ctx->q_class.reserve(sizeof(int) * cls_buf.size()));
+        CHECK(ctx->q_ctr.reserve(sizeof(int) * (2 * kQueueClasses + 2)));
         CU(cudaMemcpyAsync(ctx->q_slots.ptr, slots.data(), sizeof(int) * n_ops, cudaMemcpyHostToDevice, s));
         CU(cudaMemcpyAsync(ctx->q_pending.ptr, pending.data(), sizeof(int) * n_ops, cudaMemcpyHostToDevice, s));
         CU(cudaMemcpyAsync(ctx->q_cons.ptr, cons.data(), sizeof(int) * cons.size(), cudaMemcpyHostToDevice, s));
         CU(cudaMemcpyAsync(ctx->q_cons_start.ptr, cstart.data(), sizeof(int) * cstart.size(), cudaMemcpyHostToDevice,
                            s));
-        int ctr[4] = {0, (int)ready.size(), 0, 0};
-        CU(cudaMemcpyAsync(ctx->q_ctr.ptr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ctx->q_class.ptr, cls_buf.data(), sizeof(int) * cls_buf.size(), cudaMemcpyHostToDevice, s));
+        // counters: heads, tails, done, claimed
+        std::vector<int> ctr(2 * kQueueClasses + 2, 0);
+        for (int c = 0; c < kQueueClasses; ++c) ctr[kQueueClasses + c] = class_tail[c];
+        CU(cudaMemcpyAsync(ctx->q_ctr.ptr, ctr.data(), sizeof(int) * ctr.size(), cudaMemcpyHostToDevice, s));
         p.queue.head = ctx->q_ctr.as<int>();
-        p.queue.tail = ctx->q_ctr.as<int>() + 1;
-        p.queue.done = ctx->q_ctr.as<int>() + 2;
+        p.queue.tail = ctx->q_ctr.as<int>() + kQueueClasses;
+        p.queue.done = ctx->q_ctr.as<int>() + 2 * kQueueClasses;
+        p.queue.claimed = ctx->q_ctr.as<int>() + 2 * kQueueClasses + 1;
+        p.queue.op_class = ctx->q_class.as<int>();
+        p.queue.class_off = ctx->q_class.as<int>() + n_ops;
         p.queue.slots = ctx->q_slots.as<int>();
         p.queue.pending = ctx->q_pending.as<int>();
         p.queue.consumers = ctx->q_cons.as<int>();

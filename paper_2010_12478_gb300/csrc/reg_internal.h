@@ -77,15 +77,21 @@ struct Config {
     int metric;   // nonrigid scalar product: REG_METRIC_MEAN or REG_METRIC_GAUSS_NEWTON
 };
 
-// Ready-queue state of the persistent executor (device memory).
+// Ready-queue state of the persistent executor (device memory): one FIFO per priority class,
+// class 0 first.  An operator's class is its rank by bottom level (the longest estimated path
+// from it to the end of the DAG), so operators on long chains start before ones with slack.
+constexpr int kQueueClasses = 16;
 struct Queue {
-    int *head;         // next slot to claim
-    int *tail;         // next slot to fill
-    int *slots;        // op indices in ready order, -1 = not yet filled
+    int *head;         // [kQueueClasses] next slot to claim in each class
+    int *tail;         // [kQueueClasses] next slot to fill in each class
+    int *slots;        // class c at slots[class_off[c] ...]: op indices in ready order, -1 = not yet filled
+    const int *op_class;   // per op: its class
+    const int *class_off;  // [kQueueClasses] first slot of each class
     int *pending;      // per op: inputs not yet produced
     int *consumers;    // CSR list of ops consuming each node
     int *cons_start;   // [n_nodes + 1]
     int *done;         // number of finished ops
+    int *claimed;      // number of claimed ops, all classes
     long long timeout_ns;
 };
 

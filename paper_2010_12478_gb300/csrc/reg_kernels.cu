@@ -375,20 +375,22 @@ template <typename S, bool DERIV>
 __device__ __forceinline__ float sample_q(const S *T, int W, int H, int Tp, int xi, int yi, float vx, float vy,
                                           float &dtx, float &dty)
 {
-    vx = fminf(fmaxf(vx, -1.0e6f), 1.0e6f);   // also maps NaN into range: every access stays in bounds
-    vy = fminf(fmaxf(vy, -1.0e6f), 1.0e6f);
-    const float flx = floorf(vx), fly = floorf(vy);
-    float tx = vx - flx, ty = vy - fly;   // [0, 1), exact
-    int nx = xi + (int)flx, ny = yi + (int)fly;
-    if (tx >= 0.5f) { tx -= 1.f; ++nx; }  // nearest sample, t in [-1/2, 1/2), exact
-    if (ty >= 0.5f) { ty -= 1.f; ++ny; }
+    // nearest sample n = floor(v + 1/2), t = v - n: within rounding of [-1/2, 1/2) (at a tie either
+    // window gives the same value and derivative, the model being C1).  A NaN or huge offset
+    // converts to 0 or a saturated integer, the sum wraps, and the clamp keeps the window inside
+    // the border whatever the offset.
+    const float fnx = floorf(vx + 0.5f), fny = floorf(vy + 0.5f);
+    const float tx = vx - fnx, ty = vy - fny;
+    int nx = (int)((unsigned)xi + (unsigned)__float2int_rz(fnx));
+    int ny = (int)((unsigned)yi + (unsigned)__float2int_rz(fny));
     nx = min(max(nx, -2), W + 1);
     ny = min(max(ny, -2), H + 1);
     const S *p0 = T + (ptrdiff_t)(ny - 1) * Tp + nx;
     const S *p1 = p0 + Tp, *p2 = p1 + Tp;
-    const float ax = 0.5f - tx, bx = 0.5f + tx, ay = 0.5f - ty, by = 0.5f + ty;
-    const float wx0 = 0.5f * ax * ax, wx1 = fmaf(-tx, tx, 0.75f), wx2 = 0.5f * bx * bx;
-    const float wy0 = 0.5f * ay * ay, wy1 = fmaf(-ty, ty, 0.75f), wy2 = 0.5f * by * by;
+    // weights (1/2 - t)^2 / 2, 3/4 - t^2, (1/2 + t)^2 / 2; the last is the first plus t
+    const float ax = 0.5f - tx, ay = 0.5f - ty;
+    const float wx0 = (0.5f * ax) * ax, wx1 = fmaf(-tx, tx, 0.75f), wx2 = wx0 + tx;
+    const float wy0 = (0.5f * ay) * ay, wy1 = fmaf(-ty, ty, 0.75f), wy2 = wy0 + ty;
     const float t00 = ldS<S>(p0 - 1), t01 = ldS<S>(p0), t02 = ldS<S>(p0 + 1);
     const float t10 = ldS<S>(p1 - 1), t11 = ldS<S>(p1), t12 = ldS<S>(p1 + 1);
     const float t20 = ldS<S>(p2 - 1), t21 = ldS<S>(p2), t22 = ldS<S>(p2 + 1);
@@ -396,12 +398,13 @@ __device__ __forceinline__ float sample_q(const S *T, int W, int H, int Tp, int 
     const float a1 = fmaf(wx2, t12, fmaf(wx1, t11, wx0 * t10));
     const float a2 = fmaf(wx2, t22, fmaf(wx1, t21, wx0 * t20));
     if (DERIV) {
-        const float m2x = -2.f * tx;
+        // derivative weights t - 1/2, -2 t, t + 1/2
+        const float m2x = -2.f * tx, bx = 0.5f + tx;
         const float b0 = fmaf(bx, t02, fmaf(m2x, t01, -ax * t00));
         const float b1 = fmaf(bx, t12, fmaf(m2x, t11, -ax * t10));
         const float b2 = fmaf(bx, t22, fmaf(m2x, t21, -ax * t20));
         dtx = fmaf(wy2, b2, fmaf(wy1, b1, wy0 * b0));
-        dty = fmaf(by, a2, fmaf(-2.f * ty, a1, -ay * a0));
+        dty = fmaf(0.5f + ty, a2, fmaf(-2.f * ty, a1, -ay * a0));
     }
     return fmaf(wy2, a2, fmaf(wy1, a1, wy0 * a0));
 }
@@ -1500,30 +1503,60 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
     const bool leader = cl.block_rank() == 0 && threadIdx.x == 0;
     for (;;) {
         if (leader) {
-            int slot = atomicAdd(p.queue.head, 1);
-            int op = -1;
-            if (slot < p.n_ops) {
-                volatile int *vs = p.queue.slots;
-                long long t0 = (long long)clock64();
-                unsigned long long start;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(start));
-                unsigned ns = 64;
-                for (;;) {
-                    op = vs[slot];
-                    if (op >= 0) break;
-                    unsigned long long now;
-                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-                    if ((long long)(now - start) > p.queue.timeout_ns || *((volatile int *)p.status) != 0) {
-                        atomicCAS(p.status, 0, (int)kDevQueueTimeout);
-                        op = -2;
-                        break;
+            // claim the first ready operator of the most urgent non-empty class; every operator
+            // claimed (all classes): leave.  Waiting for work gives up after queue.timeout_ns
+            // without any operator finishing; the wait for a claimed slot's writer is bounded too.
+            const Queue &Q = p.queue;
+            volatile int *vh = Q.head, *vt = Q.tail, *vs = Q.slots, *vc = Q.claimed, *vd = Q.done;
+            unsigned long long start;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(start));
+            unsigned ns = 64;
+            int op = -1, seen = *vd;
+            for (;;) {
+                if (*vc >= p.n_ops) break;
+                // every class's head and tail in one round of loads, then the first non-empty class
+                int hs[kQueueClasses], ts[kQueueClasses];
+#pragma unroll
+                for (int c = 0; c < kQueueClasses; ++c) hs[c] = vh[c];
+#pragma unroll
+                for (int c = 0; c < kQueueClasses; ++c) ts[c] = vt[c];
+                int slot = -1;
+                bool raced = false;
+#pragma unroll
+                for (int c = 0; c < kQueueClasses; ++c)
+                    if (slot < 0 && !raced && hs[c] < ts[c]) {
+                        if (atomicCAS(Q.head + c, hs[c], hs[c] + 1) == hs[c]) slot = Q.class_off[c] + hs[c];
+                        else raced = true;   // another cluster took it: look again at once
                     }
-                    __nanosleep(ns);
-                    if (ns < 1024) ns *= 2;
+                if (raced) continue;
+                if (slot >= 0) {
+                    atomicAdd(Q.claimed, 1);
+                    // the releaser bumps the tail before it writes the slot
+                    while ((op = vs[slot]) < 0) {
+                        unsigned long long now;
+                        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                        if ((long long)(now - start) > Q.timeout_ns || *((volatile int *)p.status) != 0) {
+                            atomicCAS(p.status, 0, (int)kDevQueueTimeout);
+                            op = -2;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    break;
                 }
-                (void)t0;
-                __threadfence();
+                unsigned long long now;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                const int d = *vd;
+                if (d != seen) { seen = d; start = now; }   // progress: the wait starts again
+                if ((long long)(now - start) > Q.timeout_ns || *((volatile int *)p.status) != 0) {
+                    atomicCAS(p.status, 0, (int)kDevQueueTimeout);
+                    op = -2;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns *= 2;
             }
+            __threadfence();
             sm.idata[1] = op;
         }
         cl.sync();
@@ -1534,8 +1567,8 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
         cl.sync();
         if (cl.block_rank() == 0) {
             // publish the produced node and release its consumers, spread over the CTA's threads (a
-            // node of a Ladner-Fischer scan has up to n/2 consumers); each warp claims the queue
-            // slots of the consumers it made ready with one atomic on the tail
+            // node of a Ladner-Fischer scan has up to n/2 consumers); the lanes of a warp that make
+            // consumers of one class ready claim their slots with one atomic on that class's tail
             __threadfence();   // the cluster's writes of the node, seen through cl.sync, go first
             const int node = p.ops[op].out;
             const int cb = p.queue.cons_start[node], ce = p.queue.cons_start[node + 1];
@@ -1548,13 +1581,17 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
                     c = p.queue.consumers[e];
                     ready = atomicSub(p.queue.pending + c, 1) == 1;
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, ready);
-                if (m) {
-                    const int first = __ffs(m) - 1;
-                    int t0 = 0;
-                    if (lane == first) t0 = atomicAdd(p.queue.tail, __popc(m));
-                    t0 = __shfl_sync(0xffffffffu, t0, first);
-                    if (ready) atomicExch(p.queue.slots + t0 + __popc(m & ((1u << lane) - 1)), c);
+                if (__ballot_sync(0xffffffffu, ready)) {
+                    // lanes releasing into the same class take consecutive slots of it
+                    const int cls = ready ? p.queue.op_class[c] : -1;
+                    const unsigned grp = __match_any_sync(0xffffffffu, cls);
+                    if (ready) {
+                        const int first = __ffs(grp) - 1;
+                        int t0 = 0;
+                        if (lane == first) t0 = atomicAdd(p.queue.tail + cls, __popc(grp));
+                        t0 = __shfl_sync(grp, t0, first);
+                        atomicExch(p.queue.slots + p.queue.class_off[cls] + t0 + __popc(grp & ((1u << lane) - 1)), c);
+                    }
                 }
             }
             if (threadIdx.x == 0) atomicAdd(p.queue.done, 1);
