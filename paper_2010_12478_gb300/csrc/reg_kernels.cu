@@ -900,29 +900,39 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     cluster_reduce<NM, false>(hi, lo, sm, buf, cl, false);
 }
 
-// Sum eight per-lane values over the warp by halving exchanges: on return every lane holds the
-// total of value index 4 b4 + 2 b3 + b2 (b_k = bit k of the lane), the same in the four lanes
-// that share those bits.  9 shuffles instead of 40; fixed order, so deterministic.
-__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane)
+// Sum eight per-lane values over aligned segments of S lanes (S = 8, 16 or 32) by halving
+// exchanges: on return every lane holds its segment's total of value index 4 B1 + 2 B2 + B3, where
+// B1, B2, B3 are the lane's bits at S/2, S/4 and S/8 (the same in the S/8 lanes sharing them).
+// 2 log2(S) + 1 shuffles for S = 32 instead of 40; fixed order, so deterministic.
+template <int S>
+__device__ __forceinline__ float seg_reduce_scatter8(const float (&v)[8], int lane)
 {
-    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+    constexpr int o1 = S / 2, o2 = S / 4, o3 = S / 8;
+    const bool b1 = lane & o1, b2 = lane & o2, b3 = lane & o3;
     float a4[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float send = b4 ? v[k] : v[k + 4], keep = b4 ? v[k + 4] : v[k];
-        a4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        const float send = b1 ? v[k] : v[k + 4], keep = b1 ? v[k + 4] : v[k];
+        a4[k] = keep + __shfl_xor_sync(0xffffffffu, send, o1);
     }
     float a2[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const float send = b3 ? a4[k] : a4[k + 2], keep = b3 ? a4[k + 2] : a4[k];
-        a2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        const float send = b2 ? a4[k] : a4[k + 2], keep = b2 ? a4[k + 2] : a4[k];
+        a2[k] = keep + __shfl_xor_sync(0xffffffffu, send, o2);
     }
-    const float send = b2 ? a2[0] : a2[1], keep = b2 ? a2[1] : a2[0];
-    float t = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    const float send = b3 ? a2[0] : a2[1], keep = b3 ? a2[1] : a2[0];
+    float t = keep + __shfl_xor_sync(0xffffffffu, send, o3);
+#pragma unroll
+    for (int o = o3 / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     return t;
+}
+
+// Value index a lane holds after seg_reduce_scatter8<S>, and whether it is the segment's writer.
+template <int S>
+__device__ __forceinline__ int seg_index8(int lane)
+{
+    return ((lane & (S / 2)) ? 4 : 0) + ((lane & (S / 4)) ? 2 : 0) + ((lane & (S / 8)) ? 1 : 0);
 }
 
 // Gradient pass at c: this CTA's cells in four parity phases (no two cells of a phase share a
@@ -952,6 +962,8 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     // fast path: cell width a power of two dividing 32, spacing a power of two
     const bool pow2 = sl >= 1 && sl <= 32 && (sl & (sl - 1)) == 0 && (sl << GL.l) == G.s;
     const float dwy = (float)(32 >> lg) * GL.pl * GL.scale_inv;   // weight step between a lane's rows
+    // cells of width 16 or 8: G = 32 / sl cells per warp (below)
+    const int grp = (pow2 && (sl == 16 || sl == 8)) ? 32 / sl : 1;
     float *gpf = (float *)gp;   // band-local: control row cr0 + i at gp[i nx .. (i + 1) nx)
     for (int j = tid; j < (cr1 - cr0 + 1) * G.nx; j += kThreads) gp[j] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -960,9 +972,68 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
         const int first_row = cr0 + ((py - cr0) % 2 + 2) % 2;
         const int rows = first_row < cr1 ? (cr1 - first_row + 1) / 2 : 0;
         const int cols = (ncx - px + 1) / 2;
-        const int ncell = rows * cols;
-        for (int q = warp; q < ncell; q += kWarps) {
-            const int cyy = first_row + 2 * (q / cols), cxx = px + 2 * (q % cols);
+        // cells taken G at a time by a warp (all but a last column narrower than sl), then the rest
+        // one per warp
+        const bool has_last = ncx - 1 - px >= 0 && ((ncx - 1 - px) & 1) == 0;
+        const int gcols = grp > 1 ? cols - ((has_last && L.W - (ncx - 1) * sl != sl) ? 1 : 0) : 0;
+        const int gpr = (gcols + grp - 1) / grp;   // groups per phase row
+        const int ngroup = rows * gpr, rc = cols - gcols;
+        for (int q = warp; q < ngroup + rows * rc; q += kWarps) {
+            if (q < ngroup) {
+                // lane: column lane mod sl of cell k = lane / sl of the group, through all its rows;
+                // weights and x-interpolated control values as in the single-cell form below
+                const int ri = q / gpr, ci = (q - ri * gpr) * grp + (lane >> lg);
+                const bool valid = ci < gcols;
+                const int cyy = first_row + 2 * ri, cxx = px + 2 * min(ci, gcols - 1);
+                const int x = cxx * sl + (lane & (sl - 1));
+                const int y0 = cyy * sl, y1 = (cyy == ncy - 1) ? L.H : min(L.H, y0 + sl);
+                const int j0 = cyy * G.nx + cxx;
+                const float2 c00 = c[j0], c01 = c[j0 + 1], c10 = c[j0 + G.nx], c11 = c[j0 + G.nx + 1];
+                const float wx = fminf(fmaf(GL.pl, (float)x, GL.off) * GL.scale_inv, (float)(G.nx - 1)) - (float)cxx;
+                const float tx = fmaf(wx, c01.x - c00.x, c00.x), ty = fmaf(wx, c01.y - c00.y, c00.y);
+                const float bx = fmaf(wx, c11.x - c10.x, c10.x), by = fmaf(wx, c11.y - c10.y, c10.y);
+                const float ex = bx - tx, ey = by - ty;
+                const float wmax = (float)(G.ny - 1 - cyy), dw1 = GL.pl * GL.scale_inv;
+                float wyk = GL.off * GL.scale_inv;   // g(y0) - cyy, exact
+                float st_x = 0.f, st_y = 0.f, sb_x = 0.f, sb_y = 0.f;
+#pragma unroll 4
+                for (int y = y0; y < y1; ++y) {
+                    const float wy = fminf(wyk, wmax);
+                    wyk += dw1;
+                    float dtx, dty;
+                    const float tw = sample_q<S, true>(T, L.W, L.H, L.Tp, x, y, fmaf(wy, ex, tx), fmaf(wy, ey, ty),
+                                                       dtx, dty);
+                    const float hy = 1.f - wy;
+                    if constexpr (METRIC) {
+                        (void)tw;
+                        const float gx = dtx * dtx, gy = dty * dty, hy2 = hy * hy, wy2 = wy * wy;
+                        st_x = fmaf(hy2, gx, st_x); st_y = fmaf(hy2, gy, st_y);
+                        sb_x = fmaf(wy2, gx, sb_x); sb_y = fmaf(wy2, gy, sb_y);
+                    } else {
+                        const float rv = ldS<S>(R + (size_t)y * L.Rp + x) - L.cR;
+                        const float tv = tw - L.cR;
+                        const float F = -__fsub_rn(__fmul_rn(aP, rv - rb), __fmul_rn(bP, tv - tb));
+                        const float gx = F * dtx, gy = F * dty;
+                        st_x = fmaf(hy, gx, st_x); st_y = fmaf(hy, gy, st_y);
+                        sb_x = fmaf(wy, gx, sb_x); sb_y = fmaf(wy, gy, sb_y);
+                    }
+                }
+                const float hx = METRIC ? (1.f - wx) * (1.f - wx) : 1.f - wx, vx = METRIC ? wx * wx : wx;
+                const float m = valid ? 1.f : 0.f;
+                float acc[8] = {m * hx * st_x, m * hx * st_y, m * vx * st_x, m * vx * st_y,
+                                m * hx * sb_x, m * hx * sb_y, m * vx * sb_x, m * vx * sb_y};
+                const float tot = sl == 16 ? seg_reduce_scatter8<16>(acc, lane) : seg_reduce_scatter8<8>(acc, lane);
+                const bool writer = sl == 16 ? (lane & 1) == 0 : true;
+                if (valid && writer) {
+                    const int vi = sl == 16 ? seg_index8<16>(lane) : seg_index8<8>(lane);
+                    const int corner = vi >> 1;
+                    const int jc = (cyy + (corner >> 1) - cr0) * G.nx + cxx + (corner & 1);
+                    gpf[2 * jc + (vi & 1)] += tot;
+                }
+                continue;
+            }
+            const int r = q - ngroup;
+            const int cyy = first_row + 2 * (r / rc), cxx = px + 2 * (gcols + r % rc);
             const int x0 = cxx * sl, x1 = (cxx == ncx - 1) ? L.W : min(L.W, x0 + sl);
             const int y0 = cyy * sl, y1 = (cyy == ncy - 1) ? L.H : min(L.H, y0 + sl);
             const int w = x1 - x0, npx = w * (y1 - y0);
@@ -1046,9 +1117,9 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
                 acc[4] = fmaf(w10, gx, acc[4]); acc[5] = fmaf(w10, gy, acc[5]);
                 acc[6] = fmaf(w11, gx, acc[6]); acc[7] = fmaf(w11, gy, acc[7]);
             }
-            const float tot8 = warp_reduce_scatter8(acc, lane);
+            const float tot8 = seg_reduce_scatter8<32>(acc, lane);
             if ((lane & 3) == 0) {
-                const int vi = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                const int vi = seg_index8<32>(lane);
                 const int corner = vi >> 1;
                 const int jc = (cyy + (corner >> 1) - cr0) * G.nx + cxx + (corner & 1);
                 gpf[2 * jc + (vi & 1)] += tot8;
