@@ -728,8 +728,8 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
 // (finest-level pixels), points (jx s, jy s).  At level l a pixel x sits at
 // finest coordinate X = 2^l x + (2^l - 1)/2, and the level works on c in its
 // own pixels (c / 2^l).  Every CTA of the cluster holds the whole grid in
-// shared memory: c (current), d (descent direction), ct (trial values) and gp
-// (this CTA's partial gradient).
+// shared memory: c (current), d (descent direction), mt (scalar product) and gp
+// (this CTA's partial gradient); a trial's values c + tau d are formed where read.
 
 struct Grid {
     int nx, ny, s;   // points per axis, spacing in finest pixels
@@ -774,13 +774,13 @@ __host__ __device__ __forceinline__ int grid_band_elems(int gnx, int gny, int C)
     return ((gny - 1 + C - 1) / C + 1) * gnx;
 }
 
-// Dynamic shared memory of the nonrigid kernels, in float2 units: c, d, ct, mt (whole grid each;
-// mt the flow's scalar product per control point and axis), the band of partial gradients, then
+// Dynamic shared memory of the nonrigid kernels, in float2 units: c, d, mt (whole grid each; mt the
+// flow's scalar product per control point and axis), the band of partial gradients, then
 // (16-byte aligned) one row of gnx - 1 float4 per warp: the control values of the warp's pixel row
 // interpolated along y, (u_j, u_{j+1} - u_j).
 __host__ __device__ __forceinline__ int grid_crow_offset(int gnx, int gny, int C)
 {
-    const int o = 4 * gnx * gny + grid_band_elems(gnx, gny, C);
+    const int o = 3 * gnx * gny + grid_band_elems(gnx, gny, C);
     return o + (o & 1);
 }
 
@@ -797,14 +797,26 @@ __device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int r
     if (cr0 == cr1) r0 = r1 = L.H;
 }
 
-// Energy moments of the field ct: slots 0 St, 1 Stt, 2 Srt, with RSTAT (first pass of a level)
-// 3 Sr, 4 Srr; slot 5 = sum over control edges |dct|^2 (rank 0 only, so the cluster sum counts
-// it once).  Each warp first interpolates the control values of its row along y into crow
-// (u_j and u_{j+1} - u_j for the nx - 1 cells), so a pixel only interpolates along x.
-template <typename S, bool RSTAT, int U>
-__device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *ct, float4 *crow_all,
-                                 int r0, int r1, Smem &sm, int &buf, const cg::cluster_group &cl)
+// Energy moments of the field ct = c + tau d (TRIAL; else ct = c): slots 0 St, 1 Stt, 2 Srt, with
+// RSTAT (first pass of a level) 3 Sr, 4 Srr; slot 5 = sum over control edges |dct|^2 (rank 0 only,
+// so the cluster sum counts it once).  Each warp first interpolates the control values of its row
+// along y into crow (u_j and u_{j+1} - u_j for the nx - 1 cells), so a pixel only interpolates
+// along x.  The trial values are formed where they are read, fmaf(tau, d_j, c_j), the expression
+// an accepted step stores into c.
+template <typename S, bool RSTAT, int U, bool TRIAL>
+__device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *c, const float2 *d,
+                                 float tau, float4 *crow_all, int r0, int r1, Smem &sm, int &buf,
+                                 const cg::cluster_group &cl)
 {
+    auto ct = [&](int j) {
+        const float2 a = c[j];
+        if constexpr (TRIAL) {
+            const float2 b = d[j];
+            return make_float2(fmaf(tau, b.x, a.x), fmaf(tau, b.y, a.y));
+        } else {
+            return a;
+        }
+    };
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     constexpr int NM = 6;
     float hi[NM], lo[NM], a[NM];
@@ -821,8 +833,8 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
         const float wy = gyf - (float)iy, hy = 1.f - wy;
         __syncwarp();
         for (int j = lane; j < G.nx - 1; j += 32) {
-            const float2 a0 = ct[iy * G.nx + j], a1 = ct[(iy + 1) * G.nx + j];
-            const float2 b0 = ct[iy * G.nx + j + 1], b1 = ct[(iy + 1) * G.nx + j + 1];
+            const float2 a0 = ct(iy * G.nx + j), a1 = ct((iy + 1) * G.nx + j);
+            const float2 b0 = ct(iy * G.nx + j + 1), b1 = ct((iy + 1) * G.nx + j + 1);
             const float ux0 = fmaf(wy, a1.x, hy * a0.x), uy0 = fmaf(wy, a1.y, hy * a0.y);
             const float ux1 = fmaf(wy, b1.x, hy * b0.x), uy1 = fmaf(wy, b1.y, hy * b0.y);
             crow[j] = make_float4(ux0, uy0, ux1 - ux0, uy1 - uy0);
@@ -884,13 +896,13 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
         int k = 0;
         for (int j = threadIdx.x; j < Nc; j += kThreads) {
             const int jx = j % G.nx;
-            const float2 v = ct[j];
+            const float2 v = ct(j);
             if (jx + 1 < G.nx) {
-                const float2 w = ct[j + 1];
+                const float2 w = ct(j + 1);
                 e = fmaf(w.x - v.x, w.x - v.x, fmaf(w.y - v.y, w.y - v.y, e));
             }
             if (j + G.nx < Nc) {
-                const float2 w = ct[j + G.nx];
+                const float2 w = ct(j + G.nx);
                 e = fmaf(w.x - v.x, w.x - v.x, fmaf(w.y - v.y, w.y - v.y, e));
             }
             if (++k == kFast) { ff_acc(hi[5], lo[5], e); e = 0.f; k = 0; }
@@ -1375,7 +1387,7 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
     const int Lc = cfg.levels;
     const Grid G{p.gnx, p.gny, p.gs};
     const int Nc = G.nx * G.ny;
-    float2 *c = gbuf, *d = gbuf + Nc, *ct = gbuf + 2 * Nc, *mt = gbuf + 3 * Nc, *gp = gbuf + 4 * Nc;
+    float2 *c = gbuf, *d = gbuf + Nc, *mt = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
     float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, C));
     int buf = 0;
     // initial control values (finest px), scaled to the coarsest level
@@ -1434,14 +1446,9 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
 #pragma unroll
             for (int q = 0; q < 5; ++q) pm[q] = sm.pm[q];
             if (act == kActEnergy) {
-                grid_energy_pass<S, true, U>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
+                grid_energy_pass<S, true, U, false>(L, G, GL, c, d, 0.f, crow, r0, r1, sm, buf, cl);
             } else if (act == kActTrial) {
-                for (int j = tid; j < Nc; j += kThreads) {
-                    const float2 a = c[j], b = d[j];
-                    ct[j] = make_float2(fmaf(pm[0], b.x, a.x), fmaf(pm[0], b.y, a.y));
-                }
-                __syncthreads();
-                grid_energy_pass<S, false, U>(L, G, GL, ct, crow, r0, r1, sm, buf, cl);
+                grid_energy_pass<S, false, U, true>(L, G, GL, c, d, pm[0], crow, r0, r1, sm, buf, cl);
             } else if (act == kActMetric) {
                 grid_grad_pass<S, true>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
             } else {
@@ -1454,7 +1461,11 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
             }
             __syncthreads();
             if (sm.idata[0]) {
-                for (int j = tid; j < Nc; j += kThreads) c[j] = ct[j];
+                // the accepted trial: c + tau d with the trial's tau, as the trial pass formed it
+                for (int j = tid; j < Nc; j += kThreads) {
+                    const float2 a = c[j], b = d[j];
+                    c[j] = make_float2(fmaf(pm[0], b.x, a.x), fmaf(pm[0], b.y, a.y));
+                }
                 __syncthreads();
                 if (tid == 0) { sm.idata[0] = 0; k.tau_pend = 0.0; }
             }
@@ -1706,7 +1717,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
     } else {
         const Grid G{p.gnx, p.gny, p.gs};
         const int Nc = G.nx * G.ny;
-        float2 *c = gbuf, *d = gbuf + Nc, *mt = gbuf + 3 * Nc, *gp = gbuf + 4 * Nc;
+        float2 *c = gbuf, *d = gbuf + Nc, *mt = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
         float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, 1));
         for (int j = tid; j < Nc; j += kThreads) { c[j] = cgrid[j]; mt[j] = make_float2(1.f, 1.f); }
         __syncthreads();
@@ -1714,7 +1725,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
         GL.W = L.W; GL.H = L.H; GL.l = 0; GL.pl = 1.f; GL.off = 0.f; GL.scale_inv = 1.f / (float)G.s;
         int cr0, cr1, r0, r1;
         grid_rows(G, GL, 0, 1, cr0, cr1, r0, r1);
-        grid_energy_pass<S, true, 4>(L, G, GL, c, crow, r0, r1, sm, buf, cl);
+        grid_energy_pass<S, true, 4, false>(L, G, GL, c, c, 0.f, crow, r0, r1, sm, buf, cl);
         FieldCtl &k = sm.fctl;
         if (tid == 0) {
             memset(&k, 0, sizeof(k));
