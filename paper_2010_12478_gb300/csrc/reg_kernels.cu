@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "reg_internal.h"
+#include "reg_f2.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -313,6 +314,35 @@ __device__ __forceinline__ void for_rows(int W, int r0, int r1, RowF &&row, PixF
     flush();
 }
 
+// for_rows with the pixels of a step taken in pairs: px2(r, c, c + 32) for columns 32 apart (U
+// even); a row's partial last step goes pixel by pixel through px(r, c).
+template <int U, typename RowF, typename Pix2F, typename PixF, typename Q, typename G>
+__device__ __forceinline__ void for_rows2(int W, int r0, int r1, RowF &&row, Pix2F &&px2, PixF &&px, Q &&flush_fast,
+                                          G &&flush)
+{
+    static_assert(kFast % U == 0 && U % 2 == 0, "U even, dividing kFast");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cnt = 0;
+    for (int r = r0 + warp; r < r1; r += kWarps) {
+        row(r);
+        for (int c0 = lane; c0 < W; c0 += 32 * U) {
+            if (c0 + 32 * (U - 1) < W) {
+#pragma unroll
+                for (int u = 0; u < U; u += 2) px2(r, c0 + 32 * u, c0 + 32 * u + 32);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (c0 + 32 * u < W) px(r, c0 + 32 * u);
+            }
+            cnt += U;
+            if ((cnt & (kFast - 1)) == 0) flush_fast();
+            if ((cnt & (kChunk - 1)) == 0) flush();
+        }
+    }
+    flush_fast();
+    flush();
+}
+
 // Bilinear sample of T (storage S, pitch Tp) at p = (xi + vx, yi + vy) with clamp-to-edge,
 // where (xi, yi) is an integer pixel and (vx, vy) a small FP32 offset.  Splitting the
 // position keeps the FP32 fractional part exact to the precision of the offset, not
@@ -407,6 +437,50 @@ __device__ __forceinline__ float sample_q(const S *T, int W, int H, int Tp, int 
         dty = fmaf(0.5f + ty, a2, fmaf(-2.f * ty, a1, -ay * a0));
     }
     return fmaf(wy2, a2, fmaf(wy1, a1, wy0 * a0));
+}
+
+// Two samples of the model at once, pixel a in the .x and pixel b in the .y of every float2: the
+// steps of sample_q with each floating-point operation done on both in one packed FP32x2
+// instruction (each lane rounded as the scalar operation, so the values equal two sample_q calls).
+template <typename S, bool DERIV>
+__device__ __forceinline__ float2 sample_q2(const S *T, int W, int H, int Tp, int2 xi, int2 yi, float2 vx, float2 vy,
+                                            float2 &dtx, float2 &dty)
+{
+    const float2 h = make_float2(0.5f, 0.5f);
+    const float2 px = __fadd2_rn(vx, h), py = __fadd2_rn(vy, h);
+    const float2 fnx = make_float2(floorf(px.x), floorf(px.y)), fny = make_float2(floorf(py.x), floorf(py.y));
+    const float2 tx = __fadd2_rn(vx, make_float2(-fnx.x, -fnx.y)), ty = __fadd2_rn(vy, make_float2(-fny.x, -fny.y));
+    const int nxa = min(max((int)((unsigned)xi.x + (unsigned)__float2int_rz(fnx.x)), -2), W + 1);
+    const int nxb = min(max((int)((unsigned)xi.y + (unsigned)__float2int_rz(fnx.y)), -2), W + 1);
+    const int nya = min(max((int)((unsigned)yi.x + (unsigned)__float2int_rz(fny.x)), -2), H + 1);
+    const int nyb = min(max((int)((unsigned)yi.y + (unsigned)__float2int_rz(fny.y)), -2), H + 1);
+    const S *pa = T + (ptrdiff_t)(nya - 1) * Tp + nxa, *pb = T + (ptrdiff_t)(nyb - 1) * Tp + nxb;
+    const float2 ax = __fadd2_rn(h, make_float2(-tx.x, -tx.y)), ay = __fadd2_rn(h, make_float2(-ty.x, -ty.y));
+    const float2 wx0 = __fmul2_rn(__fmul2_rn(h, ax), ax), wy0 = __fmul2_rn(__fmul2_rn(h, ay), ay);
+    const float2 q34 = make_float2(0.75f, 0.75f);
+    const float2 wx1 = __ffma2_rn(make_float2(-tx.x, -tx.y), tx, q34), wy1 = __ffma2_rn(make_float2(-ty.x, -ty.y), ty, q34);
+    const float2 wx2 = __fadd2_rn(wx0, tx), wy2 = __fadd2_rn(wy0, ty);
+    float2 tr[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tr[r][k] = make_float2(ldS<S>(pa + r * Tp + k - 1), ldS<S>(pb + r * Tp + k - 1));
+    float2 a[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) a[r] = __ffma2_rn(wx2, tr[r][2], __ffma2_rn(wx1, tr[r][1], __fmul2_rn(wx0, tr[r][0])));
+    if (DERIV) {
+        // derivative weights t - 1/2, -2 t, t + 1/2
+        const float2 m2 = make_float2(-2.f, -2.f);
+        const float2 nax = make_float2(-ax.x, -ax.y), bx = __fadd2_rn(h, tx);
+        float2 b[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            b[r] = __ffma2_rn(bx, tr[r][2], __ffma2_rn(__fmul2_rn(m2, tx), tr[r][1], __fmul2_rn(nax, tr[r][0])));
+        dtx = __ffma2_rn(wy2, b[2], __ffma2_rn(wy1, b[1], __fmul2_rn(wy0, b[0])));
+        dty = __ffma2_rn(__fadd2_rn(h, ty), a[2], __ffma2_rn(__fmul2_rn(m2, ty), a[1],
+                                                                 __fmul2_rn(make_float2(-ay.x, -ay.y), a[0])));
+    }
+    return __ffma2_rn(wy2, a[2], __ffma2_rn(wy1, a[1], __fmul2_rn(wy0, a[0])));
 }
 
 // ================================================================== rigid
@@ -819,10 +893,14 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     };
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     constexpr int NM = 6;
-    float hi[NM], lo[NM], a[NM];
-    float e1 = 0.f, e2 = 0.f, e4 = 0.f;   // exact product rounding errors of slots 1, 2, 4
+    float hi[NM], lo[NM];
+    // per-lane partial sums of the current kFast pixels, in pairs (.x and .y: the two pixels of a
+    // packed step); e: the exact rounding errors of the products of slots 1, 2 and 4
+    float2 a[5], e1 = make_float2(0.f, 0.f), e2 = e1, e4 = e1;
 #pragma unroll
-    for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; a[m] = 0.f; }
+    for (int m = 0; m < NM; ++m) { hi[m] = 0.f; lo[m] = 0.f; }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) a[m] = make_float2(0.f, 0.f);
     const int lane = threadIdx.x & 31;
     float4 *crow = crow_all + (threadIdx.x >> 5) * (G.nx - 1);
     const S *Rrow = R;
@@ -841,25 +919,44 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
         }
         __syncwarp();
     };
+    const float2 ncr = make_float2(-L.cR, -L.cR);
+    // two pixels (r, ca) and (r, cb) with displacements (ux.x, uy.x) and (ux.y, uy.y)
+    auto pixel2 = [&](int r, int ca, int cb, float2 ux, float2 uy) {
+        float2 dtx, dty;
+        const float2 tw = sample_q2<S, false>(T, L.W, L.H, L.Tp, make_int2(ca, cb), make_int2(r, r), ux, uy, dtx, dty);
+        const float2 rv = __fadd2_rn(make_float2(ldS<S>(Rrow + ca), ldS<S>(Rrow + cb)), ncr);
+        const float2 tv = __fadd2_rn(tw, ncr);
+        a[0] = __fadd2_rn(a[0], tv);
+        acc_prod2(a[1], e1, tv, tv);
+        acc_prod2(a[2], e2, rv, tv);
+        if constexpr (RSTAT) {
+            a[3] = __fadd2_rn(a[3], rv);
+            acc_prod2(a[4], e4, rv, rv);
+        }
+    };
+    // one pixel (a row's ragged end), into the .x partial sums
     auto pixel = [&](int r, int c, float ux, float uy) {
         float dtx, dty;
         const float tw = sample_q<S, false>(T, L.W, L.H, L.Tp, c, r, ux, uy, dtx, dty);
         const float rv = ldS<S>(Rrow + c) - L.cR;
         const float tv = tw - L.cR;
-        a[0] += tv;
-        acc_prod(a[1], e1, tv, tv);
-        acc_prod(a[2], e2, rv, tv);
+        a[0].x += tv;
+        acc_prod(a[1].x, e1.x, tv, tv);
+        acc_prod(a[2].x, e2.x, rv, tv);
         if constexpr (RSTAT) {
-            a[3] += rv;
-            acc_prod(a[4], e4, rv, rv);
+            a[3].x += rv;
+            acc_prod(a[4].x, e4.x, rv, rv);
         }
     };
     auto flush_fast = [&]() {
 #pragma unroll
-        for (int m = 0; m < (RSTAT ? 5 : 3); ++m) { ff_acc(hi[m], lo[m], a[m]); a[m] = 0.f; }
-        lo[1] += e1; lo[2] += e2;
-        e1 = 0.f; e2 = 0.f;
-        if constexpr (RSTAT) { lo[4] += e4; e4 = 0.f; }
+        for (int m = 0; m < (RSTAT ? 5 : 3); ++m) {
+            ff_acc(hi[m], lo[m], a[m].x + a[m].y);
+            a[m] = make_float2(0.f, 0.f);
+        }
+        lo[1] += e1.x + e1.y; lo[2] += e2.x + e2.y;
+        e1 = make_float2(0.f, 0.f); e2 = e1;
+        if constexpr (RSTAT) { lo[4] += e4.x + e4.y; e4 = e1; }
     };
     // A lane's columns are 32 apart.  When the cell width sl at this level is a power of two
     // dividing 32, the spacing a power of two and no column reaches the grid's last line, every
@@ -871,21 +968,38 @@ __device__ void grid_energy_pass(const Lvl &L, const Grid &G, const GridLvl &GL,
     if (fast) {
         const int lgl = 31 - __clz(sl);
         const float wxl = fmaf(GL.pl, (float)(lane & (sl - 1)), GL.off) * GL.scale_inv;
-        for_rows<U>(
+        const float2 wxl2 = make_float2(wxl, wxl);
+        for_rows2<U>(
             L.W, r0, r1, row,
+            [&](int r, int ca, int cb) {
+                const float4 qa = crow[ca >> lgl], qb = crow[cb >> lgl];
+                pixel2(r, ca, cb, __ffma2_rn(wxl2, make_float2(qa.z, qb.z), make_float2(qa.x, qb.x)),
+                       __ffma2_rn(wxl2, make_float2(qa.w, qb.w), make_float2(qa.y, qb.y)));
+            },
             [&](int r, int c) {
                 const float4 q = crow[c >> lgl];
                 pixel(r, c, fmaf(wxl, q.z, q.x), fmaf(wxl, q.w, q.y));
             },
             flush_fast, []() {});
     } else {
-        for_rows<U>(
+        auto cellx = [&](int c, float &wx) {
+            const float gxf = fminf(fmaf(GL.pl, (float)c, GL.off) * GL.scale_inv, (float)(G.nx - 1));
+            const int ix = min((int)gxf, G.nx - 2);
+            wx = gxf - (float)ix;
+            return crow[ix];
+        };
+        for_rows2<U>(
             L.W, r0, r1, row,
+            [&](int r, int ca, int cb) {
+                float wa, wb;
+                const float4 qa = cellx(ca, wa), qb = cellx(cb, wb);
+                const float2 w2 = make_float2(wa, wb);
+                pixel2(r, ca, cb, __ffma2_rn(w2, make_float2(qa.z, qb.z), make_float2(qa.x, qb.x)),
+                       __ffma2_rn(w2, make_float2(qa.w, qb.w), make_float2(qa.y, qb.y)));
+            },
             [&](int r, int c) {
-                const float gxf = fminf(fmaf(GL.pl, (float)c, GL.off) * GL.scale_inv, (float)(G.nx - 1));
-                const int ix = min((int)gxf, G.nx - 2);
-                const float wx = gxf - (float)ix;
-                const float4 q = crow[ix];
+                float wx;
+                const float4 q = cellx(c, wx);
                 pixel(r, c, fmaf(wx, q.z, q.x), fmaf(wx, q.w, q.y));
             },
             flush_fast, []() {});
