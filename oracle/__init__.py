@@ -51,7 +51,8 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_rejects", ctypes.c_int),
                 ("tol_grad", ctypes.c_double), ("tol_rel_e", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double),
-                ("step_cap", ctypes.c_double), ("lambda_", ctypes.c_double), ("metric", ctypes.c_int)]
+                ("step_cap", ctypes.c_double), ("lambda_", ctypes.c_double), ("metric", ctypes.c_int),
+                ("sigma", ctypes.c_double)]
 
 
 class _Grid(ctypes.Structure):
@@ -101,6 +102,8 @@ def lib():
             L.or_bb_first_step.argtypes = [ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_double]
             L.or_bb_first_step.restype = ctypes.c_double
             L.or_warp_grid.argtypes = [gp, dp, dp, dp, dp]
+            L.or_h1_apply.argtypes = [gp, ctypes.c_double, dp, dp]
+            L.or_h1_inverse.argtypes = [gp, ctypes.c_double, dp, dp]
             _lib = L
     return _lib
 
@@ -130,11 +133,13 @@ class Config:
     lam: float = 2.0
     grid: int = 0                 # control-grid spacing of the nonrigid field (finest px), 0 = auto
     mode: str = "rigid"           # "rigid" (the paper's map, Sec. 2.3.1) or "nonrigid" (extension)
-    metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control points
+    metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control
+                                  # points, 2 H1 (identity + sigma^2 grid Laplacian)
+    sigma: float = 1.0            # metric 2: smoothing length in control-grid spacings
 
     def c(self) -> _Cfg:
         return _Cfg(self.levels, self.max_iter, self.max_rejects, self.tol_grad, self.tol_rel_e,
-                    self.armijo_c, self.tau0, self.step_cap, self.lam, self.metric)
+                    self.armijo_c, self.tau0, self.step_cap, self.lam, self.metric, self.sigma)
 
 
 @dataclasses.dataclass
@@ -245,6 +250,24 @@ def grid_metric(T, level: int, g: Grid, c, lam: float) -> np.ndarray:
     gc = g.c()
     lib().or_grid_metric(_dp(T), W, H, level, ctypes.byref(gc), _dp(cx), _dp(cy), lam, _dp(mx), _dp(my))
     return np.stack([mx, my])
+
+
+def h1_apply(g: Grid, sigma: float, v) -> np.ndarray:
+    """(I + sigma^2 Lg) v for a control-point field v [ny, nx], Lg the control grid's graph Laplacian."""
+    v = _f64(v)
+    out = np.zeros_like(v)
+    gc = g.c()
+    lib().or_h1_apply(ctypes.byref(gc), sigma, _dp(v), _dp(out))
+    return out
+
+
+def h1_inverse(g: Grid, sigma: float, rhs) -> np.ndarray:
+    """(I + sigma^2 Lg)^-1 rhs by banded Cholesky (the H1 flow's solve)."""
+    rhs = _f64(rhs)
+    out = np.zeros_like(rhs)
+    gc = g.c()
+    lib().or_h1_inverse(ctypes.byref(gc), sigma, _dp(rhs), _dp(out))
+    return out
 
 
 def grid_regulariser(g: Grid, c, lam: float, P: float) -> float:

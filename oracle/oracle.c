@@ -50,7 +50,9 @@ typedef struct {
     double tau0;       /* first trial step of each level */
     double step_cap;   /* largest step, in pixels of the current level */
     double lambda;     /* regulariser weight (nonrigid only) */
-    int metric;        /* nonrigid flow's scalar product: 0 mean over control points, 1 Gauss-Newton diagonal */
+    int metric;        /* nonrigid flow's scalar product: 0 mean over control points, 1 Gauss-Newton diagonal,
+                          2 H1 (identity plus sigma^2 times the control grid's Laplacian) */
+    double sigma;      /* metric 2: smoothing length in control-grid spacings */
 } or_cfg_t;
 
 typedef struct {
@@ -559,10 +561,86 @@ void or_grid_metric(const double *T, int W, int H, int l, const or_grid_t *g, co
     }
 }
 
+/* H1 scalar product on control-point fields (metric 2; Sec. 2.3.1 leaves the flow's scalar product
+ * open): <u, v> = (1/Nc) u^T M v per axis with M = I + sigma^2 Lg, Lg the Laplacian of the control
+ * grid's graph (the horizontal and vertical neighbour edges the regulariser sums over):
+ * (Lg v)_j = sum over neighbours k of j of (v_j - v_k).  The flow's direction d = -Nc M^-1 dE/dc is
+ * the gradient smoothed over about sigma grid spacings.                                          */
+void or_h1_apply(const or_grid_t *g, double sigma, const double *v, double *out)
+{
+    const double s2 = sigma * sigma;
+    for (int jy = 0; jy < g->ny; ++jy)
+        for (int jx = 0; jx < g->nx; ++jx) {
+            const int j = jy * g->nx + jx;
+            double lap = 0.0;
+            if (jx > 0) lap += v[j] - v[j - 1];
+            if (jx + 1 < g->nx) lap += v[j] - v[j + 1];
+            if (jy > 0) lap += v[j] - v[j - g->nx];
+            if (jy + 1 < g->ny) lap += v[j] - v[j + g->nx];
+            out[j] = v[j] + s2 * lap;
+        }
+}
+
+/* M = I + sigma^2 Lg as a symmetric band matrix (half-bandwidth nx, the row-major neighbour
+ * offsets 1 and nx), factored M = C C^T by Cholesky in band storage: C[i][j] at
+ * band[i (nx + 1) + j - i + nx] for i - nx <= j <= i.  M is positive definite (Lg is positive
+ * semidefinite), so every pivot is at least 1.                                                   */
+double *or_h1_factor(const or_grid_t *g, double sigma)
+{
+    const int n = g->nx * g->ny, p = g->nx, w = p + 1;
+    double *b = (double *)calloc((size_t)n * w, sizeof(double));
+    const double s2 = sigma * sigma;
+    /* lower half of M: diagonal 1 + s2 deg_j, -s2 for each neighbour below the diagonal */
+    for (int jy = 0; jy < g->ny; ++jy)
+        for (int jx = 0; jx < g->nx; ++jx) {
+            const int i = jy * g->nx + jx;
+            const int deg = (jx > 0) + (jx + 1 < g->nx) + (jy > 0) + (jy + 1 < g->ny);
+            b[(size_t)i * w + p] = 1.0 + s2 * deg;
+            if (jx > 0) b[(size_t)i * w + p - 1] = -s2;
+            if (jy > 0) b[(size_t)i * w + 0] = -s2;
+        }
+    for (int i = 0; i < n; ++i) {
+        const int j0 = i - p > 0 ? i - p : 0;
+        for (int j = j0; j <= i; ++j) {
+            double acc = b[(size_t)i * w + j - i + p];
+            const int k0 = (i - p > j - p ? i - p : j - p) > 0 ? (i - p > j - p ? i - p : j - p) : 0;
+            for (int k = k0; k < j; ++k) acc -= b[(size_t)i * w + k - i + p] * b[(size_t)j * w + k - j + p];
+            if (j == i) b[(size_t)i * w + p] = sqrt(acc);
+            else b[(size_t)i * w + j - i + p] = acc / b[(size_t)j * w + p];
+        }
+    }
+    return b;
+}
+
+/* x = M^-1 rhs with the factor of or_h1_factor: C y = rhs, then C^T x = y. */
+void or_h1_solve(const or_grid_t *g, const double *band, const double *rhs, double *x)
+{
+    const int n = g->nx * g->ny, p = g->nx, w = p + 1;
+    for (int i = 0; i < n; ++i) {
+        double acc = rhs[i];
+        for (int k = (i - p > 0 ? i - p : 0); k < i; ++k) acc -= band[(size_t)i * w + k - i + p] * x[k];
+        x[i] = acc / band[(size_t)i * w + p];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double acc = x[i];
+        for (int k = i + 1; k <= (i + p < n - 1 ? i + p : n - 1); ++k) acc -= band[(size_t)k * w + i - k + p] * x[k];
+        x[i] = acc / band[(size_t)i * w + p];
+    }
+}
+
+/* The solve by itself (for its pins): x = (I + sigma^2 Lg)^-1 rhs. */
+void or_h1_inverse(const or_grid_t *g, double sigma, const double *rhs, double *x)
+{
+    double *band = or_h1_factor(g, sigma);
+    or_h1_solve(g, band, rhs, x);
+    free(band);
+}
+
 /* One level of gradient flow for the control values (pixels of level l).
  * Metric: cfg->metric 1, the Gauss-Newton diagonal of or_grid_metric; 0, the
- * mean over control points, <v, w> = (1/Nc) sum v.w.  The descent direction is
- * d = -M^-1 dE/dc and tau |d_j| is a move in pixels.                       */
+ * mean over control points, <v, w> = (1/Nc) sum v.w; 2, the H1 product of
+ * or_h1_apply.  The descent direction is d = -M^-1 dE/dc (in the metric's
+ * 1/Nc normalisation: d = -Nc M^-1 g) and tau |d_j| is a move in pixels.   */
 static void or_grid_level(const double *R, const double *T, int W, int H, int l, const or_grid_t *g,
                           const or_cfg_t *cfg, double *cx, double *cy, or_stats_t *st)
 {
@@ -577,6 +655,11 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
     double *mw = (double *)malloc(sizeof(double) * 2 * Nc);
     double E, Et = 0.0, tau_acc = 0.0;
     int have_prev = 0;
+    /* H1: the factor of M and work arrays for M^-1 g and M applied to directions */
+    const int h1 = cfg->metric == 2;
+    double *band = h1 ? or_h1_factor(g, cfg->sigma) : NULL;
+    double *h1a = (double *)malloc(sizeof(double) * Nc), *h1b = (double *)malloc(sizeof(double) * Nc);
+    double *dpx = (double *)malloc(sizeof(double) * Nc), *dpy = (double *)malloc(sizeof(double) * Nc);
     if (cfg->metric == 1) {
         or_grid_metric(T, W, H, l, g, cx, cy, cfg->lambda, mx, my);
     } else {
@@ -590,12 +673,26 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
     for (int it = 0; it < cfg->max_iter; ++it) {
         /* d = -M^-1 grad E; ss = Nc |d|_M^2 = sum_j (m^x dx^2 + m^y dy^2); dmax = max_j |d_j| in px */
         double ss = 0.0, dmax = 0.0;
-        for (int j = 0; j < Nc; ++j) {
-            dx[j] = -(double)Nc * gx[j] / mx[j];
-            dy[j] = -(double)Nc * gy[j] / my[j];
-            double q = dx[j] * dx[j] + dy[j] * dy[j];
-            ss += mx[j] * dx[j] * dx[j] + my[j] * dy[j] * dy[j];
-            if (q > dmax) dmax = q;
+        if (h1) {
+            /* d = -Nc M^-1 g per axis, ss = d^T M d */
+            or_h1_solve(g, band, gx, dx);
+            or_h1_solve(g, band, gy, dy);
+            for (int j = 0; j < Nc; ++j) { dx[j] *= -(double)Nc; dy[j] *= -(double)Nc; }
+            or_h1_apply(g, cfg->sigma, dx, h1a);
+            or_h1_apply(g, cfg->sigma, dy, h1b);
+            for (int j = 0; j < Nc; ++j) {
+                const double q = dx[j] * dx[j] + dy[j] * dy[j];
+                ss += dx[j] * h1a[j] + dy[j] * h1b[j];
+                if (q > dmax) dmax = q;
+            }
+        } else {
+            for (int j = 0; j < Nc; ++j) {
+                dx[j] = -(double)Nc * gx[j] / mx[j];
+                dy[j] = -(double)Nc * gy[j] / my[j];
+                double q = dx[j] * dx[j] + dy[j] * dy[j];
+                ss += mx[j] * dx[j] * dx[j] + my[j] * dy[j] * dy[j];
+                if (q > dmax) dmax = q;
+            }
         }
         dmax = sqrt(dmax);
         double slope = -ss / (double)Nc;
@@ -603,7 +700,21 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
         if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
         for (int j = 0; j < Nc; ++j) { dc[2 * j] = dx[j]; dc[2 * j + 1] = dy[j]; }
         /* the metric's common factor 1/Nc cancels in the ratio */
-        if (have_prev) tau = or_bb_step(tau, tau_acc, dp, dc, mw, 2 * Nc);
+        if (have_prev && h1) {
+            /* <s, y>_M / <y, y>_M with y = d_prev - d, through M applied to y */
+            double num = 0.0, den = 0.0;
+            for (int j = 0; j < Nc; ++j) { h1a[j] = dpx[j] - dx[j]; h1b[j] = dpy[j] - dy[j]; }
+            double *ya = tx, *yb = ty;   /* trial buffers are free here */
+            or_h1_apply(g, cfg->sigma, h1a, ya);
+            or_h1_apply(g, cfg->sigma, h1b, yb);
+            for (int j = 0; j < Nc; ++j) {
+                num += dpx[j] * ya[j] + dpy[j] * yb[j];
+                den += h1a[j] * ya[j] + h1b[j] * yb[j];
+            }
+            tau = (num > 0.0 && den > 0.0) ? tau_acc * num / den : tau;
+        } else if (have_prev) {
+            tau = or_bb_step(tau, tau_acc, dp, dc, mw, 2 * Nc);
+        }
         if (tau * dmax > cfg->step_cap) tau = cfg->step_cap / dmax;
         int accepted = 0;
         for (int rej = 0; rej <= cfg->max_rejects; ++rej) {
@@ -620,6 +731,8 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
         st->iters[l] += 1;
         tau_acc = tau;
         memcpy(dp, dc, sizeof(double) * 2 * Nc);
+        memcpy(dpx, dx, sizeof(double) * Nc);
+        memcpy(dpy, dy, sizeof(double) * Nc);
         have_prev = 1;
         double Eold = E;
         tau = or_next_tau(E, slope, tau, Et, 1);
@@ -631,6 +744,7 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
     st->stop[l] = stop;
     if (l == 0) st->energy = E;
     free(gx); free(gy); free(dx); free(dy); free(tx); free(ty); free(dp); free(dc); free(mx); free(my); free(mw);
+    free(band); free(h1a); free(h1b); free(dpx); free(dpy);
 }
 
 /* Multilevel nonrigid registration on the control grid.  init (finest-level

@@ -633,3 +633,61 @@ def test_lookback_dag_prefixes_work_and_chain_depth(k):
     if k == 1:
         assert d.ops == O.dag_sequential(n).ops
     assert d.depth() <= (n - 1) // k + 2 * m + k
+
+
+# ------------------------------------------------------------------ the H1 scalar product (metric 2)
+def _graph_h1(ny, nx, sigma):
+    # M = I + sigma^2 L built from networkx's own grid graph and Laplacian (independent of the oracle)
+    nxlib = pytest.importorskip("networkx")
+    Gr = nxlib.grid_2d_graph(ny, nx)
+    nodes = [(r, c) for r in range(ny) for c in range(nx)]
+    L = nxlib.laplacian_matrix(Gr, nodelist=nodes).toarray().astype(np.float64)
+    return np.eye(ny * nx) + sigma * sigma * L
+
+
+@pytest.mark.parametrize("ny,nx,sigma", [(5, 7, 1.0), (9, 4, 2.5), (1, 6, 0.7)])
+def test_h1_apply_and_inverse_against_the_graph_laplacian(ny, nx, sigma):
+    g = O.Grid(nx, ny, 16, 16 * (nx - 1) + 1, 16 * (ny - 1) + 1)
+    rng = np.random.default_rng(ny * 100 + nx)
+    v = rng.standard_normal((ny, nx))
+    M = _graph_h1(ny, nx, sigma)
+    assert np.allclose(O.h1_apply(g, sigma, v).ravel(), M @ v.ravel(), rtol=0, atol=1e-12)
+    x = O.h1_inverse(g, sigma, v)
+    assert np.allclose(M @ x.ravel(), v.ravel(), rtol=0, atol=1e-11)
+    assert np.allclose(x.ravel(), np.linalg.solve(M, v.ravel()), rtol=0, atol=1e-11)
+
+
+def test_h1_inverse_on_the_cosine_modes_and_the_constant_field():
+    # the grid graph's Laplacian (free ends) has the eigenvectors cos(pi k (j + 1/2) / n) per axis,
+    # eigenvalues 2 - 2 cos(pi k / n): M^-1 divides such a mode by 1 + sigma^2 (lam_x + lam_y) and
+    # leaves a constant field as it is
+    ny, nx, sigma = 6, 9, 1.7
+    g = O.Grid(nx, ny, 8, 8 * (nx - 1) + 1, 8 * (ny - 1) + 1)
+    jy, jx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    for k, m in [(1, 0), (2, 3), (8, 5)]:
+        v = np.cos(np.pi * k * (jx + 0.5) / nx) * np.cos(np.pi * m * (jy + 0.5) / ny)
+        lam = (2 - 2 * math.cos(math.pi * k / nx)) + (2 - 2 * math.cos(math.pi * m / ny))
+        assert np.allclose(O.h1_inverse(g, sigma, v), v / (1 + sigma * sigma * lam), rtol=0, atol=1e-12)
+    assert np.allclose(O.h1_inverse(g, sigma, np.full((ny, nx), 0.37)), 0.37, rtol=0, atol=1e-13)
+    # sigma = 0: the identity
+    v = np.random.default_rng(5).standard_normal((ny, nx))
+    assert np.array_equal(O.h1_inverse(g, 0.0, v), v)
+
+
+def test_h1_flow_reaches_the_minimiser_of_the_other_scalar_products():
+    # the scalar product changes the path of the flow, not its stationary point: stopped on a tight
+    # gradient tolerance, the H1 flow, the mean flow and the Gauss-Newton flow land together; with
+    # sigma = 0 the H1 flow is the mean flow step for step (its step-size sums run in another order,
+    # hence rounding-level differences)
+    ser = synth.make_series(synth.SeriesSpec(2, 96, 96, step=1.0, field_amp=1.2, snr=(12, 12), seed=41))
+    F = ser.frames.numpy().astype(np.float64)
+    P0, P1 = O.pyramid(F[0], 2), O.pyramid(F[1], 2)
+    res = {}
+    for name, metric, sigma in [("mean", 0, 1.0), ("gn", 1, 1.0), ("h1", 2, 1.5), ("h1s0", 2, 0.0)]:
+        cfg = O.Config(levels=2, mode="nonrigid", metric=metric, sigma=sigma, tol_grad=1e-6)
+        res[name] = O.register_nonrigid(P0, P1, None, cfg)
+    g = O.grid_for(96, 96)
+    for name in ("gn", "h1"):
+        assert O.max_px_error(res[name][0], res["mean"][0], 96, 96, "nonrigid") < 2e-3, name
+    assert O.max_px_error(res["h1s0"][0], res["mean"][0], 96, 96, "nonrigid") < 1e-7
+    assert res["h1s0"][1].iters == res["mean"][1].iters
