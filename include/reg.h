@@ -137,12 +137,13 @@ typedef struct {
     int    grid;          /* REG_NONRIGID control-grid spacing in finest pixels; 0 = auto (16,
                              doubled until at most 65 points per axis); a multiple of 2^(levels-1) */
     int    metric;        /* REG_NONRIGID scalar product of the gradient flow: REG_METRIC_GAUSS_NEWTON
-                             (default) or REG_METRIC_MEAN */
+                             (default), REG_METRIC_MEAN or REG_METRIC_H1 */
     int    unroll;        /* REG_NONRIGID energy passes: pixels in flight per lane (2 or 4); 0 = auto
                              (the autotuned value, else 4) */
     int    ctas_per_sm;   /* REG_NONRIGID operator kernels: register budget sized for 3 or 4 CTAs
                              per SM (80 or 64 registers a thread); 0 = auto (the autotuned value,
                              else 4 for 16-CTA operators and 3 below) */
+    double sigma;         /* REG_METRIC_H1: smoothing length in control-grid spacings (>= 0; default 1) */
 } reg_config_t;
 
 /* Scalar product of the nonrigid gradient flow [Sec. 2.3.1 takes the flow with respect to a
@@ -153,6 +154,11 @@ typedef struct {
  * floored at 1e-3 of it: each control point's step is scaled by its own curvature. */
 #define REG_METRIC_MEAN         0
 #define REG_METRIC_GAUSS_NEWTON 1
+/* REG_METRIC_H1: <u, v> = (1/Nc) u^T (I + sigma^2 Lg) v per axis, Lg the Laplacian of the control
+ * grid's graph (the neighbour edges the regulariser sums over): the flow's direction is the
+ * gradient smoothed over about sigma grid spacings, d = -Nc (I + sigma^2 Lg)^-1 dE/dc.  Available
+ * to reg_scan, reg_scan_batch and reg_pairwise (not to streams or reg_pairwise_noalloc: REG_EINVAL). */
+#define REG_METRIC_H1           2
 
 typedef struct {
     int32_t i, k;                      /* the element this operator produced */

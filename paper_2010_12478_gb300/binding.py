@@ -35,6 +35,8 @@ EXPORTS = ["reg_config_default", "reg_ctx_create", "reg_ctx_destroy", "reg_pairw
            "reg_pairwise_noalloc", "reg_autotune", "reg_autotune_save", "reg_autotune_load",
            "reg_scan_grids", "reg_warp", "reg_scan_batch", "reg_scan_node_grids", "reg_stream_grids",
            "reg_stream_set_lookback", "reg_mock_scan", "reg_autotune_get"]
+METRIC_MEAN, METRIC_GAUSS_NEWTON, METRIC_H1 = 0, 1, 2
+REG_STOP_GRAD, REG_STOP_REL, REG_STOP_LS, REG_STOP_MAXIT = 0, 1, 2, 3
 
 
 class RegError(RuntimeError):
@@ -54,7 +56,8 @@ class reg_config_t(ctypes.Structure):
                 ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double), ("step_cap", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("storage", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("grid", ctypes.c_int),
-                ("metric", ctypes.c_int), ("unroll", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+                ("metric", ctypes.c_int), ("unroll", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("sigma", ctypes.c_double)]
 
 
 class reg_stats_t(ctypes.Structure):
@@ -168,15 +171,17 @@ class Config:
     workers: int = 0
     mem_budget: int = 0
     grid: int = 0
-    metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control points
+    metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control
+                                  # points, 2 H1 (identity + sigma^2 grid Laplacian)
     unroll: int = 0               # nonrigid energy passes: pixels per lane (2, 4); 0 = tuned or 4
     ctas_per_sm: int = 0          # nonrigid register form (3, 4); 0 = tuned or by CTAs per operator
+    sigma: float = 1.0            # metric 2 (H1): smoothing length in control-grid spacings
 
     def c(self) -> reg_config_t:
         return reg_config_t(RIGID if self.mode == "rigid" else NONRIGID, self.levels, self.max_iter,
                             self.max_rejects, self.tol_grad, self.tol_rel_e, self.armijo_c, self.tau0,
                             self.step_cap, self.lam, STORAGES[self.storage], self.cluster, self.workers,
-                            self.mem_budget, self.grid, self.metric, self.unroll, self.ctas_per_sm)
+                            self.mem_budget, self.grid, self.metric, self.unroll, self.ctas_per_sm, self.sigma)
 
 
 def stats_dict(s: reg_stats_t, levels: int) -> dict:

@@ -324,6 +324,7 @@ struct reg_ctx {
     DevBuf spyr[kMaxLevels]; // nonrigid: the B-spline model of every level at its pixel centres
     DevBuf means, level_tab, ops, stats, node_theta, node_grid, status, node_ids;
     DevBuf q_slots, q_pending, q_cons, q_cons_start, q_ctr, q_class;
+    DevBuf h1q;   // REG_METRIC_H1: cosine bases and eigenvalues of the control grid
     DevBuf tmp;
     cudaStream_t pool[kPoolStreams] = {};
     cudaEvent_t ev_pool_done[kPoolStreams] = {};
@@ -362,6 +363,7 @@ extern "C" void reg_config_default(reg_config_t *c)
     c->tol_grad = 3e-5;
     c->tol_rel_e = 0.0;
     c->metric = REG_METRIC_GAUSS_NEWTON;
+    c->sigma = 1.0;
     c->armijo_c = 0.25;
     c->tau0 = 1.0;
     c->step_cap = 0.5;
@@ -387,7 +389,9 @@ static int validate_cfg(const reg_config_t &c)
         return fail(REG_EINVAL, "cluster %d not in {0,1,2,4,8,16}", c.cluster);
     if (c.lambda < 0) return fail(REG_EINVAL, "lambda < 0");
     if (c.grid < 0) return fail(REG_EINVAL, "grid < 0");
-    if (c.metric != REG_METRIC_MEAN && c.metric != REG_METRIC_GAUSS_NEWTON) return fail(REG_EINVAL, "metric %d", c.metric);
+    if (c.metric != REG_METRIC_MEAN && c.metric != REG_METRIC_GAUSS_NEWTON && c.metric != REG_METRIC_H1)
+        return fail(REG_EINVAL, "metric %d", c.metric);
+    if (!(c.sigma >= 0.0 && c.sigma <= 1.0e3)) return fail(REG_EINVAL, "sigma %g not in [0, 1000]", c.sigma);
     if (c.unroll != 0 && c.unroll != 2 && c.unroll != 4) return fail(REG_EINVAL, "unroll %d not in {0,2,4}", c.unroll);
     if (c.ctas_per_sm != 0 && c.ctas_per_sm != 3 && c.ctas_per_sm != 4)
         return fail(REG_EINVAL, "ctas_per_sm %d not in {0,3,4}", c.ctas_per_sm);
@@ -553,6 +557,7 @@ Config dev_config(const reg_config_t &c)
     d.step_cap = c.step_cap;
     d.lambda = c.lambda;
     d.metric = c.metric;
+    d.sigma = c.sigma;
     return d;
 }
 
@@ -767,6 +772,20 @@ int prepare_params(reg_ctx *ctx, const Geometry &g, int n_frames, int n_nodes, i
         p.gs = gd.s;
         CHECK(ctx->node_grid.reserve(sizeof(float2) * (size_t)gd.nx * gd.ny * std::max(1, n_nodes)));
         p.node_grid = ctx->node_grid.as<float2>();
+        if (ctx->cfg.metric == REG_METRIC_H1) {
+            // orthonormal DCT-II bases Q[j][k] = a_k cos(pi k (j + 1/2) / n) of the free-end path
+            // graphs, a_0 = sqrt(1/n), a_k = sqrt(2/n), and their Laplacian eigenvalues 2 - 2 cos(pi k / n)
+            std::vector<float> q;
+            for (int n : {gd.nx, gd.ny})
+                for (int j = 0; j < n; ++j)
+                    for (int k = 0; k < n; ++k)
+                        q.push_back((float)(std::sqrt((k == 0 ? 1.0 : 2.0) / n) * std::cos(M_PI * k * (j + 0.5) / n)));
+            for (int n : {gd.nx, gd.ny})
+                for (int k = 0; k < n; ++k) q.push_back((float)(2.0 - 2.0 * std::cos(M_PI * k / n)));
+            CHECK(ctx->h1q.reserve(sizeof(float) * q.size()));
+            CU(cudaMemcpyAsync(ctx->h1q.ptr, q.data(), sizeof(float) * q.size(), cudaMemcpyHostToDevice, s));
+            p.h1q = ctx->h1q.as<float>();
+        }
     }
     return REG_OK;
 }
@@ -942,16 +961,20 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, const TileS
             for (int q = cstart[op.out]; q < cstart[op.out + 1]; ++q) tail = std::max(tail, blev[cons[q]]);
             blev[e] = 1.0 + std::abs(op.tmpl - op.ref) / 64.0 + tail;
         }
+        // the mock operator (Sec. 5.1, microseconds each) takes the plain FIFO: the paper's dynamic
+        // scheduling without priorities, and no polling of every class
+        const int n_class = p.cfg.mode == kModeMock ? 1 : kQueueClasses;
         std::vector<int> order(n_ops), op_class(n_ops), class_cnt(kQueueClasses, 0);
         for (int e = 0; e < n_ops; ++e) order[e] = e;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blev[a] > blev[b]; });
         for (int r = 0; r < n_ops; ++r) {
-            const int c = (int)((long long)r * kQueueClasses / std::max(1, n_ops));
+            const int c = (int)((long long)r * n_class / std::max(1, n_ops));
             op_class[order[r]] = c;
             class_cnt[c] += 1;
         }
-        std::vector<int> class_off(kQueueClasses, 0), class_tail(kQueueClasses, 0);
-        for (int c = 1; c < kQueueClasses; ++c) class_off[c] = class_off[c - 1] + class_cnt[c - 1];
+        // class_off[c] .. class_off[c + 1]: the slots of class c (kQueueClasses + 1 offsets)
+        std::vector<int> class_off(kQueueClasses + 1, 0), class_tail(kQueueClasses, 0);
+        for (int c = 1; c <= kQueueClasses; ++c) class_off[c] = class_off[c - 1] + class_cnt[c - 1];
         std::vector<int> slots(n_ops, -1);
         for (int e : ready) {
             const int c = op_class[e];
@@ -979,6 +1002,7 @@ int execute(reg_ctx *ctx, const ScanPlan &plan, Params &p, int exec, const TileS
         p.queue.tail = ctx->q_ctr.as<int>() + kQueueClasses;
         p.queue.done = ctx->q_ctr.as<int>() + 2 * kQueueClasses;
         p.queue.claimed = ctx->q_ctr.as<int>() + 2 * kQueueClasses + 1;
+        p.queue.n_class = n_class;
         p.queue.op_class = ctx->q_class.as<int>();
         p.queue.class_off = ctx->q_class.as<int>() + n_ops;
         p.queue.slots = ctx->q_slots.as<int>();

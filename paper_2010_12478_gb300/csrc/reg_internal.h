@@ -74,7 +74,8 @@ constexpr int kModeMock = 2;
 struct Config {
     int mode, levels, max_iter, max_rejects;
     double tol_grad, tol_rel_e, armijo_c, tau0, step_cap, lambda;
-    int metric;   // nonrigid scalar product: REG_METRIC_MEAN or REG_METRIC_GAUSS_NEWTON
+    int metric;   // nonrigid scalar product: REG_METRIC_MEAN, REG_METRIC_GAUSS_NEWTON or REG_METRIC_H1
+    double sigma; // REG_METRIC_H1: smoothing length in control-grid spacings
 };
 
 // Ready-queue state of the persistent executor (device memory): one FIFO per priority class,
@@ -86,12 +87,13 @@ struct Queue {
     int *tail;         // [kQueueClasses] next slot to fill in each class
     int *slots;        // class c at slots[class_off[c] ...]: op indices in ready order, -1 = not yet filled
     const int *op_class;   // per op: its class
-    const int *class_off;  // [kQueueClasses] first slot of each class
+    const int *class_off;  // [kQueueClasses + 1] first slot of each class, then the slot count
     int *pending;      // per op: inputs not yet produced
     int *consumers;    // CSR list of ops consuming each node
     int *cons_start;   // [n_nodes + 1]
     int *done;         // number of finished ops
     int *claimed;      // number of claimed ops, all classes
+    int n_class;       // classes in use (1: a plain FIFO)
     long long timeout_ns;
 };
 
@@ -105,6 +107,7 @@ struct Params {
     double *node_theta;        // [n_nodes][3]: rigid (alpha, Gx, Gy); nonrigid (0, mean c_x, mean c_y)
     float2 *node_grid;         // nonrigid: [n_nodes][gny * gnx] control values (finest px)
     const float *mock_us;      // mock operator (kModeMock): duration of each operator, microseconds
+    const float *h1q;          // REG_METRIC_H1: the control grid's cosine bases and eigenvalues (Qx, Qy, lx, ly)
     int unroll;                // nonrigid energy passes: pixels in flight per lane (2 or 4; 0 = 4)
     int minb;                  // nonrigid register form: CTAs per SM (3 or 4; 0 = 4 at 16 CTAs per
                                // operator, else 3)

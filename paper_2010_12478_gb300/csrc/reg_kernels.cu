@@ -849,13 +849,28 @@ __host__ __device__ __forceinline__ int grid_band_elems(int gnx, int gny, int C)
 }
 
 // Dynamic shared memory of the nonrigid kernels, in float2 units: c, d, mt (whole grid each; mt the
-// flow's scalar product per control point and axis), the band of partial gradients, then
-// (16-byte aligned) one row of gnx - 1 float4 per warp: the control values of the warp's pixel row
-// interpolated along y, (u_j, u_{j+1} - u_j).
-__host__ __device__ __forceinline__ int grid_crow_offset(int gnx, int gny, int C)
+// flow's scalar product per control point and axis, or with the H1 product its right-hand side),
+// with the H1 product two more whole-grid buffers t and u for its solve, the band of partial
+// gradients, then (16-byte aligned) one row of gnx - 1 float4 per warp: the control values of the
+// warp's pixel row interpolated along y, (u_j, u_{j+1} - u_j).
+struct GridLayout {
+    int c, d, mt, t, u, gp, crow;
+};
+__host__ __device__ __forceinline__ GridLayout grid_layout(int gnx, int gny, int C, bool h1)
 {
-    const int o = 3 * gnx * gny + grid_band_elems(gnx, gny, C);
-    return o + (o & 1);
+    const int Nc = gnx * gny;
+    GridLayout g;
+    g.c = 0;
+    g.d = Nc;
+    g.mt = 2 * Nc;
+    int o = 3 * Nc;
+    g.t = h1 ? o : -1;
+    g.u = h1 ? o + Nc : -1;
+    if (h1) o += 2 * Nc;
+    g.gp = o;
+    o += grid_band_elems(gnx, gny, C);
+    g.crow = o + (o & 1);
+    return g;
 }
 
 __device__ __forceinline__ void grid_rows(const Grid &G, const GridLvl &L, int rank, int C, int &cr0, int &cr1,
@@ -1061,6 +1076,78 @@ __device__ __forceinline__ int seg_index8(int lane)
     return ((lane & (S / 2)) ? 4 : 0) + ((lane & (S / 4)) ? 2 : 0) + ((lane & (S / 8)) ? 1 : 0);
 }
 
+// Buffers of the H1 scalar product (B null: another product): B the right-hand side -Nc dE/dc,
+// T and U work grids, q the cosine bases and eigenvalues of the control grid (Qx [nx][nx],
+// Qy [ny][ny], lx [nx], ly [ny], device memory), s2 = sigma^2.
+struct H1Bufs {
+    float2 *B = nullptr, *T = nullptr, *U = nullptr;
+    const float *q = nullptr;
+    float s2 = 0.f;
+};
+
+// U = (I + s2 Lg)^-1 B per axis, Lg the control grid's graph Laplacian, through its eigenbasis:
+// Lg = (Qy (x) Qx) diag(ly_m + lx_k) (Qy (x) Qx)^T with Qx, Qy the orthonormal DCT-II bases
+// (free-end path graphs), so U = Qy [(Qy^T B Qx) / (1 + s2 (ly_m + lx_k))] Qx^T: four small matrix
+// products over the grid, every CTA of the cluster the same work in the same order.
+__device__ void h1_solve(const H1Bufs &h, int nx, int ny)
+{
+    const float *Qx = h.q, *Qy = h.q + nx * nx, *lx = Qy + ny * ny, *ly = lx + nx;
+    const int Nc = nx * ny;
+    // T = B Qx
+    for (int i = threadIdx.x; i < Nc; i += kThreads) {
+        const int jy = i / nx, k = i - jy * nx;
+        float ax = 0.f, ay = 0.f;
+        for (int jx = 0; jx < nx; ++jx) {
+            const float qv = __ldg(Qx + jx * nx + k);
+            const float2 b = h.B[jy * nx + jx];
+            ax = fmaf(b.x, qv, ax);
+            ay = fmaf(b.y, qv, ay);
+        }
+        h.T[i] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    // U = (Qy^T T) / (1 + s2 (ly_m + lx_k))
+    for (int i = threadIdx.x; i < Nc; i += kThreads) {
+        const int m = i / nx, k = i - m * nx;
+        float ax = 0.f, ay = 0.f;
+        for (int jy = 0; jy < ny; ++jy) {
+            const float qv = __ldg(Qy + jy * ny + m);
+            const float2 t = h.T[jy * nx + k];
+            ax = fmaf(qv, t.x, ax);
+            ay = fmaf(qv, t.y, ay);
+        }
+        const float den = fmaf(h.s2, __ldg(ly + m) + __ldg(lx + k), 1.f);
+        h.U[i] = make_float2(ax / den, ay / den);
+    }
+    __syncthreads();
+    // T = Qy U
+    for (int i = threadIdx.x; i < Nc; i += kThreads) {
+        const int jy = i / nx, k = i - jy * nx;
+        float ax = 0.f, ay = 0.f;
+        for (int m = 0; m < ny; ++m) {
+            const float qv = __ldg(Qy + jy * ny + m);
+            const float2 u = h.U[m * nx + k];
+            ax = fmaf(qv, u.x, ax);
+            ay = fmaf(qv, u.y, ay);
+        }
+        h.T[i] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    // U = T Qx^T
+    for (int i = threadIdx.x; i < Nc; i += kThreads) {
+        const int jy = i / nx, jx = i - jy * nx;
+        float ax = 0.f, ay = 0.f;
+        for (int k = 0; k < nx; ++k) {
+            const float qv = __ldg(Qx + jx * nx + k);
+            const float2 t = h.T[jy * nx + k];
+            ax = fmaf(t.x, qv, ax);
+            ay = fmaf(t.y, qv, ay);
+        }
+        h.U[i] = make_float2(ax, ay);
+    }
+    __syncthreads();
+}
+
 // Gradient pass at c: this CTA's cells in four parity phases (no two cells of a phase share a
 // corner, so each corner is updated by one warp at a time, in a fixed order); then every CTA
 // assembles the whole gradient from the (at most two) CTAs whose band holds each control row,
@@ -1077,7 +1164,7 @@ __device__ __forceinline__ int seg_index8(int lane)
 template <typename S, bool METRIC>
 __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, const float2 *c, float2 *d,
                                float2 *mt, float2 *gp, const float *pm, int cr0, int cr1, Smem &sm,
-                               const cg::cluster_group &cl)
+                               const cg::cluster_group &cl, const H1Bufs &h1)
 {
     const S *R = (const S *)L.R, *T = (const S *)L.T;
     const float aP = pm[0], bP = pm[1], rb = pm[2], tb = pm[3], lam = pm[4];
@@ -1307,6 +1394,57 @@ __device__ void grid_grad_pass(const Lvl &L, const Grid &G, const GridLvl &GL, c
     float nmh = 0.f, nml = 0.f, dnh = 0.f, dnl = 0.f, nrun = 0.f, drun = 0.f;
     int k = 0;
     constexpr int kBatch = 4;   // points per thread whose remote loads are in flight together
+    if (h1.B) {
+        // H1 product: b = scale (lambda lap + g) = -Nc dE/dc into B, d = M^-1 b into U; then
+        // |d|_M^2 = d.b, and for the first trial <d_prev, y>_M, |y|_M^2 with y = d_prev - d, M y
+        // taken as the stencil y + s2 Lg y
+        for (int j = tid; j < Nc; j += kThreads) {
+            const int jy = j / G.nx, jx = j - jy * G.nx;
+            const int rlo = jy > 0 ? min(C - 1, (jy - 1) / max(q, 1)) : 0;
+            const int rhi = min(C - 1, jy / max(q, 1));
+            float2 g = *cl.map_shared_rank(gp + (jy - min(ncy, rlo * q)) * G.nx + jx, rlo);
+            if (rhi != rlo) {
+                const float2 w2 = *cl.map_shared_rank(gp + (jy - min(ncy, rhi * q)) * G.nx + jx, rhi);
+                g.x += w2.x;
+                g.y += w2.y;
+            }
+            const float2 cj = c[j];
+            float lx = 0.f, ly = 0.f;
+            if (jx > 0)        { const float2 v = c[j - 1];    lx += cj.x - v.x; ly += cj.y - v.y; }
+            if (jx + 1 < G.nx) { const float2 v = c[j + 1];    lx += cj.x - v.x; ly += cj.y - v.y; }
+            if (jy > 0)        { const float2 v = c[j - G.nx]; lx += cj.x - v.x; ly += cj.y - v.y; }
+            if (jy + 1 < G.ny) { const float2 v = c[j + G.nx]; lx += cj.x - v.x; ly += cj.y - v.y; }
+            h1.B[j] = make_float2(scale * fmaf(lam, lx, g.x), scale * fmaf(lam, ly, g.y));
+        }
+        __syncthreads();
+        h1_solve(h1, G.nx, G.ny);
+        auto yv = [&](int i) {
+            const float2 a = d[i], b = h1.U[i];
+            return make_float2(a.x - b.x, a.y - b.y);
+        };
+        for (int j = tid; j < Nc; j += kThreads) {
+            const int jy = j / G.nx, jx = j - jy * G.nx;
+            const float2 dj = h1.U[j], bj = h1.B[j], dold = d[j], y = yv(j);
+            float lx = 0.f, ly = 0.f;
+            if (jx > 0)        { const float2 v = yv(j - 1);    lx += y.x - v.x; ly += y.y - v.y; }
+            if (jx + 1 < G.nx) { const float2 v = yv(j + 1);    lx += y.x - v.x; ly += y.y - v.y; }
+            if (jy > 0)        { const float2 v = yv(j - G.nx); lx += y.x - v.x; ly += y.y - v.y; }
+            if (jy + 1 < G.ny) { const float2 v = yv(j + G.nx); lx += y.x - v.x; ly += y.y - v.y; }
+            const float myx = fmaf(h1.s2, lx, y.x), myy = fmaf(h1.s2, ly, y.y);
+            run = fmaf(dj.x, bj.x, fmaf(dj.y, bj.y, run));
+            nrun = fmaf(dold.x, myx, fmaf(dold.y, myy, nrun));
+            drun = fmaf(y.x, myx, fmaf(y.y, myy, drun));
+            mx = fmaxf(mx, fmaf(dj.x, dj.x, dj.y * dj.y));
+            if (++k == kFast) {
+                ff_acc(ssh, ssl, run); run = 0.f;
+                ff_acc(nmh, nml, nrun); nrun = 0.f;
+                ff_acc(dnh, dnl, drun); drun = 0.f;
+                k = 0;
+            }
+        }
+        __syncthreads();   // every d_prev was read before d is replaced
+        for (int j = tid; j < Nc; j += kThreads) d[j] = h1.U[j];
+    } else
     for (int j0 = tid; j0 < Nc; j0 += kBatch * kThreads) {
         float2 gb[kBatch];
 #pragma unroll
@@ -1501,8 +1639,13 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
     const int Lc = cfg.levels;
     const Grid G{p.gnx, p.gny, p.gs};
     const int Nc = G.nx * G.ny;
-    float2 *c = gbuf, *d = gbuf + Nc, *mt = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
-    float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, C));
+    const bool h1 = cfg.metric == REG_METRIC_H1;
+    const GridLayout lay = grid_layout(G.nx, G.ny, C, h1);
+    float2 *c = gbuf + lay.c, *d = gbuf + lay.d, *mt = gbuf + lay.mt, *gp = gbuf + lay.gp;
+    float4 *crow = (float4 *)(gbuf + lay.crow);
+    // H1 product: mt holds the right-hand side of its solve
+    const H1Bufs hb{h1 ? mt : nullptr, h1 ? gbuf + lay.t : nullptr, h1 ? gbuf + lay.u : nullptr, p.h1q,
+                    (float)(cfg.sigma * cfg.sigma)};
     int buf = 0;
     // initial control values (finest px), scaled to the coarsest level
     {
@@ -1564,9 +1707,9 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
             } else if (act == kActTrial) {
                 grid_energy_pass<S, false, U, true>(L, G, GL, c, d, pm[0], crow, r0, r1, sm, buf, cl);
             } else if (act == kActMetric) {
-                grid_grad_pass<S, true>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
+                grid_grad_pass<S, true>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl, hb);
             } else {
-                grid_grad_pass<S, false>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
+                grid_grad_pass<S, false>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl, hb);
             }
             if (tid == 0) {
                 const int next = field_step(k, cfg, sm.tot, act, sm.pm);
@@ -1650,6 +1793,7 @@ __device__ bool op_valid(const Params &p, const OpDesc &op)
         return ok(op.out) && ok(op.right) && (op.left < 0 || ok(op.left));
     }
     auto node_ok = [&](int n) { return n >= 0 && n < p.n_nodes; };
+    if (p.cfg.mode == REG_NONRIGID && p.cfg.metric == REG_METRIC_H1 && !p.h1q) return false;
     if (op.ref < 0 || op.ref >= p.n_frames || op.tmpl < 0 || op.tmpl >= p.n_frames) return false;
     if (!node_ok(op.out)) return false;
     if (op.left >= 0 && !(node_ok(op.left) && node_ok(op.right))) return false;
@@ -1708,30 +1852,62 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(start));
             unsigned ns = 64;
             int op = -1, seen = *vd;
-            for (;;) {
+            // the wait has run out once timeout_ns passed with no operator finishing (the finished
+            // count is read only then, so spinning workers do not crowd its line), or on an error
+            auto wait_expired = [&](unsigned long long now) {
+                if (*((volatile int *)p.status) != 0) return true;
+                if ((long long)(now - start) <= Q.timeout_ns) return false;
+                const int dn = *vd;
+                if (dn == seen) return true;
+                seen = dn;
+                start = now;
+                return false;
+            };
+            if (Q.n_class == 1) {
+                // one class, a plain FIFO: take a ticket, then wait for that slot to be written (the
+                // form for short operators, where polling every class's head would crowd one line)
+                const int slot = atomicAdd(Q.head, 1);
+                while (slot < p.n_ops && (op = vs[slot]) < 0) {
+                    unsigned long long now;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                    if (wait_expired(now)) {
+                        atomicCAS(p.status, 0, (int)kDevQueueTimeout);
+                        op = -2;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 1024) ns *= 2;
+                }
+            }
+            for (; Q.n_class > 1;) {
                 if (*vc >= p.n_ops) break;
-                // every class's head and tail in one round of loads, then the first non-empty class
+                // every class's head and tail in one round of loads; the first class with a ready
+                // operator is claimed with an atomic on its head (no compare-and-swap: under
+                // contention a worker may draw a slot past the tail, which a later release of that
+                // class fills; a draw past the class's last operator is void)
                 int hs[kQueueClasses], ts[kQueueClasses];
 #pragma unroll
-                for (int c = 0; c < kQueueClasses; ++c) hs[c] = vh[c];
+                for (int c = 0; c < kQueueClasses; ++c) hs[c] = c < Q.n_class ? vh[c] : 0;
 #pragma unroll
-                for (int c = 0; c < kQueueClasses; ++c) ts[c] = vt[c];
+                for (int c = 0; c < kQueueClasses; ++c) ts[c] = c < Q.n_class ? vt[c] : 0;
                 int slot = -1;
-                bool raced = false;
+                bool void_draw = false;
 #pragma unroll
                 for (int c = 0; c < kQueueClasses; ++c)
-                    if (slot < 0 && !raced && hs[c] < ts[c]) {
-                        if (atomicCAS(Q.head + c, hs[c], hs[c] + 1) == hs[c]) slot = Q.class_off[c] + hs[c];
-                        else raced = true;   // another cluster took it: look again at once
+                    if (slot < 0 && !void_draw && hs[c] < ts[c]) {
+                        const int h = atomicAdd(Q.head + c, 1);
+                        if (h < Q.class_off[c + 1] - Q.class_off[c]) slot = Q.class_off[c] + h;
+                        else void_draw = true;   // the class is used up: look again at once
                     }
-                if (raced) continue;
+                if (void_draw) continue;
                 if (slot >= 0) {
                     atomicAdd(Q.claimed, 1);
-                    // the releaser bumps the tail before it writes the slot
+                    // the releaser bumps the tail before it writes the slot; a slot drawn past the
+                    // tail is written by a later release of its class
                     while ((op = vs[slot]) < 0) {
                         unsigned long long now;
                         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-                        if ((long long)(now - start) > Q.timeout_ns || *((volatile int *)p.status) != 0) {
+                        if (wait_expired(now)) {
                             atomicCAS(p.status, 0, (int)kDevQueueTimeout);
                             op = -2;
                             break;
@@ -1742,9 +1918,7 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
                 }
                 unsigned long long now;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-                const int d = *vd;
-                if (d != seen) { seen = d; start = now; }   // progress: the wait starts again
-                if ((long long)(now - start) > Q.timeout_ns || *((volatile int *)p.status) != 0) {
+                if (wait_expired(now)) {
                     atomicCAS(p.status, 0, (int)kDevQueueTimeout);
                     op = -2;
                     break;
@@ -1831,8 +2005,9 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
     } else {
         const Grid G{p.gnx, p.gny, p.gs};
         const int Nc = G.nx * G.ny;
-        float2 *c = gbuf, *d = gbuf + Nc, *mt = gbuf + 2 * Nc, *gp = gbuf + 3 * Nc;
-        float4 *crow = (float4 *)(gbuf + grid_crow_offset(G.nx, G.ny, 1));
+        const GridLayout lay = grid_layout(G.nx, G.ny, 1, false);
+        float2 *c = gbuf + lay.c, *d = gbuf + lay.d, *mt = gbuf + lay.mt, *gp = gbuf + lay.gp;
+        float4 *crow = (float4 *)(gbuf + lay.crow);
         for (int j = tid; j < Nc; j += kThreads) { c[j] = cgrid[j]; mt[j] = make_float2(1.f, 1.f); }
         __syncthreads();
         GridLvl GL;
@@ -1855,7 +2030,7 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
         if (grad_c) {
             float pm[5];
             for (int q = 0; q < 5; ++q) pm[q] = sm.pm[q];
-            grid_grad_pass<S, false>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl);
+            grid_grad_pass<S, false>(L, G, GL, c, d, mt, gp, pm, cr0, cr1, sm, cl, H1Bufs{});
             // d = -Nc dE/dc (unit scalar product)
             const float s = -1.f / (float)Nc;
             for (int j = tid; j < Nc; j += kThreads) grad_c[j] = make_float2(s * d[j].x, s * d[j].y);
@@ -2083,11 +2258,11 @@ cudaError_t launch_pyramid(const float *frames, int N, size_t fstride, int W, in
     return cudaErrorInvalidValue;
 }
 
-// Dynamic shared memory of the nonrigid kernels (layout at grid_crow_offset).
+// Dynamic shared memory of the nonrigid kernels (layout of grid_layout).
 static size_t grid_smem(const Params &p, int cluster)
 {
     if (p.cfg.mode != REG_NONRIGID) return 0;
-    return sizeof(float2) * (size_t)grid_crow_offset(p.gnx, p.gny, cluster) +
+    return sizeof(float2) * (size_t)grid_layout(p.gnx, p.gny, cluster, p.cfg.metric == REG_METRIC_H1).crow +
            sizeof(float4) * (size_t)kWarps * (p.gnx - 1);
 }
 

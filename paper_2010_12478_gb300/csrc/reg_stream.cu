@@ -397,6 +397,8 @@ extern "C" int reg_stream_open(reg_ctx_t *ctx, int W, int H, reg_stream_t **out)
         }
     }
     int gnx = 0, gny = 0, gs = 0;
+    if (c.mode == REG_NONRIGID && c.metric == REG_METRIC_H1)
+        return host_fail(REG_EINVAL, "the H1 scalar product is available to reg_scan, reg_scan_batch and reg_pairwise");
     if (c.mode == REG_NONRIGID) {
         int rc = reg_grid_dims(W, H, c.grid, c.levels, &gnx, &gny, &gs);
         if (rc != REG_OK) return rc;

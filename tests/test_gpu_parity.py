@@ -33,7 +33,8 @@ def ctx_of(**kw):
 def ocfg(cfg: B.Config) -> O.Config:
     return O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
                     tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
-                    lam=cfg.lam, mode=cfg.mode, grid=cfg.grid, metric=cfg.metric)
+                    lam=cfg.lam, mode=cfg.mode, grid=cfg.grid, metric=cfg.metric,
+                    sigma=cfg.sigma)
 
 
 def rel(a, b):
@@ -264,6 +265,40 @@ def test_scan_nonrigid_c1_tile_shapes_match_oracle(unroll, ctas_per_sm):
     for i, o in enumerate(ref):
         err = O.max_px_error(got[i], o.phi, 128, 128, "nonrigid")
         assert err <= PX_TOL, (i, err)
+
+
+@pytest.mark.parametrize("sigma", [1.0, 2.5])
+@pytest.mark.parametrize("exec_", ["persistent", "plain"])
+def test_scan_nonrigid_h1_matches_oracle(sigma, exec_):
+    """The H1 scalar product (the gradient smoothed over sigma grid spacings): the cosine-transform
+    solve of the kernels against the oracle's banded Cholesky, through a whole nonrigid scan."""
+    F = c1_frames(6)
+    cfg = B.Config(mode="nonrigid", metric=B.METRIC_H1, sigma=sigma, cluster=4)
+    ctx = B.Context(cfg)
+    n = len(F) - 1
+    fo = torch.zeros((n, 2, 128, 128), device="cuda")
+    _, st = ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung", exec=exec_, fields_out=fo)
+    ref = oracle_scan(F, cfg, "brent_kung")
+    got = fo.cpu().numpy()
+    for i, o in enumerate(ref):
+        err = O.max_px_error(got[i], o.phi, 128, 128, "nonrigid")
+        assert err <= PX_TOL, (i, err)
+    # no level ran out of steps (the gradient norm, or a line search at the FP32 floor, ends each)
+    assert all(v != B.REG_STOP_MAXIT for s in st for v in s["stop"])
+
+
+def test_h1_pairwise_at_512_matches_oracle():
+    """A neighbour operator on a 512^2 lattice pair (33 x 33 control points) with the H1 product."""
+    spec = synth.spec_c2()
+    spec.n_frames = 2
+    F = synth.make_series(spec).frames.numpy()
+    cfg = B.Config(mode="nonrigid", metric=B.METRIC_H1, sigma=1.0)
+    ctx = B.Context(cfg)
+    fo = torch.zeros((2, 512, 512), device="cuda")
+    ctx.pairwise(torch.from_numpy(F[0]).cuda(), torch.from_numpy(F[1]).cuda(), field_out=fo)
+    oc = ocfg(cfg)
+    o = O.op_A({0: O.pyramid(F[0], oc.levels), 1: O.pyramid(F[1], oc.levels)}, 0, 1, oc)
+    assert O.max_px_error(fo.cpu().numpy(), o.phi, 512, 512, "nonrigid") <= PX_TOL
 
 
 def test_scan_two_frames():

@@ -49,6 +49,8 @@ def test_struct_layouts_match_header(lib):
     assert cfg.metric == O.Config().metric == B.Config().metric == 1
     # the launch shape is left to the autotuner unless set
     assert cfg.unroll == 0 and cfg.ctas_per_sm == 0 and B.Config().c().unroll == 0
+    # the H1 product's smoothing length
+    assert cfg.sigma == O.Config().sigma == B.Config().sigma == 1.0
 
 
 def test_errors_without_gpu_are_reported_not_crashing(lib):
@@ -64,7 +66,7 @@ def test_errors_without_gpu_are_reported_not_crashing(lib):
     bad.levels = 9
     assert lib.reg_ctx_create(ctypes.byref(bad), 0, ctypes.byref(h)) == B.REG_EINVAL
     assert b"levels" in lib.reg_last_error_message()
-    for field, value in (("unroll", 3), ("ctas_per_sm", 2)):
+    for field, value in (("unroll", 3), ("ctas_per_sm", 2), ("metric", 3), ("sigma", -1.0)):
         bad = B.reg_config_t()
         lib.reg_config_default(ctypes.byref(bad))
         setattr(bad, field, value)
