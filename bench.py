@@ -304,7 +304,7 @@ def serving(dev, mode: str, frames_per_stream: int, seed: int = 1410):
     streams = [B.Stream(ctx, S, S) for (S, _, _, _) in plan]
     # look-back of each stream's online scan: a prefix operator B (a long span) takes longer than the
     # frame interval at these rates, so the prefixes advance in k chains side by side (k frames per B)
-    lookback = {256: 2, 512: 8, 1024: 8}
+    lookback = {256: 4, 512: 2, 1024: 4}
     for (S, _, _, _), st in zip(plan, streams):
         st.set_lookback(lookback[S])
     events = sorted((t[j], k, j) for k, (_, _, _, t) in enumerate(plan) for j in range(len(t)))
@@ -465,8 +465,10 @@ def registered_series(ctx, frames, mode: str, steps: int, warmup: int, peak: flo
             "tma_staged": bool(tim["tma_staged"]),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
-                         "traffic": profile_traffic(f"warp_kernel_{'c2' if N <= 256 else 'c3'}_{mode}", "reg_warp.cu",
-                                                    "dram bytes per call (scaled)"),
+                         # the capture is of 256 frames; each frame is read and written once, so the
+                         # traffic grows in proportion to the frames of the call
+                         "traffic": (lambda t: None if t is None else round(t * N / 256))(
+                             profile_traffic(f"warp_kernel_c2_{mode}", "reg_warp.cu", "dram bytes per call (scaled)")),
                          "peak_source": peak_src, "kernel": "warp_kernel (+ mean_kernel)",
                          "algorithmic_bytes_per_call": alg}}
 

@@ -1863,7 +1863,10 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
                 start = now;
                 return false;
             };
-            if (Q.n_class == 1) {
+            // the mock operator's kernel keeps to the FIFO (the class scan's registers would halve its
+            // resident CTAs)
+            constexpr bool kClassQueue = MODE != kModeMock;
+            if (!kClassQueue || Q.n_class == 1) {
                 // one class, a plain FIFO: take a ticket, then wait for that slot to be written (the
                 // form for short operators, where polling every class's head would crowd one line)
                 const int slot = atomicAdd(Q.head, 1);
@@ -1879,7 +1882,7 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
                     if (ns < 1024) ns *= 2;
                 }
             }
-            for (; Q.n_class > 1;) {
+            for (; kClassQueue && Q.n_class > 1;) {
                 if (*vc >= p.n_ops) break;
                 // every class's head and tail in one round of loads; the first class with a ready
                 // operator is claimed with an atomic on its head (no compare-and-swap: under
@@ -1939,12 +1942,14 @@ __global__ void __launch_bounds__(kThreads, MINB) persistent_kernel(Params p)
             // publish the produced node and release its consumers, spread over the CTA's threads (a
             // node of a Ladner-Fischer scan has up to n/2 consumers); the lanes of a warp that make
             // consumers of one class ready claim their slots with one atomic on that class's tail
-            __threadfence();   // the cluster's writes of the node, seen through cl.sync, go first
             const int node = p.ops[op].out;
             const int cb = p.queue.cons_start[node], ce = p.queue.cons_start[node + 1];
             const int lane = threadIdx.x & 31;
-            for (int base = cb; base < ce; base += kThreads) {
-                const int e = base + threadIdx.x;
+            // only warps with consumers take part (most nodes have one or two: warp 0 alone); each
+            // orders the cluster's writes of the node, seen through cl.sync, before its releases
+            if (cb + (int)(threadIdx.x & ~31) < ce) __threadfence();
+            for (int base = cb + (int)(threadIdx.x & ~31); base < ce; base += kThreads) {
+                const int e = base + lane;
                 int c = -1;
                 bool ready = false;
                 if (e < ce) {
@@ -2322,7 +2327,7 @@ cudaError_t launch_ops(const Params &p, int storage, int cluster, int n_launch_o
 {
     const bool minb4 = p.minb > 0 ? p.minb == 4 : cluster >= 16;   // nonrigid register form
     const int blocks = n_launch_ops * cluster;
-    if (p.cfg.mode == kModeMock) return launch_cluster(op_kernel<kModeMock, float, 4>, blocks, cluster, s, p);
+    if (p.cfg.mode == kModeMock) return launch_cluster(op_kernel<kModeMock, float, 8>, blocks, cluster, s, p);
     if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
         case REG_F32: return launch_cluster(op_kernel<REG_RIGID, float, 4>, blocks, cluster, s, p);
@@ -2340,7 +2345,7 @@ cudaError_t launch_persistent(const Params &p, int storage, int cluster, int wor
 {
     const bool minb4 = p.minb > 0 ? p.minb == 4 : cluster >= 16;   // nonrigid register form
     const int blocks = workers * cluster;
-    if (p.cfg.mode == kModeMock) return launch_cluster(persistent_kernel<kModeMock, float, 4>, blocks, cluster, s, p);
+    if (p.cfg.mode == kModeMock) return launch_cluster(persistent_kernel<kModeMock, float, 8>, blocks, cluster, s, p);
     if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
         case REG_F32: return launch_cluster(persistent_kernel<REG_RIGID, float, 4>, blocks, cluster, s, p);
@@ -2383,7 +2388,7 @@ int persistent_resident_clusters(const Params &p, int storage, int cluster)
     const bool minb4 = p.minb > 0 ? p.minb == 4 : cluster >= 16;   // nonrigid register form
     int n = -1;
     if (p.cfg.mode == kModeMock) {
-        n = resident_clusters(persistent_kernel<kModeMock, float, 4>, cluster, p);
+        n = resident_clusters(persistent_kernel<kModeMock, float, 8>, cluster, p);
     } else if (p.cfg.mode == REG_RIGID) {
         switch (storage) {
         case REG_F32: n = resident_clusters(persistent_kernel<REG_RIGID, float, 4>, cluster, p); break;
