@@ -29,8 +29,13 @@ namespace {
 
 constexpr int kLanes = 32;          // CUDA streams the service launches operators on
 constexpr int kSlots = 24;          // frame slots per stream (frames in flight)
-constexpr int kClusterA = 4;    // CTAs per neighbour operator A (fixed: results do not depend on load)
-constexpr int kClusterB = 16;   // CTAs per B: the chain of prefixes is each stream's critical path
+// CTAs per operator unless the config sets them (fixed: results do not depend on load).  A
+// stream's operators are latency-bound: a frame's result waits for its A, its window operators
+// and its prefix B one after another, and a few streams keep only tens of operators in flight, so
+// every operator takes the largest cluster (measured on eight mixed streams: 16 CTAs for A and B
+// gave p99 21 ms from arrival, A on 4 CTAs and B on 16 gave 1.2 s).
+constexpr int kClusterA = 16;
+constexpr int kClusterB = 16;
 // Operators of one frame slot: A at 0, the look-back windows at 1..log2 k, the prefix at kOpP.
 constexpr int kMaxLookbackLog = 3;              // look-back k <= 8
 constexpr int kOpsPerSlot = kMaxLookbackLog + 2;
