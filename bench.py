@@ -520,6 +520,27 @@ def registered_series(ctx, frames, mode: str, steps: int, warmup: int, peak: flo
 
 # ------------------------------------------------------------------ mixed-size batch (c4)
 def mixed_batch(args, dev, world, rank, dist):
+    """The c4 workload as the benchmark's line (mixed_measure)."""
+    results, sizes, clocks = mixed_measure(args.mode, dev, world, rank, dist, args.steps, args.warmup)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": results["f32"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": results["f32"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c4: {WORKLOAD_TEXT['c4']}", "series": 64, "frames_per_series": 128,
+                       "sizes": sizes, "mode": args.mode,
+                       "exec": "persistent (one reg_scan_batch per size)", "cluster": 16,
+                       "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "precision": results, "clocks": clocks,
+            "roofline": None, "e2e": None, "cpu_baseline": None,
+            "note": "per-storage throughput and error; the operator-kernel roofline and the end-to-end and CPU "
+                    "baselines are reported on the c2 and c3 workloads",
+            "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
+def mixed_measure(mode, dev, world, rank, dist, steps, warmup):
     """64 series x 128 frames, sizes drawn from {256, 512, 1024}^2; per pyramid storage type the
     series of each size run as one reg_scan_batch call (persistent queue); frames/s over all
     series, and the displacement error of sampled neighbour operators against the FP64 oracle."""
@@ -541,39 +562,39 @@ def mixed_batch(args, dev, world, rank, dist):
     results = {}
     with ClockSampler(0 if dev.index is None else dev.index) as clk:
         for storage in ("f32", "bf16", "f16"):
-            ctxs = {S: B.Context(B.Config(mode=args.mode, storage=storage, cluster=16)) for S in batches}
+            ctxs = {S: B.Context(B.Config(mode=mode, storage=storage, cluster=16)) for S in batches}
             for S, b in batches.items():   # warm-up
-                for _ in range(max(1, args.warmup)):
+                for _ in range(max(1, warmup)):
                     ctxs[S].scan_batch(b, exec="persistent", want_stats=False)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            for _ in range(args.steps):
+            for _ in range(steps):
                 for S, b in batches.items():
                     ctxs[S].scan_batch(b, exec="persistent", want_stats=False)
             e1.record()
             torch.cuda.synchronize()
-            ms = world_max_ms(e0.elapsed_time(e1) / args.steps, dist, dev)
+            ms = world_max_ms(e0.elapsed_time(e1) / steps, dist, dev)
             results[storage] = {"value": round(job_rate(n_frames, world, ms), 2), "unit": UNIT,
                                 "ms_per_step": round(ms, 2)}
             del ctxs
     # precision: sampled neighbour operators of the 256^2 and 512^2 series against the oracle
     if rank == 0:
-        cfg0 = B.Config(mode=args.mode)
+        cfg0 = B.Config(mode=mode)
         oc = O.Config(levels=cfg0.levels, max_iter=cfg0.max_iter, max_rejects=cfg0.max_rejects,
                       tol_grad=cfg0.tol_grad, tol_rel_e=cfg0.tol_rel_e, armijo_c=cfg0.armijo_c, tau0=cfg0.tau0,
-                      step_cap=cfg0.step_cap, lam=cfg0.lam, mode=args.mode, grid=cfg0.grid,
+                      step_cap=cfg0.step_cap, lam=cfg0.lam, mode=mode, grid=cfg0.grid,
                       metric=cfg0.metric, sigma=cfg0.sigma)
         samples = [(S, 0, j) for S in (256, 512) if S in batches for j in (5, 77)]
         for storage in ("f32", "bf16", "f16"):
-            ctx = B.Context(B.Config(mode=args.mode, storage=storage, cluster=16))
+            ctx = B.Context(B.Config(mode=mode, storage=storage, cluster=16))
             errs = []
             for S, q, j in samples:
                 F = batches[S][q]
                 Fh = F[j:j + 2].cpu().numpy()
                 ref = O.op_A({0: O.pyramid(Fh[0], oc.levels), 1: O.pyramid(Fh[1], oc.levels)}, 0, 1, oc)
-                if args.mode == "rigid":
+                if mode == "rigid":
                     el, _ = ctx.pairwise(F[j].contiguous(), F[j + 1].contiguous())
                     errs.append(O.max_px_error(np.array(el[2:], dtype=np.float64), ref.phi, S, S, "rigid"))
                 else:
@@ -582,21 +603,7 @@ def mixed_batch(args, dev, world, rank, dist):
                     errs.append(O.max_px_error(u.cpu().numpy(), ref.phi, S, S, "nonrigid"))
             results[storage]["max_px_error_vs_oracle"] = round(max(errs), 5)
             results[storage]["operators_sampled"] = [f"{S}^2 series {q} frames {j},{j + 1}" for S, q, j in samples]
-        line = {
-            "metric": METRIC, "value": results["f32"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": results["f32"]["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"c4: {WORKLOAD_TEXT['c4']}", "series": 64, "frames_per_series": 128,
-                       "sizes": {str(S): int(b.shape[0]) for S, b in batches.items()}, "mode": args.mode,
-                       "exec": "persistent (one reg_scan_batch per size)", "cluster": 16,
-                       "l2": "inputs larger than L2",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "precision": results, "clocks": clk.summary(),
-            "roofline": None, "e2e": None, "cpu_baseline": None,
-            "note": "per-storage throughput and error; the operator-kernel roofline and the end-to-end and CPU "
-                    "baselines are reported on the c2 and c3 workloads",
-        }
-        print(json.dumps(line), flush=True)
+    return results, {str(S): int(b.shape[0]) for S, b in batches.items()}, clk.summary()
 
 
 # ------------------------------------------------------------------ main
@@ -726,7 +733,7 @@ def main():
     ev_a, ev_b = ev[:nl], ev[nl:]
 
     levels = cfg.levels
-    forms = phases = e2e = other = serve = prec = reg_series = imbalance = mock = sprod = three = None
+    forms = phases = e2e = other = serve = prec = reg_series = imbalance = mock = sprod = three = c4 = None
     if args.quick and args.warp:
         reg_series = registered_series(ctx, frames, args.mode, 1, 1, peak, peak_src, world)
     if not args.quick:
@@ -802,6 +809,10 @@ def main():
         del octx
         # ---- c2 at the three pyramid levels its description names
         three = three_levels(dev, args.mode, args.exec_) if rank == 0 else None
+        # ---- c4: 64 series of mixed sizes, one batched scan per size, three storage types
+        c4_res, c4_sizes, _ = mixed_measure(args.mode, dev, world, rank, dist, 1, 1)
+        c4 = {"workload": f"c4: {WORKLOAD_TEXT['c4']}", "sizes": c4_sizes, "storage": c4_res,
+              "exec": "persistent (one reg_scan_batch per size), 16 CTAs per operator"}
         # ---- the nonrigid flow's scalar products on the same workload (Sec. 2.3.1 leaves it open)
         if args.mode == "nonrigid":
             sprod = {}
@@ -871,7 +882,7 @@ def main():
             "imbalance": imbalance,
             "mock_operator": mock,
             "registered_series": reg_series,
-            "other_mode": other, "scalar_products": sprod, "c2_three_levels": three,
+            "other_mode": other, "scalar_products": sprod, "c2_three_levels": three, "c4_mixed": c4,
             "serving": serve,
             "precision": prec,
             "e2e": e2e,
