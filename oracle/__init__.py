@@ -52,7 +52,7 @@ class _Cfg(ctypes.Structure):
                 ("tol_grad", ctypes.c_double), ("tol_rel_e", ctypes.c_double),
                 ("armijo_c", ctypes.c_double), ("tau0", ctypes.c_double),
                 ("step_cap", ctypes.c_double), ("lambda_", ctypes.c_double), ("metric", ctypes.c_int),
-                ("sigma", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("tol_coarse", ctypes.c_double)]
 
 
 class _Grid(ctypes.Structure):
@@ -136,10 +136,11 @@ class Config:
     metric: int = 1               # nonrigid scalar product: 1 Gauss-Newton diagonal, 0 mean over control
                                   # points, 2 H1 (identity + sigma^2 grid Laplacian)
     sigma: float = 1.0            # metric 2: smoothing length in control-grid spacings
+    tol_coarse: float = 10.0      # factor on tol_grad at every level above the finest
 
     def c(self) -> _Cfg:
         return _Cfg(self.levels, self.max_iter, self.max_rejects, self.tol_grad, self.tol_rel_e,
-                    self.armijo_c, self.tau0, self.step_cap, self.lam, self.metric, self.sigma)
+                    self.armijo_c, self.tau0, self.step_cap, self.lam, self.metric, self.sigma, self.tol_coarse)
 
 
 @dataclasses.dataclass

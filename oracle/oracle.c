@@ -53,6 +53,8 @@ typedef struct {
     int metric;        /* nonrigid flow's scalar product: 0 mean over control points, 1 Gauss-Newton diagonal,
                           2 H1 (identity plus sigma^2 times the control grid's Laplacian) */
     double sigma;      /* metric 2: smoothing length in control-grid spacings */
+    double tol_coarse; /* factor on tol_grad at every level above the finest (a coarse level only
+                          supplies the next level's initial guess) */
 } or_cfg_t;
 
 typedef struct {
@@ -314,7 +316,7 @@ static void or_rigid_level(const double *R, const double *T, int W, int H,
         double d[3] = {-g[0] / m0, -g[1], -g[2]};
         double slope = g[0] * d[0] + g[1] * d[1] + g[2] * d[2];
         double gn = sqrt(-slope);
-        if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
+        if (!(gn >= cfg->tol_grad * (lvl > 0 ? cfg->tol_coarse : 1.0))) { stop = OR_STOP_GRAD; break; }
         if (have_prev) {
             const double w[3] = {m0, 1.0, 1.0};
             tau = or_bb_step(tau, tau_acc, dprev, d, w, 3);
@@ -697,7 +699,7 @@ static void or_grid_level(const double *R, const double *T, int W, int H, int l,
         dmax = sqrt(dmax);
         double slope = -ss / (double)Nc;
         double gn = sqrt(ss / (double)Nc);
-        if (!(gn >= cfg->tol_grad)) { stop = OR_STOP_GRAD; break; }
+        if (!(gn >= cfg->tol_grad * (l > 0 ? cfg->tol_coarse : 1.0))) { stop = OR_STOP_GRAD; break; }
         for (int j = 0; j < Nc; ++j) { dc[2 * j] = dx[j]; dc[2 * j + 1] = dy[j]; }
         /* the metric's common factor 1/Nc cancels in the ratio */
         if (have_prev && h1) {

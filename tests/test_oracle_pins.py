@@ -691,3 +691,25 @@ def test_h1_flow_reaches_the_minimiser_of_the_other_scalar_products():
         assert O.max_px_error(res[name][0], res["mean"][0], 96, 96, "nonrigid") < 2e-3, name
     assert O.max_px_error(res["h1s0"][0], res["mean"][0], 96, 96, "nonrigid") < 1e-7
     assert res["h1s0"][1].iters == res["mean"][1].iters
+
+
+# ------------------------------------------------------------------ the coarse levels' stop rule
+def test_coarse_level_tolerance_changes_the_path_not_the_result():
+    # a coarse level only supplies the next level's initial guess: stopped at 10x the tolerance it
+    # takes fewer evaluations, and the finest level (same tolerance) ends at the same minimiser
+    ser = synth.make_series(synth.SeriesSpec(3, 128, 128, step=1.0, field_amp=1.2, snr=(12, 12), seed=51))
+    F = ser.frames.numpy().astype(np.float64)
+    P0, P1 = O.pyramid(F[0], 2), O.pyramid(F[1], 2)
+    for mode in ("nonrigid", "rigid"):
+        res = {}
+        for tc in (1.0, 10.0):
+            cfg = O.Config(levels=2, mode=mode, tol_coarse=tc, tol_grad=1e-6)
+            res[tc] = O.register(P0, P1, O.identity(mode, 128, 128, cfg.grid), cfg)
+        assert res[10.0][1].evals[1] < res[1.0][1].evals[1], mode
+        assert O.max_px_error(res[10.0][0], res[1.0][0], 128, 128, mode) < 2e-3, mode
+    # one level: the factor never applies
+    for mode in ("nonrigid", "rigid"):
+        out = [O.register([P0[0]], [P1[0]], O.identity(mode, 128, 128, 0), O.Config(levels=1, mode=mode, tol_coarse=tc))
+               for tc in (1.0, 10.0)]
+        assert np.array_equal(np.asarray(out[0][0]), np.asarray(out[1][0])), mode
+        assert out[0][1].evals == out[1][1].evals, mode
