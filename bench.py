@@ -195,7 +195,8 @@ def oracle_sample(frames_np, cfg_bind, budget_s: float):
     oc = O.Config(levels=cfg_bind.levels, max_iter=cfg_bind.max_iter, max_rejects=cfg_bind.max_rejects,
                   tol_grad=cfg_bind.tol_grad, tol_rel_e=cfg_bind.tol_rel_e, armijo_c=cfg_bind.armijo_c,
                   tau0=cfg_bind.tau0, step_cap=cfg_bind.step_cap, lam=cfg_bind.lam, mode=cfg_bind.mode,
-                metric=cfg_bind.metric, sigma=cfg_bind.sigma)
+                metric=cfg_bind.metric, sigma=cfg_bind.sigma,
+                tol_coarse=cfg_bind.tol_coarse)
     t0 = time.perf_counter()
     pyr = {}
     ops = 0
@@ -240,7 +241,8 @@ def oracle_sample_parallel(frames_np, cfg_bind, budget_s: float, workers: int = 
     cfgd = dict(levels=cfg_bind.levels, max_iter=cfg_bind.max_iter, max_rejects=cfg_bind.max_rejects,
                 tol_grad=cfg_bind.tol_grad, tol_rel_e=cfg_bind.tol_rel_e, armijo_c=cfg_bind.armijo_c,
                 tau0=cfg_bind.tau0, step_cap=cfg_bind.step_cap, lam=cfg_bind.lam, mode=cfg_bind.mode,
-                metric=cfg_bind.metric, sigma=cfg_bind.sigma)
+                metric=cfg_bind.metric, sigma=cfg_bind.sigma,
+                tol_coarse=cfg_bind.tol_coarse)
     N = frames_np.shape[0]
     tasks = [(frames_np[3 * q:3 * q + 3].copy(), cfgd) for q in range(max(1, (N - 1) // 3))]
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
@@ -394,7 +396,8 @@ def precision(frames, mode: str, n_samples: int = 6):
     cfg0 = B.Config(mode=mode)
     oc = O.Config(levels=cfg0.levels, max_iter=cfg0.max_iter, max_rejects=cfg0.max_rejects, tol_grad=cfg0.tol_grad,
                   tol_rel_e=cfg0.tol_rel_e, armijo_c=cfg0.armijo_c, tau0=cfg0.tau0, step_cap=cfg0.step_cap,
-                  lam=cfg0.lam, mode=mode, grid=cfg0.grid, metric=cfg0.metric, sigma=cfg0.sigma)
+                  lam=cfg0.lam, mode=mode, grid=cfg0.grid, metric=cfg0.metric, sigma=cfg0.sigma,
+                  tol_coarse=cfg0.tol_coarse)
     for i in idx:
         ref[i] = O.op_A({i: O.pyramid(Fh[i], oc.levels), i + 1: O.pyramid(Fh[i + 1], oc.levels)}, i, i + 1, oc)
     out = {}
@@ -449,7 +452,8 @@ def three_levels(dev, mode: str, exec_: str, n_samples: int = 3):
     dt = time.perf_counter() - t0
     oc = O.Config(levels=3, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
                   tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
-                  lam=cfg.lam, mode=mode, grid=cfg.grid, metric=cfg.metric, sigma=cfg.sigma)
+                  lam=cfg.lam, mode=mode, grid=cfg.grid, metric=cfg.metric, sigma=cfg.sigma,
+                  tol_coarse=cfg.tol_coarse)
     Fh = frames.cpu().numpy()
     errs = []
     for i in [int(v) for v in np.linspace(0, N - 2, n_samples)]:
@@ -585,7 +589,8 @@ def mixed_measure(mode, dev, world, rank, dist, steps, warmup):
         oc = O.Config(levels=cfg0.levels, max_iter=cfg0.max_iter, max_rejects=cfg0.max_rejects,
                       tol_grad=cfg0.tol_grad, tol_rel_e=cfg0.tol_rel_e, armijo_c=cfg0.armijo_c, tau0=cfg0.tau0,
                       step_cap=cfg0.step_cap, lam=cfg0.lam, mode=mode, grid=cfg0.grid,
-                      metric=cfg0.metric, sigma=cfg0.sigma)
+                      metric=cfg0.metric, sigma=cfg0.sigma,
+                      tol_coarse=cfg0.tol_coarse)
         samples = [(S, 0, j) for S in (256, 512) if S in batches for j in (5, 77)]
         for storage in ("f32", "bf16", "f16"):
             ctx = B.Context(B.Config(mode=mode, storage=storage, cluster=16))

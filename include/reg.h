@@ -144,6 +144,9 @@ typedef struct {
                              per SM (80 or 64 registers a thread); 0 = auto (the autotuned value,
                              else 4 for 16-CTA operators and 3 below) */
     double sigma;         /* REG_METRIC_H1: smoothing length in control-grid spacings (>= 0; default 1) */
+    double tol_coarse;    /* stop at every level above the finest: tol_coarse x tol_grad (a coarse
+                             level only supplies the next level's initial guess); in [1, 1e6],
+                             default 10 */
 } reg_config_t;
 
 /* Scalar product of the nonrigid gradient flow [Sec. 2.3.1 takes the flow with respect to a

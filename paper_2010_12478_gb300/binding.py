@@ -57,7 +57,7 @@ class reg_config_t(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("storage", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("workers", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("grid", ctypes.c_int),
                 ("metric", ctypes.c_int), ("unroll", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("sigma", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("tol_coarse", ctypes.c_double)]
 
 
 class reg_stats_t(ctypes.Structure):
@@ -176,12 +176,14 @@ class Config:
     unroll: int = 0               # nonrigid energy passes: pixels per lane (2, 4); 0 = tuned or 4
     ctas_per_sm: int = 0          # nonrigid register form (3, 4); 0 = tuned or by CTAs per operator
     sigma: float = 1.0            # metric 2 (H1): smoothing length in control-grid spacings
+    tol_coarse: float = 10.0      # stop factor at every level above the finest
 
     def c(self) -> reg_config_t:
         return reg_config_t(RIGID if self.mode == "rigid" else NONRIGID, self.levels, self.max_iter,
                             self.max_rejects, self.tol_grad, self.tol_rel_e, self.armijo_c, self.tau0,
                             self.step_cap, self.lam, STORAGES[self.storage], self.cluster, self.workers,
-                            self.mem_budget, self.grid, self.metric, self.unroll, self.ctas_per_sm, self.sigma)
+                            self.mem_budget, self.grid, self.metric, self.unroll, self.ctas_per_sm, self.sigma,
+                            self.tol_coarse)
 
 
 def stats_dict(s: reg_stats_t, levels: int) -> dict:

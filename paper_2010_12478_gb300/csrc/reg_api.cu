@@ -364,6 +364,7 @@ extern "C" void reg_config_default(reg_config_t *c)
     c->tol_rel_e = 0.0;
     c->metric = REG_METRIC_GAUSS_NEWTON;
     c->sigma = 1.0;
+    c->tol_coarse = 10.0;
     c->armijo_c = 0.25;
     c->tau0 = 1.0;
     c->step_cap = 0.5;
@@ -392,6 +393,8 @@ static int validate_cfg(const reg_config_t &c)
     if (c.metric != REG_METRIC_MEAN && c.metric != REG_METRIC_GAUSS_NEWTON && c.metric != REG_METRIC_H1)
         return fail(REG_EINVAL, "metric %d", c.metric);
     if (!(c.sigma >= 0.0 && c.sigma <= 1.0e3)) return fail(REG_EINVAL, "sigma %g not in [0, 1000]", c.sigma);
+    if (!(c.tol_coarse >= 1.0 && c.tol_coarse <= 1.0e6))
+        return fail(REG_EINVAL, "tol_coarse %g not in [1, 1e6]", c.tol_coarse);
     if (c.unroll != 0 && c.unroll != 2 && c.unroll != 4) return fail(REG_EINVAL, "unroll %d not in {0,2,4}", c.unroll);
     if (c.ctas_per_sm != 0 && c.ctas_per_sm != 3 && c.ctas_per_sm != 4)
         return fail(REG_EINVAL, "ctas_per_sm %d not in {0,3,4}", c.ctas_per_sm);
@@ -558,6 +561,7 @@ Config dev_config(const reg_config_t &c)
     d.lambda = c.lambda;
     d.metric = c.metric;
     d.sigma = c.sigma;
+    d.tol_coarse = c.tol_coarse;
     return d;
 }
 

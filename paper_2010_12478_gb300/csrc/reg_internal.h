@@ -76,6 +76,7 @@ struct Config {
     double tol_grad, tol_rel_e, armijo_c, tau0, step_cap, lambda;
     int metric;   // nonrigid scalar product: REG_METRIC_MEAN, REG_METRIC_GAUSS_NEWTON or REG_METRIC_H1
     double sigma; // REG_METRIC_H1: smoothing length in control-grid spacings
+    double tol_coarse;   // factor on tol_grad at every level above the finest
 };
 
 // Ready-queue state of the persistent executor (device memory): one FIFO per priority class,

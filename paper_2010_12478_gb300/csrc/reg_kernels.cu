@@ -93,6 +93,7 @@ struct RigidCtl {
     double a, b, rbar, tbar;       // NCC terms at th
     double ta, tb, trbar, ttbar;   // at the trial point tt
     int nrej, iters, evals, stop, rejects, have_prev;
+    double tolg;   // the level's stop tolerance (tol_grad, times tol_coarse above the finest level)
 };
 
 struct FieldCtl {
@@ -101,6 +102,7 @@ struct FieldCtl {
     double ta, tb, trbar, ttbar;  // at the trial field
     int degen, tdegen;
     int nrej, iters, evals, stop, rejects, have_prev;
+    double tolg;   // the level's stop tolerance (tol_grad, times tol_coarse above the finest level)
 };
 
 // First trial of a line search after an accepted step (Barzilai and Borwein, "Two-point step size
@@ -658,7 +660,7 @@ __device__ int rigid_step(RigidCtl &k, const Config &cfg, const double *tot, int
         k.slope = g[0] * k.d[0] + g[1] * k.d[1] + g[2] * k.d[2];
         // |g|_M = sqrt(-slope); the tests compare squares (no square root unless the cap applies)
         const double gn2 = -k.slope;
-        if (!(gn2 >= cfg.tol_grad * cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
+        if (!(gn2 >= k.tolg * k.tolg)) { k.stop = REG_STOP_GRAD; return kActDone; }
         if (k.have_prev) {
             double num = 0.0, den = 0.0;
             for (int q = 0; q < 3; ++q) {
@@ -757,6 +759,8 @@ __device__ void run_rigid(const Params &p, const OpDesc &op, int op_index, Smem 
             k.tau = cfg.tau0;
             k.have_prev = 0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
+            // a coarse level only supplies the next level's initial guess: a looser stop
+            k.tolg = cfg.tol_grad * (l > 0 ? cfg.tol_coarse : 1.0);
             rigid_params(k.th, sm.pm);
             sm.action = kActEnergy;
         }
@@ -1580,7 +1584,7 @@ __device__ int field_step(FieldCtl &k, const Config &cfg, const double *tot, int
         // |g| = sqrt(ss / Nc) and the largest control step dmax = sqrt(tot[1]): compared squared
         const double ss = tot[0], dmax2 = tot[1];
         k.slope = -ss * k.invNc;
-        if (!(ss * k.invNc >= cfg.tol_grad * cfg.tol_grad)) { k.stop = REG_STOP_GRAD; return kActDone; }
+        if (!(ss * k.invNc >= k.tolg * k.tolg)) { k.stop = REG_STOP_GRAD; return kActDone; }
         // the metric (mean over control points) is a common factor of tot[2] and tot[3]
         if (k.have_prev) k.tau = bb_tau(k.tau, k.tau_acc, tot[2], tot[3]);
         if (k.tau * k.tau * dmax2 > cfg.step_cap * cfg.step_cap) k.tau = cfg.step_cap / sqrt(dmax2);
@@ -1693,6 +1697,8 @@ __device__ void run_nonrigid(const Params &p, const OpDesc &op, int op_index, Sm
             k.tau_pend = 0.0;
             k.have_prev = 0;
             k.iters = 0; k.evals = 0; k.stop = REG_STOP_MAXIT;
+            // a coarse level only supplies the next level's initial guess: a looser stop
+            k.tolg = cfg.tol_grad * (l > 0 ? cfg.tol_coarse : 1.0);
             sm.action = kActEnergy;
         }
         for (;;) {

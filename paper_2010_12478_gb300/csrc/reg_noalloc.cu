@@ -206,6 +206,7 @@ extern "C" int reg_pairwise_noalloc(const reg_config_t *cfg, int device, const f
         p.cfg.max_iter = cfg->max_iter;
         p.cfg.max_rejects = cfg->max_rejects;
         p.cfg.tol_grad = cfg->tol_grad;
+        p.cfg.tol_coarse = cfg->tol_coarse;
         p.cfg.tol_rel_e = cfg->tol_rel_e;
         p.cfg.armijo_c = cfg->armijo_c;
         p.cfg.tau0 = cfg->tau0;

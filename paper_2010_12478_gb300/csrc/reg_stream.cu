@@ -133,6 +133,7 @@ Params stream_params(reg_stream *s)
     p.cfg.max_iter = c.max_iter;
     p.cfg.max_rejects = c.max_rejects;
     p.cfg.tol_grad = c.tol_grad;
+    p.cfg.tol_coarse = c.tol_coarse;
     p.cfg.tol_rel_e = c.tol_rel_e;
     p.cfg.armijo_c = c.armijo_c;
     p.cfg.tau0 = c.tau0;

@@ -34,7 +34,8 @@ def ocfg(cfg: B.Config) -> O.Config:
     return O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
                     tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
                     lam=cfg.lam, mode=cfg.mode, grid=cfg.grid, metric=cfg.metric,
-                    sigma=cfg.sigma)
+                    sigma=cfg.sigma,
+                    tol_coarse=cfg.tol_coarse)
 
 
 def rel(a, b):

@@ -69,7 +69,8 @@ def test_stream_equals_sequential_scan_and_oracle(mode):
         assert res[i]["status"] == 0 and res[i]["done_us"] >= res[i]["submit_us"]
     oc = O.Config(levels=cfg.levels, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
                   tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
-                  lam=cfg.lam, mode=cfg.mode, metric=cfg.metric, sigma=cfg.sigma)
+                  lam=cfg.lam, mode=cfg.mode, metric=cfg.metric, sigma=cfg.sigma,
+                  tol_coarse=cfg.tol_coarse)
     ref = O.scan(F, oc, O.dag_sequential(11))
     if mode == "rigid":
         for i, o in enumerate(ref):

@@ -51,6 +51,8 @@ def test_struct_layouts_match_header(lib):
     assert cfg.unroll == 0 and cfg.ctas_per_sm == 0 and B.Config().c().unroll == 0
     # the H1 product's smoothing length
     assert cfg.sigma == O.Config().sigma == B.Config().sigma == 1.0
+    # the coarse levels' stop factor
+    assert cfg.tol_coarse == O.Config().tol_coarse == B.Config().tol_coarse == 10.0
 
 
 def test_errors_without_gpu_are_reported_not_crashing(lib):
@@ -66,7 +68,7 @@ def test_errors_without_gpu_are_reported_not_crashing(lib):
     bad.levels = 9
     assert lib.reg_ctx_create(ctypes.byref(bad), 0, ctypes.byref(h)) == B.REG_EINVAL
     assert b"levels" in lib.reg_last_error_message()
-    for field, value in (("unroll", 3), ("ctas_per_sm", 2), ("metric", 3), ("sigma", -1.0)):
+    for field, value in (("unroll", 3), ("ctas_per_sm", 2), ("metric", 3), ("sigma", -1.0), ("tol_coarse", 0.5)):
         bad = B.reg_config_t()
         lib.reg_config_default(ctypes.byref(bad))
         setattr(bad, field, value)
