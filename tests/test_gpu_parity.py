@@ -302,6 +302,25 @@ def test_h1_pairwise_at_512_matches_oracle():
     assert O.max_px_error(fo.cpu().numpy(), o.phi, 512, 512, "nonrigid") <= PX_TOL
 
 
+@pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
+def test_scan_c1_with_the_coarse_stop_factor_one_matches_oracle(mode):
+    """tol_coarse reaches both controllers: with factor 1 (every level to tol_grad) the scan still
+    matches the oracle run with the same factor."""
+    F = c1_frames(6)
+    cfg = B.Config(mode=mode, tol_coarse=1.0, cluster=4)
+    ctx = B.Context(cfg)
+    n = len(F) - 1
+    if mode == "rigid":
+        els, _ = ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung", exec="persistent")
+    else:
+        fo = torch.zeros((n, 2, 128, 128), device="cuda")
+        els, _ = ctx.scan(torch.from_numpy(F).cuda(), schedule="brent_kung", exec="persistent", fields_out=fo)
+    ref = oracle_scan(F, cfg, "brent_kung")
+    for i, o in enumerate(ref):
+        got = np.array(els[i][2:]) if mode == "rigid" else fo[i].cpu().numpy()
+        assert O.max_px_error(got, o.phi, 128, 128, mode) <= PX_TOL, (i, mode)
+
+
 def test_scan_two_frames():
     F = c1_frames(2)
     ctx = B.Context(B.Config())
