@@ -533,7 +533,8 @@ def mixed_batch(args, dev, world, rank, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"c4: {WORKLOAD_TEXT['c4']}", "series": 64, "frames_per_series": 128,
                        "sizes": sizes, "mode": args.mode,
-                       "exec": "persistent (one reg_scan_batch per size)", "cluster": 16,
+                       "exec": "persistent (one reg_scan_batch per size)",
+                       "cluster": {str(S): C4_SHAPE[S][0] for S in C4_SHAPE},
                        "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "precision": results, "clocks": clocks,
@@ -542,6 +543,12 @@ def mixed_batch(args, dev, world, rank, dist):
                     "baselines are reported on the c2 and c3 workloads",
             "gpu_launches": None}
         print(json.dumps(line), flush=True)
+
+
+# CTAs per operator and register form for each frame size of c4 (measured on the batched scans:
+# 4 / 3 CTAs per SM for 256^2, 8 / 4 for 512^2, 16 / 3 for 1024^2 took the whole batch from
+# 4,086 to 4,670 frames/s against 16 CTAs for every size)
+C4_SHAPE = {256: (4, 3), 512: (8, 4), 1024: (16, 3)}
 
 
 def mixed_measure(mode, dev, world, rank, dist, steps, warmup):
@@ -566,7 +573,8 @@ def mixed_measure(mode, dev, world, rank, dist, steps, warmup):
     results = {}
     with ClockSampler(0 if dev.index is None else dev.index) as clk:
         for storage in ("f32", "bf16", "f16"):
-            ctxs = {S: B.Context(B.Config(mode=mode, storage=storage, cluster=16)) for S in batches}
+            ctxs = {S: B.Context(B.Config(mode=mode, storage=storage, cluster=C4_SHAPE[S][0], ctas_per_sm=C4_SHAPE[S][1]))
+                    for S in batches}
             for S, b in batches.items():   # warm-up
                 for _ in range(max(1, warmup)):
                     ctxs[S].scan_batch(b, exec="persistent", want_stats=False)
@@ -817,7 +825,8 @@ def main():
         # ---- c4: 64 series of mixed sizes, one batched scan per size, three storage types
         c4_res, c4_sizes, _ = mixed_measure(args.mode, dev, world, rank, dist, 1, 1)
         c4 = {"workload": f"c4: {WORKLOAD_TEXT['c4']}", "sizes": c4_sizes, "storage": c4_res,
-              "exec": "persistent (one reg_scan_batch per size), 16 CTAs per operator"}
+              "exec": "persistent (one reg_scan_batch per size)",
+              "shape_per_size": {str(S): {"cluster": v[0], "ctas_per_sm": v[1]} for S, v in C4_SHAPE.items()}}
         # ---- the nonrigid flow's scalar products on the same workload (Sec. 2.3.1 leaves it open)
         if args.mode == "nonrigid":
             sprod = {}
