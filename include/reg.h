@@ -218,7 +218,10 @@ int reg_pairwise(reg_ctx_t *ctx, const float *R, const float *T, int W, int H, i
 
 /* Register all frames to f_0 by the scan [Sec. 3]: the N-1 neighbour
  * operators A(f_{i-1}, f_i), then B along the DAG of `schedule`.
- *   frames     fp32 [N][H][pitch], host or device (host frames are copied in).
+ *   frames     fp32 [N][H][pitch], host or device.  Host frames are staged on the device:
+ *              page-locked memory mapped at the same address (cudaHostAlloc, or
+ *              torch's pin_memory) is read over the CPU-GPU link by a copy kernel,
+ *              other host memory is copied by cudaMemcpyAsync.
  *   out        N-1 elements phi_{0,1}..phi_{0,N-1} (host or device).
  *   fields_out REG_NONRIGID: [N-1][2][H][W] fp32 (host or device), or NULL to skip
  *              the dense fields (reg_scan_grids then gives the control values).
@@ -457,7 +460,9 @@ typedef struct {
     int32_t cluster;           /* launch shape of the last operator launch: CTAs per operator, */
     int32_t unroll;            /* energy-pass pixels per lane (0 for REG_RIGID), */
     int32_t ctas_per_sm;       /* and the register form (CTAs per SM it is sized for) */
-    int32_t reserved;
+    int32_t h2d_path;          /* host frames staged by: 0 none (device frames), 1 cudaMemcpyAsync,
+                                  2 the SMs reading mapped page-locked memory */
+    double  h2d_ms;            /* with timing: device time of that staging (0 for device frames) */
 } reg_timing_t;
 
 /* Enable (1) or disable (0) event timing of the kernels launched by later calls. */

@@ -73,7 +73,8 @@ class reg_timing_t(ctypes.Structure):
                 ("graph_captures", ctypes.c_int32), ("tma_staged", ctypes.c_int32),
                 ("leaf_ops", ctypes.c_int32), ("dag_ops", ctypes.c_int32),
                 ("leaf_ms", ctypes.c_double), ("dag_ms", ctypes.c_double), ("cluster", ctypes.c_int32),
-                ("unroll", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("unroll", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("h2d_path", ctypes.c_int32),
+                ("h2d_ms", ctypes.c_double)]
 
 
 class reg_result_t(ctypes.Structure):
@@ -192,6 +193,16 @@ def stats_dict(s: reg_stats_t, levels: int) -> dict:
                 theta=list(s.theta))
 
 
+def elems_list(elems):
+    """reg_elem_t records as (i, k, alpha, gx, gy) tuples (None passes through)."""
+    return [(e.i, e.k, e.alpha, e.gx, e.gy) for e in elems] if elems is not None else None
+
+
+def stats_list(stats, levels: int):
+    """reg_stats_t records as dicts (None passes through)."""
+    return [stats_dict(s, levels) for s in stats] if stats is not None else None
+
+
 def scan_work(schedule: str, n: int) -> int:
     return lib().reg_scan_work(SCHEDULES[schedule], n)
 
@@ -257,7 +268,8 @@ class Context:
         return dict(op_launches=t.op_launches, pyramid_launches=t.pyramid_launches,
                     op_kernel_ms=t.op_kernel_ms, pyramid_ms=t.pyramid_ms, graph_captures=t.graph_captures,
                     tma_staged=t.tma_staged, leaf_ops=t.leaf_ops, dag_ops=t.dag_ops, leaf_ms=t.leaf_ms,
-                    dag_ms=t.dag_ms, cluster=t.cluster, unroll=t.unroll, ctas_per_sm=t.ctas_per_sm)
+                    dag_ms=t.dag_ms, cluster=t.cluster, unroll=t.unroll, ctas_per_sm=t.ctas_per_sm,
+                    h2d_path=t.h2d_path, h2d_ms=t.h2d_ms)
 
     # ---- operators
     def pairwise(self, R, T, init: Optional[Sequence[float]] = None, field_in=None, field_out=None,
@@ -278,8 +290,10 @@ class Context:
         return (out.i, out.k, out.alpha, out.gx, out.gy), stats_dict(st, self.cfg.levels)
 
     def scan(self, frames, schedule: str = "brent_kung", exec: str = "level", fields_out=None,
-             out_elems=None, want_stats: bool = True, stream=None, split: bool = False):
-        """reg_scan; split=True runs every A leaf before the first B and times the phases apart."""
+             out_elems=None, want_stats: bool = True, stream=None, split: bool = False, raw: bool = False):
+        """reg_scan; split=True runs every A leaf before the first B and times the phases apart.
+        raw=True returns the host arrays as reg_scan filled them (reg_elem_t and reg_stats_t
+        records); elems_list() and stats_list() convert them later."""
         N, H, W = frames.shape
         n = N - 1
         m = scan_work(schedule, n)
@@ -289,13 +303,14 @@ class Context:
         ex = EXECS[exec] | (SPLIT_PHASES if split else 0)
         check(lib().reg_scan(self.h, _ptr(frames), N, W, H, W, SCHEDULES[schedule], ex, out_ptr,
                              _ptr(fields_out), stats, _stream(stream)), "reg_scan")
-        el = [(e.i, e.k, e.alpha, e.gx, e.gy) for e in elems] if elems is not None else None
-        st = [stats_dict(s, self.cfg.levels) for s in stats] if stats is not None else None
-        return el, st
+        if raw:
+            return elems, stats
+        return elems_list(elems), stats_list(stats, self.cfg.levels)
 
     def scan_batch(self, frames, schedule: str = "brent_kung", exec: str = "persistent", fields_out=None,
-                   want_stats: bool = True, stream=None):
-        """S series [S, N, H, W] in one call; returns per-series element lists and stats."""
+                   want_stats: bool = True, stream=None, raw: bool = False):
+        """S series [S, N, H, W] in one call; returns per-series element lists and stats
+        (raw=True: the host arrays reg_scan_batch filled, series after series)."""
         S, N, H, W = frames.shape
         n = N - 1
         m = scan_work(schedule, n)
@@ -304,6 +319,8 @@ class Context:
         check(lib().reg_scan_batch(self.h, _ptr(frames), S, N, W, H, W, SCHEDULES[schedule], EXECS[exec],
                                    ctypes.addressof(elems), _ptr(fields_out), stats, _stream(stream)),
               "reg_scan_batch")
+        if raw:
+            return elems, stats
         el = [[(e.i, e.k, e.alpha, e.gx, e.gy) for e in elems[q * n:(q + 1) * n]] for q in range(S)]
         st = None
         if stats is not None:

@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>   // cuPointerGetAttribute's types (resolved at run time)
+
 #include "reg_internal.h"
 #include "reg_host.h"
 
@@ -113,6 +115,42 @@ bool is_device_ptr(const void *p)
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+using PointerAttrFn = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+PointerAttrFn pointer_attr_fn()
+{
+    static PointerAttrFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (PointerAttrFn) nullptr;
+        }
+        return (PointerAttrFn)f;
+    }();
+    return fn;
+}
+
+// p when [p, p + bytes) lies in one page-locked host allocation that the current device reads
+// at the same address (mapped under unified addressing), else null.
+const void *mapped_host_ptr(const void *p, size_t bytes)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || a.devicePointer != p) return nullptr;
+    PointerAttrFn fn = pointer_attr_fn();
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (!fn || fn(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)p) != CUDA_SUCCESS ||
+        fn(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)p) != CUDA_SUCCESS)
+        return nullptr;
+    const uintptr_t b = (uintptr_t)p;
+    return b >= start && b - start <= size && bytes <= size - (b - start) ? p : nullptr;
 }
 
 size_t storage_bytes(int storage) { return storage == REG_F32 ? 4 : 2; }
@@ -347,6 +385,7 @@ struct reg_ctx {
     std::vector<cudaEvent_t> tev;   // timing events, used in pairs
     size_t tev_used = 0;
     std::vector<std::pair<int, int>> op_pairs, pyr_pairs;
+    std::pair<int, int> h2d_pair = {-1, -1};   // copy of host frames to the device
     size_t split_from = 0, split_at = 0;   // REG_EXEC_SPLIT_PHASES: op_pairs [from, at) = A, [at, end) = B
     bool split = false;
     reg_timing_t last = {};
@@ -463,6 +502,7 @@ void timing_reset(reg_ctx *ctx)
     ctx->pyr_pairs.clear();
     ctx->split = false;
     ctx->split_from = ctx->split_at = 0;
+    ctx->h2d_pair = {-1, -1};
     memset(&ctx->last, 0, sizeof(ctx->last));
 }
 
@@ -493,6 +533,7 @@ void timing_resolve(reg_ctx *ctx)
     };
     ctx->last.op_kernel_ms = sum(ctx->op_pairs);
     ctx->last.pyramid_ms = sum(ctx->pyr_pairs);
+    ctx->last.h2d_ms = sum(std::vector<std::pair<int, int>>{ctx->h2d_pair});
     if (ctx->split) {
         std::vector<std::pair<int, int>> a(ctx->op_pairs.begin() + ctx->split_from, ctx->op_pairs.begin() + ctx->split_at);
         std::vector<std::pair<int, int>> b(ctx->op_pairs.begin() + ctx->split_at, ctx->op_pairs.end());
@@ -1171,7 +1212,16 @@ int scan_impl(reg_ctx_t *ctx, const float *frames, int S, int N, int W, int H, i
     if (!is_device_ptr(frames)) {
         size_t bytes = sizeof(float) * (size_t)NF * H * pitch;
         CHECK(ctx->frames_dev.reserve(bytes));
-        CU(cudaMemcpyAsync(ctx->frames_dev.ptr, frames, bytes, cudaMemcpyHostToDevice, s));
+        const int c0 = timing_mark(ctx, s);
+        const void *mapped = mapped_host_ptr(frames, bytes);
+        if (mapped && bytes % 16 == 0 && (uintptr_t)mapped % 16 == 0) {
+            CU(launch_stage_copy(ctx->frames_dev.ptr, mapped, bytes, 8 * ctx->num_sms, s));
+            ctx->last.h2d_path = 2;
+        } else {
+            CU(cudaMemcpyAsync(ctx->frames_dev.ptr, frames, bytes, cudaMemcpyHostToDevice, s));
+            ctx->last.h2d_path = 1;
+        }
+        ctx->h2d_pair = {c0, timing_mark(ctx, s)};
         dframes = ctx->frames_dev.as<float>();
     }
     CHECK(build_pyramids(ctx, g, dframes, NF, (size_t)H * pitch, pitch, 0, NF, s));

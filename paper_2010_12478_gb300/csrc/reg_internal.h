@@ -157,6 +157,9 @@ struct WarpJob {
 size_t warp_workspace_bytes(int N, int W, int H, bool mean);
 // *used_tma = 1 when the source boxes were staged by TMA (aligned frames, pitch % 4 == 0).
 cudaError_t launch_warp(const WarpJob &j, cudaStream_t s, int *used_tma);
+// dst (device) = bytes of src, host memory the device reads at the same address; both 16-byte
+// aligned, bytes a multiple of 16 (else cudaErrorInvalidValue).  `blocks` CTAs of 256 threads.
+cudaError_t launch_stage_copy(void *dst, const void *src, size_t bytes, int blocks, cudaStream_t s);
 cudaError_t launch_grid_gather(const float2 *src, const int *nodes, int n, int Nc, float2 *dst, cudaStream_t s);
 cudaError_t launch_energy(const Params &p, int storage, const double *theta_dev,
                           const float2 *grid_dev, double *out_dev, float2 *grad_dev,

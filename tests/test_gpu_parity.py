@@ -206,6 +206,36 @@ def test_scan_host_frames_equal_device_frames():
     assert a == b
 
 
+@pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
+def test_scan_staging_paths_agree(mode):
+    # device frames (no staging), page-locked frames (the SMs read them over the link: also a view
+    # that starts inside its allocation), pageable frames, and page-locked frames whose size or
+    # start is not a multiple of 16 bytes (both cudaMemcpyAsync) give bit-identical scans
+    ctx = B.Context(B.Config(mode=mode, cluster=2))
+    ctx.set_timing(True)
+    cases = []
+    spec = synth.spec_c1()
+    spec.n_frames, spec.H, spec.W = 7, 67, 93        # 7 * 67 * 93 * 4 bytes: not a multiple of 16
+    odd = synth.make_series(spec).frames
+    F = torch.from_numpy(c1_frames(9))
+    pinned = torch.empty((11,) + F.shape[1:], pin_memory=True)
+    pinned[2:] = F
+    flat = torch.empty(F.numel() + 1, pin_memory=True)
+    flat[1:] = F.reshape(-1)
+    for frames, path in ((F.cuda(), 0), (F.clone().pin_memory(), 2), (pinned[2:], 2), (F.numpy(), 1),
+                         (flat[1:].view(F.shape), 1)):
+        el, st = ctx.scan(frames, exec="persistent")
+        t = ctx.last_timing()
+        assert t["h2d_path"] == path
+        assert (t["h2d_ms"] > 0) == (path > 0)
+        cases.append((el, [x["evals"] for x in st]))
+    assert all(c == cases[0] for c in cases[1:])
+    a, _ = ctx.scan(odd.cuda(), exec="persistent")
+    b, _ = ctx.scan(odd.pin_memory(), exec="persistent")
+    assert ctx.last_timing()["h2d_path"] == 1
+    assert a == b
+
+
 def test_scan_is_deterministic_and_independent_of_executor():
     F = c1_frames(12)
     ctx = B.Context(B.Config(cluster=2))

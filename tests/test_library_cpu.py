@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header(lib):
     assert ctypes.sizeof(B.reg_elem_t) == 20          # 20-byte scan element (Sec. 5)
     assert ctypes.sizeof(B.reg_stats_t) == 144
-    assert ctypes.sizeof(B.reg_timing_t) == 72
+    assert ctypes.sizeof(B.reg_timing_t) == 80
     cfg = B.reg_config_t()
     lib.reg_config_default(ctypes.byref(cfg))
     assert cfg.levels == 2 and cfg.mode == B.RIGID and cfg.storage == B.F32
