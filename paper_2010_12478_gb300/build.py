@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
-SOURCES = ["reg_kernels.cu", "reg_api.cu", "reg_stream.cu", "reg_noalloc.cu", "reg_warp.cu"]
+SOURCES = ["reg_kernels.cu", "reg_api.cu", "reg_stream.cu", "reg_noalloc.cu", "reg_warp.cu", "reg_stage.cu"]
 
 
 def _nvcc() -> str:
