@@ -575,6 +575,13 @@ def test_scan_batch_equals_per_series_scans(exec_):
                 g1 = torch.zeros((6, ny, nx, 2), device="cuda")
                 ctx.scan_grids(g1)
                 assert torch.equal(g1, gb[q])
+        # the same batch from page-locked host memory (staged by the SMs)
+        ctx.set_timing(True)
+        els_h, st_h = ctx.scan_batch(Fb.cpu().pin_memory(), schedule="brent_kung", exec=exec_)
+        assert ctx.last_timing()["h2d_path"] == 2
+        ctx.set_timing(False)
+        assert els_h == els_b
+        assert [[s["energy"] for s in x] for x in st_h] == [[s["energy"] for s in x] for x in st_b]
 
 
 def test_pitched_frames_and_odd_grid_spacing_through_the_c_abi():
