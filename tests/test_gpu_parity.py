@@ -703,14 +703,17 @@ def test_node_grids_end_with_a_pairwise_call():
     assert e.value.code == B.REG_ESTATE
 
 
-def test_c3_full_size_nonrigid_sampled_operators_match_oracle():
-    # the 4,096-frame nonrigid scan through the persistent device queue; the B operators with the
-    # largest drift between their frames (prefixes f_0 -> f_k far down the series, where part of f_0
-    # has no counterpart in f_k) and random ones, against the oracle fed the GPU's exact inputs
+@pytest.mark.parametrize("cluster,ctas_per_sm", [(4, 3), (8, 4)])
+def test_c3_full_size_nonrigid_sampled_operators_match_oracle(cluster, ctas_per_sm):
+    # the 4,096-frame nonrigid scan through the persistent device queue, in both launch shapes the
+    # autotuner chooses between on this workload (4 CTAs per operator with the 80-register form, 8
+    # with the 64-register form); the B operators with the largest drift between their frames
+    # (prefixes f_0 -> f_k far down the series, where part of f_0 has no counterpart in f_k) and
+    # random ones, against the oracle fed the GPU's exact inputs
     spec = synth.spec_c3()
     ser = synth.make_series(spec, device="cuda")
     frames = ser.frames
-    cfg = B.Config(mode="nonrigid", cluster=4)
+    cfg = B.Config(mode="nonrigid", cluster=cluster, ctas_per_sm=ctas_per_sm, unroll=4)
     oc = ocfg(cfg)
     ctx = B.Context(cfg)
     n = spec.n_frames - 1
