@@ -167,6 +167,21 @@ def algorithmic_bytes(stats, H, W, levels, storage_bytes, mode):
     return total
 
 
+def pyramid_bytes(N, H, W, levels, storage_bytes, mode):
+    """Bytes the pyramid build must move per step: each frame read once, and each stored level
+    (with its 3-sample border in the nonrigid model) and each stored B-spline model at the pixel
+    centres (nonrigid) written once."""
+    pad = 3 if mode == "nonrigid" else 0
+    total = 4.0 * H * W
+    h, w = H, W
+    for _ in range(levels):
+        total += storage_bytes * (w + 2 * pad) * (h + 2 * pad)
+        if mode == "nonrigid":
+            total += storage_bytes * w * h
+        h, w = (h + 1) // 2, (w + 1) // 2
+    return N * total
+
+
 def profile_traffic(name: str, src: str, key: str):
     """A DRAM-traffic figure from a committed ncu summary (profiles/<name>.md), if that summary
     was taken on the current kernel source (its sha256 prefix); else None."""
@@ -745,6 +760,15 @@ def main():
     traffic = profile_traffic(f"{kname}_{args.workload}_{args.mode}", "reg_kernels.cu",
                               "dram bytes per step (scaled)") if N == WORKLOAD_FRAMES[args.workload] else None
     gpu_launches = int(sum(t["op_launches"] + t["pyramid_launches"] for t in tim))
+    # the pyramid build (its kernels' event time within the same steps)
+    pyr_ms = sum(t["pyramid_ms"] for t in tim) / len(tim)
+    pyr_alg = pyramid_bytes(N, H, W, cfg.levels, sb, cfg.mode)
+    pyr_gbs = pyr_alg / (pyr_ms / 1e3) / 1e9 if pyr_ms > 0 else 0.0
+    pyramid = {"bound": "hbm", "achieved": round(pyr_gbs, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(pyr_gbs / peak, 4), "ms_per_step": round(pyr_ms, 3),
+               "launches_per_step": sum(t["pyramid_launches"] for t in tim) / len(tim),
+               "algorithmic_bytes_per_step": pyr_alg,
+               "note": "frames read once, stored levels (with border) and B-spline models written once"}
     ev = np.array([sum(s["evals"]) for s in st_list[0]])
     nl = N - 1
     ev_a, ev_b = ev[:nl], ev[nl:]
@@ -895,6 +919,7 @@ def main():
                          "caveat": "issue-bound, not DRAM-bound: the two pyramids of an operator stay in L2 "
                                    "(see the committed ncu summaries); the algorithmic bytes are read from L2 "
                                    "many times over"},
+            "pyramid_roofline": pyramid,
             "forms": forms,
             "phases": phases,
             "imbalance": imbalance,

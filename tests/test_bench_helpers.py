@@ -21,6 +21,16 @@ def test_algorithmic_bytes_counts_two_levels_per_evaluation():
     assert bench.algorithmic_bytes([{"evals": [1, 1]}], 5, 7, 2, 2, "rigid") == 2 * 2 * 35 + 2 * 2 * 12
 
 
+def test_pyramid_bytes_by_hand():
+    # rigid, fp32, 2 levels of 4 x 6: frame read 4*24, levels 4*24 + 4*6 (2 x 3) written
+    assert bench.pyramid_bytes(1, 4, 6, 2, 4, "rigid") == 4 * 24 + 4 * 24 + 4 * 6
+    # nonrigid, 2-byte storage, one level of 5 x 7 on 3 frames: frame read 4*35, the level with its
+    # 3-sample border (11 x 13) and the model at the pixel centres (5 x 7) written
+    assert bench.pyramid_bytes(3, 5, 7, 1, 2, "nonrigid") == 3 * (4 * 35 + 2 * 11 * 13 + 2 * 35)
+    # odd sizes round the coarser level up: 5 x 7 -> 3 x 4
+    assert bench.pyramid_bytes(1, 5, 7, 2, 4, "rigid") == 4 * 35 + 4 * 35 + 4 * 12
+
+
 def test_profile_traffic_is_used_only_for_the_profiled_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     src = tmp_path / "paper_2010_12478_gb300" / "csrc"
