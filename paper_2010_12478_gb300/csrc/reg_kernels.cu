@@ -2052,14 +2052,32 @@ __global__ void __launch_bounds__(kThreads) energy_kernel(Params p, const double
 // ================================================================== pyramid
 // All kernels take a batch of frames (grid.z or grid.x = frame).  Level pointers address pixel
 // (0, 0) of frame 0; rows are `pitch` elements apart and frames `stride` elements apart.
+// Level 0 in storage type: a CTA of kL0Threads covers kL0Rows rows of kL0Cols columns, each thread
+// kL0Rows x (kL0Cols / kL0Threads) samples with every load issued before the first store.
+constexpr int kL0Threads = 256, kL0Rows = 4, kL0Cols = 1024;
 template <typename S>
-__global__ void pyr_level0(const float *frames, size_t fstride, int W, int H, int pitch, S *out, size_t ostride,
-                           int opitch)
+__global__ void __launch_bounds__(kL0Threads) pyr_level0(const float *frames, size_t fstride, int W, int H,
+                                                         int pitch, S *out, size_t ostride, int opitch)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-    const size_t f = blockIdx.z;
-    if (c < W && r < H)
-        out[f * ostride + (size_t)r * opitch + c] = toS<S>(__ldg(frames + f * fstride + (size_t)r * pitch + c));
+    constexpr int CB = kL0Cols / kL0Threads;
+    const int c0 = blockIdx.x * kL0Cols + threadIdx.x, r0 = blockIdx.y * kL0Rows;
+    const float *src = frames + blockIdx.z * fstride;
+    S *dst = out + blockIdx.z * ostride;
+    float v[kL0Rows][CB];
+#pragma unroll
+    for (int i = 0; i < kL0Rows; ++i)
+#pragma unroll
+        for (int j = 0; j < CB; ++j) {
+            const int r = r0 + i, c = c0 + j * kL0Threads;
+            v[i][j] = r < H && c < W ? __ldg(src + (size_t)r * pitch + c) : 0.f;
+        }
+#pragma unroll
+    for (int i = 0; i < kL0Rows; ++i)
+#pragma unroll
+        for (int j = 0; j < CB; ++j) {
+            const int r = r0 + i, c = c0 + j * kL0Threads;
+            if (r < H && c < W) dst[(size_t)r * opitch + c] = toS<S>(v[i][j]);
+        }
 }
 
 // Level l+1 from level l: 2x2 box average, last odd row/column clamped.
@@ -2104,20 +2122,31 @@ __global__ void pyr_border(S *lvl, size_t stride, int W, int H, int pad, const f
 // The quadratic B-spline model at the pixel centres: the separable filter (1/8, 3/4, 1/8) of a
 // bordered level (its border, the level's mean, supplies the outer taps), with the operations of
 // sample_q at a zero offset, so that a frame registered to itself matches bit for bit.  Written
-// as a plain W x H level.
+// as a plain W x H level.  A thread walks kSmoothRows rows down one column and carries the
+// horizontal filter of the rows above and at the current one, so each output row reads one row
+// of three taps.
+constexpr int kSmoothRows = 16;
 template <typename S>
 __global__ void pyr_smooth(const S *src, size_t sstride, int spitch, int W, int H, S *dst, size_t dstride)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-    if (c >= W || r >= H) return;
-    const S *p = src + blockIdx.z * sstride + (size_t)r * spitch + c;
-    float row[3];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, r0 = blockIdx.y * kSmoothRows;
+    if (c >= W || r0 >= H) return;
+    const S *p = src + blockIdx.z * sstride + (ptrdiff_t)r0 * spitch + c;
+    S *q = dst + blockIdx.z * dstride + (size_t)r0 * W + c;
+    // the horizontal filter of row r0 + k of the bordered level (k = -1 .. kSmoothRows)
+    auto hrow = [&](int k) {
+        const S *x = p + (ptrdiff_t)k * spitch;
+        return fmaf(0.125f, ldS<S>(x + 1), fmaf(0.75f, ldS<S>(x), 0.125f * ldS<S>(x - 1)));
+    };
+    float a = hrow(-1), b = hrow(0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const S *q = p + (ptrdiff_t)(k - 1) * spitch;
-        row[k] = fmaf(0.125f, ldS<S>(q + 1), fmaf(0.75f, ldS<S>(q), 0.125f * ldS<S>(q - 1)));
+    for (int k = 0; k < kSmoothRows; ++k) {
+        if (r0 + k >= H) break;
+        const float d = hrow(k + 1);
+        q[(size_t)k * W] = toS<S>(fmaf(0.125f, d, fmaf(0.75f, b, 0.125f * a)));
+        a = b;
+        b = d;
     }
-    dst[blockIdx.z * dstride + (size_t)r * W + c] = toS<S>(fmaf(0.125f, row[2], fmaf(0.75f, row[1], 0.125f * row[0])));
 }
 
 // Mean of one level of each frame (one CTA per frame), deterministic float-float sum.
@@ -2222,8 +2251,8 @@ static cudaError_t pyramid_t(const float *frames, int N, size_t fstride, int W, 
         w = (w + 1) / 2;
         h = (h + 1) / 2;
     }
-    pyr_level0<S><<<dim3((W + 127) / 128, H, N), 128, 0, s>>>(frames, fstride, W, H, pitch, lv[0], o.raw_stride[0],
-                                                              level_pitch(W, o.pad));
+    pyr_level0<S><<<dim3((W + kL0Cols - 1) / kL0Cols, (H + kL0Rows - 1) / kL0Rows, N), kL0Threads, 0, s>>>(
+        frames, fstride, W, H, pitch, lv[0], o.raw_stride[0], level_pitch(W, o.pad));
     w = W; h = H;
     for (int l = 0; l + 1 < levels; ++l) {
         int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
@@ -2242,8 +2271,8 @@ static cudaError_t pyramid_t(const float *frames, int N, size_t fstride, int W, 
             pyr_border<S><<<dim3((nb + 127) / 128, 1, N), 128, 0, s>>>(lv[l], o.raw_stride[l], w, h, o.pad,
                                                                        means + l, levels);
             if (o.smooth[l])
-                pyr_smooth<S><<<dim3((w + 127) / 128, h, N), 128, 0, s>>>(lv[l], o.raw_stride[l], level_pitch(w, o.pad),
-                                                                          w, h, (S *)o.smooth[l], o.smooth_stride[l]);
+                pyr_smooth<S><<<dim3((w + 127) / 128, (h + kSmoothRows - 1) / kSmoothRows, N), 128, 0, s>>>(
+                    lv[l], o.raw_stride[l], level_pitch(w, o.pad), w, h, (S *)o.smooth[l], o.smooth_stride[l]);
         }
         w = (w + 1) / 2;
         h = (h + 1) / 2;
