@@ -237,8 +237,8 @@ int reg_scan(reg_ctx_t *ctx, const float *frames, int N, int W, int H, int pitch
 /* S independent series of N frames each (same W, H) registered in one call: the
  * operators of all series share the executor's launches (and, with
  * REG_EXEC_PERSISTENT, one device queue), so series with uneven iteration counts
+ * fill the GPU together.  Each series is the scan of reg_scan [Sec. 3].
  *   frames     fp32 [S][N][H][pitch], host or device (host frames staged as in reg_scan).
- *   frames     fp32 [S][N][H][pitch], host or device.
  *   out        S x (N-1) elements, series-major; indices i, k are series-local.
  *   fields_out REG_NONRIGID: [S][N-1][2][H][W] or NULL.
  *   per_op     optional host array of S x (the per-series count of reg_scan),
