@@ -2080,19 +2080,33 @@ __global__ void __launch_bounds__(kL0Threads) pyr_level0(const float *frames, si
         }
 }
 
-// Level l+1 from level l: 2x2 box average, last odd row/column clamped.
+// Level l+1 from level l: 2x2 box average, last odd row/column clamped.  A thread makes kDnRows
+// samples of one column, every load issued before the first store.
+constexpr int kDnThreads = 128, kDnRows = 8;
 template <typename S>
-__global__ void pyr_down(const S *src, size_t sstride, int spitch, int W, int H, S *dst, size_t dstride, int dpitch)
+__global__ void __launch_bounds__(kDnThreads) pyr_down(const S *src, size_t sstride, int spitch, int W, int H,
+                                                       S *dst, size_t dstride, int dpitch)
 {
     const int w2 = (W + 1) / 2, h2 = (H + 1) / 2;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-    if (c >= w2 || r >= h2) return;
+    const int c = blockIdx.x * kDnThreads + threadIdx.x, rb = blockIdx.y * kDnRows;
+    if (c >= w2) return;
     src += blockIdx.z * sstride;
     dst += blockIdx.z * dstride;
-    int r0 = 2 * r, r1 = min(2 * r + 1, H - 1), c0 = 2 * c, c1 = min(2 * c + 1, W - 1);
-    float v = ((ldS<S>(src + (size_t)r0 * spitch + c0) + ldS<S>(src + (size_t)r0 * spitch + c1)) +
-               ldS<S>(src + (size_t)r1 * spitch + c0)) + ldS<S>(src + (size_t)r1 * spitch + c1);
-    dst[(size_t)r * dpitch + c] = toS<S>(0.25f * v);
+    const int c0 = 2 * c, c1 = min(2 * c + 1, W - 1);
+    float v[kDnRows];
+#pragma unroll
+    for (int k = 0; k < kDnRows; ++k) {
+        v[k] = 0.f;
+        const int r = rb + k;
+        if (r < h2) {
+            const int r0 = 2 * r, r1 = min(2 * r + 1, H - 1);
+            v[k] = ((ldS<S>(src + (size_t)r0 * spitch + c0) + ldS<S>(src + (size_t)r0 * spitch + c1)) +
+                    ldS<S>(src + (size_t)r1 * spitch + c0)) + ldS<S>(src + (size_t)r1 * spitch + c1);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kDnRows; ++k)
+        if (rb + k < h2) dst[(size_t)(rb + k) * dpitch + c] = toS<S>(0.25f * v[k]);
 }
 
 // Border of `pad` samples around a W x H level (pitch W + 2 pad) holding the level's mean (frame
@@ -2159,12 +2173,20 @@ __global__ void __launch_bounds__(kThreads) level_mean(const S *img, size_t stri
     const int n = W * H;
     float hi = 0.f, lo = 0.f;
     for (int base = 0; base < n; base += kThreads * kChunk) {
-        float a = 0.f;
-        const int e = min(n, base + kThreads * kChunk);
-        for (int i = base + threadIdx.x; i < e; i += kThreads) {
-            const int r = i / W;
-            a += ldS<S>(img + (size_t)r * pitch + (i - r * W));
+        // a thread's kChunk samples of the chunk, loaded first, then summed in index order
+        float x[kChunk];
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+            const int i = base + threadIdx.x + k * kThreads;
+            x[k] = 0.f;
+            if (i < n) {
+                const int r = i / W;
+                x[k] = ldS<S>(img + (size_t)r * pitch + (i - r * W));
+            }
         }
+        float a = 0.f;
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) a += x[k];
         ff_acc(hi, lo, a);
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -2256,9 +2278,8 @@ static cudaError_t pyramid_t(const float *frames, int N, size_t fstride, int W, 
     w = W; h = H;
     for (int l = 0; l + 1 < levels; ++l) {
         int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
-        pyr_down<S><<<dim3((w2 + 127) / 128, h2, N), 128, 0, s>>>(lv[l], o.raw_stride[l], level_pitch(w, o.pad), w, h,
-                                                                  lv[l + 1], o.raw_stride[l + 1],
-                                                                  level_pitch(w2, o.pad));
+        pyr_down<S><<<dim3((w2 + kDnThreads - 1) / kDnThreads, (h2 + kDnRows - 1) / kDnRows, N), kDnThreads, 0, s>>>(
+            lv[l], o.raw_stride[l], level_pitch(w, o.pad), w, h, lv[l + 1], o.raw_stride[l + 1], level_pitch(w2, o.pad));
         w = w2; h = h2;
     }
     w = W; h = H;
