@@ -167,6 +167,29 @@ def test_bspline_derivative_matches_central_differences():
         assert gx == pytest.approx(fx, abs=1e-7) and gy == pytest.approx(fy, abs=1e-7)
 
 
+def test_image_models_equal_scipy_spline_evaluation():
+    # an independent implementation of both image models: scipy.ndimage evaluates a B-spline of
+    # order 2 with the samples as its coefficients (prefilter=False) and the constant beyond the
+    # frame ("grid-constant"), and bilinear interpolation with the edge replicated ("nearest"), at
+    # positions inside the frame, on its border and well outside it
+    nd = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(87)
+    T = rng.uniform(0.0, 1.0, (9, 12))
+    out = 0.37
+    h = 1e-6
+
+    def q(x, y):
+        return nd.map_coordinates(T, [[y], [x]], order=2, prefilter=False, mode="grid-constant", cval=out)[0]
+
+    for px, py in rng.uniform([-4.0, -4.0], [15.0, 12.0], size=(200, 2)):
+        v, gx, gy = O.sample_q(T, float(px), float(py), outside=out)
+        assert v == pytest.approx(q(px, py), abs=1e-14)
+        assert gx == pytest.approx((q(px + h, py) - q(px - h, py)) / (2 * h), abs=1e-8)
+        assert gy == pytest.approx((q(px, py + h) - q(px, py - h)) / (2 * h), abs=1e-8)
+        b = nd.map_coordinates(T, [[py], [px]], order=1, mode="nearest")[0]
+        assert O.sample(T, float(px), float(py))[0] == pytest.approx(b, abs=1e-14)
+
+
 def test_ncc_by_hand_on_2x2():
     R = np.array([[0.0, 1.0], [2.0, 3.0]])
     T = np.array([[1.0, 0.0], [3.0, 2.0]])
