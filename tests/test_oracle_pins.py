@@ -278,6 +278,22 @@ def test_grid_field_interpolates_control_points_and_affine_fields():
                                                     A[1, 0] * X1 + A[1, 1] * Y1 + bb[1]]), atol=1e-12)
 
 
+def test_grid_field_equals_scipy_linear_grid_interpolation():
+    # the dense field of random control values against scipy's piecewise-linear interpolation on
+    # the same grid of points (0, s, 2 s, ...) along each axis, including grids whose last cell
+    # extends past the frame and a spacing that is not a power of two
+    interp = pytest.importorskip("scipy.interpolate")
+    for W, H, sp in ((50, 34, 8), (128, 96, 16), (37, 41, 5)):
+        g = O.grid_for(W, H, sp)
+        c = np.random.default_rng(15).uniform(-1.0, 1.0, size=(2, g.ny, g.nx))
+        u = O.grid_dense(g, c)
+        Y, X = np.mgrid[0:H, 0:W].astype(np.float64)
+        pts = np.stack([Y.ravel(), X.ravel()], 1)
+        for k in range(2):
+            f = interp.RegularGridInterpolator((np.arange(g.ny) * g.s, np.arange(g.nx) * g.s), c[k], method="linear")
+            np.testing.assert_allclose(u[k], f(pts).reshape(H, W), atol=1e-14)
+
+
 # ---------------------------------------------------------------- identical frames
 @pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
 def test_identical_frames_give_exact_identity(mode):
