@@ -294,6 +294,26 @@ def test_grid_field_equals_scipy_linear_grid_interpolation():
             np.testing.assert_allclose(u[k], f(pts).reshape(H, W), atol=1e-14)
 
 
+def test_grid_composition_equals_scipy_interpolation_at_the_displaced_points():
+    # B's initial guess (Sec. 2.3.2) on the control grid: c_j = c1_j + u2(X_j + c1_j), with u2
+    # evaluated by scipy's piecewise-linear grid interpolation of c2, for random fields whose
+    # displaced control points stay on the grid
+    interp = pytest.importorskip("scipy.interpolate")
+    g = O.grid_for(128, 96, 16)
+    rng = np.random.default_rng(16)
+    c1 = rng.uniform(-3.0, 3.0, size=(2, g.ny, g.nx))
+    c2 = rng.uniform(-3.0, 3.0, size=(2, g.ny, g.nx))
+    jy, jx = np.mgrid[0:g.ny, 0:g.nx].astype(np.float64)
+    Xj, Yj = jx * g.s, jy * g.s
+    c1[0] = np.clip(c1[0], -Xj, (g.nx - 1) * g.s - Xj)
+    c1[1] = np.clip(c1[1], -Yj, (g.ny - 1) * g.s - Yj)
+    got = O.compose_grid(g, c1, c2)
+    pts = np.stack([(Yj + c1[1]).ravel(), (Xj + c1[0]).ravel()], 1)
+    for k in range(2):
+        f = interp.RegularGridInterpolator((np.arange(g.ny) * g.s, np.arange(g.nx) * g.s), c2[k], method="linear")
+        np.testing.assert_allclose(got[k], c1[k] + f(pts).reshape(g.ny, g.nx), atol=1e-13)
+
+
 # ---------------------------------------------------------------- identical frames
 @pytest.mark.parametrize("mode", ["rigid", "nonrigid"])
 def test_identical_frames_give_exact_identity(mode):
